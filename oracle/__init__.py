@@ -1,0 +1,277 @@
+"""FP64 CPU oracle for MRF DGS (ctypes wrapper around ``mrf_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg use it. The GPU library never imports it and it
+never imports the GPU library; the two share only ``mrf_synth`` (random draws).
+
+Every function follows the paper directly:
+  * ``simulate`` / ``simulate_state``: Appendix Eq. A2 with the hard-pulse RF
+    form and the recovery term of Eq. A1.
+  * ``cc``: Eq. 1.
+  * ``bruteforce``: argmax of Eq. 1 over every valid grid entry.
+  * ``zoom`` / ``zoom_generic``: MRF-ZOOM, Theory (df search steps 1-4, Fig. 1
+    1D ZOOM, Fig. 2 2D ZOOM) with the schedule of Experiment 2 steps 1-5.
+Parity unpinned: ZOOM on grids too large for exhaustive search (only
+local-optimality and windowed brute-force checks apply there).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mrf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle_mrf.so")
+_lock = threading.Lock()
+_lib = None
+
+MAX_LEVELS = 16
+
+
+class OrSeq(C.Structure):
+    _fields_ = [("n", C.c_int32), ("flip", C.POINTER(C.c_double)), ("phase", C.POINTER(C.c_double)),
+                ("tr", C.POINTER(C.c_double)), ("te", C.POINTER(C.c_double)),
+                ("inversion", C.c_int32), ("inv_delay", C.c_double)]
+
+
+class OrGrid(C.Structure):
+    _fields_ = [("t1_min", C.c_double), ("t1_step", C.c_double), ("n_t1", C.c_int32),
+                ("t2_min", C.c_double), ("t2_step", C.c_double), ("n_t2", C.c_int32),
+                ("df_min", C.c_double), ("df_step", C.c_double), ("n_df", C.c_int32),
+                ("require_t2_lt_t1", C.c_int32)]
+
+
+class OrZoomOpts(C.Structure):
+    _fields_ = [("omega_hz", C.c_double), ("t1_init_ms", C.c_double), ("t2_init_ms", C.c_double),
+                ("s1a_step_frac", C.c_double), ("s1b_half_frac", C.c_double),
+                ("s1b_step_frac", C.c_double), ("s3_half_frac", C.c_double),
+                ("n_s2", C.c_int32), ("s2_t1_ms", C.c_double * MAX_LEVELS),
+                ("s2_t2_ms", C.c_double * MAX_LEVELS), ("n_s4", C.c_int32),
+                ("s4_param", C.c_int32 * MAX_LEVELS), ("s4_ms", C.c_double * MAX_LEVELS)]
+
+
+SCORE_FN = C.CFUNCTYPE(C.c_double, C.c_void_p, C.c_int32, C.c_int32, C.c_int32)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, C11, OpenMP, no FMA contraction)."""
+    with _lock:
+        if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+            return _LIB_PATH
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", "-D_DEFAULT_SOURCE", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = C.CDLL(path)
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int32)
+        lp = C.POINTER(C.c_int64)
+        L.or_simulate_state.argtypes = [C.POINTER(OrSeq), C.c_double, C.c_double, C.c_double, dp, dp, dp]
+        L.or_simulate.argtypes = [C.POINTER(OrSeq), C.c_int64, dp, dp, dp, dp]
+        L.or_cc.argtypes = [C.c_int32, dp, dp]
+        L.or_cc.restype = C.c_double
+        L.or_grid_count.argtypes = [C.POINTER(OrGrid)]
+        L.or_grid_count.restype = C.c_int64
+        L.or_grid_index.argtypes = [C.POINTER(OrGrid), C.c_int32, C.c_int32, C.c_int32]
+        L.or_grid_index.restype = C.c_int64
+        L.or_grid_params.argtypes = [C.POINTER(OrGrid), C.c_int64, ip, ip, ip]
+        L.or_grid_params.restype = C.c_int64
+        L.or_bruteforce.argtypes = [C.POINTER(OrSeq), C.POINTER(OrGrid), dp, C.c_int64, C.c_int32, lp, dp, dp, dp]
+        L.or_zoom_generic.argtypes = [C.POINTER(OrGrid), C.POINTER(OrZoomOpts), C.c_double, SCORE_FN, C.c_void_p,
+                                      ip, dp, ip, dp, C.c_int32, ip, ip, dp]
+        L.or_zoom.argtypes = [C.POINTER(OrSeq), C.POINTER(OrGrid), C.POINTER(OrZoomOpts), dp, C.c_int64,
+                              ip, dp, dp, dp, ip, dp]
+        L.or_default_omega.argtypes = [C.POINTER(OrSeq)]
+        L.or_default_omega.restype = C.c_double
+        L.or_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+class _SeqHandle:
+    """Keeps the numpy arrays alive while the C struct points at them."""
+
+    def __init__(self, seq):
+        self.flip = np.ascontiguousarray(seq.flip_rad, np.float64)
+        self.phase = np.ascontiguousarray(seq.rf_phase_rad, np.float64) if seq.rf_phase_rad is not None else None
+        self.tr = np.ascontiguousarray(seq.tr_ms, np.float64)
+        self.te = np.ascontiguousarray(seq.te_ms, np.float64)
+        self.c = OrSeq(int(self.flip.shape[0]), _dp(self.flip),
+                       _dp(self.phase) if self.phase is not None else C.POINTER(C.c_double)(),
+                       _dp(self.tr), _dp(self.te), int(seq.inversion), float(seq.inv_delay_ms))
+
+
+def _grid(g) -> OrGrid:
+    return OrGrid(g.t1_min, g.t1_step, g.n_t1, g.t2_min, g.t2_step, g.n_t2,
+                  g.df_min, g.df_step, g.n_df, g.require_t2_lt_t1)
+
+
+def default_zoom_opts(**kw) -> OrZoomOpts:
+    """Experiment 2 schedule: df search (coarse step 6/7 omega, window +-omega
+    at omega/20, probes at k omega), 2D ZOOM at 200 then 100 ms, df refinement
+    over +-omega/2 at the finest step, 1D ZOOMs T1@100, T2@100, T1@50/20/10,
+    T2@50/20/10, final 2D ZOOM at the finest step. Start at T1/T2 = 1000/100 ms."""
+    o = OrZoomOpts()
+    o.omega_hz = kw.get("omega_hz", 0.0)
+    o.t1_init_ms = kw.get("t1_init_ms", 1000.0)
+    o.t2_init_ms = kw.get("t2_init_ms", 100.0)
+    o.s1a_step_frac = kw.get("s1a_step_frac", 6.0 / 7.0)
+    o.s1b_half_frac = kw.get("s1b_half_frac", 1.0)
+    o.s1b_step_frac = kw.get("s1b_step_frac", 1.0 / 20.0)
+    o.s3_half_frac = kw.get("s3_half_frac", 0.5)
+    s2 = kw.get("s2", [(200.0, 200.0), (100.0, 100.0)])
+    o.n_s2 = len(s2)
+    for i, (h1, h2) in enumerate(s2):
+        o.s2_t1_ms[i] = h1
+        o.s2_t2_ms[i] = h2
+    s4 = kw.get("s4", [(0, 100.0), (1, 100.0), (0, 50.0), (0, 20.0), (0, 10.0),
+                       (1, 50.0), (1, 20.0), (1, 10.0)])
+    o.n_s4 = len(s4)
+    for i, (p, h) in enumerate(s4):
+        o.s4_param[i] = p
+        o.s4_ms[i] = h
+    return o
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def simulate_state(seq, t1, t2, df, m_init=None):
+    """(signal (n,) complex128, state (n, 3)) of one fingerprint."""
+    h = _SeqHandle(seq)
+    n = h.c.n
+    sig = np.zeros(2 * n)
+    st = np.zeros(3 * n)
+    mi = None
+    if m_init is not None:
+        mi = np.ascontiguousarray(m_init, np.float64)
+    rc = lib().or_simulate_state(C.byref(h.c), float(t1), float(t2), float(df),
+                                 _dp(mi) if mi is not None else C.POINTER(C.c_double)(), _dp(sig), _dp(st))
+    assert rc == 0
+    return sig[0::2] + 1j * sig[1::2], st.reshape(n, 3)
+
+
+def simulate(seq, t1, t2, df):
+    """(count, n) complex128 fingerprints for parameter arrays."""
+    t1 = np.ascontiguousarray(np.atleast_1d(t1), np.float64)
+    t2 = np.ascontiguousarray(np.broadcast_to(t2, t1.shape), np.float64)
+    df = np.ascontiguousarray(np.broadcast_to(df, t1.shape), np.float64)
+    h = _SeqHandle(seq)
+    n = h.c.n
+    out = np.zeros((t1.shape[0], n, 2))
+    rc = lib().or_simulate(C.byref(h.c), t1.shape[0], _dp(t1), _dp(t2), _dp(df), _dp(out))
+    assert rc == 0
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def _interleave(x):
+    x = np.asarray(x, np.complex128)
+    out = np.empty(x.shape + (2,))
+    out[..., 0] = x.real
+    out[..., 1] = x.imag
+    return np.ascontiguousarray(out)
+
+
+def cc(x, d) -> float:
+    xi, di = _interleave(x), _interleave(d)
+    return float(lib().or_cc(xi.shape[0], _dp(xi), _dp(di)))
+
+
+def grid_count(g) -> int:
+    return int(lib().or_grid_count(C.byref(_grid(g))))
+
+
+def grid_index(g, a, b, c) -> int:
+    return int(lib().or_grid_index(C.byref(_grid(g)), int(a), int(b), int(c)))
+
+
+def grid_params(g):
+    gc = _grid(g)
+    n = int(lib().or_grid_count(C.byref(gc)))
+    a = np.zeros(n, np.int32)
+    b = np.zeros(n, np.int32)
+    c = np.zeros(n, np.int32)
+    lib().or_grid_params(C.byref(gc), n, _ip(a), _ip(b), _ip(c))
+    return a, b, c
+
+
+def bruteforce(seq, g, x, k: int = 1):
+    """Top-k by Eq. 1 for each voxel. Returns dict(idx (V,k), cc (V,k), m0 (V,), phase (V,))."""
+    h = _SeqHandle(seq)
+    xi = _interleave(np.atleast_2d(x))
+    V = xi.shape[0]
+    idx = np.zeros((V, k), np.int64)
+    ccs = np.zeros((V, k))
+    m0 = np.zeros(V)
+    ph = np.zeros(V)
+    rc = lib().or_bruteforce(C.byref(h.c), C.byref(_grid(g)), _dp(xi), V, k,
+                             idx.ctypes.data_as(C.POINTER(C.c_int64)), _dp(ccs), _dp(m0), _dp(ph))
+    if rc != 0:
+        raise RuntimeError(f"or_bruteforce failed: {rc}")
+    return dict(idx=idx, cc=ccs, m0=m0, phase=ph)
+
+
+def default_omega(seq) -> float:
+    return float(lib().or_default_omega(C.byref(_SeqHandle(seq).c)))
+
+
+def zoom(seq, g, x, opts=None):
+    """MRF-ZOOM per voxel. Returns dict(abc (V,3), cc, m0, phase, evaluated, min_margin)."""
+    h = _SeqHandle(seq)
+    xi = _interleave(np.atleast_2d(x))
+    V = xi.shape[0]
+    o = opts if opts is not None else default_zoom_opts()
+    abc = np.zeros((V, 3), np.int32)
+    ccs = np.zeros(V)
+    m0 = np.zeros(V)
+    ph = np.zeros(V)
+    ev = np.zeros(V, np.int32)
+    mm = np.zeros(V)
+    rc = lib().or_zoom(C.byref(h.c), C.byref(_grid(g)), C.byref(o), _dp(xi), V,
+                       _ip(abc), _dp(ccs), _dp(m0), _dp(ph), _ip(ev), _dp(mm))
+    if rc != 0:
+        raise RuntimeError(f"or_zoom failed: {rc}")
+    return dict(abc=abc, cc=ccs, m0=m0, phase=ph, evaluated=ev, min_margin=mm)
+
+
+def zoom_generic(g, score, omega, opts=None, trace_cap=100000):
+    """ZOOM over a Python score(a, b, c) -> float (test hook for the stage machine)."""
+    o = opts if opts is not None else default_zoom_opts()
+    cb = SCORE_FN(lambda _ctx, a, b, c: float(score(a, b, c)))
+    abc = np.zeros(3, np.int32)
+    ccv = np.zeros(1)
+    ev = np.zeros(1, np.int32)
+    mm = np.zeros(1)
+    tn = np.zeros(1, np.int32)
+    tr = np.zeros((trace_cap, 4), np.int32)
+    tcc = np.zeros(trace_cap)
+    rc = lib().or_zoom_generic(C.byref(_grid(g)), C.byref(o), float(omega), cb, None,
+                               _ip(abc), _dp(ccv), _ip(ev), _dp(mm), trace_cap, _ip(tn), _ip(tr), _dp(tcc))
+    if rc != 0:
+        raise RuntimeError(f"or_zoom_generic failed: {rc}")
+    n = min(int(tn[0]), trace_cap)
+    return dict(abc=tuple(int(v) for v in abc), cc=float(ccv[0]), evaluated=int(ev[0]),
+                min_margin=float(mm[0]), trace=tr[:n].copy(), trace_cc=tcc[:n].copy())

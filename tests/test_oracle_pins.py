@@ -1,0 +1,342 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle.
+
+Simulator (Appendix, Eq. A1/A2): closed forms for pure T1 recovery, pure T2
+decay with precession, magnitude conservation, the textbook balanced-SSFP
+steady state, exact df periodicity for a constant TR (Property II), and the
+general RF-phase rotation against Rodrigues' formula.
+CC (Eq. 1): a hand example, self-correlation, scale invariance, the bound.
+Grid: closed-form entry counts.
+Brute force: exact recovery of noise-free on-grid voxels (Experiment 2) and an
+independent exhaustive top-k with noise.
+ZOOM: a hand-derived trace on an analytic score (tests/golden), recovery of
+on-grid voxels, local optimality, and equality with brute force when omega
+equals the df resolution (Experiment 2).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import mrf_synth as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _seq(n, flip, tr, te, inversion=0, delay=0.0, phase=None):
+    flip = np.broadcast_to(np.asarray(flip, float), (n,)).copy()
+    tr = np.broadcast_to(np.asarray(tr, float), (n,)).copy()
+    te = np.broadcast_to(np.asarray(te, float), (n,)).copy()
+    ph = np.zeros(n) if phase is None else np.broadcast_to(np.asarray(phase, float), (n,)).copy()
+    return S.Sequence(flip, ph, tr, te, inversion, delay)
+
+
+# ----------------------------------------------------------------- simulator
+
+def test_pure_t1_recovery_after_inversion(oracle_lib):
+    """Zero flip angles after an ideal inversion: Mz(t) = 1 - 2 exp(-t/T1), no
+    transverse signal, sampled TE_j after pulse j."""
+    rng = np.random.default_rng(5)
+    n = 60
+    tr = rng.uniform(5, 15, n)
+    te = tr * rng.uniform(0.1, 0.9, n)
+    seq = _seq(n, 0.0, tr, te, inversion=1, delay=20.0)
+    T1 = 837.0
+    sig, st = oracle_lib.simulate_state(seq, T1, 95.0, 13.0)
+    t = 20.0 + np.concatenate([[0.0], np.cumsum(tr)[:-1]]) + te
+    np.testing.assert_allclose(st[:, 2], 1.0 - 2.0 * np.exp(-t / T1), rtol=0, atol=1e-13)
+    assert np.max(np.abs(sig)) < 1e-15   # sin(pi) rounding only
+
+
+def test_pure_t2_decay_and_precession(oracle_lib):
+    """One pulse of +90 degrees from equilibrium, then zero flips: the hard
+    pulse R_x(-alpha) puts M on +y, so s(t) = i exp(-t/T2) exp(+i 2 pi df t)
+    (counterclockwise R_off), and Mz(t) = 1 - exp(-t/T1)."""
+    rng = np.random.default_rng(6)
+    n = 40
+    tr = rng.uniform(8, 14, n)
+    te = tr * rng.uniform(0.2, 0.8, n)
+    flip = np.zeros(n)
+    flip[0] = math.pi / 2
+    seq = _seq(n, flip, tr, te)
+    T1, T2, df = 1200.0, 80.0, 17.5
+    sig, st = oracle_lib.simulate_state(seq, T1, T2, df)
+    t = np.concatenate([[0.0], np.cumsum(tr)[:-1]]) + te   # time since the pulse
+    expect = 1j * np.exp(-t / T2) * np.exp(1j * 2 * np.pi * df * t / 1000.0)
+    np.testing.assert_allclose(sig, expect, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(st[:, 2], 1.0 - np.exp(-t / T1), rtol=0, atol=1e-13)
+
+
+def test_magnitude_conserved_without_relaxation(oracle_lib):
+    seq = S.sequence(3, 300)
+    seq = S.Sequence(seq.flip_rad, np.random.default_rng(1).uniform(0, 2 * np.pi, 300),
+                     seq.tr_ms, seq.te_ms, 1, 20.0)
+    _, st = oracle_lib.simulate_state(seq, math.inf, math.inf, 23.7)
+    np.testing.assert_allclose(np.linalg.norm(st, axis=1), 1.0, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("alpha_deg,T1,T2", [(30.0, 800.0, 60.0), (60.0, 1500.0, 200.0), (10.0, 300.0, 250.0)])
+def test_bssfp_steady_state(oracle_lib, alpha_deg, T1, T2):
+    """Alternating +-alpha, constant TR, TE = TR/2, on resonance: the signal
+    magnitude converges to the textbook balanced-SSFP steady state
+    sin(a)(1-E1)sqrt(E2) / (1 - (E1-E2)cos(a) - E1 E2)."""
+    n, TR = 4000, 10.0
+    a = math.radians(alpha_deg)
+    flip = a * np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    seq = _seq(n, flip, TR, TR / 2)
+    sig, _ = oracle_lib.simulate_state(seq, T1, T2, 0.0)
+    E1, E2 = math.exp(-TR / T1), math.exp(-TR / T2)
+    ss = math.sin(a) * (1 - E1) * math.sqrt(E2) / (1 - (E1 - E2) * math.cos(a) - E1 * E2)
+    np.testing.assert_allclose(np.abs(sig[-10:]), ss, rtol=1e-10)
+
+
+def test_df_period_is_one_over_tr(oracle_lib):
+    """Property II made exact: with a constant TR, df and df + 1000/TR Hz give
+    fingerprints that differ by a constant phase, so CC = 1."""
+    rng = np.random.default_rng(7)
+    n, TR = 250, 12.5
+    seq = _seq(n, rng.uniform(-1, 1, n), TR, TR / 2, inversion=1, delay=20.0)
+    for df in (-30.0, 0.0, 12.3):
+        s0 = oracle_lib.simulate(seq, 900.0, 70.0, df)[0]
+        s1 = oracle_lib.simulate(seq, 900.0, 70.0, df + 1000.0 / TR)[0]
+        assert abs(oracle_lib.cc(s0, s1) - 1.0) < 1e-12
+        np.testing.assert_allclose(s1, -s0, atol=1e-12)  # TE = TR/2 -> phase pi
+        s2 = oracle_lib.simulate(seq, 900.0, 70.0, df + 0.37 * 1000.0 / TR)[0]
+        assert oracle_lib.cc(s0, s2) < 0.999
+
+
+def test_rf_phase_is_rotation_about_tilted_axis(oracle_lib):
+    """R_z(phi) R_x(-alpha) R_z(-phi) is a rotation by -alpha about the axis
+    (cos phi, sin phi, 0): compare with Rodrigues' formula."""
+    rng = np.random.default_rng(8)
+    for _ in range(20):
+        alpha, phi = rng.uniform(-3, 3), rng.uniform(-4, 4)
+        m = rng.normal(size=3)
+        seq = _seq(1, alpha, 0.0, 0.0, phase=phi)
+        _, st = oracle_lib.simulate_state(seq, 1e3, 1e2, 0.0, m_init=m)
+        k = np.array([math.cos(phi), math.sin(phi), 0.0])
+        th = -alpha
+        rod = (m * math.cos(th) + np.cross(k, m) * math.sin(th) + k * np.dot(k, m) * (1 - math.cos(th)))
+        np.testing.assert_allclose(st[0], rod, atol=1e-13)
+
+
+# ----------------------------------------------------------------- CC (Eq. 1)
+
+def test_cc_hand_values(oracle_lib):
+    assert oracle_lib.cc([1, 1j], [1, 1]) == pytest.approx(math.sqrt(2) / 2, abs=1e-15)
+    assert oracle_lib.cc([1, 1], [1, -1]) == pytest.approx(0.0, abs=1e-15)
+    assert oracle_lib.cc([1j, 0], [1, 0]) == pytest.approx(1.0, abs=1e-15)
+    assert oracle_lib.cc([3 + 4j, 0], [0, 2]) == pytest.approx(0.0, abs=1e-15)
+
+
+def test_cc_invariants(oracle_lib):
+    rng = np.random.default_rng(9)
+    for _ in range(10):
+        x = rng.normal(size=64) + 1j * rng.normal(size=64)
+        d = rng.normal(size=64) + 1j * rng.normal(size=64)
+        assert oracle_lib.cc(x, x) == pytest.approx(1.0, abs=1e-14)
+        c = complex(*rng.normal(size=2))
+        assert oracle_lib.cc(c * x, d) == pytest.approx(oracle_lib.cc(x, d), abs=1e-14)
+        assert 0.0 <= oracle_lib.cc(x, d) <= 1.0
+
+
+# ----------------------------------------------------------------- grid
+
+def _closed_form_count(g):
+    t1, _, _ = S.grid_values(g)
+    # number of T2 values strictly below T1: ceil((T1 - t2_min) / t2_step), clipped
+    nb = np.clip(np.ceil((t1 - g.t2_min) / g.t2_step - 1e-9), 0, g.n_t2).astype(np.int64)
+    return int(nb.sum()) * g.n_df
+
+
+@pytest.mark.parametrize("name", list(S.GRIDS))
+def test_grid_counts(oracle_lib, name):
+    g = S.GRIDS[name]
+    assert oracle_lib.grid_count(g) == _closed_form_count(g)
+
+
+def test_grid_order_and_index(oracle_lib):
+    g = S.GRIDS["tiny"]
+    a, b, c = oracle_lib.grid_params(g)
+    ea, eb, ec = S.grid_valid_params(g)
+    assert (a == ea).all() and (b == eb).all() and (c == ec).all()
+    g2 = S.Grid(100.0, 50.0, 7, 40.0, 30.0, 6, -5.0, 2.5, 5)
+    a, b, c = oracle_lib.grid_params(g2)
+    for i in range(0, a.shape[0], 7):
+        assert oracle_lib.grid_index(g2, a[i], b[i], c[i]) == i
+    assert oracle_lib.grid_index(g2, 0, 5, 0) == -1   # T2 = 190 >= T1 = 100
+
+
+# ----------------------------------------------------------------- brute force
+
+def _tiny_voxels(oracle_lib, v, snr, seed=100):
+    g = S.GRIDS["tiny"]
+    seq = S.sequence(0, 200)
+    ph = S.phantom_ongrid(seed, v, g)
+    clean = oracle_lib.simulate(seq, ph["t1"], ph["t2"], ph["df"])
+    g_re, g_im = S.noise_draws(seed, v, seq.n)
+    x = S.compose_voxels(clean, ph["m0"], ph["phase"], g_re, g_im, snr)
+    return seq, g, ph, x
+
+
+def test_bruteforce_recovers_noise_free_on_grid(oracle_lib):
+    """Experiment 2: targets on grid points are found exactly; CC = 1 and M0,
+    phase are the applied scale (Theory: proton density from the scale)."""
+    seq, g, ph, x = _tiny_voxels(oracle_lib, 64, None)
+    r = oracle_lib.bruteforce(seq, g, x, k=2)
+    assert (r["idx"][:, 0] == ph["index"]).all()
+    np.testing.assert_allclose(r["cc"][:, 0], 1.0, atol=1e-12)
+    assert (r["cc"][:, 1] < 1.0 - 1e-6).all()
+    np.testing.assert_allclose(r["m0"], ph["m0"], rtol=1e-12)
+    np.testing.assert_allclose(np.angle(np.exp(1j * (r["phase"] - ph["phase"]))), 0.0, atol=1e-12)
+
+
+def test_bruteforce_topk_matches_exhaustive_numpy(oracle_lib):
+    seq, g, ph, x = _tiny_voxels(oracle_lib, 32, 30.0)
+    k = 5
+    r = oracle_lib.bruteforce(seq, g, x, k=k)
+    t1, t2, df = S.grid_values(g)
+    a, b, c = S.grid_valid_params(g)
+    D = oracle_lib.simulate(seq, t1[a], t2[b], df[c])
+    ip = x @ D.conj().T
+    cc = np.abs(ip) / (np.linalg.norm(x, axis=1)[:, None] * np.linalg.norm(D, axis=1)[None, :])
+    order = np.lexsort((np.broadcast_to(np.arange(D.shape[0]), cc.shape), -cc), axis=1)[:, :k]
+    assert (r["idx"] == order).all()
+    np.testing.assert_allclose(r["cc"], np.take_along_axis(cc, order, 1), atol=1e-13)
+    best = order[:, 0]
+    m0 = np.abs(ip[np.arange(32), best]) / np.linalg.norm(D[best], axis=1) ** 2
+    np.testing.assert_allclose(r["m0"], m0, rtol=1e-12)
+
+
+# ----------------------------------------------------------------- ZOOM
+
+def _read_trace():
+    rows = []
+    with open(os.path.join(GOLDEN, "zoom_quadratic_trace.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(v) for v in line.split()])
+    return np.array(rows, np.int32)
+
+
+def test_zoom_hand_trace(oracle_lib):
+    g = S.Grid(0.0, 1.0, 41, 0.0, 1.0, 41, 0.0, 1.0, 21, 0)
+    f = lambda a, b, c: -(a - 27) ** 2 - 2 * (b - 13) ** 2 - 3 * (c - 11) ** 2
+    o = oracle_lib.default_zoom_opts(t1_init_ms=20.0, t2_init_ms=20.0,
+                                     s2=[(8.0, 8.0), (4.0, 4.0)],
+                                     s4=[(0, 4.0), (1, 4.0), (0, 2.0), (0, 1.0), (1, 2.0), (1, 1.0)])
+    r = oracle_lib.zoom_generic(g, f, 7.0, o)
+    expect = _read_trace()
+    assert r["trace"].shape == expect.shape
+    assert (r["trace"] == expect).all()
+    assert r["abc"] == (27, 13, 11) and r["cc"] == 0.0
+    assert r["evaluated"] == 76 and r["min_margin"] == 0.0
+
+
+def test_zoom_skips_invalid_points(oracle_lib):
+    """Points with T2 >= T1 or outside the grid score -inf and are never evaluated."""
+    g = S.Grid(0.0, 1.0, 30, 0.0, 1.0, 30, 0.0, 1.0, 5, 1)
+    seen = []
+
+    def f(a, b, c):
+        seen.append((a, b, c))
+        return -abs(a - 12) - abs(b - 11) - abs(c - 2)
+
+    r = oracle_lib.zoom_generic(g, f, 3.0, oracle_lib.default_zoom_opts(t1_init_ms=5.0, t2_init_ms=9.0,
+                                                                         s2=[(4.0, 4.0)], s4=[(0, 2.0), (1, 2.0)]))
+    assert all(0 <= b < a < 30 and 0 <= c < 5 for a, b, c in seen)
+    assert r["abc"] == (12, 11, 2)
+    assert r["evaluated"] == len(seen)
+
+
+def test_zoom_recovers_noise_free_on_grid(oracle_lib):
+    seq, g, ph, x = _tiny_voxels(oracle_lib, 64, None)
+    z = oracle_lib.zoom(seq, g, x)
+    assert (z["abc"][:, 0] == ph["a"]).all() and (z["abc"][:, 1] == ph["b"]).all()
+    np.testing.assert_allclose(z["cc"], 1.0, atol=1e-12)
+    np.testing.assert_allclose(z["m0"], ph["m0"], rtol=1e-12)
+
+
+def test_zoom_final_point_is_local_optimum(oracle_lib):
+    """Local-optimality certificate at the finest step, checked with Eq. 1
+    evaluated directly (not through the ZOOM code)."""
+    seq = S.sequence(1, 300)
+    g = S.Grid(300.0, 20.0, 60, 20.0, 5.0, 50, -20.0, 1.0, 41)
+    p = S.phantom_offgrid(11, 12, t1_range=(400, 1400), t2_range=(30, 200), df_range=(-15, 15))
+    clean = oracle_lib.simulate(seq, p["t1"], p["t2"], p["df"])
+    x = S.compose_voxels(clean, p["m0"], p["phase"], *S.noise_draws(11, 12, seq.n), 25.0)
+    z = oracle_lib.zoom(seq, g, x)
+    t1, t2, df = S.grid_values(g)
+    for v in range(12):
+        a, b, c = z["abc"][v]
+        d0 = oracle_lib.simulate(seq, t1[a], t2[b], df[c])[0]
+        c0 = oracle_lib.cc(x[v], d0)
+        assert c0 == pytest.approx(z["cc"][v], abs=1e-12)
+        for da in (-1, 0, 1):
+            for db in (-1, 0, 1):
+                aa, bb = a + da, b + db
+                if (da, db) == (0, 0) or not (0 <= aa < g.n_t1 and 0 <= bb < g.n_t2) or t2[bb] >= t1[aa]:
+                    continue
+                dn = oracle_lib.simulate(seq, t1[aa], t2[bb], df[c])[0]
+                assert oracle_lib.cc(x[v], dn) <= c0
+
+
+def test_zoom_with_omega_at_resolution_is_brute_force_in_df(oracle_lib):
+    """Experiment 2: with omega equal to the df resolution the df search is a
+    full scan, i.e. brute force over df."""
+    seq = S.sequence(2, 200)
+    g = S.Grid(900.0, 1.0, 1, 80.0, 1.0, 1, -30.0, 1.0, 61)
+    p = S.phantom_offgrid(12, 6, t1_range=(899, 901), t2_range=(79, 81), df_range=(-28, 28))
+    clean = oracle_lib.simulate(seq, p["t1"], p["t2"], p["df"])
+    x = S.compose_voxels(clean, p["m0"], p["phase"], *S.noise_draws(12, 6, seq.n), 5.0)
+    z = oracle_lib.zoom(seq, g, x, oracle_lib.default_zoom_opts(omega_hz=1.0, t1_init_ms=900, t2_init_ms=80))
+    bf = oracle_lib.bruteforce(seq, g, x, k=1)
+    assert (z["abc"][:, 2] == bf["idx"][:, 0]).all()
+    np.testing.assert_allclose(z["cc"], bf["cc"][:, 0], atol=1e-14)
+
+
+def test_zoom_centre_is_running_maximum(oracle_lib):
+    """The accepted centre value never decreases along the trace."""
+    seq = S.sequence(0, 200)
+    g = S.GRIDS["tiny"]
+    x = oracle_lib.simulate(seq, 733.0, 71.0, 0.0)[0]
+    x = x + 0.01 * np.random.default_rng(3).normal(size=x.shape)
+    t1, t2, df = S.grid_values(g)
+    cache = {}
+
+    def score(a, b, c):
+        key = (a, b, c)
+        if key not in cache:
+            cache[key] = oracle_lib.cc(x, oracle_lib.simulate(seq, t1[a], t2[b], df[c])[0])
+        return cache[key]
+
+    r = oracle_lib.zoom_generic(g, score, oracle_lib.default_omega(seq))
+    # moves and scans only ever accept a strictly better point, so the final
+    # centre holds the maximum of everything evaluated
+    assert r["cc"] == r["trace_cc"].max()
+    z = oracle_lib.zoom(seq, g, x[None, :])
+    assert tuple(z["abc"][0]) == r["abc"]
+    assert z["evaluated"][0] == r["evaluated"]
+
+
+def test_zoom_neighbour_ties_follow_scan_order(oracle_lib):
+    """Two neighbours tie for best: the move goes to the first one in the
+    fixed scan order (T1 offset outer, -1 before +1)."""
+    g = S.Grid(0.0, 1.0, 41, 0.0, 1.0, 41, 0.0, 1.0, 1, 0)
+    f = lambda a, b, c: -float(min((a - 16) ** 2, (a - 24) ** 2)) - float((b - 20) ** 2)
+    o = oracle_lib.default_zoom_opts(t1_init_ms=20.0, t2_init_ms=20.0, s2=[(4.0, 4.0)], s4=[])
+    r = oracle_lib.zoom_generic(g, f, 1.0, o)
+    assert r["abc"] == (16, 20, 0)
+    assert r["min_margin"] == 0.0
+
+
+def test_bruteforce_exact_ties_go_to_smaller_index(oracle_lib):
+    """T1 values so large that exp(-t/T1) rounds to 1 give bitwise identical
+    fingerprints, hence exactly tied CC: the smaller linear index ranks first."""
+    seq = S.sequence(4, 64)
+    g = S.Grid(1e300, 1e290, 3, 50.0, 10.0, 2, -5.0, 5.0, 3)
+    x = oracle_lib.simulate(seq, 1e300, 60.0, 0.0)
+    r = oracle_lib.bruteforce(seq, g, x, k=4)
+    # entries (a, b=1, c=1) for a = 0, 1, 2 are identical -> indices 4, 10, 16
+    assert list(r["idx"][0, :3]) == [4, 10, 16]
+    assert r["cc"][0, 0] == r["cc"][0, 1] == r["cc"][0, 2]
