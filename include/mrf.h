@@ -1,0 +1,307 @@
+/*
+ * mrf.h -- C ABI of the GB300 (sm_103a) MRF dictionary generating and
+ * searching (DGS) library.
+ *
+ * Method: Z. Wang, "MRF-ZOOM: A Fast Dictionary Searching Algorithm for
+ * Magnetic Resonance Fingerprinting". A fingerprint is the Bloch-simulated
+ * transverse signal of an IR-bSSFP train (Appendix, Eq. A2); a voxel's
+ * acquired fingerprint is matched to the dictionary entry of highest complex
+ * correlation (Theory, Eq. 1), by brute force over a (T1, T2, df) grid or by
+ * the MRF-ZOOM coordinate search (Theory; Methods, Experiment 2).
+ *
+ * Conventions for every entry point:
+ *   - Return value: MRF_OK (0), MRF_PENDING (1, serving only) or a negative
+ *     MRF_E_* code. Nothing throws across this boundary. mrf_last_error()
+ *     returns a message for the calling thread's most recent failure.
+ *   - Units: milliseconds for times and T1/T2, Hz for off-resonance df,
+ *     radians for angles.
+ *   - Complex data are interleaved (re, im) float32 pairs ("complex64").
+ *   - Pointers named *_dev are device pointers on the context's device; the
+ *     caller owns them and keeps them alive until the stream reaches the
+ *     call. Pointers named *_host are host memory owned by the caller.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Calls that
+ *     take a stream are asynchronous on it unless stated otherwise.
+ *   - Objects returned through `**out` (sequence, dictionary) are owned by the
+ *     library and released with the matching *_free call.
+ *   - Invalid arguments return MRF_E_INVALID and leave outputs untouched.
+ *   - No CPU fallback exists: every computation runs in this library's CUDA
+ *     kernels for sm_103a; without a usable device calls return MRF_E_CUDA.
+ */
+#ifndef MRF_H
+#define MRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MRF_OK = 0,
+    MRF_PENDING = 1,
+    MRF_E_INVALID = -1,     /* bad argument, descriptor or state */
+    MRF_E_NOMEM = -2,       /* device or host allocation failed */
+    MRF_E_BUDGET = -3,      /* would exceed the context's HBM budget */
+    MRF_E_TIMEOUT = -4,     /* a bounded wait ran out (host poll or device spin) */
+    MRF_E_CUDA = -5,        /* CUDA runtime / driver error */
+    MRF_E_NOTFOUND = -6,    /* unknown ticket or handle */
+    MRF_E_UNSUPPORTED = -7  /* valid request this build does not implement */
+};
+
+typedef enum {
+    MRF_F32 = 0,      /* FP32-equivalent: normalised entries split into bf16 hi + lo,
+                         three tensor-core products (hi.hi + hi.lo + lo.hi) */
+    MRF_BF16 = 1,     /* normalised entries rounded to bf16 (nearest even) */
+    MRF_FP8E4M3 = 2   /* normalised entries scaled to max |value| = 448 per entry,
+                         stored as fp8 e4m3 with an fp32 per-entry scale */
+} mrf_dtype;
+
+typedef struct mrf_ctx mrf_ctx;
+typedef struct mrf_seq mrf_seq;
+typedef struct mrf_dict mrf_dict;
+
+/* Thread-local message of the calling thread's last failing call ("" if none). */
+const char *mrf_last_error(void);
+
+/* Library version string, e.g. "mrf-gb300 1.0 sm_103a". */
+const char *mrf_version(void);
+
+/* Create a context on CUDA device `device`. `hbm_budget_bytes` caps the
+ * device memory the library itself allocates for this context (sequences,
+ * dictionaries, tables, scratch, serving buffers); 0 means "free memory at
+ * creation". The library allocates nothing outside the budget and returns
+ * MRF_E_BUDGET instead. Errors: MRF_E_INVALID (no such device, not sm_103),
+ * MRF_E_CUDA. */
+int mrf_ctx_create(int device, size_t hbm_budget_bytes, mrf_ctx **out);
+
+/* Destroy a context: stops serving, waits for its work, frees everything it owns. */
+void mrf_ctx_destroy(mrf_ctx *ctx);
+
+/* Device bytes currently charged to the context's budget, and the budget. */
+int mrf_ctx_memory(const mrf_ctx *ctx, size_t *used_bytes, size_t *budget_bytes);
+
+/* Synchronise `stream` and report device-side failures of the context's
+ * kernels since the last check: MRF_E_TIMEOUT when a kernel's bounded wait ran
+ * out (the kernel returned early, its outputs are invalid, the context stays
+ * usable). Asynchronous entry points report such failures only here. */
+int mrf_stream_sync(mrf_ctx *ctx, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Sequence (Methods: IR-bSSFP train; Appendix: hard RF pulse)              */
+
+/* Acquisition train of n timepoints. For timepoint j the simulator applies
+ * the hard RF pulse R_z(phi_j) R_x(-alpha_j) R_z(-phi_j) (Appendix, small-beta
+ * form), evolves TE_j, samples s_j = Mx + i My, then evolves TR_j - TE_j.
+ * With inversion != 0 an ideal 180 degree pulse about x and inv_delay_ms of
+ * free evolution come first. Equilibrium magnetisation M0 = 1. */
+typedef struct {
+    int32_t n;                   /* timepoints, >= 1 */
+    const double *flip_rad;      /* n signed flip angles alpha_j */
+    const double *rf_phase_rad;  /* n RF phases phi_j, or NULL for all zero */
+    const double *tr_ms;         /* n repetition times, > 0 */
+    const double *te_ms;         /* n echo times, 0 <= TE_j <= TR_j */
+    int32_t inversion;           /* 0 or 1 */
+    double inv_delay_ms;         /* >= 0 */
+} mrf_sequence_desc;
+
+/* Copy a host sequence to the device (FP64 host values; per-timepoint RF
+ * rotation coefficients are formed in FP64 on the host and stored as FP32).
+ * Synchronous. Errors: MRF_E_INVALID (n < 1, non-finite values, TE outside
+ * [0, TR], TR <= 0), MRF_E_BUDGET, MRF_E_CUDA. */
+int mrf_sequence_load(mrf_ctx *ctx, const mrf_sequence_desc *desc, mrf_seq **out);
+int mrf_sequence_free(mrf_ctx *ctx, mrf_seq *seq);
+
+/* ------------------------------------------------------------------------ */
+/* Parameter grid (Theory: ranges R, S, Q of T1, T2, df)                    */
+
+/* Value i of an axis is min + i * step (no cumulative sums). An entry
+ * (a, b, c) is valid iff T2_b < T1_a when require_t2_lt_t1 != 0. The linear
+ * dictionary index runs over valid entries with T1 outermost, then T2, then
+ * df innermost. */
+typedef struct {
+    double t1_min, t1_step; int32_t n_t1;
+    double t2_min, t2_step; int32_t n_t2;
+    double df_min, df_step; int32_t n_df;
+    int32_t require_t2_lt_t1;
+} mrf_grid_desc;
+
+/* Number of valid entries, or a negative MRF_E_INVALID for a bad grid. */
+int64_t mrf_grid_count(const mrf_grid_desc *grid);
+
+/* (a, b, c) of linear index `index` (host only). MRF_E_INVALID if out of range. */
+int mrf_grid_unravel(const mrf_grid_desc *grid, int64_t index, int32_t *a, int32_t *b, int32_t *c);
+
+/* ------------------------------------------------------------------------ */
+/* Fingerprint simulation (Appendix, Eq. A2)                                */
+
+/* Simulate `count` fingerprints for parameter triples t1/t2/df (device
+ * float32 arrays, ms / ms / Hz) into out_dev (count x n complex64,
+ * row-major, not normalised). One GPU thread per fingerprint, FP32 state.
+ * Errors: MRF_E_INVALID, MRF_E_CUDA. */
+int mrf_simulate(mrf_ctx *ctx, const mrf_seq *seq, int64_t count, const float *t1_dev,
+                 const float *t2_dev, const float *df_dev, void *out_dev, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Dictionary (Theory: unit-norm entries so that CC is |inner product|)     */
+
+/* Generate the whole grid's dictionary on the device: Bloch recurrence per
+ * entry in FP32, then normalisation to unit L2 norm and storage in `dtype`
+ * (see mrf_dtype). Entry e's row is the interleaved (re, im) signal,
+ * zero-padded to `ld` elements. The library owns the dictionary memory,
+ * charged to the budget. Runs on `stream`; the dictionary is usable by later
+ * work on that stream. Errors: MRF_E_INVALID (bad grid, zero entries),
+ * MRF_E_BUDGET, MRF_E_NOMEM, MRF_E_CUDA. */
+int mrf_dict_generate(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, mrf_dtype dtype,
+                      void *stream, mrf_dict **out);
+int mrf_dict_free(mrf_ctx *ctx, mrf_dict *dict);
+
+/* Read-only view of a dictionary's device storage (for inspection/tests). */
+typedef struct {
+    int64_t entries;       /* D, valid grid entries */
+    int32_t n;             /* timepoints */
+    int32_t ld;            /* row length in elements: 2n rounded up to 128 */
+    int32_t dtype;         /* mrf_dtype */
+    const void *hi_dev;    /* D x ld: bf16 (F32 hi, BF16) or e4m3 bytes (FP8) */
+    const void *lo_dev;    /* D x ld bf16 residual (F32 only), else NULL */
+    const float *norm_dev; /* D: L2 norm of the un-normalised FP32 signal */
+    const float *scale_dev;/* D: FP8 dequantisation scale (FP8 only), else NULL */
+    size_t bytes;          /* device bytes charged to the budget */
+} mrf_dict_info;
+int mrf_dict_query(const mrf_dict *dict, mrf_dict_info *info);
+
+/* ------------------------------------------------------------------------ */
+/* Matching                                                                 */
+
+/* One result per voxel (host or device array of structs, 56 bytes each).
+ * Brute force: index/i_* of the best entry by Eq. 1; cc = CC of that entry;
+ * m0 = |<x, d>| / ||d||^2 and phase = arg <x, d> on the un-normalised entry
+ * d (Theory: proton density from the signal scale); entries_evaluated = D;
+ * min_margin = CC gap between the best and the second-best re-scored
+ * candidate (-1 when only one candidate is re-scored).
+ * ZOOM: the same fields for the final grid point; entries_evaluated counts
+ * candidate evaluations of the search and min_margin is the smallest gap
+ * between the two best values of any decision it took. */
+typedef struct {
+    int64_t index;               /* linear dictionary index, -1 if none */
+    int32_t i_t1, i_t2, i_df;    /* grid indices (a, b, c) */
+    float t1_ms, t2_ms, df_hz;
+    float cc;
+    float m0;
+    float phase;
+    int32_t entries_evaluated;
+    float min_margin;
+} mrf_result;
+
+typedef struct {
+    int32_t precision;   /* mrf_dtype; must equal the dictionary's dtype */
+    int32_t top_k;       /* candidates kept by the tensor-core pass: 1, 2, 4, 8, 16 or 32 */
+    int32_t rescore;     /* 1: re-simulate the top_k in FP32, rank by FP64 CC,
+                            ties to the smaller index. 0: keep the tensor-core
+                            rank-1 candidate (its cc/m0/phase still come from an
+                            FP32 re-simulation with FP64 accumulation). */
+} mrf_match_opts;
+
+/* Brute-force DGS for V voxels (fp_dev: V x n complex64, row-major, any
+ * scale and phase, n = the dictionary's sequence length). The score matrix is
+ * never stored: each voxel's running top_k is kept on chip while the
+ * dictionary streams through the tensor cores. The re-score re-simulates
+ * with the sequence the dictionary was generated from (the dictionary keeps
+ * its own copy). Scratch is taken from the stream-ordered pool and charged
+ * to the budget for the call's duration. V = 0 is a no-op. out_dev: V
+ * results. Errors: MRF_E_INVALID (dtype mismatch, bad top_k), MRF_E_BUDGET,
+ * MRF_E_CUDA; device-side wait failures surface in mrf_stream_sync. */
+int mrf_match_bruteforce(mrf_ctx *ctx, const mrf_dict *dict, const void *fp_dev, int64_t V,
+                         const mrf_match_opts *opts, mrf_result *out_dev, void *stream);
+
+/* The tensor-core pass alone: per voxel the top_k (linear index, approximate
+ * CC^2 of the normalised pair) in descending order, ties to the smaller
+ * index. idx_dev: V x top_k int64, cc2_dev: V x top_k float32. */
+int mrf_match_topk(mrf_ctx *ctx, const mrf_dict *dict, const void *fp_dev, int64_t V, int32_t precision,
+                   int32_t top_k, int64_t *idx_dev, float *cc2_dev, void *stream);
+
+/* MRF-ZOOM options (Methods, Experiment 2). Steps are physical (ms / Hz) and
+ * are snapped to whole grid steps (round half up, at least 1). */
+#define MRF_ZOOM_MAX_LEVELS 16
+typedef struct {
+    double omega_hz;        /* df pseudo-period; <= 0: 1000 / min_j TR_j (Property II) */
+    double t1_init_ms;      /* start of the df search (default 1000) */
+    double t2_init_ms;      /* (default 100) */
+    double s1a_step_frac;   /* step 1a: coarse df scan step, x omega (6/7) */
+    double s1b_half_frac;   /* step 1b: window half-width, x omega (1) */
+    double s1b_step_frac;   /* step 1b: window step, x omega (1/20) */
+    double s3_half_frac;    /* step 3: finest-step df window half-width, x omega (1/2) */
+    int32_t n_s2;           /* step 2: 2D ZOOM levels (200, 100 ms) */
+    double s2_t1_ms[MRF_ZOOM_MAX_LEVELS];
+    double s2_t2_ms[MRF_ZOOM_MAX_LEVELS];
+    int32_t n_s4;           /* step 4: interleaved 1D ZOOMs */
+    int32_t s4_param[MRF_ZOOM_MAX_LEVELS];   /* 0: T1, 1: T2 */
+    double s4_ms[MRF_ZOOM_MAX_LEVELS];
+} mrf_zoom_opts;
+
+/* Fill `opts` with the schedule of Experiment 2 (T1@100, T2@100, T1@50/20/10,
+ * T2@50/20/10 for step 4; final 2D ZOOM at the finest step). */
+void mrf_zoom_opts_default(mrf_zoom_opts *opts);
+
+/* MRF-ZOOM for V voxels, every candidate simulated on the fly (no
+ * dictionary). fp_dev: V x n complex64. out_dev: V results. The grid may be
+ * far larger than any dictionary (it is never materialised). Errors:
+ * MRF_E_INVALID, MRF_E_BUDGET, MRF_E_TIMEOUT, MRF_E_CUDA. */
+int mrf_zoom_search(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, const mrf_zoom_opts *opts,
+                    const void *fp_dev, int64_t V, mrf_result *out_dev, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of slice requests                           */
+
+typedef enum { MRF_MODE_BRUTE = 0, MRF_MODE_ZOOM = 1 } mrf_mode;
+
+typedef struct {
+    int32_t mode;                 /* mrf_mode */
+    const mrf_dict *dict;         /* MRF_MODE_BRUTE: resident dictionary */
+    mrf_match_opts match;         /* MRF_MODE_BRUTE options */
+    const mrf_seq *seq;           /* sequence (both modes) */
+    const mrf_grid_desc *grid;    /* MRF_MODE_ZOOM grid (copied at submit) */
+    const mrf_zoom_opts *zoom;    /* MRF_MODE_ZOOM options (copied), NULL = default */
+    const void *fp_host;          /* V x n complex64, copied at submit */
+    int64_t V;
+} mrf_request;
+
+typedef struct {
+    int32_t max_inflight;         /* launches in flight at once (streams), >= 1 */
+    int32_t max_batch_voxels;     /* voxels merged into one launch */
+    size_t request_bytes_budget;  /* device bytes for queued+running request buffers;
+                                     0 = what remains of the context budget */
+} mrf_serve_config;
+
+/* Start the serving loop (a library-owned host thread). */
+int mrf_serve_start(mrf_ctx *ctx, const mrf_serve_config *cfg);
+
+/* Enqueue a request; returns immediately with a ticket. The fingerprints are
+ * copied, so fp_host may be reused on return. A request whose buffers could
+ * never fit the budget returns MRF_E_BUDGET; otherwise it waits for memory.
+ * Errors: MRF_E_INVALID, MRF_E_BUDGET. */
+int mrf_serve_submit(mrf_ctx *ctx, const mrf_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_ms (0 = just check) for a ticket. MRF_OK: out_host (V
+ * results, caller-owned) is filled and the ticket retired. MRF_PENDING: not
+ * done yet (timeout_ms = 0). MRF_E_TIMEOUT: still running after timeout_ms.
+ * MRF_E_NOTFOUND: unknown or retired ticket. Never blocks beyond timeout_ms. */
+int mrf_serve_poll(mrf_ctx *ctx, uint64_t ticket, int32_t timeout_ms, mrf_result *out_host);
+
+/* Cancel a queued (not yet launched) request; MRF_E_NOTFOUND otherwise. */
+int mrf_serve_cancel(mrf_ctx *ctx, uint64_t ticket);
+
+typedef struct {
+    uint64_t submitted, admitted, completed, rejected, cancelled, launches;
+    uint64_t queued_now, running_now;
+    size_t request_bytes_in_use, request_bytes_peak;
+} mrf_serve_stats;
+int mrf_serve_get_stats(mrf_ctx *ctx, mrf_serve_stats *stats);
+
+/* Stop accepting work, finish what is admitted, join the thread. */
+int mrf_serve_stop(mrf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRF_H */

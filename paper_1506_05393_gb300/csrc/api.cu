@@ -1,0 +1,515 @@
+// C-ABI entry points: context, budget, sequence, grid, dictionary, simulation,
+// matching and ZOOM dispatch. Kernels live in bloch.cu, match.cu and zoom.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "mrf_internal.h"
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return set_error(MRF_E_NOMEM, m);
+    return set_error(MRF_E_CUDA, m);
+}
+
+extern "C" const char *mrf_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char *mrf_version(void) { return "mrf-gb300 1.0 sm_103a"; }
+
+// ---------------------------------------------------------------------------
+// budget
+
+int budget_charge(mrf_ctx *ctx, size_t bytes)
+{
+    size_t cur = ctx->used.load();
+    for (;;) {
+        if (cur + bytes > ctx->budget)
+            return set_error(MRF_E_BUDGET, "HBM budget exceeded: need " + std::to_string(bytes) + " B, " +
+                                                std::to_string(ctx->budget - cur) + " B left of " +
+                                                std::to_string(ctx->budget));
+        if (ctx->used.compare_exchange_weak(cur, cur + bytes)) return MRF_OK;
+    }
+}
+
+void budget_release(mrf_ctx *ctx, size_t bytes) { ctx->used.fetch_sub(bytes); }
+
+int dev_alloc(mrf_ctx *ctx, void **p, size_t bytes, const char *what)
+{
+    *p = nullptr;
+    if (bytes == 0) return MRF_OK;
+    int rc = budget_charge(ctx, bytes);
+    if (rc) return rc;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        budget_release(ctx, bytes);
+        *p = nullptr;
+        return cuda_fail(e, what);
+    }
+    return MRF_OK;
+}
+
+void dev_free(mrf_ctx *ctx, void *p, size_t bytes)
+{
+    if (!p) return;
+    cudaFree(p);
+    budget_release(ctx, bytes);
+}
+
+int check_device_error(mrf_ctx *ctx, cudaStream_t stream)
+{
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    int flag = 0;
+    e = cudaMemcpy(&flag, ctx->err_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read device error flag");
+    if (flag) {
+        cudaMemset(ctx->err_flag, 0, sizeof(int));
+        if (flag == kDeviceErrTimeout)
+            return set_error(MRF_E_TIMEOUT, "a device-side bounded wait ran out (kernel returned early)");
+        return set_error(MRF_E_CUDA, "device-side check failed (code " + std::to_string(flag) + ")");
+    }
+    return MRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// context
+
+extern "C" int mrf_ctx_create(int device, size_t hbm_budget_bytes, mrf_ctx **out)
+{
+    if (!out) return set_error(MRF_E_INVALID, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return set_error(MRF_E_INVALID, "no such CUDA device");
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    if (!(prop.major == 10 && prop.minor == 3))
+        return set_error(MRF_E_INVALID, std::string("this build targets sm_103a only; device is sm_") +
+                                            std::to_string(prop.major) + std::to_string(prop.minor));
+    size_t free_b = 0, total_b = 0;
+    e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+    mrf_ctx *c = new mrf_ctx();
+    c->device = device;
+    c->sm_count = prop.multiProcessorCount;
+    c->cc_major = prop.major;
+    c->cc_minor = prop.minor;
+    c->budget = hbm_budget_bytes ? hbm_budget_bytes : free_b;
+    e = cudaMalloc(&c->err_flag, sizeof(int));
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(err flag)"); }
+    cudaMemset(c->err_flag, 0, sizeof(int));
+    // keep stream-ordered scratch in the pool between calls
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = c;
+    return MRF_OK;
+}
+
+extern "C" int mrf_serve_stop(mrf_ctx *ctx);
+
+extern "C" void mrf_ctx_destroy(mrf_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->serve) mrf_serve_stop(ctx);
+    cudaDeviceSynchronize();
+    cudaFree(ctx->err_flag);
+    delete ctx;
+}
+
+extern "C" int mrf_ctx_memory(const mrf_ctx *ctx, size_t *used_bytes, size_t *budget_bytes)
+{
+    if (!ctx) return set_error(MRF_E_INVALID, "ctx is NULL");
+    if (used_bytes) *used_bytes = ctx->used.load();
+    if (budget_bytes) *budget_bytes = ctx->budget;
+    return MRF_OK;
+}
+
+extern "C" int mrf_stream_sync(mrf_ctx *ctx, void *stream)
+{
+    if (!ctx) return set_error(MRF_E_INVALID, "ctx is NULL");
+    cudaSetDevice(ctx->device);
+    return check_device_error(ctx, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// sequence
+
+static bool is_fin(double v) { return isfinite(v) != 0; }
+
+extern "C" int mrf_sequence_load(mrf_ctx *ctx, const mrf_sequence_desc *d, mrf_seq **out)
+{
+    if (!ctx || !d || !out) return set_error(MRF_E_INVALID, "NULL argument");
+    *out = nullptr;
+    const int n = d->n;
+    if (n < 1 || !d->flip_rad || !d->tr_ms || !d->te_ms) return set_error(MRF_E_INVALID, "sequence: n < 1 or NULL array");
+    if (d->inversion != 0 && d->inversion != 1) return set_error(MRF_E_INVALID, "sequence: inversion must be 0 or 1");
+    if (!is_fin(d->inv_delay_ms) || d->inv_delay_ms < 0) return set_error(MRF_E_INVALID, "sequence: bad inversion delay");
+    bool xonly = true, symmetric = true;
+    double min_tr = INFINITY;
+    for (int j = 0; j < n; ++j) {
+        double a = d->flip_rad[j], tr = d->tr_ms[j], te = d->te_ms[j];
+        double ph = d->rf_phase_rad ? d->rf_phase_rad[j] : 0.0;
+        if (!is_fin(a) || !is_fin(tr) || !is_fin(te) || !is_fin(ph))
+            return set_error(MRF_E_INVALID, "sequence: non-finite value at j=" + std::to_string(j));
+        if (!(tr > 0) || te < 0 || te > tr)
+            return set_error(MRF_E_INVALID, "sequence: need TR > 0 and 0 <= TE <= TR at j=" + std::to_string(j));
+        if (fabs(sin(ph)) > 1e-12) xonly = false;
+        if (fabs(te - (tr - te)) > 1e-12 * tr) symmetric = false;
+        if (tr < min_tr) min_tr = tr;
+    }
+    std::vector<float4> rfx(n);
+    std::vector<float> rfg(12 * (size_t)n, 0.f);
+    std::vector<float2> tau(n);
+    for (int j = 0; j < n; ++j) {
+        double a = d->flip_rad[j], ph = d->rf_phase_rad ? d->rf_phase_rad[j] : 0.0;
+        // Hard pulse R_z(phi) R_x(-alpha) R_z(-phi) (Appendix). For phi = k pi it is
+        // a rotation about x by beta = -alpha (k even) or +alpha (k odd).
+        double beta = cos(ph) > 0 ? -a : a;
+        double c = cos(beta), s = sin(beta), sh = sin(0.5 * beta);
+        rfx[j] = make_float4((float)c, (float)s, (float)(2.0 * sh * sh), 0.f);
+        // general matrix: rotation by -alpha about (cos phi, sin phi, 0) (Rodrigues)
+        double kx = cos(ph), ky = sin(ph), th = -a;
+        double ct = cos(th), st = sin(th), vt = 2.0 * sin(0.5 * th) * sin(0.5 * th);
+        double R[9] = {ct + kx * kx * vt, kx * ky * vt, ky * st,
+                       ky * kx * vt, ct + ky * ky * vt, -kx * st,
+                       -ky * st, kx * st, ct};
+        double omr22 = vt;   // 1 - R22 = 1 - cos(th)
+        for (int q = 0; q < 9; ++q) rfg[12 * (size_t)j + q] = (float)R[q];
+        rfg[12 * (size_t)j + 9] = (float)omr22;
+        tau[j] = make_float2((float)d->te_ms[j], (float)(d->tr_ms[j] - d->te_ms[j]));
+    }
+    cudaSetDevice(ctx->device);
+    mrf_seq *s = new mrf_seq();
+    s->n = n; s->xonly = xonly; s->symmetric = symmetric; s->inversion = d->inversion;
+    s->inv_delay = d->inv_delay_ms; s->min_tr = min_tr;
+    size_t b1 = sizeof(float4) * n, b2 = sizeof(float) * 12 * (size_t)n, b3 = sizeof(float2) * n;
+    int rc = dev_alloc(ctx, (void **)&s->rfx, b1, "sequence rfx");
+    if (!rc) rc = dev_alloc(ctx, (void **)&s->rfg, b2, "sequence rfg");
+    if (!rc) rc = dev_alloc(ctx, (void **)&s->tau, b3, "sequence tau");
+    if (rc) { seq_release(ctx, s); return rc; }
+    s->bytes = b1 + b2 + b3;
+    cudaError_t e = cudaMemcpy(s->rfx, rfx.data(), b1, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->rfg, rfg.data(), b2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->tau, tau.data(), b3, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { seq_release(ctx, s); return cuda_fail(e, "sequence upload"); }
+    *out = s;
+    return MRF_OK;
+}
+
+void seq_release(mrf_ctx *ctx, mrf_seq *s)
+{
+    if (!s) return;
+    if (s->rfx) dev_free(ctx, s->rfx, sizeof(float4) * s->n);
+    if (s->rfg) dev_free(ctx, s->rfg, sizeof(float) * 12 * (size_t)s->n);
+    if (s->tau) dev_free(ctx, s->tau, sizeof(float2) * s->n);
+    delete s;
+}
+
+int seq_clone(mrf_ctx *ctx, const mrf_seq *src, mrf_seq **out)
+{
+    mrf_seq *s = new mrf_seq(*src);
+    s->rfx = nullptr; s->rfg = nullptr; s->tau = nullptr;
+    size_t b1 = sizeof(float4) * src->n, b2 = sizeof(float) * 12 * (size_t)src->n, b3 = sizeof(float2) * src->n;
+    int rc = dev_alloc(ctx, (void **)&s->rfx, b1, "sequence rfx");
+    if (!rc) rc = dev_alloc(ctx, (void **)&s->rfg, b2, "sequence rfg");
+    if (!rc) rc = dev_alloc(ctx, (void **)&s->tau, b3, "sequence tau");
+    if (rc) { seq_release(ctx, s); return rc; }
+    cudaError_t e = cudaMemcpy(s->rfx, src->rfx, b1, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->rfg, src->rfg, b2, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->tau, src->tau, b3, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) { seq_release(ctx, s); return cuda_fail(e, "sequence copy"); }
+    *out = s;
+    return MRF_OK;
+}
+
+extern "C" int mrf_sequence_free(mrf_ctx *ctx, mrf_seq *seq)
+{
+    if (!ctx || !seq) return set_error(MRF_E_INVALID, "NULL argument");
+    cudaSetDevice(ctx->device);
+    seq_release(ctx, seq);
+    return MRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// grid
+
+int grid_validate(const mrf_grid_desc *g)
+{
+    if (!g) return set_error(MRF_E_INVALID, "grid is NULL");
+    if (g->n_t1 < 1 || g->n_t2 < 1 || g->n_df < 1) return set_error(MRF_E_INVALID, "grid: counts must be >= 1");
+    if (!(g->t1_step > 0) || !(g->t2_step > 0) || !(g->df_step > 0))
+        return set_error(MRF_E_INVALID, "grid: steps must be > 0");
+    if (!is_fin(g->t1_min) || !is_fin(g->t2_min) || !is_fin(g->df_min) || !is_fin(g->t1_step) ||
+        !is_fin(g->t2_step) || !is_fin(g->df_step))
+        return set_error(MRF_E_INVALID, "grid: non-finite value");
+    if (!(g->t1_min > 0) || !(g->t2_min > 0)) return set_error(MRF_E_INVALID, "grid: T1 and T2 must be > 0");
+    if (g->require_t2_lt_t1 != 0 && g->require_t2_lt_t1 != 1)
+        return set_error(MRF_E_INVALID, "grid: require_t2_lt_t1 must be 0 or 1");
+    return MRF_OK;
+}
+
+static double t1v(const mrf_grid_desc *g, int a) { return g->t1_min + (double)a * g->t1_step; }
+static double t2v(const mrf_grid_desc *g, int b) { return g->t2_min + (double)b * g->t2_step; }
+
+static int32_t nb_valid(const mrf_grid_desc *g, int a)
+{
+    if (!g->require_t2_lt_t1) return g->n_t2;
+    int32_t k = 0;
+    for (int b = 0; b < g->n_t2; ++b) if (t2v(g, b) < t1v(g, a)) k = b + 1;
+    return k;
+}
+
+extern "C" int64_t mrf_grid_count(const mrf_grid_desc *g)
+{
+    int rc = grid_validate(g);
+    if (rc) return rc;
+    int64_t total = 0;
+    for (int a = 0; a < g->n_t1; ++a) total += (int64_t)nb_valid(g, a) * g->n_df;
+    return total;
+}
+
+extern "C" int mrf_grid_unravel(const mrf_grid_desc *g, int64_t index, int32_t *a, int32_t *b, int32_t *c)
+{
+    int rc = grid_validate(g);
+    if (rc) return rc;
+    if (index < 0) return set_error(MRF_E_INVALID, "index < 0");
+    int64_t off = 0;
+    for (int aa = 0; aa < g->n_t1; ++aa) {
+        int64_t cnt = (int64_t)nb_valid(g, aa) * g->n_df;
+        if (index < off + cnt) {
+            int64_t rem = index - off;
+            if (a) *a = aa;
+            if (b) *b = (int32_t)(rem / g->n_df);
+            if (c) *c = (int32_t)(rem % g->n_df);
+            return MRF_OK;
+        }
+        off += cnt;
+    }
+    return set_error(MRF_E_INVALID, "index beyond the grid");
+}
+
+int grid_upload(mrf_ctx *ctx, const mrf_grid_desc *g, GridBuf *out)
+{
+    int rc = grid_validate(g);
+    if (rc) return rc;
+    GridBuf gb;
+    gb.desc = *g;
+    std::vector<float> t1(g->n_t1), t2(g->n_t2), df(g->n_df);
+    std::vector<int64_t> aoff(g->n_t1 + 1);
+    std::vector<int32_t> nb(g->n_t1);
+    for (int a = 0; a < g->n_t1; ++a) t1[a] = (float)t1v(g, a);
+    for (int b = 0; b < g->n_t2; ++b) t2[b] = (float)t2v(g, b);
+    for (int c = 0; c < g->n_df; ++c) df[c] = (float)(g->df_min + (double)c * g->df_step);
+    aoff[0] = 0;
+    for (int a = 0; a < g->n_t1; ++a) {
+        nb[a] = nb_valid(g, a);
+        aoff[a + 1] = aoff[a] + (int64_t)nb[a] * g->n_df;
+    }
+    gb.count = aoff[g->n_t1];
+    size_t bt1 = 4 * (size_t)g->n_t1, bt2 = 4 * (size_t)g->n_t2, bdf = 4 * (size_t)g->n_df;
+    size_t bao = 8 * (size_t)(g->n_t1 + 1), bnb = 4 * (size_t)g->n_t1;
+    rc = dev_alloc(ctx, (void **)&gb.t1, bt1, "grid t1");
+    if (!rc) rc = dev_alloc(ctx, (void **)&gb.t2, bt2, "grid t2");
+    if (!rc) rc = dev_alloc(ctx, (void **)&gb.df, bdf, "grid df");
+    if (!rc) rc = dev_alloc(ctx, (void **)&gb.a_off, bao, "grid offsets");
+    if (!rc) rc = dev_alloc(ctx, (void **)&gb.nb, bnb, "grid nb");
+    gb.bytes = bt1 + bt2 + bdf + bao + bnb;
+    if (rc) { grid_release(ctx, &gb); return rc; }
+    cudaError_t e = cudaMemcpy(gb.t1, t1.data(), bt1, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(gb.t2, t2.data(), bt2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(gb.df, df.data(), bdf, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(gb.a_off, aoff.data(), bao, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(gb.nb, nb.data(), bnb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { grid_release(ctx, &gb); return cuda_fail(e, "grid upload"); }
+    *out = gb;
+    return MRF_OK;
+}
+
+void grid_release(mrf_ctx *ctx, GridBuf *g)
+{
+    const mrf_grid_desc &d = g->desc;
+    if (g->t1) dev_free(ctx, g->t1, 4 * (size_t)d.n_t1);
+    if (g->t2) dev_free(ctx, g->t2, 4 * (size_t)d.n_t2);
+    if (g->df) dev_free(ctx, g->df, 4 * (size_t)d.n_df);
+    if (g->a_off) dev_free(ctx, g->a_off, 8 * (size_t)(d.n_t1 + 1));
+    if (g->nb) dev_free(ctx, g->nb, 4 * (size_t)d.n_t1);
+    *g = GridBuf();
+}
+
+// ---------------------------------------------------------------------------
+// simulation and dictionary
+
+extern "C" int mrf_simulate(mrf_ctx *ctx, const mrf_seq *seq, int64_t count, const float *t1, const float *t2,
+                            const float *df, void *out, void *stream)
+{
+    if (!ctx || !seq) return set_error(MRF_E_INVALID, "NULL argument");
+    if (count < 0) return set_error(MRF_E_INVALID, "count < 0");
+    if (count == 0) return MRF_OK;
+    if (!t1 || !t2 || !df || !out) return set_error(MRF_E_INVALID, "NULL device array");
+    cudaSetDevice(ctx->device);
+    return launch_simulate(ctx, seq, count, t1, t2, df, out, (cudaStream_t)stream);
+}
+
+static int dict_ld(int n) { return ((2 * n + 127) / 128) * 128; }
+
+extern "C" int mrf_dict_free(mrf_ctx *ctx, mrf_dict *d)
+{
+    if (!ctx || !d) return set_error(MRF_E_INVALID, "NULL argument");
+    cudaSetDevice(ctx->device);
+    const size_t ebytes = d->dtype == MRF_FP8E4M3 ? 1 : 2;
+    const size_t rows = (size_t)d->entries * d->ld * ebytes;
+    if (d->hi) dev_free(ctx, d->hi, rows);
+    if (d->lo) dev_free(ctx, d->lo, rows);
+    if (d->norm) dev_free(ctx, d->norm, 4 * (size_t)d->entries);
+    if (d->scale) dev_free(ctx, d->scale, 4 * (size_t)d->entries);
+    grid_release(ctx, &d->grid);
+    seq_release(ctx, d->seq);
+    delete d;
+    return MRF_OK;
+}
+
+extern "C" int mrf_dict_generate(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, mrf_dtype dtype,
+                                 void *stream, mrf_dict **out)
+{
+    if (!ctx || !seq || !grid || !out) return set_error(MRF_E_INVALID, "NULL argument");
+    *out = nullptr;
+    if (dtype != MRF_F32 && dtype != MRF_BF16 && dtype != MRF_FP8E4M3)
+        return set_error(MRF_E_INVALID, "unknown dtype");
+    int64_t count = mrf_grid_count(grid);
+    if (count < 0) return (int)count;
+    if (count == 0) return set_error(MRF_E_INVALID, "grid has no valid entry");
+    if (count > (int64_t)INT32_MAX) return set_error(MRF_E_UNSUPPORTED, "dictionaries above 2^31 entries");
+    cudaSetDevice(ctx->device);
+    mrf_dict *d = new mrf_dict();
+    d->dtype = dtype;
+    d->entries = count;
+    d->n = seq->n;
+    d->ld = dict_ld(seq->n);
+    int rc = seq_clone(ctx, seq, &d->seq);
+    if (rc) { delete d; return rc; }
+    rc = grid_upload(ctx, grid, &d->grid);
+    const size_t ebytes = dtype == MRF_FP8E4M3 ? 1 : 2;
+    const size_t rows = (size_t)count * d->ld * ebytes;
+    if (!rc) rc = dev_alloc(ctx, &d->hi, rows, "dictionary");
+    if (!rc && dtype == MRF_F32) rc = dev_alloc(ctx, &d->lo, rows, "dictionary residual");
+    if (!rc) rc = dev_alloc(ctx, (void **)&d->norm, 4 * (size_t)count, "dictionary norms");
+    if (!rc && dtype == MRF_FP8E4M3) rc = dev_alloc(ctx, (void **)&d->scale, 4 * (size_t)count, "dictionary scales");
+    if (rc) { mrf_dict_free(ctx, d); return rc; }
+    d->bytes = rows * (dtype == MRF_F32 ? 2 : 1) + 4 * (size_t)count * (dtype == MRF_FP8E4M3 ? 2 : 1) +
+               d->grid.bytes + d->seq->bytes;
+    rc = launch_dict_generate(ctx, d, (cudaStream_t)stream);
+    if (rc) { mrf_dict_free(ctx, d); return rc; }
+    *out = d;
+    return MRF_OK;
+}
+
+extern "C" int mrf_dict_query(const mrf_dict *d, mrf_dict_info *info)
+{
+    if (!d || !info) return set_error(MRF_E_INVALID, "NULL argument");
+    info->entries = d->entries;
+    info->n = d->n;
+    info->ld = d->ld;
+    info->dtype = d->dtype;
+    info->hi_dev = d->hi;
+    info->lo_dev = d->lo;
+    info->norm_dev = d->norm;
+    info->scale_dev = d->scale;
+    info->bytes = d->bytes;
+    return MRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// matching and ZOOM
+
+static bool valid_topk(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32; }
+
+extern "C" int mrf_match_bruteforce(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V,
+                                    const mrf_match_opts *o, mrf_result *out, void *stream)
+{
+    if (!ctx || !d || !o) return set_error(MRF_E_INVALID, "NULL argument");
+    if (V < 0) return set_error(MRF_E_INVALID, "V < 0");
+    if (o->precision != d->dtype) return set_error(MRF_E_INVALID, "precision differs from the dictionary dtype");
+    if (!valid_topk(o->top_k)) return set_error(MRF_E_INVALID, "top_k must be 1, 2, 4, 8, 16 or 32");
+    if (o->rescore != 0 && o->rescore != 1) return set_error(MRF_E_INVALID, "rescore must be 0 or 1");
+    if (V == 0) return MRF_OK;
+    if (!fp || !out) return set_error(MRF_E_INVALID, "NULL device buffer");
+    cudaSetDevice(ctx->device);
+    return run_match(ctx, d, fp, V, o->precision, o->top_k, o->rescore, out, nullptr, nullptr,
+                     (cudaStream_t)stream);
+}
+
+extern "C" int mrf_match_topk(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_t precision,
+                              int32_t top_k, int64_t *idx, float *cc2, void *stream)
+{
+    if (!ctx || !d) return set_error(MRF_E_INVALID, "NULL argument");
+    if (V < 0) return set_error(MRF_E_INVALID, "V < 0");
+    if (precision != d->dtype) return set_error(MRF_E_INVALID, "precision differs from the dictionary dtype");
+    if (!valid_topk(top_k)) return set_error(MRF_E_INVALID, "top_k must be 1, 2, 4, 8, 16 or 32");
+    if (V == 0) return MRF_OK;
+    if (!fp || !idx || !cc2) return set_error(MRF_E_INVALID, "NULL device buffer");
+    cudaSetDevice(ctx->device);
+    return run_match(ctx, d, fp, V, precision, top_k, 0, nullptr, idx, cc2, (cudaStream_t)stream);
+}
+
+extern "C" void mrf_zoom_opts_default(mrf_zoom_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->omega_hz = 0.0;
+    o->t1_init_ms = 1000.0;
+    o->t2_init_ms = 100.0;
+    o->s1a_step_frac = 6.0 / 7.0;
+    o->s1b_half_frac = 1.0;
+    o->s1b_step_frac = 1.0 / 20.0;
+    o->s3_half_frac = 0.5;
+    o->n_s2 = 2;
+    o->s2_t1_ms[0] = 200.0; o->s2_t2_ms[0] = 200.0;
+    o->s2_t1_ms[1] = 100.0; o->s2_t2_ms[1] = 100.0;
+    const int p[8] = {0, 1, 0, 0, 0, 1, 1, 1};
+    const double h[8] = {100.0, 100.0, 50.0, 20.0, 10.0, 50.0, 20.0, 10.0};
+    o->n_s4 = 8;
+    for (int i = 0; i < 8; ++i) { o->s4_param[i] = p[i]; o->s4_ms[i] = h[i]; }
+}
+
+extern "C" int mrf_zoom_search(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid,
+                               const mrf_zoom_opts *opts, const void *fp, int64_t V, mrf_result *out,
+                               void *stream)
+{
+    if (!ctx || !seq || !grid) return set_error(MRF_E_INVALID, "NULL argument");
+    int rc = grid_validate(grid);
+    if (rc) return rc;
+    if (V < 0) return set_error(MRF_E_INVALID, "V < 0");
+    mrf_zoom_opts def;
+    if (!opts) { mrf_zoom_opts_default(&def); opts = &def; }
+    if (opts->n_s2 < 0 || opts->n_s2 > MRF_ZOOM_MAX_LEVELS || opts->n_s4 < 0 || opts->n_s4 > MRF_ZOOM_MAX_LEVELS)
+        return set_error(MRF_E_INVALID, "zoom: level counts out of range");
+    for (int i = 0; i < opts->n_s4; ++i)
+        if (opts->s4_param[i] != 0 && opts->s4_param[i] != 1) return set_error(MRF_E_INVALID, "zoom: s4_param must be 0/1");
+    if (!(opts->s1a_step_frac > 0) || !(opts->s1b_step_frac > 0) || opts->s1b_half_frac < 0 || opts->s3_half_frac < 0)
+        return set_error(MRF_E_INVALID, "zoom: bad df search fractions");
+    if (V == 0) return MRF_OK;
+    if (!fp || !out) return set_error(MRF_E_INVALID, "NULL device buffer");
+    cudaSetDevice(ctx->device);
+    return run_zoom(ctx, seq, grid, opts, fp, V, out, (cudaStream_t)stream);
+}

@@ -1,0 +1,357 @@
+// Bloch-recurrence kernels: dictionary generation (normalise + quantise) and
+// on-the-fly simulation of arbitrary parameter triples.
+//
+// Dictionary generation (Theory: brute-force DGS simulates every grid entry;
+// entries normalised to unit norm so CC is |inner product|):
+//   one thread per entry, FP32 recurrence in registers (bloch.cuh);
+//   pass 1 accumulates ||d||^2 (and max |d| for FP8);
+//   pass 2 re-runs the recurrence and writes the normalised, quantised row.
+// Rows are staged per warp in shared memory (32 entries x 128 bytes, XOR
+// swizzled on 16-byte chunks) and leave as fully coalesced 16-byte stores, so
+// the kernel streams HBM writes at one pass of the output.
+// Evolution factors come from tables indexed by grid axis (E1 by T1, E2 by T2,
+// e^{i theta} by df), built once per dictionary with CUDA's expf/sincospif.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+#include "bloch.cuh"
+#include "mrf_internal.h"
+
+namespace {
+
+constexpr int kGenThreads = 128;
+
+struct Tables {
+    const float2 *e1;    // [n_t1][n]: (E1 over TE_j, E1 over TR_j - TE_j)
+    const float2 *e2;    // [n_t2][n]
+    const float4 *cis;   // [n][n_df]: (cos, sin) over TE_j, then over TR_j - TE_j
+    const float *e1_inv; // [n_t1]: E1 over the inversion delay
+};
+
+__global__ void tables_kernel(SeqDev s, GridDev g, float2 *e1, float2 *e2, float4 *cis, float *e1_inv)
+{
+    const int64_t n = s.n;
+    const int64_t n1 = (int64_t)g.n_t1 * n, n2 = (int64_t)g.n_t2 * n, n3 = n * g.n_df;
+    const int64_t total = n1 + n2 + n3 + g.n_t1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n1) {
+            const int a = (int)(i / n), j = (int)(i % n);
+            const float2 t = s.tau[j];
+            const float T1 = g.t1[a];
+            e1[i] = make_float2(expf(-t.x / T1), expf(-t.y / T1));
+        } else if (i < n1 + n2) {
+            const int64_t k = i - n1;
+            const int b = (int)(k / n), j = (int)(k % n);
+            const float2 t = s.tau[j];
+            const float T2 = g.t2[b];
+            e2[k] = make_float2(expf(-t.x / T2), expf(-t.y / T2));
+        } else if (i < n1 + n2 + n3) {
+            const int64_t k = i - n1 - n2;
+            const int j = (int)(k / g.n_df), c = (int)(k % g.n_df);
+            const float2 t = s.tau[j];
+            const float f = g.df[c] * 1.0e-3f;
+            float ta = f * t.x, tb = f * t.y;
+            ta -= rintf(ta);
+            tb -= rintf(tb);
+            float sa, ca, sb, cb;
+            sincospif(2.0f * ta, &sa, &ca);
+            sincospif(2.0f * tb, &sb, &cb);
+            cis[k] = make_float4(ca, sa, cb, sb);
+        } else {
+            const int a = (int)(i - n1 - n2 - n3);
+            e1_inv[a] = expf(-s.inv_delay / g.t1[a]);
+        }
+    }
+}
+
+// Linear entry index -> (a, b, c): binary search over the T1 offsets.
+__device__ __forceinline__ void unravel(const GridDev &g, int64_t e, int &a, int &b, int &c)
+{
+    int lo = 0, hi = g.n_t1 - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&g.a_off[mid]) <= e) lo = mid; else hi = mid - 1;
+    }
+    a = lo;
+    const int64_t rem = e - __ldg(&g.a_off[a]);
+    b = (int)(rem / g.n_df);
+    c = (int)(rem % g.n_df);
+}
+
+// One timepoint with tabulated factors.
+template <bool XONLY>
+__device__ __forceinline__ void step_tab(Bloch &st, const SeqDev &s, const Tables &t, int n, int n_df, int a, int b,
+                                         int c, int j, float &sr, float &si)
+{
+    bloch_rf<XONLY>(st, s, j);
+    const float2 e1 = __ldg(&t.e1[(int64_t)a * n + j]);
+    const float2 e2 = __ldg(&t.e2[(int64_t)b * n + j]);
+    const float4 z = __ldg(&t.cis[(int64_t)j * n_df + c]);
+    bloch_evolve(st, e1.x, e2.x * z.x, e2.x * z.y);
+    sr = st.mx;
+    si = st.my;
+    bloch_evolve(st, e1.y, e2.y * z.z, e2.y * z.w);
+}
+
+// Packs timepoint values into 16-byte vectors for the staged row writer.
+template <int OUT>
+struct Packer;
+
+// F32 (hi + lo bf16) and BF16: 4 bytes per timepoint per array.
+template <>
+struct Packer<MRF_F32> {
+    static constexpr int kBpt = 4;
+    uint32_t hi[4], lo[4];
+    __device__ __forceinline__ void put(int slot, float vr, float vi, float)
+    {
+        __nv_bfloat162 h = __floats2bfloat162_rn(vr, vi);
+        float2 hf = __bfloat1622float2(h);
+        __nv_bfloat162 l = __floats2bfloat162_rn(vr - hf.x, vi - hf.y);
+        hi[slot] = *reinterpret_cast<uint32_t *>(&h);
+        lo[slot] = *reinterpret_cast<uint32_t *>(&l);
+    }
+};
+
+template <>
+struct Packer<MRF_BF16> {
+    static constexpr int kBpt = 4;
+    uint32_t hi[4], lo[4];
+    __device__ __forceinline__ void put(int slot, float vr, float vi, float)
+    {
+        __nv_bfloat162 h = __floats2bfloat162_rn(vr, vi);
+        hi[slot] = *reinterpret_cast<uint32_t *>(&h);
+    }
+};
+
+// FP8 e4m3: 2 bytes per timepoint; values multiplied by the per-entry 1/scale.
+template <>
+struct Packer<MRF_FP8E4M3> {
+    static constexpr int kBpt = 2;
+    uint32_t hi[4], lo[4];
+    __device__ __forceinline__ void put(int slot, float vr, float vi, float qs)
+    {
+        __nv_fp8x2_storage_t q = __nv_cvt_float2_to_fp8x2(make_float2(vr * qs, vi * qs), __NV_SATFINITE, __NV_E4M3);
+        const int word = slot >> 1, half = slot & 1;
+        if (half == 0) hi[word] = (uint32_t)q;
+        else hi[word] |= ((uint32_t)q) << 16;
+    }
+};
+
+template <int OUT, bool XONLY>
+__global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev g, Tables t, int64_t D, int ld,
+                                                               uint8_t *out_hi, uint8_t *out_lo, float *norm_out,
+                                                               float *scale_out)
+{
+    using P = Packer<OUT>;
+    constexpr int kBpt = P::kBpt;               // bytes per timepoint per array
+    constexpr int kPerVec = 16 / kBpt;          // timepoints per 16-byte vector
+    constexpr int kJ = 128 / kBpt;              // timepoints per 128-byte row chunk
+    constexpr bool kTwo = (OUT == MRF_F32);
+
+    __shared__ uint4 stage_hi[kGenThreads / 32][32][8];
+    __shared__ uint4 stage_lo[kTwo ? kGenThreads / 32 : 1][32][8];
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * kGenThreads + threadIdx.x;
+    const int64_t row0 = (int64_t)blockIdx.x * kGenThreads + warp * 32;
+    const bool live = e < D;
+    const int n = s.n;
+    int a = 0, b = 0, c = 0;
+    if (live) unravel(g, e, a, b, c);
+    const float e1inv = live && s.inversion ? __ldg(&t.e1_inv[a]) : 1.f;
+
+    // pass 1: norm (blocked FP32 partial sums, Kahan-compensated total)
+    float tot = 0.f, comp = 0.f, amax = 0.f;
+    Bloch st;
+    if (live) {
+        bloch_init(st);
+        if (s.inversion) { bloch_invert(st); st.w *= e1inv; }
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            float part = 0.f;
+            const int j1 = min(n, j0 + 32);
+            for (int j = j0; j < j1; ++j) {
+                float sr, si;
+                step_tab<XONLY>(st, s, t, n, g.n_df, a, b, c, j, sr, si);
+                part = fmaf(sr, sr, fmaf(si, si, part));
+                if (OUT == MRF_FP8E4M3) amax = fmaxf(amax, fmaxf(fabsf(sr), fabsf(si)));
+            }
+            const float y = part - comp;
+            const float tt = tot + y;
+            comp = (tt - tot) - y;
+            tot = tt;
+        }
+    }
+    const float nrm = sqrtf(tot);
+    const float inv = nrm > 0.f ? 1.0f / nrm : 0.f;
+    float qs = 1.f;
+    if (live) {
+        norm_out[e] = nrm;
+        if (OUT == MRF_FP8E4M3) {
+            const float mx = amax * inv;                      // max |normalised component|
+            const float scale = mx > 0.f ? mx / 448.0f : 1.0f;
+            qs = inv / scale;                                 // raw value -> e4m3 code scale
+            scale_out[e] = scale;
+        } else {
+            qs = inv;
+        }
+    }
+
+    // pass 2: re-run, write normalised rows through the warp stage
+    if (live) {
+        bloch_init(st);
+        if (s.inversion) { bloch_invert(st); st.w *= e1inv; }
+    }
+    const int row_bytes = ld * (OUT == MRF_FP8E4M3 ? 1 : 2);
+    const int tp_row = row_bytes / kBpt;      // timepoint slots per row (incl. padding)
+    for (int j0 = 0; j0 < tp_row; j0 += kJ) {
+#pragma unroll 1
+        for (int q = 0; q < 8; ++q) {
+            P pk;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { pk.hi[u] = 0u; pk.lo[u] = 0u; }
+#pragma unroll
+            for (int u = 0; u < kPerVec; ++u) {
+                const int j = j0 + q * kPerVec + u;
+                float vr = 0.f, vi = 0.f;
+                if (live && j < n) {
+                    float sr, si;
+                    step_tab<XONLY>(st, s, t, n, g.n_df, a, b, c, j, sr, si);
+                    vr = sr;
+                    vi = si;
+                }
+                pk.put(u, vr * (OUT == MRF_FP8E4M3 ? 1.f : qs), vi * (OUT == MRF_FP8E4M3 ? 1.f : qs),
+                       OUT == MRF_FP8E4M3 ? qs : 1.f);
+            }
+            const int pq = q ^ (lane & 7);
+            stage_hi[warp][lane][pq] = make_uint4(pk.hi[0], pk.hi[1], pk.hi[2], pk.hi[3]);
+            if (kTwo) stage_lo[kTwo ? warp : 0][lane][pq] = make_uint4(pk.lo[0], pk.lo[1], pk.lo[2], pk.lo[3]);
+        }
+        __syncwarp();
+        const int qq = lane & 7;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = i * 4 + (lane >> 3);
+            const int64_t row = row0 + r;
+            if (row < D) {
+                const size_t off = (size_t)row * row_bytes + (size_t)j0 * kBpt + qq * 16;
+                const uint4 vh = stage_hi[warp][r][qq ^ (r & 7)];
+                __stcs(reinterpret_cast<uint4 *>(out_hi + off), vh);
+                if (kTwo) {
+                    const uint4 vl = stage_lo[kTwo ? warp : 0][r][qq ^ (r & 7)];
+                    __stcs(reinterpret_cast<uint4 *>(out_lo + off), vl);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Arbitrary (T1, T2, df) per thread, complex64 rows of n timepoints, not normalised.
+template <bool XONLY>
+__global__ void __launch_bounds__(128) simulate_kernel(SeqDev s, int64_t count, const float *t1, const float *t2,
+                                                       const float *df, float2 *out, int staged)
+{
+    __shared__ uint4 stage[4][32][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t e = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    const int64_t row0 = (int64_t)blockIdx.x * 128 + warp * 32;
+    const bool live = e < count;
+    const int n = s.n;
+    Relax r = relax_make(live ? t1[e] : 1.f, live ? t2[e] : 1.f, live ? df[e] : 0.f);
+    Bloch st;
+    bloch_start(st, s, r);
+    if (staged) {
+        // staged (n even, out 16-byte aligned): 16 timepoints (128 bytes) per
+        // row chunk, 2 per 16-byte vector
+        for (int j0 = 0; j0 < n; j0 += 16) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int j = j0 + 2 * q + u;
+                    if (live && j < n) bloch_step_otf<XONLY>(st, s, r, j, v[2 * u], v[2 * u + 1]);
+                }
+                stage[warp][lane][q ^ (lane & 7)] = make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]),
+                                                               __float_as_uint(v[2]), __float_as_uint(v[3]));
+            }
+            __syncwarp();
+            const int qq = lane & 7;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int rr = i * 4 + (lane >> 3);
+                const int64_t row = row0 + rr;
+                const int j = j0 + 2 * qq;
+                if (row < count && j < n) {
+                    const uint4 val = stage[warp][rr][qq ^ (rr & 7)];
+                    *reinterpret_cast<uint4 *>(out + (size_t)row * n + j) = val;
+                }
+            }
+            __syncwarp();
+        }
+    } else if (live) {
+        for (int j = 0; j < n; ++j) {
+            float sr, si;
+            bloch_step_otf<XONLY>(st, s, r, j, sr, si);
+            out[(size_t)e * n + j] = make_float2(sr, si);
+        }
+    }
+}
+
+}  // namespace
+
+int launch_dict_generate(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream)
+{
+    const SeqDev s = d->seq->dev();
+    const GridDev g = d->grid.dev();
+    const int n = s.n;
+    // evolution-factor tables in stream-ordered scratch
+    const size_t b1 = sizeof(float2) * (size_t)g.n_t1 * n, b2 = sizeof(float2) * (size_t)g.n_t2 * n;
+    const size_t b3 = sizeof(float4) * (size_t)n * g.n_df, b4 = sizeof(float) * (size_t)g.n_t1;
+    const size_t tb = b1 + b2 + b3 + b4 + 256 * 4;
+    int rc = budget_charge(ctx, tb);
+    if (rc) return rc;
+    uint8_t *tab = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&tab, tb, stream);
+    if (e != cudaSuccess) { budget_release(ctx, tb); return cuda_fail(e, "table scratch"); }
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    float2 *e1 = (float2 *)tab;
+    float2 *e2 = (float2 *)(tab + al(b1));
+    float4 *cis = (float4 *)(tab + al(b1) + al(b2));
+    float *e1i = (float *)(tab + al(b1) + al(b2) + al(b3));
+    tables_kernel<<<4 * ctx->sm_count, 256, 0, stream>>>(s, g, e1, e2, cis, e1i);
+    Tables t{e1, e2, cis, e1i};
+    const int64_t blocks = (d->entries + kGenThreads - 1) / kGenThreads;
+    uint8_t *hi = (uint8_t *)d->hi, *lo = (uint8_t *)d->lo;
+#define MRF_GEN(OUT, XO) dict_gen_kernel<OUT, XO><<<(unsigned)blocks, kGenThreads, 0, stream>>>(s, g, t, d->entries, d->ld, hi, lo, d->norm, d->scale)
+    if (s.xonly) {
+        if (d->dtype == MRF_F32) MRF_GEN(MRF_F32, true);
+        else if (d->dtype == MRF_BF16) MRF_GEN(MRF_BF16, true);
+        else MRF_GEN(MRF_FP8E4M3, true);
+    } else {
+        if (d->dtype == MRF_F32) MRF_GEN(MRF_F32, false);
+        else if (d->dtype == MRF_BF16) MRF_GEN(MRF_BF16, false);
+        else MRF_GEN(MRF_FP8E4M3, false);
+    }
+#undef MRF_GEN
+    e = cudaGetLastError();
+    cudaFreeAsync(tab, stream);
+    budget_release(ctx, tb);
+    if (e != cudaSuccess) return cuda_fail(e, "dictionary generation launch");
+    return MRF_OK;
+}
+
+int launch_simulate(mrf_ctx *ctx, const mrf_seq *seq, int64_t count, const float *t1, const float *t2,
+                    const float *df, void *out, cudaStream_t stream)
+{
+    (void)ctx;
+    const SeqDev s = seq->dev();
+    const int64_t blocks = (count + 127) / 128;
+    const int staged = (s.n % 2 == 0) && (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+    if (s.xonly) simulate_kernel<true><<<(unsigned)blocks, 128, 0, stream>>>(s, count, t1, t2, df, (float2 *)out, staged);
+    else simulate_kernel<false><<<(unsigned)blocks, 128, 0, stream>>>(s, count, t1, t2, df, (float2 *)out, staged);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "simulate launch");
+    return MRF_OK;
+}

@@ -1,0 +1,722 @@
+// Brute-force DGS matcher (Theory: argmax of Eq. 1 over every grid entry).
+//
+// With unit-norm voxels x and entries d, CC(x, d) = |sum_j x_j conj(d_j)|.
+// Writing each voxel as two real rows of length 2n over interleaved (re, im)
+// timepoints,
+//     row 2v   = ( xr_0,  xi_0,  xr_1,  xi_1, ...)
+//     row 2v+1 = ( xi_0, -xr_0,  xi_1, -xr_1, ...)
+// and each entry as (dr_0, di_0, dr_1, di_1, ...), the product of the 2V x 2n
+// voxel matrix with the n-row-major dictionary gives Re <x, d> in row 2v and
+// Im <x, d> in row 2v+1: the complex correlation is one real GEMM whose 2 x 2
+// blocks are the complex products.
+//
+// The GEMM runs on the 5th-generation tensor cores: 128 voxel rows (64
+// voxels) x 256 entries per tile, fp32 accumulators in TMEM (two 256-column
+// buffers), operand tiles staged by TMA with 128-byte swizzle. A persistent
+// warp-specialised CTA per SM: warp 0 issues TMA, warp 1 issues tcgen05.mma,
+// warps 2-5 read the accumulators (tcgen05.ld), form CC^2 = Re^2 + Im^2 and
+// keep each voxel's running top-k in registers. The V x D score matrix never
+// leaves the SM; each (voxel block, dictionary chunk) work unit writes only
+// its top-k, merged across chunks afterwards.
+//
+// Precisions: MRF_F32 = bf16 hi/lo split with three products
+// (hi.hi + hi.lo + lo.hi, ~2^-16 relative per term); MRF_BF16 = one bf16
+// product; MRF_FP8E4M3 = one e4m3 product (kind::f8f6f4) with per-entry and
+// per-voxel scales applied to CC^2.
+//
+// Re-score (Discussion: normalised-CC errors fixed by a non-normalised final
+// comparison): each voxel's candidates are re-simulated in FP32 and their CC
+// taken with FP64 accumulation; the best (ties to the smaller index) wins.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "bloch.cuh"
+#include "mrf_internal.h"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int BM = 128;          // voxel rows per tile (64 voxels)
+constexpr int BN = 256;          // dictionary entries per tile
+constexpr int kThreads = 192;    // 6 warps: TMA, MMA, 4 x epilogue
+constexpr uint64_t kWaitLimitNs = 4000000000ull;   // 4 s per barrier wait
+
+template <int MODE>
+struct Cfg;
+template <>
+struct Cfg<MRF_F32> {
+    static constexpr int kBK = 64, kStages = 2, kOps = 2;   // hi and lo of each operand
+};
+template <>
+struct Cfg<MRF_BF16> {
+    static constexpr int kBK = 64, kStages = 4, kOps = 1;
+};
+template <>
+struct Cfg<MRF_FP8E4M3> {
+    static constexpr int kBK = 128, kStages = 4, kOps = 1;
+};
+
+constexpr int kTileA = BM * 128;   // bytes of one A operand tile (128 rows x 128 B)
+constexpr int kTileB = BN * 128;   // bytes of one B operand tile (256 rows x 128 B)
+
+template <int MODE>
+constexpr int stage_bytes() { return Cfg<MODE>::kOps * (kTileA + kTileB); }
+template <int MODE>
+constexpr int smem_bytes() { return Cfg<MODE>::kStages * stage_bytes<MODE>() + 1024; }
+
+struct MatchParams {
+    int64_t D;           // dictionary entries
+    int64_t V;           // voxels
+    int n_tiles;         // ceil(D / BN)
+    int n_mb;            // voxel blocks of 64
+    int n_chunks;        // dictionary chunks per voxel block
+    int k_blocks;        // K blocks of 128 bytes
+    int last_ksteps;     // MMA k-steps in the last K block (rest is zero padding)
+    const float *colscale;   // FP8: per-entry dequantisation scale, else nullptr
+    float2 *part;        // [V][n_chunks][K]: (cc2, idx bits)
+    int *err;
+};
+
+// order: higher cc2 first, then smaller index
+__device__ __forceinline__ bool before(float c, int i, float oc, int oi)
+{
+    return c > oc || (c == oc && i < oi);
+}
+
+template <int K>
+struct TopK {
+    float v[K];
+    int i[K];
+    __device__ __forceinline__ void reset()
+    {
+#pragma unroll
+        for (int q = 0; q < K; ++q) { v[q] = -1.0f; i[q] = 0x7fffffff; }
+    }
+    // insert with the full order (used for merges)
+    __device__ __forceinline__ void insert(float c, int idx)
+    {
+        if (!before(c, idx, v[K - 1], i[K - 1])) return;
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            if (before(c, idx, v[q], i[q])) {
+                const float tc = v[q];
+                const int ti = i[q];
+                v[q] = c; i[q] = idx;
+                c = tc; idx = ti;
+            }
+        }
+    }
+    // insert a column visited in increasing index order (strict > suffices to enter)
+    __device__ __forceinline__ void push(float c, int idx)
+    {
+        if (c > v[K - 1]) insert(c, idx);
+    }
+};
+
+template <int MODE, int K>
+__global__ void __launch_bounds__(kThreads, 1)
+    match_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
+                 const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapB2,
+                 MatchParams p)
+{
+    using C = Cfg<MODE>;
+    constexpr int S = C::kStages;
+    constexpr uint32_t kStageBytes = stage_bytes<MODE>();
+    constexpr uint32_t kIdesc = MODE == MRF_FP8E4M3 ? make_idesc(0, 0, BM, BN) : make_idesc(1, 1, BM, BN);
+
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], tfull_bar[2], tempty_bar[2], drain_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    // stage s: [A_hi | A_lo? | B_hi | B_lo?]
+    auto tileA = [&](int s, int op) { return smem + s * kStageBytes + op * kTileA; };
+    auto tileB = [&](int s, int op) { return smem + s * kStageBytes + C::kOps * kTileA + op * kTileB; };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
+        for (int a = 0; a < 2; ++a) { mbar_init(&tfull_bar[a], 1); mbar_init(&tempty_bar[a], 4); }
+        mbar_init(&drain_bar, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0 && lane == 0) {
+        tma_prefetch_desc(&mapA);
+        tma_prefetch_desc(&mapB);
+        if (C::kOps == 2) { tma_prefetch_desc(&mapA2); tma_prefetch_desc(&mapB2); }
+    }
+    if (warp == 1) {
+        tmem_alloc(&tmem_slot, 2 * BN);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_slot;
+
+    const int n_units = p.n_mb * p.n_chunks;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            bool issued[S];
+            uint32_t issued_ph[S];
+            for (int q = 0; q < S; ++q) { issued[q] = false; issued_ph[q] = 0; }
+            for (int u = blockIdx.x; u < n_units && !abort_flag; u += gridDim.x) {
+                const int chunk = u / p.n_mb, mb = u % p.n_mb;
+                const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
+                const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
+                for (int t = t0; t < t1; ++t) {
+                    for (int kb = 0; kb < p.k_blocks; ++kb) {
+                        if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kWaitLimitNs)) goto producer_done;
+                        mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
+                        const int kx = kb * C::kBK;
+                        tma_load_2d(tileA(s, 0), &mapA, &full_bar[s], kx, mb * BM);
+                        if (C::kOps == 2) tma_load_2d(tileA(s, 1), &mapA2, &full_bar[s], kx, mb * BM);
+                        tma_load_2d(tileB(s, 0), &mapB, &full_bar[s], kx, t * BN);
+                        if (C::kOps == 2) tma_load_2d(tileB(s, 1), &mapB2, &full_bar[s], kx, t * BN);
+                        issued[s] = true;
+                        issued_ph[s] = ph;
+                        if (++s == S) { s = 0; ph ^= 1; }
+                    }
+                }
+            }
+        producer_done:
+            // every load issued into shared memory must land before the CTA exits
+            for (int q = 0; q < S; ++q) {
+                if (!issued[q]) continue;
+                const uint64_t t0 = global_timer_ns();
+                while (!mbar_try_wait(&full_bar[q], issued_ph[q])) {
+                    if (global_timer_ns() - t0 > kWaitLimitNs) { atomicExch(p.err, 1); break; }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            int s = 0, acc = 0;
+            uint32_t ph = 0, acc_ph = 0;
+            bool any = false;
+            for (int u = blockIdx.x; u < n_units && !abort_flag; u += gridDim.x) {
+                const int chunk = u / p.n_mb;
+                const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
+                const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
+                for (int t = t0; t < t1; ++t) {
+                    if (!mbar_wait_bounded(&tempty_bar[acc], acc_ph ^ 1, &abort_flag, p.err, kWaitLimitNs)) goto mma_done;
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+                    for (int kb = 0; kb < p.k_blocks; ++kb) {
+                        if (!mbar_wait_bounded(&full_bar[s], ph, &abort_flag, p.err, kWaitLimitNs)) goto mma_done;
+                        tc_fence_after();
+                        const uint64_t a0 = smem_desc_sw128(tileA(s, 0));
+                        const uint64_t b0 = smem_desc_sw128(tileB(s, 0));
+                        const int nk = (kb == p.k_blocks - 1) ? p.last_ksteps : 4;
+                        for (int kk = 0; kk < nk; ++kk) {
+                            // advance 32 bytes along K inside the swizzled 128-byte rows
+                            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+                            const uint32_t accum = (kb | kk) != 0;
+                            if (MODE == MRF_FP8E4M3) {
+                                mma_f8(d_tmem, a0 + adv, b0 + adv, kIdesc, accum);
+                            } else {
+                                mma_f16(d_tmem, a0 + adv, b0 + adv, kIdesc, accum);
+                                if (MODE == MRF_F32) {
+                                    const uint64_t a1 = smem_desc_sw128(tileA(s, 1));
+                                    const uint64_t b1 = smem_desc_sw128(tileB(s, 1));
+                                    mma_f16(d_tmem, a0 + adv, b1 + adv, kIdesc, 1u);
+                                    mma_f16(d_tmem, a1 + adv, b0 + adv, kIdesc, 1u);
+                                }
+                            }
+                        }
+                        mma_commit(&empty_bar[s]);   // frees the stage when these MMAs finish
+                        any = true;
+                        if (++s == S) { s = 0; ph ^= 1; }
+                    }
+                    mma_commit(&tfull_bar[acc]);     // accumulator ready for the epilogue
+                    if (++acc == 2) { acc = 0; acc_ph ^= 1; }
+                }
+            }
+        mma_done:
+            if (any) {
+                // all issued MMAs must finish before TMEM is released
+                mma_commit(&drain_bar);
+                const uint64_t t0 = global_timer_ns();
+                while (!mbar_try_wait(&drain_bar, 0)) {
+                    if (global_timer_ns() - t0 > kWaitLimitNs) { atomicExch(p.err, 1); break; }
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: TMEM -> CC^2 -> running top-k ----------------
+        const int quad = warp & 3;                 // TMEM lane quadrant this warp may access
+        const int row = quad * 32 + lane;          // voxel row within the tile
+        const int par = row & 1;                   // 0: Re row, 1: Im row
+        int acc = 0;
+        uint32_t acc_ph = 0;
+        TopK<K> tk;
+        for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+            if (__any_sync(0xffffffffu, abort_flag != 0)) break;
+            const int chunk = u / p.n_mb, mb = u % p.n_mb;
+            const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
+            const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
+            tk.reset();
+            for (int t = t0; t < t1; ++t) {
+                const bool ok = mbar_wait_bounded(&tfull_bar[acc], acc_ph, &abort_flag, p.err, kWaitLimitNs);
+                if (!__all_sync(0xffffffffu, ok)) goto epi_done;   // leave as a whole warp
+                tc_fence_after();
+                const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+                for (int ch = 0; ch < BN / 32; ++ch) {
+                    uint32_t r[32];
+                    tmem_ld_32x32b_x32(tbase + ch * 32, r);
+                    tmem_wait_ld();
+                    const int col0 = t * BN + ch * 32 + (par ? 16 : 0);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float mine_lo = __uint_as_float(r[q]);
+                        const float mine_hi = __uint_as_float(r[16 + q]);
+                        const float send = par ? mine_lo : mine_hi;
+                        const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+                        const float re = par ? recv : mine_lo;
+                        const float im = par ? mine_hi : recv;
+                        float c2 = fmaf(re, re, im * im);
+                        const int col = col0 + q;
+                        if (col < p.D) {
+                            if (MODE == MRF_FP8E4M3) {
+                                const float sc = __ldg(&p.colscale[col]);
+                                c2 *= sc * sc;
+                            }
+                            tk.push(c2, col);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty_bar[acc]);
+                if (++acc == 2) { acc = 0; acc_ph ^= 1; }
+            }
+            // merge the Re/Im pair's lists (each covered half of the columns)
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                const float ov = __shfl_xor_sync(0xffffffffu, tk.v[q], 1);
+                const int oi = __shfl_xor_sync(0xffffffffu, tk.i[q], 1);
+                tk.insert(ov, oi);
+            }
+            const int64_t v = (int64_t)mb * (BM / 2) + (row >> 1);
+            if (par == 0 && v < p.V) {
+                float2 *dst = p.part + ((size_t)v * p.n_chunks + chunk) * K;
+#pragma unroll
+                for (int q = 0; q < K; ++q) dst[q] = make_float2(tk.v[q], __int_as_float(tk.i[q]));
+            }
+        }
+    epi_done:;
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 2 * BN);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// voxel prep: normalise and lay out the two real rows per voxel
+
+template <int MODE>
+__global__ void __launch_bounds__(256) voxel_prep_kernel(const float2 *x, int64_t V, int n, int ld, uint8_t *a_hi,
+                                                         uint8_t *a_lo, float *row_scale)
+{
+    const int64_t v = blockIdx.x;
+    __shared__ float red[2][8];
+    float ss = 0.f, mx = 0.f;
+    const bool live = v < V;
+    if (live) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const float2 z = x[(size_t)v * n + j];
+            ss = fmaf(z.x, z.x, fmaf(z.y, z.y, ss));
+            mx = fmaxf(mx, fmaxf(fabsf(z.x), fabsf(z.y)));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = ss; red[1][threadIdx.x >> 5] = mx; }
+    __syncthreads();
+    ss = 0.f; mx = 0.f;
+    for (int w = 0; w < 8; ++w) { ss += red[0][w]; mx = fmaxf(mx, red[1][w]); }
+    const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
+    float qs = inv;
+    if (MODE == MRF_FP8E4M3) {
+        const float m = mx * inv;
+        const float scale = m > 0.f ? m / 448.0f : 1.0f;
+        qs = inv / scale;
+        if (threadIdx.x == 0) row_scale[v] = live ? scale : 0.f;
+    }
+    const int half = ld / 2;   // timepoint slots per row
+    for (int j = threadIdx.x; j < half; j += blockDim.x) {
+        float xr = 0.f, xi = 0.f;
+        if (live && j < n) {
+            const float2 z = x[(size_t)v * n + j];
+            xr = z.x * qs;
+            xi = z.y * qs;
+        }
+        const size_t r0 = (size_t)(2 * v) * ld, r1 = (size_t)(2 * v + 1) * ld;
+        if (MODE == MRF_FP8E4M3) {
+            __nv_fp8x2_storage_t q0 = __nv_cvt_float2_to_fp8x2(make_float2(xr, xi), __NV_SATFINITE, __NV_E4M3);
+            __nv_fp8x2_storage_t q1 = __nv_cvt_float2_to_fp8x2(make_float2(xi, -xr), __NV_SATFINITE, __NV_E4M3);
+            reinterpret_cast<__nv_fp8x2_storage_t *>(a_hi + r0)[j] = q0;
+            reinterpret_cast<__nv_fp8x2_storage_t *>(a_hi + r1)[j] = q1;
+        } else {
+            __nv_bfloat162 h0 = __floats2bfloat162_rn(xr, xi);
+            __nv_bfloat162 h1 = __floats2bfloat162_rn(xi, -xr);
+            reinterpret_cast<__nv_bfloat162 *>(a_hi + 2 * r0)[j] = h0;
+            reinterpret_cast<__nv_bfloat162 *>(a_hi + 2 * r1)[j] = h1;
+            if (MODE == MRF_F32) {
+                const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+                reinterpret_cast<__nv_bfloat162 *>(a_lo + 2 * r0)[j] = __floats2bfloat162_rn(xr - f0.x, xi - f0.y);
+                reinterpret_cast<__nv_bfloat162 *>(a_lo + 2 * r1)[j] = __floats2bfloat162_rn(xi - f1.x, -xr - f1.y);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// merge the per-chunk top-k lists of each voxel (one warp per voxel)
+
+template <int K>
+__global__ void merge_kernel(const float2 *part, int64_t V, int n_chunks, const float *row_scale, int64_t *idx_out,
+                             float *cc2_out)
+{
+    const int64_t v = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (v >= V) return;
+    const int total = n_chunks * K;
+    const float2 *src = part + (size_t)v * total;
+    const float rs = row_scale ? row_scale[v] : 1.f;
+    const float rs2 = rs * rs;
+    int last_i = -1;
+    float last_c = 3.4e38f;
+    for (int q = 0; q < K; ++q) {
+        // best candidate strictly after (last_c, last_i) in the order
+        float bc = -2.f;
+        int bi = 0x7fffffff;
+        for (int k = lane; k < total; k += 32) {
+            const float2 e = src[k];
+            const float c = e.x;
+            const int i = __float_as_int(e.y);
+            if (i == 0x7fffffff) continue;
+            if (!before(c, i, last_c, last_i) && before(c, i, bc, bi)) { bc = c; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oc = __shfl_xor_sync(0xffffffffu, bc, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (before(oc, oi, bc, bi)) { bc = oc; bi = oi; }
+        }
+        if (lane == 0) {
+            idx_out[(size_t)v * K + q] = bi == 0x7fffffff ? -1 : (int64_t)bi;
+            cc2_out[(size_t)v * K + q] = bi == 0x7fffffff ? -1.f : bc * rs2;
+        }
+        last_c = bc;
+        last_i = bi;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// re-score: FP32 re-simulation of each candidate, FP64 accumulation of the
+// inner product and norms, best by FP64 CC (ties to the smaller index)
+
+__device__ __forceinline__ void unravel_dev(const GridDev &g, int64_t e, int &a, int &b, int &c)
+{
+    int lo = 0, hi = g.n_t1 - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&g.a_off[mid]) <= e) lo = mid; else hi = mid - 1;
+    }
+    a = lo;
+    const int64_t rem = e - __ldg(&g.a_off[a]);
+    b = (int)(rem / g.n_df);
+    c = (int)(rem % g.n_df);
+}
+
+template <bool XONLY>
+__global__ void rescore_kernel(SeqDev s, GridDev g, const float2 *x, int64_t V, int K, const int64_t *cand,
+                               const float *cand_cc2, int rank, int64_t D, mrf_result *out)
+{
+    const int64_t v = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (v >= V) return;
+    const int n = s.n;
+    const float2 *xv = x + (size_t)v * n;
+    // ||x||^2 in FP64
+    double xx = 0.0;
+    for (int j = lane; j < n; j += 32) {
+        const float2 z = xv[j];
+        xx += (double)z.x * z.x + (double)z.y * z.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) xx += __shfl_xor_sync(0xffffffffu, xx, o);
+
+    const int ncand = rank ? K : 1;
+    const int64_t e = lane < ncand ? cand[(size_t)v * K + lane] : -1;
+    const bool live = e >= 0;
+    int a = 0, b = 0, c = 0;
+    if (live) unravel_dev(g, e, a, b, c);
+    Relax r = relax_make(live ? g.t1[a] : 1.f, live ? g.t2[b] : 1.f, live ? g.df[c] : 0.f);
+    Bloch st;
+    bloch_start(st, s, r);
+    double ipr = 0.0, ipi = 0.0, dd = 0.0;
+    for (int j0 = 0; j0 < n; j0 += 8) {
+        float pr = 0.f, pi = 0.f, pd = 0.f;
+        const int j1 = min(n, j0 + 8);
+        for (int j = j0; j < j1; ++j) {
+            float sr, si;
+            bloch_step_otf<XONLY>(st, s, r, j, sr, si);
+            const float2 z = __ldg(&xv[j]);
+            // x conj(d) = (xr dr + xi di) + i (xi dr - xr di)
+            pr = fmaf(z.x, sr, fmaf(z.y, si, pr));
+            pi = fmaf(z.y, sr, fmaf(-z.x, si, pi));
+            pd = fmaf(sr, sr, fmaf(si, si, pd));
+        }
+        ipr += (double)pr;
+        ipi += (double)pi;
+        dd += (double)pd;
+    }
+    const double mag = sqrt(ipr * ipr + ipi * ipi);
+    double cc = (live && dd > 0.0 && xx > 0.0) ? mag / sqrt(xx * dd) : -1.0;
+    // best by FP64 CC, ties to the smaller index; also the runner-up CC
+    double bc = cc, sc = -2.0;
+    int64_t bi = live ? e : INT64_MAX;
+    int bl = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double oc = __shfl_xor_sync(0xffffffffu, bc, o);
+        const double os = __shfl_xor_sync(0xffffffffu, sc, o);
+        const long long oi = __shfl_xor_sync(0xffffffffu, (long long)bi, o);
+        const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+        const bool take = oc > bc || (oc == bc && oi < bi);
+        const double lose = take ? bc : oc;
+        sc = fmax(fmax(sc, os), lose);
+        if (take) { bc = oc; bi = oi; bl = ol; }
+    }
+    const double wr = __shfl_sync(0xffffffffu, ipr, bl);
+    const double wi = __shfl_sync(0xffffffffu, ipi, bl);
+    const double wd = __shfl_sync(0xffffffffu, dd, bl);
+    const int wa = __shfl_sync(0xffffffffu, a, bl), wb = __shfl_sync(0xffffffffu, b, bl),
+              wc = __shfl_sync(0xffffffffu, c, bl);
+    if (lane == 0) {
+        mrf_result res;
+        if (bi == INT64_MAX || bc < 0.0) {
+            res.index = -1; res.i_t1 = res.i_t2 = res.i_df = -1;
+            res.t1_ms = res.t2_ms = res.df_hz = 0.f;
+            res.cc = 0.f; res.m0 = 0.f; res.phase = 0.f;
+        } else {
+            res.index = bi;
+            res.i_t1 = wa; res.i_t2 = wb; res.i_df = wc;
+            res.t1_ms = g.t1[wa]; res.t2_ms = g.t2[wb]; res.df_hz = g.df[wc];
+            res.cc = (float)bc;
+            res.m0 = wd > 0.0 ? (float)(sqrt(wr * wr + wi * wi) / wd) : 0.f;
+            res.phase = (float)atan2(wi, wr);
+        }
+        res.entries_evaluated = (int32_t)D;
+        res.min_margin = (ncand > 1 && sc > -1.5) ? (float)(bc - sc) : -1.f;
+        (void)cand_cc2;
+        out[v] = res;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// 2D K-major map: rows x ld elements, box = (128 bytes of K) x box_rows, 128-byte swizzle.
+int make_map(CUtensorMap *m, const void *base, int64_t rows, int ld, int elem_bytes, int box_rows)
+{
+    auto enc = get_encode();
+    if (!enc) return set_error(MRF_E_CUDA, "cuTensorMapEncodeTiled unavailable");
+    const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * elem_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(MRF_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return MRF_OK;
+}
+
+int gcd_i(int a, int b) { while (b) { int t = a % b; a = b; b = t; } return a; }
+
+template <int MODE, int K>
+int launch_match_k(mrf_ctx *ctx, const CUtensorMap &mA, const CUtensorMap &mA2, const CUtensorMap &mB,
+                   const CUtensorMap &mB2, const MatchParams &p, cudaStream_t stream)
+{
+    static bool attr_set = false;   // per instantiation, set once under the context mutex
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(match_kernel<MODE, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem_bytes<MODE>());
+        if (e != cudaSuccess) return cuda_fail(e, "matcher shared-memory attribute");
+        attr_set = true;
+    }
+    const int units = p.n_mb * p.n_chunks;
+    const int grid = std::min(units, ctx->sm_count);
+    match_kernel<MODE, K><<<grid, kThreads, smem_bytes<MODE>(), stream>>>(mA, mA2, mB, mB2, p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "matcher launch");
+    return MRF_OK;
+}
+
+template <int MODE>
+int launch_match_mode(mrf_ctx *ctx, int K, const CUtensorMap &mA, const CUtensorMap &mA2, const CUtensorMap &mB,
+                      const CUtensorMap &mB2, const MatchParams &p, cudaStream_t stream)
+{
+    switch (K) {
+    case 1: return launch_match_k<MODE, 1>(ctx, mA, mA2, mB, mB2, p, stream);
+    case 2: return launch_match_k<MODE, 2>(ctx, mA, mA2, mB, mB2, p, stream);
+    case 4: return launch_match_k<MODE, 4>(ctx, mA, mA2, mB, mB2, p, stream);
+    case 8: return launch_match_k<MODE, 8>(ctx, mA, mA2, mB, mB2, p, stream);
+    case 16: return launch_match_k<MODE, 16>(ctx, mA, mA2, mB, mB2, p, stream);
+    case 32: return launch_match_k<MODE, 32>(ctx, mA, mA2, mB, mB2, p, stream);
+    }
+    return set_error(MRF_E_INVALID, "top_k");
+}
+
+}  // namespace
+
+std::mutex g_match_attr_mu;
+
+int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_t precision, int32_t top_k,
+              int rescore, mrf_result *out, int64_t *idx_out, float *cc2_out, cudaStream_t stream)
+{
+    const int mode = precision;
+    const int K = top_k;
+    const int64_t V_pad = (V + 63) / 64 * 64;
+    const int n_mb = (int)(V_pad / 64);
+    const int ebytes = mode == MRF_FP8E4M3 ? 1 : 2;
+    const int n_tiles = (int)((d->entries + BN - 1) / BN);
+    // chunks: make units a multiple of the SM count where possible
+    int n_chunks = ctx->sm_count / gcd_i(n_mb, ctx->sm_count);
+    n_chunks = std::max(1, std::min(n_chunks, n_tiles));
+    const int kbe = mode == MRF_FP8E4M3 ? 128 : 64;    // elements per K block
+    const int k_blocks = (2 * d->n + kbe - 1) / kbe;   // K blocks holding at least one real element
+    const int k_valid = 2 * d->n - (k_blocks - 1) * kbe;  // real elements in the last one (1..kbe)
+    const int kstep = mode == MRF_FP8E4M3 ? 32 : 16;
+    const int last_ksteps = (k_valid + kstep - 1) / kstep;
+
+    // scratch: A operands, row scales, partial lists, candidates
+    auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+    const size_t bA = (size_t)(2 * V_pad) * d->ld * ebytes;
+    const size_t bA2 = mode == MRF_F32 ? bA : 0;
+    const size_t bRS = mode == MRF_FP8E4M3 ? sizeof(float) * V_pad : 0;
+    const size_t bP = sizeof(float2) * (size_t)V * n_chunks * K;
+    const size_t bI = idx_out ? 0 : sizeof(int64_t) * (size_t)V * K;
+    const size_t bC = cc2_out ? 0 : sizeof(float) * (size_t)V * K;
+    const size_t total = al(bA) + al(bA2) + al(bRS) + al(bP) + al(bI) + al(bC);
+    int rc = budget_charge(ctx, total);
+    if (rc) return rc;
+    uint8_t *ws = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&ws, total, stream);
+    if (e != cudaSuccess) { budget_release(ctx, total); return cuda_fail(e, "matcher scratch"); }
+    uint8_t *pA = ws;
+    uint8_t *pA2 = pA + al(bA);
+    float *pRS = (float *)(pA2 + al(bA2));
+    float2 *pP = (float2 *)((uint8_t *)pRS + al(bRS));
+    int64_t *pI = idx_out ? idx_out : (int64_t *)((uint8_t *)pP + al(bP));
+    float *pC = cc2_out ? cc2_out : (float *)((uint8_t *)pP + al(bP) + al(bI));
+
+    auto finish = [&](int code) {
+        cudaFreeAsync(ws, stream);
+        budget_release(ctx, total);
+        return code;
+    };
+
+    // 1. voxel prep
+    if (mode == MRF_F32)
+        voxel_prep_kernel<MRF_F32><<<(unsigned)V_pad, 256, 0, stream>>>((const float2 *)fp, V, d->n, d->ld, pA, pA2, pRS);
+    else if (mode == MRF_BF16)
+        voxel_prep_kernel<MRF_BF16><<<(unsigned)V_pad, 256, 0, stream>>>((const float2 *)fp, V, d->n, d->ld, pA, pA2, pRS);
+    else
+        voxel_prep_kernel<MRF_FP8E4M3><<<(unsigned)V_pad, 256, 0, stream>>>((const float2 *)fp, V, d->n, d->ld, pA, pA2, pRS);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return finish(cuda_fail(e, "voxel prep launch"));
+
+    // 2. tensor-core pass
+    CUtensorMap mA, mA2, mB, mB2;
+    rc = make_map(&mA, pA, 2 * V_pad, d->ld, ebytes, BM);
+    if (!rc) rc = make_map(&mB, d->hi, d->entries, d->ld, ebytes, BN);
+    if (!rc && mode == MRF_F32) rc = make_map(&mA2, pA2, 2 * V_pad, d->ld, ebytes, BM);
+    if (!rc && mode == MRF_F32) rc = make_map(&mB2, d->lo, d->entries, d->ld, ebytes, BN);
+    if (rc) return finish(rc);
+    if (mode != MRF_F32) { mA2 = mA; mB2 = mB; }
+    MatchParams p;
+    p.D = d->entries;
+    p.V = V;
+    p.n_tiles = n_tiles;
+    p.n_mb = n_mb;
+    p.n_chunks = n_chunks;
+    p.k_blocks = k_blocks;
+    p.last_ksteps = last_ksteps;
+    p.colscale = mode == MRF_FP8E4M3 ? d->scale : nullptr;
+    p.part = pP;
+    p.err = ctx->err_flag;
+    {
+        std::lock_guard<std::mutex> lk(g_match_attr_mu);
+        if (mode == MRF_F32) rc = launch_match_mode<MRF_F32>(ctx, K, mA, mA2, mB, mB2, p, stream);
+        else if (mode == MRF_BF16) rc = launch_match_mode<MRF_BF16>(ctx, K, mA, mA2, mB, mB2, p, stream);
+        else rc = launch_match_mode<MRF_FP8E4M3>(ctx, K, mA, mA2, mB, mB2, p, stream);
+    }
+    if (rc) return finish(rc);
+
+    // 3. merge chunk lists
+    const unsigned mblocks = (unsigned)((V + 3) / 4);
+    switch (K) {
+    case 1: merge_kernel<1><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
+    case 2: merge_kernel<2><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
+    case 4: merge_kernel<4><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
+    case 8: merge_kernel<8><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
+    case 16: merge_kernel<16><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
+    case 32: merge_kernel<32><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return finish(cuda_fail(e, "merge launch"));
+
+    // 4. re-score / finalize
+    if (out) {
+        const SeqDev s = d->seq->dev();
+        const GridDev g = d->grid.dev();
+        if (s.xonly)
+            rescore_kernel<true><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, out);
+        else
+            rescore_kernel<false><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, out);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return finish(cuda_fail(e, "re-score launch"));
+    }
+    return finish(MRF_OK);
+}

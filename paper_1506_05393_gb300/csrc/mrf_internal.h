@@ -1,0 +1,136 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the public ABI (include/mrf.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+
+#include "../../include/mrf.h"
+
+// ---------------------------------------------------------------------------
+// Device-side views (plain structs passed by value to kernels)
+
+// Sequence on the device. RF coefficients are in "deficit" form: the state is
+// (Mx, My, W) with W = 1 - Mz (equilibrium M0 = 1), so that the longitudinal
+// relaxation of Eq. A1 becomes W <- E1 W, a product with no cancellation.
+struct SeqDev {
+    int n;
+    int xonly;          // every RF phase is a multiple of pi: R_RF is a rotation about x
+    int symmetric;      // TE_j == TR_j - TE_j for every j (one evolution factor per step)
+    int inversion;
+    float inv_delay;    // ms
+    const float4 *rfx;  // xonly: (c, s, 1 - c, 0) of the x-rotation by beta_j
+    const float *rfg;   // general: 12 floats per j: R00..R22 row-major, 1 - R22, 0, 0
+    const float2 *tau;  // (TE_j, TR_j - TE_j) in ms
+};
+
+struct GridDev {
+    int n_t1, n_t2, n_df;
+    const float *t1;        // n_t1 values, ms
+    const float *t2;        // n_t2 values, ms
+    const float *df;        // n_df values, Hz
+    const int64_t *a_off;   // n_t1 + 1: linear index of the first entry with T1 index a
+    const int32_t *nb;      // n_t1: number of valid T2 indices for T1 index a
+    int64_t count;
+};
+
+// ---------------------------------------------------------------------------
+// Host-side objects behind the opaque ABI handles
+
+struct mrf_seq {
+    int32_t n = 0;
+    int xonly = 0, symmetric = 0, inversion = 0;
+    double inv_delay = 0.0;
+    double min_tr = 0.0;
+    float4 *rfx = nullptr;
+    float *rfg = nullptr;
+    float2 *tau = nullptr;
+    size_t bytes = 0;
+    SeqDev dev() const {
+        SeqDev s;
+        s.n = n; s.xonly = xonly; s.symmetric = symmetric; s.inversion = inversion;
+        s.inv_delay = (float)inv_delay; s.rfx = rfx; s.rfg = rfg; s.tau = tau;
+        return s;
+    }
+};
+
+// Device copy of a grid's axis values and index offsets.
+struct GridBuf {
+    mrf_grid_desc desc{};
+    float *t1 = nullptr, *t2 = nullptr, *df = nullptr;
+    int64_t *a_off = nullptr;
+    int32_t *nb = nullptr;
+    int64_t count = 0;
+    size_t bytes = 0;
+    GridDev dev() const {
+        GridDev g;
+        g.n_t1 = desc.n_t1; g.n_t2 = desc.n_t2; g.n_df = desc.n_df;
+        g.t1 = t1; g.t2 = t2; g.df = df; g.a_off = a_off; g.nb = nb; g.count = count;
+        return g;
+    }
+};
+
+struct mrf_dict {
+    mrf_seq *seq = nullptr;     // private copy of the generating sequence
+    GridBuf grid;
+    int32_t dtype = 0;
+    int64_t entries = 0;
+    int32_t n = 0, ld = 0;
+    void *hi = nullptr;
+    void *lo = nullptr;
+    float *norm = nullptr;
+    float *scale = nullptr;
+    size_t bytes = 0;
+};
+
+struct ServeState;   // serve.cpp
+
+struct mrf_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    size_t budget = 0;
+    std::atomic<size_t> used{0};
+    int *err_flag = nullptr;     // device int: set by kernels whose bounded waits run out
+    std::mutex mu;
+    ServeState *serve = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// Helpers implemented in api.cu
+
+int set_error(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+int budget_charge(mrf_ctx *ctx, size_t bytes);
+void budget_release(mrf_ctx *ctx, size_t bytes);
+int dev_alloc(mrf_ctx *ctx, void **p, size_t bytes, const char *what);
+void dev_free(mrf_ctx *ctx, void *p, size_t bytes);
+int grid_validate(const mrf_grid_desc *g);
+int grid_upload(mrf_ctx *ctx, const mrf_grid_desc *g, GridBuf *out);
+void grid_release(mrf_ctx *ctx, GridBuf *g);
+int seq_clone(mrf_ctx *ctx, const mrf_seq *src, mrf_seq **out);
+void seq_release(mrf_ctx *ctx, mrf_seq *s);
+int check_device_error(mrf_ctx *ctx, cudaStream_t stream);   // synchronises; reads err_flag
+
+// ---------------------------------------------------------------------------
+// Launchers implemented in the kernel translation units
+
+// bloch.cu
+int launch_dict_generate(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream);
+int launch_simulate(mrf_ctx *ctx, const mrf_seq *seq, int64_t count, const float *t1, const float *t2,
+                    const float *df, void *out, cudaStream_t stream);
+
+// match.cu
+int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_t precision, int32_t top_k,
+              int rescore, mrf_result *out, int64_t *idx_out, float *cc2_out, cudaStream_t stream);
+
+// zoom.cu
+int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, const mrf_zoom_opts *opts,
+             const void *fp, int64_t V, mrf_result *out, cudaStream_t stream);
+
+constexpr int kDeviceErrTimeout = 1;
+constexpr int kDeviceErrBounds = 2;

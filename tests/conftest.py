@@ -18,3 +18,36 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def M():
+    import paper_1506_05393_gb300 as M
+    M.lib()
+    return M
+
+
+@pytest.fixture(scope="session")
+def ctx(M):
+    """One library context on cuda:0 for the whole GPU session."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test collected but no CUDA device is visible")
+    torch.cuda.init()
+    c = M.mrf_ctx_create(0, 0)
+    yield c
+    M.mrf_ctx_destroy(c)
+
+
+class DevView:
+    """__cuda_array_interface__ view of a raw device pointer (no copy)."""
+
+    def __init__(self, ptr, nbytes):
+        self.__cuda_array_interface__ = {"shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), True),
+                                         "version": 3, "strides": None}
+
+
+def device_bytes(ptr, nbytes):
+    """A uint8 CUDA tensor aliasing library-owned device memory."""
+    import torch
+    return torch.as_tensor(DevView(ptr, nbytes), device="cuda")

@@ -1,0 +1,26 @@
+"""Shared test inputs: seeded phantoms whose clean signals come from the FP64 oracle."""
+import numpy as np
+
+import mrf_synth as S
+
+
+def ongrid_voxels(orc, seq, grid, v, snr, seed):
+    """Voxels on random valid grid points (M0, phase, noise from mrf_synth)."""
+    ph = S.phantom_ongrid(seed, v, grid)
+    clean = orc.simulate(seq, ph["t1"], ph["t2"], ph["df"])
+    g_re, g_im = S.noise_draws(seed, v, seq.n)
+    return ph, S.compose_voxels(clean, ph["m0"], ph["phase"], g_re, g_im, snr)
+
+
+def offgrid_voxels(orc, seq, v, snr, seed, **ranges):
+    """Off-grid voxels: log-uniform T1/T2 (T2 < T1), uniform df (mrf_synth recipe)."""
+    ph = S.phantom_offgrid(seed, v, **ranges)
+    clean = orc.simulate(seq, ph["t1"], ph["t2"], ph["df"])
+    g_re, g_im = S.noise_draws(seed, v, seq.n)
+    return ph, S.compose_voxels(clean, ph["m0"], ph["phase"], g_re, g_im, snr)
+
+
+def rel_l2(a, b, axis=-1):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.linalg.norm(a - b, axis=axis) / np.linalg.norm(b, axis=axis)

@@ -1,0 +1,131 @@
+"""GPU Bloch simulation and dictionary generation against the FP64 oracle
+(Appendix, Eq. A2). Fingerprints must agree within 1e-5 relative L2."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import mrf_synth as S
+from conftest import device_bytes
+from helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_simulate(M, ctx, seq, t1, t2, df):
+    h = M.mrf_sequence_load(ctx, seq)
+    try:
+        T1 = torch.tensor(t1, dtype=torch.float32, device="cuda")
+        T2 = torch.tensor(t2, dtype=torch.float32, device="cuda")
+        DF = torch.tensor(df, dtype=torch.float32, device="cuda")
+        out = torch.empty((len(t1), seq.n), dtype=torch.complex64, device="cuda")
+        M.mrf_simulate(ctx, h, T1, T2, DF, out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+    finally:
+        M.mrf_sequence_free(ctx, h)
+
+
+def _random_params(seed, count):
+    p = S.phantom_offgrid(seed, count, t1_range=(100.0, 4000.0), t2_range=(10.0, 400.0), df_range=(-40.0, 40.0))
+    return p["t1"], p["t2"], p["df"]
+
+
+@pytest.mark.parametrize("n", [1000, 200, 201])
+def test_simulate_matches_oracle(M, ctx, oracle_lib, n):
+    seq = S.sequence(1, n)
+    t1, t2, df = _random_params(30 + n, 384)
+    gpu = _gpu_simulate(M, ctx, seq, t1, t2, df)
+    ref = oracle_lib.simulate(seq, t1, t2, df)
+    err = rel_l2(gpu, ref)
+    assert err.max() < 1e-5, f"max rel L2 {err.max():.3g}"
+
+
+def test_simulate_general_rf_phase_and_asymmetric_te(M, ctx, oracle_lib):
+    base = S.sequence(5, 300)
+    rng = np.random.default_rng(77)
+    seq = S.Sequence(base.flip_rad, rng.uniform(0, 2 * math.pi, 300), base.tr_ms, base.tr_ms * 0.3, 1, 15.0)
+    t1, t2, df = _random_params(41, 256)
+    err = rel_l2(_gpu_simulate(M, ctx, seq, t1, t2, df), oracle_lib.simulate(seq, t1, t2, df))
+    assert err.max() < 1e-5, f"max rel L2 {err.max():.3g}"
+
+
+def test_simulate_without_inversion(M, ctx, oracle_lib):
+    base = S.sequence(6, 256)
+    seq = S.Sequence(base.flip_rad, base.rf_phase_rad, base.tr_ms, base.te_ms, 0, 0.0)
+    t1, t2, df = _random_params(42, 128)
+    err = rel_l2(_gpu_simulate(M, ctx, seq, t1, t2, df), oracle_lib.simulate(seq, t1, t2, df))
+    assert err.max() < 1e-5
+
+
+def _dict_rows(M, d, dtype):
+    info = M.mrf_dict_query(d)
+    D, ld = info.entries, info.ld
+    eb = 1 if dtype == M.MRF_FP8E4M3 else 2
+    hi = device_bytes(info.hi_dev, D * ld * eb).cpu().numpy()
+    norm = device_bytes(info.norm_dev, 4 * D).cpu().numpy().view(np.float32)
+    if dtype == M.MRF_FP8E4M3:
+        q = torch.from_numpy(hi).view(torch.float8_e4m3fn).float().numpy().reshape(D, ld)
+        sc = device_bytes(info.scale_dev, 4 * D).cpu().numpy().view(np.float32)
+        vals = q * sc[:, None]
+    else:
+        vals = torch.from_numpy(hi).view(torch.bfloat16).float().numpy().reshape(D, ld).astype(np.float64)
+        if dtype == M.MRF_F32:
+            lo = device_bytes(info.lo_dev, D * ld * 2).cpu()
+            vals = vals + lo.view(torch.bfloat16).float().numpy().reshape(D, ld)
+    n = info.n
+    return vals[:, 0:2 * n:2] + 1j * vals[:, 1:2 * n:2], vals[:, 2 * n:], norm, info
+
+
+@pytest.mark.parametrize("dtype,tol", [(0, 1e-5), (1, 3e-3), (2, 7e-2)])
+def test_dictionary_tiny_matches_oracle(M, ctx, oracle_lib, dtype, tol):
+    seq = S.sequence(0, 200)
+    g = S.GRIDS["tiny"]
+    h = M.mrf_sequence_load(ctx, seq)
+    d = M.mrf_dict_generate(ctx, h, g, dtype)
+    torch.cuda.synchronize()
+    try:
+        rows, pad, norm, info = _dict_rows(M, d, dtype)
+        assert info.entries == 193 and info.ld == 512
+        a, b, c = oracle_lib.grid_params(g)
+        t1, t2, df = S.grid_values(g)
+        ref = oracle_lib.simulate(seq, t1[a], t2[b], df[c])
+        refn = ref / np.linalg.norm(ref, axis=1, keepdims=True)
+        err = rel_l2(rows, refn)
+        assert err.max() < tol, f"dtype {dtype}: max rel L2 {err.max():.3g}"
+        np.testing.assert_allclose(norm, np.linalg.norm(ref, axis=1), rtol=1e-5)
+        assert np.all(pad == 0)
+    finally:
+        M.mrf_dict_free(ctx, d)
+        M.mrf_sequence_free(ctx, h)
+
+
+def test_dictionary_full_size_sampled(M, ctx, oracle_lib):
+    """The 614,508-entry FP32-equivalent dictionary at N = 1000: sampled rows."""
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["fp32_brute"]
+    h = M.mrf_sequence_load(ctx, seq)
+    d = M.mrf_dict_generate(ctx, h, g, M.MRF_F32)
+    torch.cuda.synchronize()
+    try:
+        info = M.mrf_dict_query(d)
+        D, ld = info.entries, info.ld
+        assert D == 614508 and ld == 2048
+        rng = np.random.default_rng(3)
+        idx = np.unique(np.concatenate([rng.integers(0, D, 250), [0, D - 1]]))
+        hi = device_bytes(info.hi_dev, D * ld * 2).view(torch.bfloat16).view(D, ld)
+        lo = device_bytes(info.lo_dev, D * ld * 2).view(torch.bfloat16).view(D, ld)
+        it = torch.from_numpy(idx).cuda()
+        vals = (hi[it].double() + lo[it].double()).cpu().numpy()
+        rows = vals[:, 0:2000:2] + 1j * vals[:, 1:2000:2]
+        params = [M.mrf_grid_unravel(g, int(i)) for i in idx]
+        t1, t2, df = S.grid_values(g)
+        ref = oracle_lib.simulate(seq, t1[[p[0] for p in params]], t2[[p[1] for p in params]], df[[p[2] for p in params]])
+        refn = ref / np.linalg.norm(ref, axis=1, keepdims=True)
+        err = rel_l2(rows, refn)
+        assert err.max() < 1e-5, f"max rel L2 {err.max():.3g}"
+        assert torch.count_nonzero(hi[it][:, 2000:]).item() == 0
+    finally:
+        M.mrf_dict_free(ctx, d)
+        M.mrf_sequence_free(ctx, h)

@@ -1,0 +1,172 @@
+"""GPU brute-force DGS (tensor-core matcher + re-score) against the FP64
+oracle's brute force (Theory: argmax of Eq. 1 over every grid entry).
+
+Bar: CC within 1e-5 absolute; matched index identical except where the
+oracle's top-two CC gap is below 1e-6 (those are counted and reported)."""
+import numpy as np
+import pytest
+import torch
+
+import mrf_synth as S
+from helpers import offgrid_voxels, ongrid_voxels
+
+pytestmark = pytest.mark.gpu
+
+GAP_EXCUSE = 1e-6
+CC_TOL = 1e-5
+
+
+def _run(M, ctx, d, x, precision, top_k, rescore):
+    fp = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+    out = M.empty_results(x.shape[0])
+    M.mrf_match_bruteforce(ctx, d, fp, M.match_opts(precision, top_k, rescore), out)
+    M.mrf_stream_sync(ctx)
+    return M.results_to_numpy(out)[: x.shape[0]]
+
+
+def _topk(M, ctx, d, x, precision, k):
+    fp = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+    idx = torch.empty((x.shape[0], k), dtype=torch.int64, device="cuda")
+    cc2 = torch.empty((x.shape[0], k), dtype=torch.float32, device="cuda")
+    M.mrf_match_topk(ctx, d, fp, precision, k, idx, cc2)
+    M.mrf_stream_sync(ctx)
+    return idx.cpu().numpy(), cc2.cpu().numpy()
+
+
+def _compare(res, ref, label):
+    gap = ref["cc"][:, 0] - ref["cc"][:, 1]
+    same = res["index"] == ref["idx"][:, 0]
+    excused = gap < GAP_EXCUSE
+    bad = ~same & ~excused
+    assert not bad.any(), (f"{label}: {bad.sum()} voxels differ with gap >= {GAP_EXCUSE}: "
+                           f"gpu {res['index'][bad][:5]} oracle {ref['idx'][bad, 0][:5]} gap {gap[bad][:5]}")
+    ok = same
+    assert np.abs(res["cc"][ok] - ref["cc"][ok, 0]).max() < CC_TOL
+    return int((~same).sum()), int(excused.sum())
+
+
+@pytest.fixture(scope="module")
+def tiny(M, ctx, oracle_lib):
+    seq = S.sequence(0, 200)
+    g = S.GRIDS["tiny"]
+    h = M.mrf_sequence_load(ctx, seq)
+    dicts = {dt: M.mrf_dict_generate(ctx, h, g, dt) for dt in (M.MRF_F32, M.MRF_BF16, M.MRF_FP8E4M3)}
+    ph, x = ongrid_voxels(oracle_lib, seq, g, 256, 30.0, 100)
+    ref = oracle_lib.bruteforce(seq, g, x, k=8)
+    yield dict(seq=seq, grid=g, h=h, dicts=dicts, x=x, ph=ph, ref=ref)
+    for d in dicts.values():
+        M.mrf_dict_free(ctx, d)
+    M.mrf_sequence_free(ctx, h)
+
+
+@pytest.fixture(scope="module")
+def ragged(M, ctx, oracle_lib):
+    """Several 256-entry tiles with a ragged tail, and V not a multiple of 64."""
+    seq = S.sequence(2, 200)
+    g = S.Grid(150.0, 45.0, 37, 12.0, 9.0, 33, -12.0, 3.0, 9)
+    h = M.mrf_sequence_load(ctx, seq)
+    dicts = {dt: M.mrf_dict_generate(ctx, h, g, dt) for dt in (M.MRF_F32, M.MRF_BF16, M.MRF_FP8E4M3)}
+    ph, x = offgrid_voxels(oracle_lib, seq, 150, 25.0, 7, t1_range=(200.0, 1700.0), t2_range=(15.0, 300.0),
+                           df_range=(-11.0, 11.0))
+    ref = oracle_lib.bruteforce(seq, g, x, k=8)
+    yield dict(seq=seq, grid=g, h=h, dicts=dicts, x=x, ph=ph, ref=ref, D=oracle_lib.grid_count(g))
+    for d in dicts.values():
+        M.mrf_dict_free(ctx, d)
+    M.mrf_sequence_free(ctx, h)
+
+
+def test_tiny_fp32_recovers_on_grid_voxels(M, ctx, tiny):
+    res = _run(M, ctx, tiny["dicts"][M.MRF_F32], tiny["x"], M.MRF_F32, 4, 1)
+    _compare(res, tiny["ref"], "tiny fp32")
+    np.testing.assert_allclose(res["m0"], tiny["ref"]["m0"], rtol=1e-4)
+    dphi = np.angle(np.exp(1j * (res["phase"] - tiny["ref"]["phase"])))
+    assert np.abs(dphi).max() < 1e-4
+    assert (res["entries_evaluated"] == 193).all()
+
+
+def test_tiny_topk_lists(M, ctx, tiny):
+    idx, cc2 = _topk(M, ctx, tiny["dicts"][M.MRF_F32], tiny["x"], M.MRF_F32, 8)
+    ref = tiny["ref"]
+    np.testing.assert_allclose(np.sqrt(np.maximum(cc2, 0)), ref["cc"], atol=1e-5)
+    # where consecutive oracle CCs are well separated, the order must agree
+    sep = np.diff(ref["cc"], axis=1) < -1e-5
+    for v in range(idx.shape[0]):
+        for q in range(7):
+            if sep[v, : q + 1].all():
+                assert idx[v, q] == ref["idx"][v, q]
+
+
+@pytest.mark.parametrize("precision,top_k", [(0, 1), (0, 4), (1, 8), (1, 32), (2, 32)])
+def test_ragged_all_precisions(M, ctx, ragged, precision, top_k):
+    res = _run(M, ctx, ragged["dicts"][precision], ragged["x"], precision, top_k, 1)
+    diff, exc = _compare(res, ragged["ref"], f"ragged p{precision} k{top_k}")
+    assert (res["entries_evaluated"] == ragged["D"]).all()
+    print(f"ragged precision={precision} k={top_k}: differ={diff} excused={exc}")
+
+
+def test_ragged_no_rescore_keeps_tensor_core_rank1(M, ctx, ragged):
+    idx, _ = _topk(M, ctx, ragged["dicts"][M.MRF_BF16], ragged["x"], M.MRF_BF16, 1)
+    res = _run(M, ctx, ragged["dicts"][M.MRF_BF16], ragged["x"], M.MRF_BF16, 1, 0)
+    assert (res["index"] == idx[:, 0]).all()
+
+
+def test_topk_larger_than_dictionary(M, ctx, oracle_lib):
+    seq = S.sequence(3, 64)
+    g = S.Grid(300.0, 100.0, 4, 20.0, 40.0, 3, 0.0, 1.0, 1)   # 12 entries
+    h = M.mrf_sequence_load(ctx, seq)
+    d = M.mrf_dict_generate(ctx, h, g, M.MRF_F32)
+    try:
+        ph, x = offgrid_voxels(oracle_lib, seq, 5, 30.0, 9, t1_range=(300.0, 600.0), t2_range=(20.0, 100.0),
+                               df_range=(-0.1, 0.1))
+        idx, cc2 = _topk(M, ctx, d, x, M.MRF_F32, 32)
+        assert (idx[:, 12:] == -1).all() and (idx[:, :12] >= 0).all()
+        assert sorted(idx[0, :12].tolist()) == list(range(12))
+        res = _run(M, ctx, d, x, M.MRF_F32, 32, 1)
+        ref = oracle_lib.bruteforce(seq, g, x, k=2)
+        assert (res["index"] == ref["idx"][:, 0]).all()
+    finally:
+        M.mrf_dict_free(ctx, d)
+        M.mrf_sequence_free(ctx, h)
+
+
+def test_empty_and_invalid_calls(M, ctx, tiny):
+    d = tiny["dicts"][M.MRF_F32]
+    out = M.empty_results(1)
+    L = M.lib()
+    import ctypes as C
+    o = M.match_opts(M.MRF_F32, 4, 1)
+    assert L.mrf_match_bruteforce(ctx, d, None, 0, C.byref(o), None, None) == M.MRF_OK
+    bad = M.match_opts(M.MRF_BF16, 4, 1)
+    fp = torch.zeros((1, 200), dtype=torch.complex64, device="cuda")
+    assert L.mrf_match_bruteforce(ctx, d, C.c_void_p(fp.data_ptr()), 1, C.byref(bad), C.c_void_p(out.data_ptr()), None) == M.MRF_E_INVALID
+    bad = M.match_opts(M.MRF_F32, 3, 1)
+    assert L.mrf_match_bruteforce(ctx, d, C.c_void_p(fp.data_ptr()), 1, C.byref(bad), C.c_void_p(out.data_ptr()), None) == M.MRF_E_INVALID
+
+
+def test_zero_voxel_gives_no_match(M, ctx, tiny):
+    x = np.zeros((3, 200), np.complex128)
+    x[1] = tiny["x"][0]
+    res = _run(M, ctx, tiny["dicts"][M.MRF_F32], x, M.MRF_F32, 4, 1)
+    assert res["index"][0] == -1 and res["index"][2] == -1
+    assert res["index"][1] == tiny["ref"]["idx"][0, 0]
+
+
+def test_full_size_fp32_sampled(M, ctx, oracle_lib):
+    """64x64 slice, N = 1000, 614,508 entries (the benchmark workload): all
+    4096 voxels matched on the GPU, 12 sampled voxels checked against the
+    oracle's exhaustive search."""
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["fp32_brute"]
+    ph, x = offgrid_voxels(oracle_lib, seq, 4096, 20.0, 101)
+    h = M.mrf_sequence_load(ctx, seq)
+    d = M.mrf_dict_generate(ctx, h, g, M.MRF_F32)
+    try:
+        res = _run(M, ctx, d, x, M.MRF_F32, 4, 1)
+        pick = np.random.default_rng(5).choice(4096, 12, replace=False)
+        ref = oracle_lib.bruteforce(seq, g, x[pick], k=2)
+        diff, exc = _compare(res[pick], ref, "full fp32")
+        print(f"full-size fp32: differ={diff} excused={exc} of 12")
+        assert (res["index"] >= 0).all()
+    finally:
+        M.mrf_dict_free(ctx, d)
+        M.mrf_sequence_free(ctx, h)
