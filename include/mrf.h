@@ -87,6 +87,21 @@ int mrf_ctx_memory(const mrf_ctx *ctx, size_t *used_bytes, size_t *budget_bytes)
  * usable). Asynchronous entry points report such failures only here. */
 int mrf_stream_sync(mrf_ctx *ctx, void *stream);
 
+/* Kernel accounting (no counterpart in the paper; used to measure the
+ * kernels against their rooflines). Launch counts are always kept. With
+ * profiling enabled, CUDA events are recorded on the launching stream around
+ * the dictionary-generation, matcher and ZOOM kernels, and their durations
+ * accumulate into the *_ms fields. */
+typedef struct {
+    uint64_t launches;            /* every kernel this context launched */
+    uint64_t dictgen_launches, matcher_launches, zoom_launches;
+    double dictgen_ms, matcher_ms, zoom_ms;   /* event-timed launches only */
+    uint64_t dictgen_timed, matcher_timed, zoom_timed;
+} mrf_profile;
+int mrf_profile_enable(mrf_ctx *ctx, int on);
+/* Synchronises on pending profile events. reset != 0 zeroes all counters. */
+int mrf_profile_read(mrf_ctx *ctx, mrf_profile *out, int reset);
+
 /* ------------------------------------------------------------------------ */
 /* Sequence (Methods: IR-bSSFP train; Appendix: hard RF pulse)              */
 

@@ -92,6 +92,13 @@ class ServeStats(C.Structure):
                 ("request_bytes_in_use", C.c_size_t), ("request_bytes_peak", C.c_size_t)]
 
 
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("dictgen_launches", C.c_uint64), ("matcher_launches", C.c_uint64),
+                ("zoom_launches", C.c_uint64), ("dictgen_ms", C.c_double), ("matcher_ms", C.c_double),
+                ("zoom_ms", C.c_double), ("dictgen_timed", C.c_uint64), ("matcher_timed", C.c_uint64),
+                ("zoom_timed", C.c_uint64)]
+
+
 # one mrf_result (56 bytes, 8-byte aligned)
 RESULT_DTYPE = np.dtype([("index", "<i8"), ("i_t1", "<i4"), ("i_t2", "<i4"), ("i_df", "<i4"),
                          ("t1_ms", "<f4"), ("t2_ms", "<f4"), ("df_hz", "<f4"), ("cc", "<f4"), ("m0", "<f4"),
@@ -106,7 +113,7 @@ EXPORTS = [
     "mrf_sequence_load", "mrf_sequence_free", "mrf_grid_count", "mrf_grid_unravel", "mrf_simulate",
     "mrf_dict_generate", "mrf_dict_free", "mrf_dict_query", "mrf_match_bruteforce", "mrf_match_topk",
     "mrf_zoom_opts_default", "mrf_zoom_search", "mrf_serve_start", "mrf_serve_submit", "mrf_serve_poll",
-    "mrf_serve_cancel", "mrf_serve_get_stats", "mrf_serve_stop",
+    "mrf_serve_cancel", "mrf_serve_get_stats", "mrf_serve_stop", "mrf_profile_enable", "mrf_profile_read",
 ]
 
 
@@ -150,6 +157,8 @@ def lib():
         L.mrf_serve_cancel.argtypes = [vp, C.c_uint64]
         L.mrf_serve_get_stats.argtypes = [vp, C.POINTER(ServeStats)]
         L.mrf_serve_stop.argtypes = [vp]
+        L.mrf_profile_enable.argtypes = [vp, C.c_int]
+        L.mrf_profile_read.argtypes = [vp, C.POINTER(Profile), C.c_int]
         _lib = L
     return _lib
 
@@ -325,6 +334,16 @@ def mrf_serve_get_stats(ctx) -> ServeStats:
 
 def mrf_serve_stop(ctx) -> None:
     check(lib().mrf_serve_stop(ctx), "mrf_serve_stop")
+
+
+def mrf_profile_enable(ctx, on: bool = True) -> None:
+    check(lib().mrf_profile_enable(ctx, 1 if on else 0), "mrf_profile_enable")
+
+
+def mrf_profile_read(ctx, reset: bool = False) -> Profile:
+    p = Profile()
+    check(lib().mrf_profile_read(ctx, C.byref(p), 1 if reset else 0), "mrf_profile_read")
+    return p
 
 
 # ----------------------------------------------------------------------------- helpers

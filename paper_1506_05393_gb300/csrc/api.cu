@@ -153,6 +153,73 @@ extern "C" int mrf_stream_sync(mrf_ctx *ctx, void *stream)
 }
 
 // ---------------------------------------------------------------------------
+// kernel accounting
+
+ProfScope::ProfScope(mrf_ctx *c, int k, cudaStream_t s) : ctx(c), kind(k), stream(s)
+{
+    ctx->kind_launches[kind].fetch_add(1);
+    ctx->launches.fetch_add(1);
+    if (ctx->profiling.load()) {
+        if (cudaEventCreate(&start) == cudaSuccess) cudaEventRecord(start, stream);
+        else start = nullptr;
+    }
+}
+
+ProfScope::~ProfScope()
+{
+    if (!start) return;
+    cudaEvent_t stop;
+    if (cudaEventCreate(&stop) != cudaSuccess) { cudaEventDestroy(start); return; }
+    cudaEventRecord(stop, stream);
+    std::lock_guard<std::mutex> lk(ctx->prof_mu);
+    ctx->prof_pending.push_back(ProfEvent{kind, start, stop});
+}
+
+extern "C" int mrf_profile_enable(mrf_ctx *ctx, int on)
+{
+    if (!ctx) return set_error(MRF_E_INVALID, "ctx is NULL");
+    ctx->profiling.store(on != 0);
+    return MRF_OK;
+}
+
+extern "C" int mrf_profile_read(mrf_ctx *ctx, mrf_profile *out, int reset)
+{
+    if (!ctx || !out) return set_error(MRF_E_INVALID, "NULL argument");
+    cudaSetDevice(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->prof_mu);
+    for (auto &ev : ctx->prof_pending) {
+        cudaEventSynchronize(ev.stop);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev.start, ev.stop) == cudaSuccess) {
+            ctx->prof_ms[ev.kind] += ms;
+            ctx->prof_timed[ev.kind] += 1;
+        }
+        cudaEventDestroy(ev.start);
+        cudaEventDestroy(ev.stop);
+    }
+    ctx->prof_pending.clear();
+    out->launches = ctx->launches.load();
+    out->dictgen_launches = ctx->kind_launches[kProfDictGen].load();
+    out->matcher_launches = ctx->kind_launches[kProfMatcher].load();
+    out->zoom_launches = ctx->kind_launches[kProfZoom].load();
+    out->dictgen_ms = ctx->prof_ms[kProfDictGen];
+    out->matcher_ms = ctx->prof_ms[kProfMatcher];
+    out->zoom_ms = ctx->prof_ms[kProfZoom];
+    out->dictgen_timed = ctx->prof_timed[kProfDictGen];
+    out->matcher_timed = ctx->prof_timed[kProfMatcher];
+    out->zoom_timed = ctx->prof_timed[kProfZoom];
+    if (reset) {
+        ctx->launches = 0;
+        for (int k = 0; k < kProfKinds; ++k) {
+            ctx->kind_launches[k] = 0;
+            ctx->prof_ms[k] = 0;
+            ctx->prof_timed[k] = 0;
+        }
+    }
+    return MRF_OK;
+}
+
+// ---------------------------------------------------------------------------
 // sequence
 
 static bool is_fin(double v) { return isfinite(v) != 0; }
@@ -343,6 +410,50 @@ int grid_upload(mrf_ctx *ctx, const mrf_grid_desc *g, GridBuf *out)
     if (e == cudaSuccess) e = cudaMemcpy(gb.nb, nb.data(), bnb, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { grid_release(ctx, &gb); return cuda_fail(e, "grid upload"); }
     *out = gb;
+    return MRF_OK;
+}
+
+int grid_upload_async(mrf_ctx *ctx, const mrf_grid_desc *g, cudaStream_t stream, GridDev *out, void **block,
+                      size_t *bytes)
+{
+    int rc = grid_validate(g);
+    if (rc) return rc;
+    const size_t nt1 = g->n_t1, nt2 = g->n_t2, ndf = g->n_df;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_t2 = al(4 * nt1), o_df = o_t2 + al(4 * nt2), o_ao = o_df + al(4 * ndf);
+    const size_t o_nb = o_ao + al(8 * (nt1 + 1)), total = o_nb + al(4 * nt1);
+    std::vector<uint8_t> h(total, 0);
+    float *t1 = (float *)h.data(), *t2 = (float *)(h.data() + o_t2), *df = (float *)(h.data() + o_df);
+    int64_t *ao = (int64_t *)(h.data() + o_ao);
+    int32_t *nb = (int32_t *)(h.data() + o_nb);
+    for (int a = 0; a < g->n_t1; ++a) t1[a] = (float)t1v(g, a);
+    for (int b = 0; b < g->n_t2; ++b) t2[b] = (float)t2v(g, b);
+    for (int c = 0; c < g->n_df; ++c) df[c] = (float)(g->df_min + (double)c * g->df_step);
+    ao[0] = 0;
+    for (int a = 0; a < g->n_t1; ++a) {
+        nb[a] = nb_valid(g, a);
+        ao[a + 1] = ao[a] + (int64_t)nb[a] * g->n_df;
+    }
+    rc = budget_charge(ctx, total);
+    if (rc) return rc;
+    uint8_t *d = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d, total, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), total, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) {
+        if (d) cudaFreeAsync(d, stream);
+        budget_release(ctx, total);
+        return cuda_fail(e, "grid upload");
+    }
+    out->n_t1 = g->n_t1; out->n_t2 = g->n_t2; out->n_df = g->n_df;
+    out->t1 = (const float *)d;
+    out->t2 = (const float *)(d + o_t2);
+    out->df = (const float *)(d + o_df);
+    out->a_off = (const int64_t *)(d + o_ao);
+    out->nb = (const int32_t *)(d + o_nb);
+    out->count = ao[g->n_t1];
+    *block = d;
+    *bytes = total;
+    // pageable source: cudaMemcpyAsync has staged it before returning, so h may go
     return MRF_OK;
 }
 

@@ -321,10 +321,13 @@ int launch_dict_generate(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream)
     float4 *cis = (float4 *)(tab + al(b1) + al(b2));
     float *e1i = (float *)(tab + al(b1) + al(b2) + al(b3));
     tables_kernel<<<4 * ctx->sm_count, 256, 0, stream>>>(s, g, e1, e2, cis, e1i);
+    count_launch(ctx);
     Tables t{e1, e2, cis, e1i};
     const int64_t blocks = (d->entries + kGenThreads - 1) / kGenThreads;
     uint8_t *hi = (uint8_t *)d->hi, *lo = (uint8_t *)d->lo;
 #define MRF_GEN(OUT, XO) dict_gen_kernel<OUT, XO><<<(unsigned)blocks, kGenThreads, 0, stream>>>(s, g, t, d->entries, d->ld, hi, lo, d->norm, d->scale)
+    {
+    ProfScope prof(ctx, kProfDictGen, stream);
     if (s.xonly) {
         if (d->dtype == MRF_F32) MRF_GEN(MRF_F32, true);
         else if (d->dtype == MRF_BF16) MRF_GEN(MRF_BF16, true);
@@ -333,6 +336,7 @@ int launch_dict_generate(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream)
         if (d->dtype == MRF_F32) MRF_GEN(MRF_F32, false);
         else if (d->dtype == MRF_BF16) MRF_GEN(MRF_BF16, false);
         else MRF_GEN(MRF_FP8E4M3, false);
+    }
     }
 #undef MRF_GEN
     e = cudaGetLastError();
@@ -345,7 +349,7 @@ int launch_dict_generate(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream)
 int launch_simulate(mrf_ctx *ctx, const mrf_seq *seq, int64_t count, const float *t1, const float *t2,
                     const float *df, void *out, cudaStream_t stream)
 {
-    (void)ctx;
+    count_launch(ctx);
     const SeqDev s = seq->dev();
     const int64_t blocks = (count + 127) / 128;
     const int staged = (s.n % 2 == 0) && (reinterpret_cast<uintptr_t>(out) % 16 == 0);

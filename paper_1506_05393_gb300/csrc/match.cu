@@ -304,12 +304,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) mbar_arrive(&tempty_bar[acc]);
                 if (++acc == 2) { acc = 0; acc_ph ^= 1; }
             }
-            // merge the Re/Im pair's lists (each covered half of the columns)
+            // merge the Re/Im pair's lists (each covered half of the columns):
+            // only the even lane inserts, so the odd lane's list stays intact
+            // while it is being read
 #pragma unroll
             for (int q = 0; q < K; ++q) {
                 const float ov = __shfl_xor_sync(0xffffffffu, tk.v[q], 1);
                 const int oi = __shfl_xor_sync(0xffffffffu, tk.i[q], 1);
-                tk.insert(ov, oi);
+                if (par == 0) tk.insert(ov, oi);
             }
             const int64_t v = (int64_t)mb * (BM / 2) + (row >> 1);
             if (par == 0 && v < p.V) {
@@ -417,7 +419,7 @@ __global__ void merge_kernel(const float2 *part, int64_t V, int n_chunks, const 
             const float c = e.x;
             const int i = __float_as_int(e.y);
             if (i == 0x7fffffff) continue;
-            if (!before(c, i, last_c, last_i) && before(c, i, bc, bi)) { bc = c; bi = i; }
+            if (before(last_c, last_i, c, i) && before(c, i, bc, bi)) { bc = c; bi = i; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -587,6 +589,7 @@ int launch_match_k(mrf_ctx *ctx, const CUtensorMap &mA, const CUtensorMap &mA2, 
     }
     const int units = p.n_mb * p.n_chunks;
     const int grid = std::min(units, ctx->sm_count);
+    ProfScope prof(ctx, kProfMatcher, stream);
     match_kernel<MODE, K><<<grid, kThreads, smem_bytes<MODE>(), stream>>>(mA, mA2, mB, mB2, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "matcher launch");
@@ -664,6 +667,7 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
         voxel_prep_kernel<MRF_BF16><<<(unsigned)V_pad, 256, 0, stream>>>((const float2 *)fp, V, d->n, d->ld, pA, pA2, pRS);
     else
         voxel_prep_kernel<MRF_FP8E4M3><<<(unsigned)V_pad, 256, 0, stream>>>((const float2 *)fp, V, d->n, d->ld, pA, pA2, pRS);
+    count_launch(ctx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return finish(cuda_fail(e, "voxel prep launch"));
 
@@ -704,6 +708,7 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     case 16: merge_kernel<16><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
     case 32: merge_kernel<32><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
     }
+    count_launch(ctx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return finish(cuda_fail(e, "merge launch"));
 
@@ -715,6 +720,7 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
             rescore_kernel<true><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, out);
         else
             rescore_kernel<false><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, out);
+        count_launch(ctx);
         e = cudaGetLastError();
         if (e != cudaSuccess) return finish(cuda_fail(e, "re-score launch"));
     }

@@ -8,6 +8,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/mrf.h"
 
@@ -89,6 +90,13 @@ struct mrf_dict {
 
 struct ServeState;   // serve.cpp
 
+enum ProfKind { kProfDictGen = 0, kProfMatcher = 1, kProfZoom = 2, kProfKinds = 3 };
+
+struct ProfEvent {
+    int kind;
+    cudaEvent_t start, stop;
+};
+
 struct mrf_ctx {
     int device = 0;
     int sm_count = 0;
@@ -98,7 +106,27 @@ struct mrf_ctx {
     int *err_flag = nullptr;     // device int: set by kernels whose bounded waits run out
     std::mutex mu;
     ServeState *serve = nullptr;
+    // kernel accounting
+    std::atomic<uint64_t> launches{0};
+    std::atomic<uint64_t> kind_launches[kProfKinds];
+    std::atomic<bool> profiling{false};
+    std::mutex prof_mu;
+    std::vector<ProfEvent> prof_pending;
+    double prof_ms[kProfKinds] = {0, 0, 0};
+    uint64_t prof_timed[kProfKinds] = {0, 0, 0};
+    mrf_ctx() { for (auto &k : kind_launches) k = 0; }
 };
+
+// Profiling hooks around a main kernel launch (no-ops unless enabled).
+struct ProfScope {
+    mrf_ctx *ctx;
+    int kind;
+    cudaStream_t stream;
+    cudaEvent_t start = nullptr;
+    ProfScope(mrf_ctx *c, int k, cudaStream_t s);
+    ~ProfScope();
+};
+inline void count_launch(mrf_ctx *ctx, int n = 1) { ctx->launches.fetch_add((uint64_t)n); }
 
 // ---------------------------------------------------------------------------
 // Helpers implemented in api.cu
@@ -112,6 +140,9 @@ void dev_free(mrf_ctx *ctx, void *p, size_t bytes);
 int grid_validate(const mrf_grid_desc *g);
 int grid_upload(mrf_ctx *ctx, const mrf_grid_desc *g, GridBuf *out);
 void grid_release(mrf_ctx *ctx, GridBuf *g);
+// stream-ordered upload into one pool block; free with cudaFreeAsync + budget_release
+int grid_upload_async(mrf_ctx *ctx, const mrf_grid_desc *g, cudaStream_t stream, GridDev *out, void **block,
+                      size_t *bytes);
 int seq_clone(mrf_ctx *ctx, const mrf_seq *src, mrf_seq **out);
 void seq_release(mrf_ctx *ctx, mrf_seq *s);
 int check_device_error(mrf_ctx *ctx, cudaStream_t stream);   // synchronises; reads err_flag

@@ -1,9 +1,448 @@
-// MRF-ZOOM kernel (placeholder until the persistent search kernel lands).
+// MRF-ZOOM (Theory: df search steps 1-4, 1D ZOOM of Fig. 1, 2D ZOOM of
+// Fig. 2; Methods, Experiment 2 steps 1-5), every candidate simulated on the
+// fly -- no dictionary.
+//
+// One warp per voxel; warps pull voxels from an atomic work counter
+// (persistent kernel, a few warps per SM). Each move or scan evaluates its
+// candidate set with one candidate per lane: the lane runs the FP32 Bloch
+// recurrence for its (T1, T2, df) and accumulates <x, d> and ||d||^2 in
+// 16-timepoint FP32 blocks with compensated (Kahan) block sums. The decision
+// (best candidate, ties to the earliest in the canonical scan order; move
+// only when strictly better than the centre) is taken from warp-shuffle
+// reductions, so all lanes follow the same control flow. The host turns
+// physical step sizes into whole grid steps (round half up, at least 1,
+// consecutive duplicates dropped) exactly as the stage machine defines them.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "bloch.cuh"
 #include "mrf_internal.h"
 
-int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, const mrf_zoom_opts *opts,
-             const void *fp, int64_t V, mrf_result *out, cudaStream_t stream)
+namespace {
+
+constexpr int kMaxLevels = MRF_ZOOM_MAX_LEVELS;
+constexpr int kZoomThreads = 256;   // 8 voxels (warps) per CTA
+
+struct ZoomPlan {
+    int a0, b0;          // start of the df search
+    int hA;              // step 1a: coarse df step
+    int K1b, hB;         // step 1b: k = -K1b..K1b (k != 0), step hB
+    int hC;              // step 1c: probe spacing (omega)
+    int W3;              // step 3: half-width at the finest step
+    int n_s2;
+    int s2_h1[kMaxLevels], s2_h2[kMaxLevels];
+    int n_s4;
+    int s4_p[kMaxLevels], s4_h[kMaxLevels];
+};
+
+struct ZoomArgs {
+    SeqDev s;
+    GridDev g;
+    ZoomPlan plan;
+    const float2 *x;
+    int64_t V;
+    mrf_result *out;
+    int *counter;
+    int *err;
+    int max_moves;
+};
+
+struct Kahan {
+    float s, c;
+    __device__ __forceinline__ void init() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void add(float v)
+    {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+// Evolution factors with the SFU sine/cosine (argument reduced to [-pi, pi]).
+__device__ __forceinline__ void factors_fast(const Relax &r, float tau, float &e1, float &zr, float &zi)
 {
-    (void)ctx; (void)seq; (void)grid; (void)opts; (void)fp; (void)V; (void)out; (void)stream;
-    return set_error(MRF_E_UNSUPPORTED, "MRF-ZOOM kernel not built yet");
+    e1 = exp2f(r.k1 * tau);
+    const float e2 = exp2f(r.k2 * tau);
+    float t = r.f * tau;
+    t -= rintf(t);
+    float sn, cs;
+    __sincosf(6.283185307179586f * t, &sn, &cs);
+    zr = e2 * cs;
+    zi = e2 * sn;
+}
+
+// Simulate one candidate and correlate it with x (all lanes call this together).
+template <bool XONLY>
+__device__ __forceinline__ void sim_dot(const SeqDev &s, const float2 *__restrict__ x, float T1, float T2, float df,
+                                        float &ipr, float &ipi, float &dd)
+{
+    const Relax r = relax_make(T1, T2, df);
+    Bloch st;
+    bloch_start(st, s, r);
+    Kahan kr, ki, kd;
+    kr.init(); ki.init(); kd.init();
+    const int n = s.n;
+    for (int j0 = 0; j0 < n; j0 += 16) {
+        float pr = 0.f, pi = 0.f, pd = 0.f;
+        const int j1 = min(n, j0 + 16);
+        for (int j = j0; j < j1; ++j) {
+            bloch_rf<XONLY>(st, s, j);
+            const float2 tau = __ldg(&s.tau[j]);
+            float e1, zr, zi;
+            factors_fast(r, tau.x, e1, zr, zi);
+            bloch_evolve(st, e1, zr, zi);
+            const float sr = st.mx, si = st.my;
+            if (s.symmetric) {
+                bloch_evolve(st, e1, zr, zi);
+            } else {
+                factors_fast(r, tau.y, e1, zr, zi);
+                bloch_evolve(st, e1, zr, zi);
+            }
+            const float2 z = __ldg(&x[j]);
+            // x conj(d)
+            pr = fmaf(z.x, sr, fmaf(z.y, si, pr));
+            pi = fmaf(z.y, sr, fmaf(-z.x, si, pi));
+            pd = fmaf(sr, sr, fmaf(si, si, pd));
+        }
+        kr.add(pr);
+        ki.add(pi);
+        kd.add(pd);
+    }
+    ipr = kr.s;
+    ipi = ki.s;
+    dd = kd.s;
+}
+
+__device__ __forceinline__ bool point_valid(const GridDev &g, int a, int b, int c)
+{
+    return a >= 0 && a < g.n_t1 && b >= 0 && c >= 0 && c < g.n_df && b < __ldg(&g.nb[a]);
+}
+
+// Per-voxel search state shared (identically) by all lanes of the warp.
+struct Search {
+    int a, b, c;
+    float centre;             // CC of the centre
+    float cr, ci, cd;         // <x, d> and ||d||^2 of the centre
+    int evaluated;
+    float min_margin;
+    float inv_xn;
+};
+
+struct Eval {
+    float v;                  // CC, -inf if the point is not evaluated
+    float ipr, ipi, dd;
+};
+
+template <bool XONLY>
+__device__ __forceinline__ Eval eval_point(const ZoomArgs &A, const float2 *x, float inv_xn, bool want, int a, int b,
+                                           int c)
+{
+    const bool ok = want && point_valid(A.g, a, b, c);
+    const float T1 = ok ? __ldg(&A.g.t1[a]) : 1000.f;
+    const float T2 = ok ? __ldg(&A.g.t2[b]) : 100.f;
+    const float df = ok ? __ldg(&A.g.df[c]) : 0.f;
+    Eval e;
+    sim_dot<XONLY>(A.s, x, T1, T2, df, e.ipr, e.ipi, e.dd);
+    if (ok) {
+        const float mag = sqrtf(fmaf(e.ipr, e.ipr, e.ipi * e.ipi));
+        e.v = (e.dd > 0.f && inv_xn > 0.f) ? mag * inv_xn * rsqrtf(e.dd) : 0.f;
+    } else {
+        e.v = -INFINITY;
+    }
+    return e;
+}
+
+// Warp argmax: highest value, ties to the smallest position. Returns the lane
+// holding it (valid when the value is finite).
+__device__ __forceinline__ int warp_best(float v, int pos, float &best)
+{
+    float bv = v;
+    int bp = pos, bl = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+        if (ov > bv || (ov == bv && op < bp)) { bv = ov; bp = op; bl = ol; }
+    }
+    best = bv;
+    return bl;
+}
+
+// Two largest finite values across the warp (plus a running pair).
+__device__ __forceinline__ void warp_top2(float v, float &t1, float &t2)
+{
+    float a = isfinite(v) ? v : -INFINITY, b = -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oa = __shfl_xor_sync(0xffffffffu, a, o);
+        const float ob = __shfl_xor_sync(0xffffffffu, b, o);
+        const float hi = fmaxf(a, oa), lo = fminf(a, oa);
+        b = fmaxf(lo, fmaxf(b, ob));
+        a = hi;
+    }
+    // merge with the running pair
+    const float hi = fmaxf(t1, a), lo = fminf(t1, a);
+    t2 = fmaxf(lo, fmaxf(t2, b));
+    t1 = hi;
+}
+
+__device__ __forceinline__ void close_margin(Search &S, float t1, float t2)
+{
+    if (isfinite(t2)) S.min_margin = fminf(S.min_margin, t1 - t2);
+}
+
+// Adopt lane `bl`'s evaluation as the new centre.
+__device__ __forceinline__ void take(Search &S, const Eval &e, int bl, int na, int nb, int nc, float bv)
+{
+    S.a = __shfl_sync(0xffffffffu, na, bl);
+    S.b = __shfl_sync(0xffffffffu, nb, bl);
+    S.c = __shfl_sync(0xffffffffu, nc, bl);
+    S.cr = __shfl_sync(0xffffffffu, e.ipr, bl);
+    S.ci = __shfl_sync(0xffffffffu, e.ipi, bl);
+    S.cd = __shfl_sync(0xffffffffu, e.dd, bl);
+    S.centre = bv;
+}
+
+// One scan over an ordered candidate list along df at fixed (a, b): the list
+// position p maps to c = c_start + p * step; `skip` is excluded. The running
+// best (value S.centre at S.c) is replaced only by a strictly better value.
+template <bool XONLY>
+__device__ void df_scan(const ZoomArgs &A, const float2 *x, Search &S, int count, int c_start, int step, int skip,
+                        bool with_centre)
+{
+    float t1 = with_centre ? S.centre : -INFINITY, t2 = -INFINITY;
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < count; base += 32) {
+        const int p = base + lane;
+        const int c = c_start + p * step;
+        const bool want = p < count && c != skip;
+        const Eval e = eval_point<XONLY>(A, x, S.inv_xn, want, S.a, S.b, c);
+        S.evaluated += __popc(__ballot_sync(0xffffffffu, isfinite(e.v)));
+        warp_top2(e.v, t1, t2);
+        float bv;
+        const int bl = warp_best(e.v, p, bv);
+        if (bv > S.centre) take(S, e, bl, S.a, S.b, c, bv);
+    }
+    close_margin(S, t1, t2);
+}
+
+// 2D ZOOM at (h1, h2): the 8 neighbours in the fixed order (T1 offset outer).
+template <bool XONLY>
+__device__ bool move2d(const ZoomArgs &A, const float2 *x, Search &S, int h1, int h2)
+{
+    const int lane = threadIdx.x & 31;
+    const int k = lane < 4 ? lane : lane + 1;        // skip the centre (0, 0)
+    const int da = k / 3 - 1, db = k % 3 - 1;
+    for (int it = 0; it < A.max_moves; ++it) {
+        const int na = S.a + da * h1, nb = S.b + db * h2;
+        const Eval e = eval_point<XONLY>(A, x, S.inv_xn, lane < 8, na, nb, S.c);
+        S.evaluated += __popc(__ballot_sync(0xffffffffu, isfinite(e.v)));
+        float t1 = S.centre, t2 = -INFINITY;
+        warp_top2(e.v, t1, t2);
+        close_margin(S, t1, t2);
+        float bv;
+        const int bl = warp_best(e.v, lane, bv);
+        if (bv > S.centre) take(S, e, bl, na, nb, S.c, bv);
+        else return true;
+    }
+    return false;
+}
+
+// 1D ZOOM along T1 (param 0) or T2 (param 1) at half-width h: left then right.
+template <bool XONLY>
+__device__ bool move1d(const ZoomArgs &A, const float2 *x, Search &S, int param, int h)
+{
+    const int lane = threadIdx.x & 31;
+    const int sgn = lane == 0 ? -1 : 1;
+    for (int it = 0; it < A.max_moves; ++it) {
+        const int na = S.a + (param == 0 ? sgn * h : 0), nb = S.b + (param == 1 ? sgn * h : 0);
+        const Eval e = eval_point<XONLY>(A, x, S.inv_xn, lane < 2, na, nb, S.c);
+        S.evaluated += __popc(__ballot_sync(0xffffffffu, isfinite(e.v)));
+        float t1 = S.centre, t2 = -INFINITY;
+        warp_top2(e.v, t1, t2);
+        close_margin(S, t1, t2);
+        float bv;
+        const int bl = warp_best(e.v, lane, bv);
+        if (bv > S.centre) take(S, e, bl, na, nb, S.c, bv);
+        else return true;
+    }
+    return false;
+}
+
+template <bool XONLY>
+__global__ void __launch_bounds__(kZoomThreads) zoom_kernel(ZoomArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const ZoomPlan &P = A.plan;
+    for (;;) {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(A.counter, 1);
+        v = __shfl_sync(0xffffffffu, v, 0);
+        if (v >= A.V) break;
+        const int n = A.s.n;
+        const float2 *x = A.x + (size_t)v * n;
+        float xx = 0.f;
+        for (int j = lane; j < n; j += 32) {
+            const float2 z = __ldg(&x[j]);
+            xx = fmaf(z.x, z.x, fmaf(z.y, z.y, xx));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) xx += __shfl_xor_sync(0xffffffffu, xx, o);
+
+        Search S;
+        S.a = P.a0; S.b = P.b0; S.c = 0;
+        S.centre = -INFINITY;
+        S.cr = S.ci = 0.f; S.cd = 0.f;
+        S.evaluated = 0;
+        S.min_margin = INFINITY;
+        S.inv_xn = xx > 0.f ? rsqrtf(xx) : 0.f;
+        bool ok = true;
+
+        // step 1a: coarse scan of the whole df range (no prior centre)
+        const int nA = (A.g.n_df + P.hA - 1) / P.hA;
+        df_scan<XONLY>(A, x, S, nA, 0, P.hA, -1, false);
+        // step 1b: window around the optimum
+        {
+            const int c0 = S.c;
+            const int count = 2 * P.K1b + 1;
+            df_scan<XONLY>(A, x, S, count, c0 - P.K1b * P.hB, P.hB, c0, true);
+        }
+        // step 1c: probes at whole multiples of omega
+        {
+            const int c0 = S.c;
+            const int start = c0 - (c0 / P.hC) * P.hC;
+            const int count = (A.g.n_df - 1 - start) / P.hC + 1;
+            df_scan<XONLY>(A, x, S, count, start, P.hC, c0, true);
+        }
+        // step 2: 2D ZOOM at the coarse levels
+        for (int l = 0; l < P.n_s2 && ok; ++l) ok = move2d<XONLY>(A, x, S, P.s2_h1[l], P.s2_h2[l]);
+        // step 3: finest-step df window
+        {
+            const int c0 = S.c;
+            df_scan<XONLY>(A, x, S, 2 * P.W3 + 1, c0 - P.W3, 1, c0, true);
+        }
+        // step 4: interleaved 1D ZOOMs
+        for (int l = 0; l < P.n_s4 && ok; ++l) ok = move1d<XONLY>(A, x, S, P.s4_p[l], P.s4_h[l]);
+        // step 5: final 2D ZOOM at the finest step
+        if (ok) ok = move2d<XONLY>(A, x, S, 1, 1);
+        if (!ok && lane == 0) atomicExch(A.err, kDeviceErrBounds);
+
+        if (lane == 0) {
+            mrf_result r;
+            const bool have = isfinite(S.centre);
+            r.index = have ? A.g.a_off[S.a] + (int64_t)S.b * A.g.n_df + S.c : -1;
+            r.i_t1 = S.a; r.i_t2 = S.b; r.i_df = S.c;
+            r.t1_ms = A.g.t1[S.a]; r.t2_ms = A.g.t2[S.b]; r.df_hz = A.g.df[S.c];
+            r.cc = have ? S.centre : 0.f;
+            r.m0 = S.cd > 0.f ? sqrtf(S.cr * S.cr + S.ci * S.ci) / S.cd : 0.f;
+            r.phase = atan2f(S.ci, S.cr);
+            r.entries_evaluated = S.evaluated;
+            r.min_margin = isfinite(S.min_margin) ? S.min_margin : -1.f;
+            A.out[v] = r;
+        }
+    }
+}
+
+int snap(double h_phys, double step)
+{
+    const int h = (int)floor(h_phys / step + 0.5);
+    return h < 1 ? 1 : h;
+}
+
+}  // namespace
+
+int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mrf_zoom_opts *o, const void *fp,
+             int64_t V, mrf_result *out, cudaStream_t stream)
+{
+    // plan on the host, in FP64, with the stage machine's snapping rules
+    const double omega = o->omega_hz > 0 ? o->omega_hz : 1000.0 / seq->min_tr;
+    ZoomPlan P{};
+    int a = (int)floor((o->t1_init_ms - gd->t1_min) / gd->t1_step + 0.5);
+    int b = (int)floor((o->t2_init_ms - gd->t2_min) / gd->t2_step + 0.5);
+    a = std::max(0, std::min(a, gd->n_t1 - 1));
+    b = std::max(0, std::min(b, gd->n_t2 - 1));
+    auto valid = [&](int aa, int bb) {
+        if (!gd->require_t2_lt_t1) return true;
+        return gd->t2_min + (double)bb * gd->t2_step < gd->t1_min + (double)aa * gd->t1_step;
+    };
+    while (b > 0 && !valid(a, b)) --b;
+    while (a < gd->n_t1 - 1 && !valid(a, b)) ++a;
+    if (!valid(a, b)) return set_error(MRF_E_INVALID, "zoom: the grid has no valid starting point");
+    P.a0 = a;
+    P.b0 = b;
+    P.hA = snap(o->s1a_step_frac * omega, gd->df_step);
+    const int W1 = (int)floor(o->s1b_half_frac * omega / gd->df_step + 0.5);
+    P.hB = snap(o->s1b_step_frac * omega, gd->df_step);
+    P.K1b = W1 / P.hB;
+    P.hC = snap(omega, gd->df_step);
+    P.W3 = (int)floor(o->s3_half_frac * omega / gd->df_step + 0.5);
+    int ph1 = -1, ph2 = -1;
+    for (int l = 0; l < o->n_s2; ++l) {
+        const int h1 = snap(o->s2_t1_ms[l], gd->t1_step), h2 = snap(o->s2_t2_ms[l], gd->t2_step);
+        if (h1 == ph1 && h2 == ph2) continue;
+        ph1 = h1; ph2 = h2;
+        P.s2_h1[P.n_s2] = h1;
+        P.s2_h2[P.n_s2] = h2;
+        P.n_s2++;
+    }
+    int pp = -1, phh = -1;
+    for (int l = 0; l < o->n_s4; ++l) {
+        const int p = o->s4_param[l];
+        const int h = snap(o->s4_ms[l], p == 0 ? gd->t1_step : gd->t2_step);
+        if (p == pp && h == phh) continue;
+        pp = p; phh = h;
+        P.s4_p[P.n_s4] = p;
+        P.s4_h[P.n_s4] = h;
+        P.n_s4++;
+    }
+
+    GridDev gdev;
+    void *gblock = nullptr;
+    size_t gbytes = 0;
+    int rc = grid_upload_async(ctx, gd, stream, &gdev, &gblock, &gbytes);
+    if (rc) return rc;
+    int *counter = nullptr;
+    rc = budget_charge(ctx, 256);
+    if (rc) { cudaFreeAsync(gblock, stream); budget_release(ctx, gbytes); return rc; }
+    cudaError_t e = cudaMallocAsync((void **)&counter, 256, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+    if (e != cudaSuccess) {
+        budget_release(ctx, 256);
+        cudaFreeAsync(gblock, stream);
+        budget_release(ctx, gbytes);
+        return cuda_fail(e, "zoom scratch");
+    }
+    ZoomArgs A;
+    A.s = seq->dev();
+    A.g = gdev;
+    A.plan = P;
+    A.x = (const float2 *)fp;
+    A.V = V;
+    A.out = out;
+    A.counter = counter;
+    A.err = ctx->err_flag;
+    A.max_moves = 1 << 20;
+    int per_sm = 0;
+    if (A.s.xonly) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<true>, kZoomThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<false>, kZoomThreads, 0);
+    per_sm = std::max(1, per_sm);
+    const int64_t warps_needed = V;
+    int64_t blocks = std::min<int64_t>((int64_t)per_sm * ctx->sm_count, (warps_needed + 7) / 8);
+    blocks = std::max<int64_t>(blocks, 1);
+    {
+        ProfScope prof(ctx, kProfZoom, stream);
+        if (A.s.xonly) zoom_kernel<true><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
+        else zoom_kernel<false><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
+    }
+    e = cudaGetLastError();
+    cudaFreeAsync(counter, stream);
+    cudaFreeAsync(gblock, stream);
+    budget_release(ctx, 256 + gbytes);
+    if (e != cudaSuccess) return cuda_fail(e, "zoom launch");
+    return MRF_OK;
 }

@@ -43,7 +43,7 @@ class DevView:
     """__cuda_array_interface__ view of a raw device pointer (no copy)."""
 
     def __init__(self, ptr, nbytes):
-        self.__cuda_array_interface__ = {"shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), False),
                                          "version": 3, "strides": None}
 
 

@@ -1,0 +1,140 @@
+"""GPU MRF-ZOOM against the FP64 oracle's ZOOM (Theory: df search, 1D and
+2D ZOOM; Methods, Experiment 2 steps 1-5).
+
+Bar: final grid point identical except where the oracle trace's smallest
+decision margin is below 1e-6 (counted); CC within 1e-5; where the final
+points agree and no margin is close, the number of candidate evaluations is
+identical too (same trace length)."""
+import numpy as np
+import pytest
+import torch
+
+import mrf_synth as S
+from helpers import offgrid_voxels, ongrid_voxels
+
+pytestmark = pytest.mark.gpu
+
+MARGIN_EXCUSE = 1e-6
+
+
+def _gpu_zoom(M, ctx, seq, g, x, **kw):
+    h = M.mrf_sequence_load(ctx, seq)
+    try:
+        fp = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+        out = M.empty_results(x.shape[0])
+        M.mrf_zoom_search(ctx, h, g, M.zoom_opts(**kw), fp, out)
+        M.mrf_stream_sync(ctx)
+        return M.results_to_numpy(out)[: x.shape[0]]
+    finally:
+        M.mrf_sequence_free(ctx, h)
+
+
+def _compare(orc, g, res, ref, label):
+    abc = np.stack([res["i_t1"], res["i_t2"], res["i_df"]], 1)
+    same = (abc == ref["abc"]).all(1)
+    excused = ref["min_margin"] < MARGIN_EXCUSE
+    bad = ~same & ~excused
+    assert not bad.any(), (f"{label}: {bad.sum()} voxels differ with margin >= {MARGIN_EXCUSE}: "
+                           f"gpu {abc[bad][:4].tolist()} oracle {ref['abc'][bad][:4].tolist()} "
+                           f"margin {ref['min_margin'][bad][:4]}")
+    assert np.abs(res["cc"][same] - ref["cc"][same]).max() < 1e-5
+    idx = np.array([orc.grid_index(g, *p) for p in ref["abc"]])
+    assert (res["index"][same] == idx[same]).all()
+    firm = same & (ref["min_margin"] >= 1e-5)
+    assert (res["entries_evaluated"][firm] == ref["evaluated"][firm]).all()
+    return int((~same).sum()), int(excused.sum())
+
+
+def test_zoom_tiny_on_grid(M, ctx, oracle_lib):
+    seq = S.sequence(0, 200)
+    g = S.GRIDS["tiny"]
+    ph, x = ongrid_voxels(oracle_lib, seq, g, 256, 30.0, 100)
+    res = _gpu_zoom(M, ctx, seq, g, x)
+    ref = oracle_lib.zoom(seq, g, x)
+    diff, exc = _compare(oracle_lib, g, res, ref, "tiny")
+    print(f"zoom tiny: differ={diff} excused={exc}")
+
+
+def test_zoom_noise_free_recovery(M, ctx, oracle_lib):
+    seq = S.sequence(0, 200)
+    g = S.GRIDS["tiny"]
+    ph, x = ongrid_voxels(oracle_lib, seq, g, 64, None, 200)
+    res = _gpu_zoom(M, ctx, seq, g, x)
+    assert (res["i_t1"] == ph["a"]).all() and (res["i_t2"] == ph["b"]).all()
+    np.testing.assert_allclose(res["cc"], 1.0, atol=1e-5)
+    np.testing.assert_allclose(res["m0"], ph["m0"], rtol=1e-4)
+
+
+def test_zoom_3d_grid_offgrid_voxels(M, ctx, oracle_lib):
+    """df searched too: the full df stage machine (steps 1a-1c, 3)."""
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["fp32_brute"]
+    ph, x = offgrid_voxels(oracle_lib, seq, 96, 20.0, 101)
+    res = _gpu_zoom(M, ctx, seq, g, x)
+    ref = oracle_lib.zoom(seq, g, x)
+    diff, exc = _compare(oracle_lib, g, res, ref, "fp32_brute grid")
+    print(f"zoom 3d: differ={diff} excused={exc}")
+
+
+def test_zoom_fine_grid_subset(M, ctx, oracle_lib):
+    """The 2.4e9-entry grid (1 ms / 0.5 ms / 0.1 Hz) on a 16x16 voxel subset.
+    Decisions there separate candidates by less than 1e-6, so the traces may
+    part; what must hold: CC of the GPU result within 1e-5 of the oracle's,
+    and the GPU's final point is a local optimum of the oracle's FP64 CC at
+    the finest step (up to 1e-6)."""
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["zoom_fine"]
+    ph, x = offgrid_voxels(oracle_lib, seq, 256, 20.0, 103)
+    res = _gpu_zoom(M, ctx, seq, g, x)
+    ref = oracle_lib.zoom(seq, g, x)
+    abc = np.stack([res["i_t1"], res["i_t2"], res["i_df"]], 1)
+    same = (abc == ref["abc"]).all(1)
+    firm = ref["min_margin"] >= MARGIN_EXCUSE
+    assert (same | ~firm).all()
+    assert np.abs(res["cc"] - ref["cc"]).max() < 1e-5
+    t1, t2, df = S.grid_values(g)
+    pts, owner = [], []
+    for v in range(0, 256, 4):
+        a, b, c = abc[v]
+        for da in (-1, 0, 1):
+            for db in (-1, 0, 1):
+                aa, bb = a + da, b + db
+                if 0 <= aa < g.n_t1 and 0 <= bb < g.n_t2 and t2[bb] < t1[aa]:
+                    pts.append((aa, bb, c, da == 0 and db == 0))
+                    owner.append(v)
+    pts = np.array(pts)
+    d = oracle_lib.simulate(seq, t1[pts[:, 0]], t2[pts[:, 1]], df[pts[:, 2]])
+    owner = np.array(owner)
+    cc = np.abs(np.sum(d.conj() * x[owner], 1)) / (np.linalg.norm(d, axis=1) * np.linalg.norm(x[owner], axis=1))
+    for v in np.unique(owner):
+        sel = owner == v
+        centre = cc[sel & (pts[:, 3] == 1)][0]
+        assert cc[sel].max() <= centre + 1e-6
+        assert abs(centre - res["cc"][v]) < 1e-5
+    print(f"zoom fine: same={int(same.sum())}/256 firm={int(firm.sum())} "
+          f"max |dCC|={np.abs(res['cc'] - ref['cc']).max():.2e} mean evaluated={ref['evaluated'].mean():.0f}")
+
+
+def test_zoom_custom_schedule_and_general_rf(M, ctx, oracle_lib):
+    import math
+    base = S.sequence(5, 300)
+    rng = np.random.default_rng(17)
+    seq = S.Sequence(base.flip_rad, rng.uniform(0, 2 * math.pi, 300), base.tr_ms, base.tr_ms * 0.4, 1, 20.0)
+    g = S.Grid(200.0, 10.0, 120, 20.0, 4.0, 60, -20.0, 0.5, 81)
+    ph, x = offgrid_voxels(oracle_lib, seq, 40, 30.0, 55, t1_range=(300.0, 1200.0), t2_range=(30.0, 200.0),
+                           df_range=(-15.0, 15.0))
+    kw = dict(t1_init_ms=700.0, t2_init_ms=80.0, s2=[(150.0, 60.0), (60.0, 24.0)], s4=[(0, 40.0), (1, 16.0), (0, 20.0), (1, 8.0)])
+    res = _gpu_zoom(M, ctx, seq, g, x, **kw)
+    ref = oracle_lib.zoom(seq, g, x, oracle_lib.default_zoom_opts(**kw))
+    _compare(oracle_lib, g, res, ref, "custom")
+
+
+def test_zoom_empty_batch(M, ctx):
+    import ctypes as C
+    seq = S.sequence(0, 50)
+    h = M.mrf_sequence_load(ctx, seq)
+    try:
+        g = M.grid_desc(S.GRIDS["tiny"])
+        assert M.lib().mrf_zoom_search(ctx, h, C.byref(g), None, None, 0, None, None) == M.MRF_OK
+    finally:
+        M.mrf_sequence_free(ctx, h)
