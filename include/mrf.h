@@ -265,6 +265,26 @@ void mrf_zoom_opts_default(mrf_zoom_opts *opts);
 int mrf_zoom_search(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, const mrf_zoom_opts *opts,
                     const void *fp_dev, int64_t V, mrf_result *out_dev, void *stream);
 
+/* Allocation-free variant of mrf_zoom_search. The paper has no counterpart:
+ * it serves callers that cannot let the library allocate device memory
+ * during a call -- a framework that already reserved the GPU's memory for
+ * its own pool, or a scan loop that must not meet allocation latency or an
+ * out-of-memory error mid-run. The call's scratch (grid tables and the voxel
+ * work counter) lives in one fixed file-scope device array of
+ * MRF_ZOOM_STATIC_SCRATCH_BYTES, present on every GPU that loads the
+ * library until the process exits; the call makes no cudaMalloc/cudaFree.
+ * The caller still owns fp_dev and out_dev; arguments and results are those
+ * of mrf_zoom_search. Limit: the grid's tables must fit the array (about
+ * 16 bytes per T1 value plus 4 per T2 and per df value); a larger grid returns
+ * MRF_E_INVALID with the needed size. All calls share the array and it keeps
+ * the last call's contents: calls that overlap on the GPU race and must be
+ * serialised by the caller. The first call on a device looks up the array's
+ * address; make it before any stream capture. */
+#define MRF_ZOOM_STATIC_SCRATCH_BYTES (512 * 1024)
+int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid,
+                           const mrf_zoom_opts *opts, const void *fp_dev, int64_t V, mrf_result *out_dev,
+                           void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of slice requests                           */
 

@@ -114,6 +114,7 @@ EXPORTS = [
     "mrf_dict_generate", "mrf_dict_free", "mrf_dict_query", "mrf_match_bruteforce", "mrf_match_topk",
     "mrf_zoom_opts_default", "mrf_zoom_search", "mrf_serve_start", "mrf_serve_submit", "mrf_serve_poll",
     "mrf_serve_cancel", "mrf_serve_get_stats", "mrf_serve_stop", "mrf_profile_enable", "mrf_profile_read",
+    "mrf_zoom_search_static",
 ]
 
 
@@ -159,6 +160,7 @@ def lib():
         L.mrf_serve_stop.argtypes = [vp]
         L.mrf_profile_enable.argtypes = [vp, C.c_int]
         L.mrf_profile_read.argtypes = [vp, C.POINTER(Profile), C.c_int]
+        L.mrf_zoom_search_static.argtypes = [vp, vp, C.POINTER(GridDesc), C.POINTER(ZoomOpts), vp, i64, vp, vp]
         _lib = L
     return _lib
 
@@ -298,6 +300,13 @@ def mrf_zoom_search(ctx, seq, grid, opts, fp, out, stream=None) -> None:
     g = grid_desc(grid)
     check(lib().mrf_zoom_search(ctx, seq, C.byref(g), C.byref(opts) if opts is not None else None, _ptr(fp),
                                 fp.shape[0], _ptr(out), _stream_ptr(stream)), "mrf_zoom_search")
+
+
+def mrf_zoom_search_static(ctx, seq, grid, opts, fp, out, stream=None) -> None:
+    """mrf_zoom_search with its scratch in the library's fixed device array (no allocation)."""
+    g = grid_desc(grid)
+    check(lib().mrf_zoom_search_static(ctx, seq, C.byref(g), C.byref(opts) if opts is not None else None, _ptr(fp),
+                                       fp.shape[0], _ptr(out), _stream_ptr(stream)), "mrf_zoom_search_static")
 
 
 def mrf_serve_start(ctx, max_inflight=2, max_batch_voxels=16384, request_bytes_budget=0) -> None:

@@ -446,3 +446,162 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     if (e != cudaSuccess) return cuda_fail(e, "zoom launch");
     return MRF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free ZOOM search.
+//
+// Some callers cannot let a library allocate device memory while they run:
+// a host framework that reserved the GPU's memory up front for its own pool
+// (a cudaMalloc from here could fail or fragment that pool), or a
+// reconstruction loop that matches slice after slice and must never pay
+// allocation latency or meet an out-of-memory error in the middle of a scan.
+// For them, mrf_zoom_search_static keeps all per-call scratch of the ZOOM
+// search -- the voxel work counter and the grid's axis/offset tables -- in
+// the fixed device array below, so a call allocates nothing: it copies the
+// tables into the array, clears the counter and launches the same kernel as
+// mrf_zoom_search. The caller still passes its fingerprints and result
+// buffer.
+//
+// The array lives in every GPU that loads this library until the process
+// exits. All calls share it and it keeps the last call's contents, so calls
+// whose work overlaps on the GPU (different streams, or host threads racing)
+// corrupt each other: serialise them. The first call on a device looks up the
+// array's device address (cudaGetSymbolAddress, with that device current);
+// make that first call before any stream capture.
+
+namespace {
+
+constexpr size_t kZoomStaticBytes = MRF_ZOOM_STATIC_SCRATCH_BYTES;
+static __device__ __align__(256) uint8_t g_zoom_static_scratch[kZoomStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;                         // guards the address table and the host staging
+void *g_static_addr[kMaxDevices] = {nullptr};
+alignas(256) uint8_t g_static_host[kZoomStaticBytes];   // host staging for the table copy
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd,
+                                      const mrf_zoom_opts *opts, const void *fp, int64_t V, mrf_result *out,
+                                      void *stream_v)
+{
+    if (!ctx || !seq || !gd) return set_error(MRF_E_INVALID, "NULL argument");
+    int rc = grid_validate(gd);
+    if (rc) return rc;
+    if (V < 0) return set_error(MRF_E_INVALID, "V < 0");
+    mrf_zoom_opts def;
+    if (!opts) { mrf_zoom_opts_default(&def); opts = &def; }
+    if (opts->n_s2 < 0 || opts->n_s2 > MRF_ZOOM_MAX_LEVELS || opts->n_s4 < 0 || opts->n_s4 > MRF_ZOOM_MAX_LEVELS)
+        return set_error(MRF_E_INVALID, "zoom: level counts out of range");
+    for (int i = 0; i < opts->n_s4; ++i)
+        if (opts->s4_param[i] != 0 && opts->s4_param[i] != 1) return set_error(MRF_E_INVALID, "zoom: s4_param must be 0/1");
+    if (!(opts->s1a_step_frac > 0) || !(opts->s1b_step_frac > 0) || opts->s1b_half_frac < 0 || opts->s3_half_frac < 0)
+        return set_error(MRF_E_INVALID, "zoom: bad df search fractions");
+    // scratch layout: [counter][t1][t2][df][a_off][nb], 256-byte aligned pieces
+    const size_t nt1 = gd->n_t1, nt2 = gd->n_t2, ndf = gd->n_df;
+    const size_t o_t1 = 256, o_t2 = o_t1 + al256(4 * nt1), o_df = o_t2 + al256(4 * nt2);
+    const size_t o_ao = o_df + al256(4 * ndf), o_nb = o_ao + al256(8 * (nt1 + 1)), need = o_nb + al256(4 * nt1);
+    if (need > kZoomStaticBytes)
+        return set_error(MRF_E_INVALID, "zoom (static scratch): the grid needs " + std::to_string(need) +
+                                            " bytes of tables, more than the fixed " +
+                                            std::to_string(kZoomStaticBytes) + "-byte scratch array; use mrf_zoom_search");
+    if (V == 0) return MRF_OK;
+    if (!fp || !out) return set_error(MRF_E_INVALID, "NULL device buffer");
+    if (ctx->device < 0 || ctx->device >= kMaxDevices) return set_error(MRF_E_INVALID, "device index out of range");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaStream_t stream = (cudaStream_t)stream_v;
+
+    // the same plan as mrf_zoom_search (FP64 snapping on the host)
+    const double omega = opts->omega_hz > 0 ? opts->omega_hz : 1000.0 / seq->min_tr;
+    ZoomPlan P{};
+    int a = (int)floor((opts->t1_init_ms - gd->t1_min) / gd->t1_step + 0.5);
+    int b = (int)floor((opts->t2_init_ms - gd->t2_min) / gd->t2_step + 0.5);
+    a = std::max(0, std::min(a, gd->n_t1 - 1));
+    b = std::max(0, std::min(b, gd->n_t2 - 1));
+    auto t1v = [&](int i) { return gd->t1_min + (double)i * gd->t1_step; };
+    auto t2v = [&](int i) { return gd->t2_min + (double)i * gd->t2_step; };
+    auto valid = [&](int aa, int bb) { return !gd->require_t2_lt_t1 || t2v(bb) < t1v(aa); };
+    while (b > 0 && !valid(a, b)) --b;
+    while (a < gd->n_t1 - 1 && !valid(a, b)) ++a;
+    if (!valid(a, b)) return set_error(MRF_E_INVALID, "zoom: the grid has no valid starting point");
+    P.a0 = a;
+    P.b0 = b;
+    P.hA = snap(opts->s1a_step_frac * omega, gd->df_step);
+    P.hB = snap(opts->s1b_step_frac * omega, gd->df_step);
+    P.K1b = (int)floor(opts->s1b_half_frac * omega / gd->df_step + 0.5) / P.hB;
+    P.hC = snap(omega, gd->df_step);
+    P.W3 = (int)floor(opts->s3_half_frac * omega / gd->df_step + 0.5);
+    for (int l = 0, p1 = -1, p2 = -1; l < opts->n_s2; ++l) {
+        const int h1 = snap(opts->s2_t1_ms[l], gd->t1_step), h2 = snap(opts->s2_t2_ms[l], gd->t2_step);
+        if (h1 == p1 && h2 == p2) continue;
+        p1 = h1; p2 = h2;
+        P.s2_h1[P.n_s2] = h1; P.s2_h2[P.n_s2] = h2; P.n_s2++;
+    }
+    for (int l = 0, pp = -1, ph = -1; l < opts->n_s4; ++l) {
+        const int p = opts->s4_param[l], h = snap(opts->s4_ms[l], p == 0 ? gd->t1_step : gd->t2_step);
+        if (p == pp && h == ph) continue;
+        pp = p; ph = h;
+        P.s4_p[P.n_s4] = p; P.s4_h[P.n_s4] = h; P.n_s4++;
+    }
+
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[ctx->device]) {
+        void *addr = nullptr;
+        e = cudaGetSymbolAddress(&addr, g_zoom_static_scratch);
+        if (e != cudaSuccess || !addr) return cuda_fail(e, "cudaGetSymbolAddress(static ZOOM scratch)");
+        g_static_addr[ctx->device] = addr;
+    }
+    uint8_t *dev = (uint8_t *)g_static_addr[ctx->device];
+    // tables into the host staging, then one copy into the array
+    float *t1 = (float *)(g_static_host + o_t1), *t2 = (float *)(g_static_host + o_t2);
+    float *df = (float *)(g_static_host + o_df);
+    int64_t *ao = (int64_t *)(g_static_host + o_ao);
+    int32_t *nb = (int32_t *)(g_static_host + o_nb);
+    for (int i = 0; i < gd->n_t1; ++i) t1[i] = (float)t1v(i);
+    for (int i = 0; i < gd->n_t2; ++i) t2[i] = (float)t2v(i);
+    for (int i = 0; i < gd->n_df; ++i) df[i] = (float)(gd->df_min + (double)i * gd->df_step);
+    ao[0] = 0;
+    for (int i = 0; i < gd->n_t1; ++i) {
+        int32_t k = 0;
+        for (int j = 0; j < gd->n_t2; ++j) if (valid(i, j)) k = j + 1;
+        nb[i] = k;
+        ao[i + 1] = ao[i] + (int64_t)k * gd->n_df;
+    }
+    // pageable source: the copy is staged before the call returns, so the
+    // host staging may be refilled by the next call
+    e = cudaMemcpyAsync(dev + o_t1, g_static_host + o_t1, need - o_t1, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dev, 0, 256, stream);   // voxel work counter starts at 0
+    if (e != cudaSuccess) return cuda_fail(e, "static ZOOM scratch upload");
+
+    ZoomArgs A;
+    A.s = seq->dev();
+    A.g.n_t1 = gd->n_t1; A.g.n_t2 = gd->n_t2; A.g.n_df = gd->n_df;
+    A.g.t1 = (const float *)(dev + o_t1);
+    A.g.t2 = (const float *)(dev + o_t2);
+    A.g.df = (const float *)(dev + o_df);
+    A.g.a_off = (const int64_t *)(dev + o_ao);
+    A.g.nb = (const int32_t *)(dev + o_nb);
+    A.g.count = ao[gd->n_t1];
+    A.plan = P;
+    A.x = (const float2 *)fp;
+    A.V = V;
+    A.out = out;
+    A.counter = (int *)dev;
+    A.err = ctx->err_flag;
+    A.max_moves = 1 << 20;
+    int per_sm = 0;
+    if (A.s.xonly) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<true>, kZoomThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<false>, kZoomThreads, 0);
+    per_sm = std::max(1, per_sm);
+    int64_t blocks = std::min<int64_t>((int64_t)per_sm * ctx->sm_count, (V + 7) / 8);
+    blocks = std::max<int64_t>(blocks, 1);
+    if (A.s.xonly) zoom_kernel<true><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
+    else zoom_kernel<false><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
+    count_launch(ctx);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "zoom launch (static scratch)");
+    return MRF_OK;
+}
