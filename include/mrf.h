@@ -175,7 +175,8 @@ int mrf_dict_free(mrf_ctx *ctx, mrf_dict *dict);
 typedef struct {
     int64_t entries;       /* D, valid grid entries */
     int32_t n;             /* timepoints */
-    int32_t ld;            /* row length in elements: 2n rounded up to 128 */
+    int32_t ld;            /* row stride in elements: 2n rounded up to 128, plus 128 bytes of
+                              padding (rows off a power-of-two stride); entries past 2n are 0 */
     int32_t dtype;         /* mrf_dtype */
     const void *hi_dev;    /* D x ld: bf16 (F32 hi, BF16) or e4m3 bytes (FP8) */
     const void *lo_dev;    /* D x ld bf16 residual (F32 only), else NULL */

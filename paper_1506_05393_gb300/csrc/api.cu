@@ -482,7 +482,9 @@ extern "C" int mrf_simulate(mrf_ctx *ctx, const mrf_seq *seq, int64_t count, con
     return launch_simulate(ctx, seq, count, t1, t2, df, out, (cudaStream_t)stream);
 }
 
-static int dict_ld(int n) { return ((2 * n + 127) / 128) * 128; }
+// Row length in elements: 2n rounded up to 128, plus 128 bytes so that rows do
+// not sit on a power-of-two stride (which crowds them into few L2 sets).
+static int dict_ld(int n, int dtype) { return ((2 * n + 127) / 128) * 128 + (dtype == MRF_FP8E4M3 ? 128 : 64); }
 
 extern "C" int mrf_dict_free(mrf_ctx *ctx, mrf_dict *d)
 {
@@ -516,7 +518,7 @@ extern "C" int mrf_dict_generate(mrf_ctx *ctx, const mrf_seq *seq, const mrf_gri
     d->dtype = dtype;
     d->entries = count;
     d->n = seq->n;
-    d->ld = dict_ld(seq->n);
+    d->ld = dict_ld(seq->n, dtype);
     int rc = seq_clone(ctx, seq, &d->seq);
     if (rc) { delete d; return rc; }
     rc = grid_upload(ctx, grid, &d->grid);

@@ -44,38 +44,42 @@ namespace {
 
 constexpr int BM = 128;          // voxel rows per tile (64 voxels)
 constexpr int BN = 256;          // dictionary entries per tile
-constexpr int kThreads = 192;    // 6 warps: TMA, MMA, 4 x epilogue
 constexpr uint64_t kWaitLimitNs = 4000000000ull;   // 4 s per barrier wait
 
 template <int MODE>
 struct Cfg;
+// FP32-equivalent: hi and lo of both operands, one voxel block per CTA
 template <>
 struct Cfg<MRF_F32> {
-    static constexpr int kBK = 64, kStages = 2, kOps = 2;   // hi and lo of each operand
+    static constexpr int kBK = 64, kStages = 2, kOps = 2, kNB = 1;
 };
+// BF16 / FP8: two voxel blocks per CTA share each dictionary tile (two
+// accumulators), which halves the dictionary bytes per flop through L2
 template <>
 struct Cfg<MRF_BF16> {
-    static constexpr int kBK = 64, kStages = 4, kOps = 1;
+    static constexpr int kBK = 64, kStages = 3, kOps = 1, kNB = 2;
 };
 template <>
 struct Cfg<MRF_FP8E4M3> {
-    static constexpr int kBK = 128, kStages = 4, kOps = 1;
+    static constexpr int kBK = 128, kStages = 3, kOps = 1, kNB = 2;
 };
 
 constexpr int kTileA = BM * 128;   // bytes of one A operand tile (128 rows x 128 B)
 constexpr int kTileB = BN * 128;   // bytes of one B operand tile (256 rows x 128 B)
 
 template <int MODE>
-constexpr int stage_bytes() { return Cfg<MODE>::kOps * (kTileA + kTileB); }
+constexpr int stage_bytes() { return Cfg<MODE>::kOps * (Cfg<MODE>::kNB * kTileA + kTileB); }
 template <int MODE>
 constexpr int smem_bytes() { return Cfg<MODE>::kStages * stage_bytes<MODE>() + 1024; }
+template <int MODE>
+constexpr int threads_of() { return 64 + 128 * Cfg<MODE>::kNB; }
 
 struct MatchParams {
     int64_t D;           // dictionary entries
     int64_t V;           // voxels
     int n_tiles;         // ceil(D / BN)
-    int n_mb;            // voxel blocks of 64
-    int n_chunks;        // dictionary chunks per voxel block
+    int n_vu;            // voxel units (kNB voxel blocks of 64 voxels each)
+    int n_chunks;        // dictionary chunks per voxel unit
     int k_blocks;        // K blocks of 128 bytes
     int last_ksteps;     // MMA k-steps in the last K block (rest is zero padding)
     const float *colscale;   // FP8: per-entry dequantisation scale, else nullptr
@@ -89,6 +93,8 @@ __device__ __forceinline__ bool before(float c, int i, float oc, int oi)
     return c > oc || (c == oc && i < oi);
 }
 
+// Sorted (descending) top-K list in registers. Insertion computes the slot
+// with K independent comparisons and shifts with selects (no serial chain).
 template <int K>
 struct TopK {
     float v[K];
@@ -98,52 +104,58 @@ struct TopK {
 #pragma unroll
         for (int q = 0; q < K; ++q) { v[q] = -1.0f; i[q] = 0x7fffffff; }
     }
-    // insert with the full order (used for merges)
     __device__ __forceinline__ void insert(float c, int idx)
     {
-        if (!before(c, idx, v[K - 1], i[K - 1])) return;
+        int pos = 0;
 #pragma unroll
-        for (int q = 0; q < K; ++q) {
-            if (before(c, idx, v[q], i[q])) {
-                const float tc = v[q];
-                const int ti = i[q];
-                v[q] = c; i[q] = idx;
-                c = tc; idx = ti;
-            }
+        for (int q = 0; q < K; ++q) pos += before(v[q], i[q], c, idx) ? 1 : 0;
+        if (pos >= K) return;
+#pragma unroll
+        for (int q = K - 1; q > 0; --q) {
+            const bool sh = q > pos, here = q == pos;
+            v[q] = sh ? v[q - 1] : (here ? c : v[q]);
+            i[q] = sh ? i[q - 1] : (here ? idx : i[q]);
         }
-    }
-    // insert a column visited in increasing index order (strict > suffices to enter)
-    __device__ __forceinline__ void push(float c, int idx)
-    {
-        if (c > v[K - 1]) insert(c, idx);
+        if (pos == 0) { v[0] = c; i[0] = idx; }
     }
 };
 
+__device__ __forceinline__ float sel16(const float (&a)[16], int q)
+{
+    float r = a[0];
+#pragma unroll
+    for (int k = 1; k < 16; ++k) r = (q == k) ? a[k] : r;
+    return r;
+}
+
 template <int MODE, int K>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(threads_of<MODE>(), 1)
     match_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
                  const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapB2,
                  MatchParams p)
 {
     using C = Cfg<MODE>;
     constexpr int S = C::kStages;
+    constexpr int NB = C::kNB;                  // voxel blocks per CTA
+    constexpr int NBUF = NB == 1 ? 2 : 1;       // accumulator buffers (TMEM holds 512 columns)
+    constexpr int NEPI = 4 * NB;                // epilogue warps
     constexpr uint32_t kStageBytes = stage_bytes<MODE>();
     constexpr uint32_t kIdesc = MODE == MRF_FP8E4M3 ? make_idesc(0, 0, BM, BN) : make_idesc(1, 1, BM, BN);
 
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], tfull_bar[2], tempty_bar[2], drain_bar;
+    __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], tfull_bar[NBUF], tempty_bar[NBUF], drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
 
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    // stage s: [A_hi | A_lo? | B_hi | B_lo?]
-    auto tileA = [&](int s, int op) { return smem + s * kStageBytes + op * kTileA; };
-    auto tileB = [&](int s, int op) { return smem + s * kStageBytes + C::kOps * kTileA + op * kTileB; };
+    // stage s: [A(block 0..NB-1, hi) | A lo? | B hi | B lo?]
+    auto tileA = [&](int s, int op, int i) { return smem + s * kStageBytes + (op * NB + i) * kTileA; };
+    auto tileB = [&](int s, int op) { return smem + s * kStageBytes + C::kOps * NB * kTileA + op * kTileB; };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) { mbar_init(&full_bar[s], 1); mbar_init(&empty_bar[s], 1); }
-        for (int a = 0; a < 2; ++a) { mbar_init(&tfull_bar[a], 1); mbar_init(&tempty_bar[a], 4); }
+        for (int q = 0; q < S; ++q) { mbar_init(&full_bar[q], 1); mbar_init(&empty_bar[q], 1); }
+        for (int a = 0; a < NBUF; ++a) { mbar_init(&tfull_bar[a], 1); mbar_init(&tempty_bar[a], NEPI); }
         mbar_init(&drain_bar, 1);
         abort_flag = 0;
         fence_mbar_init();
@@ -162,18 +174,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem_base = tmem_slot;
 
-    const int n_units = p.n_mb * p.n_chunks;
+    const int n_units = p.n_vu * p.n_chunks;
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
+            // voxel operands are re-read for every dictionary tile: keep them in L2
+            const uint64_t keep = l2_policy_keep();
             int s = 0;
             uint32_t ph = 0;
             bool issued[S];
             uint32_t issued_ph[S];
             for (int q = 0; q < S; ++q) { issued[q] = false; issued_ph[q] = 0; }
             for (int u = blockIdx.x; u < n_units && !abort_flag; u += gridDim.x) {
-                const int chunk = u / p.n_mb, mb = u % p.n_mb;
+                const int chunk = u / p.n_vu, vu = u % p.n_vu;
                 const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
                 const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
                 for (int t = t0; t < t1; ++t) {
@@ -181,8 +195,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kWaitLimitNs)) goto producer_done;
                         mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
                         const int kx = kb * C::kBK;
-                        tma_load_2d(tileA(s, 0), &mapA, &full_bar[s], kx, mb * BM);
-                        if (C::kOps == 2) tma_load_2d(tileA(s, 1), &mapA2, &full_bar[s], kx, mb * BM);
+#pragma unroll
+                        for (int i = 0; i < NB; ++i) {
+                            const int row = (vu * NB + i) * BM;
+                            tma_load_2d_hint(tileA(s, 0, i), &mapA, &full_bar[s], kx, row, keep);
+                            if (C::kOps == 2) tma_load_2d_hint(tileA(s, 1, i), &mapA2, &full_bar[s], kx, row, keep);
+                        }
                         tma_load_2d(tileB(s, 0), &mapB, &full_bar[s], kx, t * BN);
                         if (C::kOps == 2) tma_load_2d(tileB(s, 1), &mapB2, &full_bar[s], kx, t * BN);
                         issued[s] = true;
@@ -204,36 +222,39 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            int s = 0, acc = 0;
-            uint32_t ph = 0, acc_ph = 0;
+            int s = 0, buf = 0;
+            uint32_t ph = 0, buf_ph = 0;
             bool any = false;
             for (int u = blockIdx.x; u < n_units && !abort_flag; u += gridDim.x) {
-                const int chunk = u / p.n_mb;
+                const int chunk = u / p.n_vu;
                 const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
                 const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
                 for (int t = t0; t < t1; ++t) {
-                    if (!mbar_wait_bounded(&tempty_bar[acc], acc_ph ^ 1, &abort_flag, p.err, kWaitLimitNs)) goto mma_done;
+                    if (!mbar_wait_bounded(&tempty_bar[buf], buf_ph ^ 1, &abort_flag, p.err, kWaitLimitNs)) goto mma_done;
                     tc_fence_after();
-                    const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
                     for (int kb = 0; kb < p.k_blocks; ++kb) {
                         if (!mbar_wait_bounded(&full_bar[s], ph, &abort_flag, p.err, kWaitLimitNs)) goto mma_done;
                         tc_fence_after();
-                        const uint64_t a0 = smem_desc_sw128(tileA(s, 0));
                         const uint64_t b0 = smem_desc_sw128(tileB(s, 0));
                         const int nk = (kb == p.k_blocks - 1) ? p.last_ksteps : 4;
                         for (int kk = 0; kk < nk; ++kk) {
                             // advance 32 bytes along K inside the swizzled 128-byte rows
                             const uint64_t adv = (uint64_t)(kk * 32) >> 4;
                             const uint32_t accum = (kb | kk) != 0;
-                            if (MODE == MRF_FP8E4M3) {
-                                mma_f8(d_tmem, a0 + adv, b0 + adv, kIdesc, accum);
-                            } else {
-                                mma_f16(d_tmem, a0 + adv, b0 + adv, kIdesc, accum);
-                                if (MODE == MRF_F32) {
-                                    const uint64_t a1 = smem_desc_sw128(tileA(s, 1));
-                                    const uint64_t b1 = smem_desc_sw128(tileB(s, 1));
-                                    mma_f16(d_tmem, a0 + adv, b1 + adv, kIdesc, 1u);
-                                    mma_f16(d_tmem, a1 + adv, b0 + adv, kIdesc, 1u);
+#pragma unroll
+                            for (int i = 0; i < NB; ++i) {
+                                const uint32_t d_tmem = tmem_base + (uint32_t)((buf * NB + i) * BN);
+                                const uint64_t a0 = smem_desc_sw128(tileA(s, 0, i));
+                                if (MODE == MRF_FP8E4M3) {
+                                    mma_f8(d_tmem, a0 + adv, b0 + adv, kIdesc, accum);
+                                } else {
+                                    mma_f16(d_tmem, a0 + adv, b0 + adv, kIdesc, accum);
+                                    if (MODE == MRF_F32) {
+                                        const uint64_t a1 = smem_desc_sw128(tileA(s, 1, i));
+                                        const uint64_t b1 = smem_desc_sw128(tileB(s, 1));
+                                        mma_f16(d_tmem, a0 + adv, b1 + adv, kIdesc, 1u);
+                                        mma_f16(d_tmem, a1 + adv, b0 + adv, kIdesc, 1u);
+                                    }
                                 }
                             }
                         }
@@ -241,8 +262,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         any = true;
                         if (++s == S) { s = 0; ph ^= 1; }
                     }
-                    mma_commit(&tfull_bar[acc]);     // accumulator ready for the epilogue
-                    if (++acc == 2) { acc = 0; acc_ph ^= 1; }
+                    mma_commit(&tfull_bar[buf]);     // accumulators ready for the epilogue
+                    if (++buf == NBUF) { buf = 0; buf_ph ^= 1; }
                 }
             }
         mma_done:
@@ -257,29 +278,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ---------------- epilogue: TMEM -> CC^2 -> running top-k ----------------
+        const int blk = (warp - 2) / 4;            // which voxel block of the unit
         const int quad = warp & 3;                 // TMEM lane quadrant this warp may access
         const int row = quad * 32 + lane;          // voxel row within the tile
         const int par = row & 1;                   // 0: Re row, 1: Im row
-        int acc = 0;
-        uint32_t acc_ph = 0;
+        int buf = 0;
+        uint32_t buf_ph = 0;
         TopK<K> tk;
         for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
             if (__any_sync(0xffffffffu, abort_flag != 0)) break;
-            const int chunk = u / p.n_mb, mb = u % p.n_mb;
+            const int chunk = u / p.n_vu, vu = u % p.n_vu;
             const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
             const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
             tk.reset();
+            float thr = -1.0f;                     // current K-th best
             for (int t = t0; t < t1; ++t) {
-                const bool ok = mbar_wait_bounded(&tfull_bar[acc], acc_ph, &abort_flag, p.err, kWaitLimitNs);
+                const bool ok = mbar_wait_bounded(&tfull_bar[buf], buf_ph, &abort_flag, p.err, kWaitLimitNs);
                 if (!__all_sync(0xffffffffu, ok)) goto epi_done;   // leave as a whole warp
                 tc_fence_after();
-                const uint32_t tbase = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * BN);
+                const uint32_t tbase =
+                    tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)((buf * NB + blk) * BN);
 #pragma unroll 1
                 for (int ch = 0; ch < BN / 32; ++ch) {
                     uint32_t r[32];
                     tmem_ld_32x32b_x32(tbase + ch * 32, r);
                     tmem_wait_ld();
                     const int col0 = t * BN + ch * 32 + (par ? 16 : 0);
+                    float c2v[16];
+                    uint32_t mask = 0;
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const float mine_lo = __uint_as_float(r[q]);
@@ -290,19 +316,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const float im = par ? mine_hi : recv;
                         float c2 = fmaf(re, re, im * im);
                         const int col = col0 + q;
-                        if (col < p.D) {
-                            if (MODE == MRF_FP8E4M3) {
-                                const float sc = __ldg(&p.colscale[col]);
-                                c2 *= sc * sc;
-                            }
-                            tk.push(c2, col);
+                        if (MODE == MRF_FP8E4M3) {
+                            const float sc = col < p.D ? __ldg(&p.colscale[col]) : 0.f;
+                            c2 *= sc * sc;
                         }
+                        c2v[q] = c2;
+                        mask |= (col < p.D && c2 > thr) ? (1u << q) : 0u;
+                    }
+                    // columns arrive in increasing index order: strictly better enters
+                    while (mask) {
+                        const int q = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        tk.insert(sel16(c2v, q), col0 + q);
+                        thr = tk.v[K - 1];
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty_bar[acc]);
-                if (++acc == 2) { acc = 0; acc_ph ^= 1; }
+                if (lane == 0) mbar_arrive(&tempty_bar[buf]);
+                if (++buf == NBUF) { buf = 0; buf_ph ^= 1; }
             }
             // merge the Re/Im pair's lists (each covered half of the columns):
             // only the even lane inserts, so the odd lane's list stays intact
@@ -311,9 +343,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int q = 0; q < K; ++q) {
                 const float ov = __shfl_xor_sync(0xffffffffu, tk.v[q], 1);
                 const int oi = __shfl_xor_sync(0xffffffffu, tk.i[q], 1);
-                if (par == 0) tk.insert(ov, oi);
+                if (par == 0 && oi != 0x7fffffff) tk.insert(ov, oi);
             }
-            const int64_t v = (int64_t)mb * (BM / 2) + (row >> 1);
+            const int64_t v = (int64_t)(vu * NB + blk) * (BM / 2) + (row >> 1);
             if (par == 0 && v < p.V) {
                 float2 *dst = p.part + ((size_t)v * p.n_chunks + chunk) * K;
 #pragma unroll
@@ -587,10 +619,10 @@ int launch_match_k(mrf_ctx *ctx, const CUtensorMap &mA, const CUtensorMap &mA2, 
         if (e != cudaSuccess) return cuda_fail(e, "matcher shared-memory attribute");
         attr_set = true;
     }
-    const int units = p.n_mb * p.n_chunks;
+    const int units = p.n_vu * p.n_chunks;
     const int grid = std::min(units, ctx->sm_count);
     ProfScope prof(ctx, kProfMatcher, stream);
-    match_kernel<MODE, K><<<grid, kThreads, smem_bytes<MODE>(), stream>>>(mA, mA2, mB, mB2, p);
+    match_kernel<MODE, K><<<grid, threads_of<MODE>(), smem_bytes<MODE>(), stream>>>(mA, mA2, mB, mB2, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "matcher launch");
     return MRF_OK;
@@ -620,12 +652,13 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
 {
     const int mode = precision;
     const int K = top_k;
-    const int64_t V_pad = (V + 63) / 64 * 64;
-    const int n_mb = (int)(V_pad / 64);
+    const int nb = mode == MRF_F32 ? Cfg<MRF_F32>::kNB : Cfg<MRF_BF16>::kNB;   // voxel blocks per CTA
+    const int n_vu = (int)((V + 64 * nb - 1) / (64 * nb));
+    const int64_t V_pad = (int64_t)n_vu * nb * 64;
     const int ebytes = mode == MRF_FP8E4M3 ? 1 : 2;
     const int n_tiles = (int)((d->entries + BN - 1) / BN);
     // chunks: make units a multiple of the SM count where possible
-    int n_chunks = ctx->sm_count / gcd_i(n_mb, ctx->sm_count);
+    int n_chunks = ctx->sm_count / gcd_i(n_vu, ctx->sm_count);
     n_chunks = std::max(1, std::min(n_chunks, n_tiles));
     const int kbe = mode == MRF_FP8E4M3 ? 128 : 64;    // elements per K block
     const int k_blocks = (2 * d->n + kbe - 1) / kbe;   // K blocks holding at least one real element
@@ -683,7 +716,7 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     p.D = d->entries;
     p.V = V;
     p.n_tiles = n_tiles;
-    p.n_mb = n_mb;
+    p.n_vu = n_vu;
     p.n_chunks = n_chunks;
     p.k_blocks = k_blocks;
     p.last_ksteps = last_ksteps;

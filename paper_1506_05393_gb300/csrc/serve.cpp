@@ -75,7 +75,8 @@ size_t batch_bytes(const mrf_ctx *ctx, const Req &r, int64_t V)
 {
     size_t b = (size_t)V * r.n * 8 + (size_t)V * sizeof(mrf_result) + 4096;
     if (r.mode == MRF_MODE_BRUTE) {
-        const int64_t vp = (V + 63) / 64 * 64;
+        const int64_t blk = r.dict->dtype == MRF_F32 ? 64 : 128;   // voxels per matcher work unit
+        const int64_t vp = (V + blk - 1) / blk * blk;
         const size_t eb = r.dict->dtype == MRF_FP8E4M3 ? 1 : 2;
         b += (size_t)(2 * vp) * r.dict->ld * eb * (r.dict->dtype == MRF_F32 ? 2 : 1);
         b += (size_t)V * ctx->sm_count * r.match.top_k * 8 + (size_t)V * r.match.top_k * 12 + 8 * 1024;

@@ -231,47 +231,125 @@ __device__ void df_scan(const ZoomArgs &A, const float2 *x, Search &S, int count
     close_margin(S, t1, t2);
 }
 
-// 2D ZOOM at (h1, h2): the 8 neighbours in the fixed order (T1 offset outer).
+// Speculative batches. A round evaluates more points than the next canonical
+// decision needs (a whole line of 1D points, a 5x5 block of 2D points); the
+// canonical eager decisions are then replayed on those values, lane by lane
+// through shuffles, until a decision needs a point outside the batch. The
+// replay takes exactly the decisions, margins and evaluation counts of the
+// one-move-per-round search: values are deterministic, so a point evaluated
+// speculatively has the value the canonical search would compute.
+
+// 2D ZOOM at (h1, h2): each round evaluates the 5x5 block (offsets -2..2 in
+// units of h) around the current centre; the replay visits the 8 neighbours
+// in the fixed order (T1 offset outer, -1 before +1).
 template <bool XONLY>
 __device__ bool move2d(const ZoomArgs &A, const float2 *x, Search &S, int h1, int h2)
 {
     const int lane = threadIdx.x & 31;
-    const int k = lane < 4 ? lane : lane + 1;        // skip the centre (0, 0)
-    const int da = k / 3 - 1, db = k % 3 - 1;
-    for (int it = 0; it < A.max_moves; ++it) {
-        const int na = S.a + da * h1, nb = S.b + db * h2;
-        const Eval e = eval_point<XONLY>(A, x, S.inv_xn, lane < 8, na, nb, S.c);
-        S.evaluated += __popc(__ballot_sync(0xffffffffu, isfinite(e.v)));
-        float t1 = S.centre, t2 = -INFINITY;
-        warp_top2(e.v, t1, t2);
-        close_margin(S, t1, t2);
-        float bv;
-        const int bl = warp_best(e.v, lane, bv);
-        if (bv > S.centre) take(S, e, bl, na, nb, S.c, bv);
-        else return true;
+    // lane -> block offset: 24 points of the 5x5 block without its centre
+    const int k = lane < 12 ? lane : lane + 1;
+    const int oa = k / 5 - 2, ob = k % 5 - 2;
+    int moves = 0;
+    for (;;) {
+        const int ba = S.a, bb = S.b;                 // block centre
+        const float bc = S.centre;                    // its value (known)
+        const float bcr = S.cr, bci = S.ci, bcd = S.cd;
+        const int na = ba + oa * h1, nb = bb + ob * h2;
+        const Eval e = eval_point<XONLY>(A, x, S.inv_xn, lane < 24, na, nb, S.c);
+        int ma = 0, mb = 0;                           // replay position in block units
+        for (;;) {
+            if (ma < -1 || ma > 1 || mb < -1 || mb > 1) break;   // neighbours leave the block
+            if (++moves > A.max_moves) return false;
+            float best = -INFINITY, t1 = S.centre, t2 = -INFINITY;
+            int bl = -1, bda = 0, bdb = 0, cnt = 0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                if (q == 4) continue;
+                const int da = q / 3 - 1, db = q % 3 - 1;
+                const int pa = ma + da, pb = mb + db;
+                float v;
+                int src = -1;
+                if (pa == 0 && pb == 0) {
+                    v = bc;
+                } else {
+                    const int kk = (pa + 2) * 5 + (pb + 2);
+                    src = kk < 12 ? kk : kk - 1;
+                    v = __shfl_sync(0xffffffffu, e.v, src);
+                }
+                if (isfinite(v)) {
+                    ++cnt;
+                    if (v > t1) { t2 = t1; t1 = v; } else if (v > t2) t2 = v;
+                }
+                if (v > best) { best = v; bl = src; bda = da; bdb = db; }
+            }
+            S.evaluated += cnt;
+            close_margin(S, t1, t2);
+            if (!(best > S.centre)) return true;      // the centre wins: this level is done
+            ma += bda;
+            mb += bdb;
+            if (bl >= 0) {
+                take(S, e, bl, na, nb, S.c, best);
+            } else {                                  // back to the block centre (values only rise, so unused)
+                S.a = ba; S.b = bb; S.centre = best; S.cr = bcr; S.ci = bci; S.cd = bcd;
+            }
+        }
+        // the next decision needs points outside this block: re-centre
+        S.a = ba + ma * h1;
+        S.b = bb + mb * h2;
     }
-    return false;
 }
 
-// 1D ZOOM along T1 (param 0) or T2 (param 1) at half-width h: left then right.
+// 1D ZOOM along T1 (param 0) or T2 (param 1) at half-width h: each round
+// evaluates the points at -16h..16h; the replay compares left then right.
 template <bool XONLY>
 __device__ bool move1d(const ZoomArgs &A, const float2 *x, Search &S, int param, int h)
 {
     const int lane = threadIdx.x & 31;
-    const int sgn = lane == 0 ? -1 : 1;
-    for (int it = 0; it < A.max_moves; ++it) {
-        const int na = S.a + (param == 0 ? sgn * h : 0), nb = S.b + (param == 1 ? sgn * h : 0);
-        const Eval e = eval_point<XONLY>(A, x, S.inv_xn, lane < 2, na, nb, S.c);
-        S.evaluated += __popc(__ballot_sync(0xffffffffu, isfinite(e.v)));
-        float t1 = S.centre, t2 = -INFINITY;
-        warp_top2(e.v, t1, t2);
-        close_margin(S, t1, t2);
-        float bv;
-        const int bl = warp_best(e.v, lane, bv);
-        if (bv > S.centre) take(S, e, bl, na, nb, S.c, bv);
-        else return true;
+    const int off = lane < 16 ? lane - 16 : lane - 15;      // -16..-1, 1..16
+    int moves = 0;
+    for (;;) {
+        const int ba = S.a, bb = S.b;
+        const float bc = S.centre;
+        const float bcr = S.cr, bci = S.ci, bcd = S.cd;
+        const int na = ba + (param == 0 ? off * h : 0), nb = bb + (param == 1 ? off * h : 0);
+        const Eval e = eval_point<XONLY>(A, x, S.inv_xn, true, na, nb, S.c);
+        int m = 0;
+        for (;;) {
+            if (m <= -16 || m >= 16) break;
+            if (++moves > A.max_moves) return false;
+            float vals[2];
+            int srcs[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int p = m + (q == 0 ? -1 : 1);
+                if (p == 0) { vals[q] = bc; srcs[q] = -1; }
+                else {
+                    srcs[q] = p < 0 ? p + 16 : p + 15;
+                    vals[q] = __shfl_sync(0xffffffffu, e.v, srcs[q]);
+                }
+            }
+            float t1 = S.centre, t2 = -INFINITY;
+            int cnt = 0;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float v = vals[q];
+                if (isfinite(v)) {
+                    ++cnt;
+                    if (v > t1) { t2 = t1; t1 = v; } else if (v > t2) t2 = v;
+                }
+            }
+            S.evaluated += cnt;
+            close_margin(S, t1, t2);
+            const int pick = vals[1] > vals[0] ? 1 : 0;
+            const float best = vals[pick];
+            if (!(best > S.centre)) return true;
+            m += pick == 0 ? -1 : 1;
+            if (srcs[pick] >= 0) take(S, e, srcs[pick], na, nb, S.c, best);
+            else { S.a = ba; S.b = bb; S.centre = best; S.cr = bcr; S.ci = bci; S.cd = bcd; }
+        }
+        S.a = ba + (param == 0 ? m * h : 0);
+        S.b = bb + (param == 1 ? m * h : 0);
     }
-    return false;
 }
 
 template <bool XONLY>
