@@ -57,6 +57,28 @@ def peaks():
         return p
 
 
+# ---------------------------------------------------------------------------- ranks
+
+def rank_seed(rank: int) -> int:
+    """Phantom seed of a rank's slice: every rank matches its own slice."""
+    return 101 + 1000 * rank
+
+
+def reduce_max(value: float, dist) -> float:
+    """Slowest rank's time (max over ranks); identity without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def whole_job_rate(world: int, voxels_per_rank: int, ms: float) -> float:
+    """Voxels per second of the whole job: all ranks' voxels over the slowest time."""
+    return world * voxels_per_rank / ms * 1e3
+
+
 # ---------------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -149,7 +171,15 @@ def timed(fn, reps):
     return s.elapsed_time(e) / reps
 
 
-def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz):
+def param_errors(res, ph):
+    """Median absolute T1 / T2 / df error of matched voxels against the phantom's truth."""
+    ok = res["index"] >= 0
+    return {"t1_ms": float(np.median(np.abs(res["t1_ms"][ok] - ph["t1"][ok]))),
+            "t2_ms": float(np.median(np.abs(res["t2_ms"][ok] - ph["t2"][ok]))),
+            "df_hz": float(np.median(np.abs(res["df_hz"][ok] - ph["df"][ok])))}
+
+
+def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
     """One timing per extra mode, with index agreement against FP32 brute force."""
     import torch
     modes = {}
@@ -183,11 +213,14 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz):
                  "peak_tflops": peak, "peak_note": "bf16 measured" + (" x 2 (fp8 nominal ratio)" if dtype == 2 else "")}
         if ref_index is not None:
             entry["index_agreement_vs_fp32"] = float(np.mean(res["index"] == ref_index))
+        if ph is not None:
+            entry["median_abs_error_vs_truth"] = param_errors(res, ph)
         M.mrf_dict_free(ctx, d)
         modes[name] = entry
         return res
 
     match_mode("bf16_rescore_k8", GRID, M.MRF_BF16, 8, fp32_index)
+    match_mode("bf16_rescore_k32", GRID, M.MRF_BF16, 32, fp32_index)
     match_mode("fp8_rescore_k32", GRID, M.MRF_FP8E4M3, 32, fp32_index)
 
     # ZOOM on the same grid and voxels (agreement with brute force)
@@ -200,6 +233,8 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz):
     modes["zoom_same_grid"] = {"grid": GRID, "voxels_per_s": V / ms * 1e3, "ms": ms,
                                "mean_entries_evaluated": float(res["entries_evaluated"].mean()),
                                "index_agreement_vs_fp32": float(np.mean(res["index"] == fp32_index))}
+    if ph is not None:
+        modes["zoom_same_grid"]["median_abs_error_vs_truth"] = param_errors(res, ph)
 
     # finer grids: BF16 / FP8 + re-score on the 12,024,855-entry grid, FP32 there for agreement
     ref = match_mode("fp32_fine_grid", "precision", M.MRF_F32, 4)
@@ -242,6 +277,102 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz):
                      "note": f"{FLOPS_PER_TP:.0f} FP32 flops per timepoint per evaluated candidate; peak = "
                              f"{sms} SMs x 128 FMA/clk x 2 x {clk:.0f} MHz"}}
     return modes
+
+
+def run_serving_trace(M, n_requests=40, seed=104, rate_hz=50.0, budget_gb=120.0, max_inflight=3):
+    """Poisson stream of slice requests through the serving loop: voxel counts
+    uniform over {16x16, 32x32, 64x64, 128x128}, modes uniform over FP32 brute
+    force (614,508-entry grid), BF16 + re-score (12,024,855-entry grid) and
+    ZOOM (2.4e9-entry grid); dictionaries and sequence resident; admission
+    under the HBM budget. Latency = completion - arrival."""
+    import threading
+    import torch
+    ctx = M.mrf_ctx_create(0, int(budget_gb * 1e9))
+    try:
+        seq = S.sequence(1, N_TP)
+        h = M.mrf_sequence_load(ctx, seq)
+        d32 = M.mrf_dict_generate(ctx, h, S.GRIDS["fp32_brute"], M.MRF_F32)
+        d16 = M.mrf_dict_generate(ctx, h, S.GRIDS["precision"], M.MRF_BF16)
+        torch.cuda.synchronize()
+        used, budget = M.mrf_ctx_memory(ctx)
+        _, pool = make_slice(M, ctx, h, seed, 128 * 128, 20.0)
+        rng = np.random.default_rng(seed)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, n_requests))
+        sizes = rng.choice([256, 1024, 4096, 16384], n_requests)
+        modes = rng.integers(0, 3, n_requests)
+        offs = [int(rng.integers(0, 128 * 128 - v + 1)) for v in sizes]
+        zo = M.zoom_opts()
+        gz = M.grid_desc(S.GRIDS["zoom_fine"])
+        M.mrf_serve_start(ctx, max_inflight=max_inflight, max_batch_voxels=32768)
+        tickets, keep = [None] * n_requests, []
+        done_t = [None] * n_requests
+        t0 = time.perf_counter()
+        lock = threading.Lock()
+
+        def submitter():
+            for i in range(n_requests):
+                delay = t0 + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                x = pool[offs[i]: offs[i] + sizes[i]]
+                r = M.Request()
+                r.mode = M.MRF_MODE_BRUTE if modes[i] < 2 else M.MRF_MODE_ZOOM
+                r.V = int(sizes[i])
+                r.fp_host = x.ctypes.data
+                if modes[i] == 0:
+                    r.dict, r.match = d32.value, M.match_opts(M.MRF_F32, 4, 1)
+                elif modes[i] == 1:
+                    r.dict, r.match = d16.value, M.match_opts(M.MRF_BF16, 8, 1)
+                else:
+                    r.seq, r.grid, r.zoom = h.value, C_pointer(gz), C_pointer(zo)
+                t = M.mrf_serve_submit(ctx, r)
+                with lock:
+                    tickets[i] = t
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        pending = set(range(n_requests))
+        outs = {}
+        while pending:
+            for i in list(pending):
+                with lock:
+                    t = tickets[i]
+                if t is None:
+                    continue
+                if i not in outs:
+                    outs[i] = np.zeros(int(sizes[i]), M.RESULT_DTYPE)
+                rc = M.mrf_serve_poll_rc(ctx, t, 0, outs[i])
+                if rc == M.MRF_OK:
+                    done_t[i] = time.perf_counter() - t0
+                    pending.discard(i)
+                elif rc != M.MRF_PENDING:
+                    raise M.MrfError(rc, M.last_error())
+            time.sleep(0.0005)
+        th.join()
+        st = M.mrf_serve_get_stats(ctx)
+        M.mrf_serve_stop(ctx)
+        lat = (np.array(done_t) - arrivals) * 1e3
+        span = max(done_t) - arrivals[0]
+        res = {"requests": n_requests, "rate_hz": rate_hz, "budget_gb": budget_gb,
+               "resident_gb": used / 1e9, "voxels": int(sizes.sum()),
+               "voxels_per_s": float(sizes.sum() / span), "p50_ms": float(np.percentile(lat, 50)),
+               "p99_ms": float(np.percentile(lat, 99)), "max_inflight": max_inflight,
+               "launches": int(st.launches), "peak_request_bytes_gb": st.request_bytes_peak / 1e9,
+               "by_mode": {name: {"requests": int((modes == m).sum()),
+                                  "p50_ms": float(np.percentile(lat[modes == m], 50)) if (modes == m).any() else None}
+                           for m, name in enumerate(["fp32_brute", "bf16_rescore_fine", "zoom_fine"])},
+               "note": "offered load exceeds one GPU (about 6 GPU-seconds per second): latencies include queueing"}
+        M.mrf_dict_free(ctx, d32)
+        M.mrf_dict_free(ctx, d16)
+        M.mrf_sequence_free(ctx, h)
+        return res
+    finally:
+        M.mrf_ctx_destroy(ctx)
+
+
+def C_pointer(x):
+    import ctypes
+    return ctypes.pointer(x)
 
 
 def cpu_baseline(seq, x_np):
@@ -347,6 +478,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-modes", action="store_true", help="skip the extra mode measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace measurement")
     ap.add_argument("--ncu-case", choices=["matcher", "matcher_bf16", "matcher_fp8", "zoom", "dictgen"],
                     help="run one small launch of a kernel for an ncu capture, print nothing else")
     args = ap.parse_args()
@@ -377,7 +509,7 @@ def main():
     seq_h = M.mrf_sequence_load(ctx, seq)
     g = S.GRIDS[GRID]
     D = M.mrf_grid_count(g)
-    ph, x_np = make_slice(M, ctx, seq_h, 101 + 1000 * rank, V_SLICE, 20.0)
+    ph, x_np = make_slice(M, ctx, seq_h, rank_seed(rank), V_SLICE, 20.0)
     x_dev = torch.from_numpy(x_np).cuda()
     out = M.empty_results(V_SLICE)
     stream = torch.cuda.current_stream()
@@ -415,11 +547,8 @@ def main():
     rc = M.lib().mrf_stream_sync(ctx, M._stream_ptr(stream))
     if rc != 0:
         raise M.MrfError(rc, M.last_error())
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
-    value = world * V_SLICE / ms * 1e3
+    ms = reduce_max(ms, dist)
+    value = whole_job_rate(world, V_SLICE, ms)
 
     # end to end through the public API: pinned host fingerprints in, results out
     x_pin = torch.from_numpy(x_np).pin_memory()
@@ -442,10 +571,7 @@ def main():
     for _ in range(args.steps):
         e2e_step()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    if dist:
-        t = torch.tensor([e2e_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t[0])
+    e2e_ms = reduce_max(e2e_ms, dist)
 
     matcher_ms = prof.matcher_ms / max(prof.matcher_timed, 1)
     flops = 8.0 * N_TP * D * V_SLICE
@@ -473,17 +599,23 @@ def main():
                    "phantom": "T1 log-U(200,3000) ms, T2 log-U(20,300) ms (T2<T1), df U(-40,40) Hz, "
                               "M0 U(0.5,1), SNR 20 complex Gaussian; seed 101 + 1000*rank"},
         "clocks": clk,
-        "e2e": {"value": world * V_SLICE / e2e_ms * 1e3, "unit": UNIT,
+        "e2e": {"value": whole_job_rate(world, V_SLICE, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": int(x_pin.numel() * 8), "d2h_bytes_per_step": int(out_pin.numel())},
         "gpu_launches": int(prof.launches),
+        "step_breakdown_ms": {"matcher": matcher_ms,
+                              "dict_generate": prof.dictgen_ms / max(prof.dictgen_timed, 1),
+                              "rest": ms - matcher_ms - prof.dictgen_ms / max(prof.dictgen_timed, 1)},
         "roofline": roof,
     }
+    line["median_abs_error_vs_truth"] = param_errors(fp32_res, ph)
     if not args.no_modes:
-        line["modes"] = run_modes(M, ctx, seq, seq_h, x_dev, fp32_res["index"], pk, clk.get("sm_mhz"))
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(seq, x_np)
+        line["modes"] = run_modes(M, ctx, seq, seq_h, x_dev, fp32_res["index"], pk, clk.get("sm_mhz"), ph)
     M.mrf_sequence_free(ctx, seq_h)
     M.mrf_ctx_destroy(ctx)
+    if not args.no_serving and not args.no_modes:
+        line["serving"] = run_serving_trace(M)
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(seq, x_np)
     print(json.dumps(line), flush=True)
 
 

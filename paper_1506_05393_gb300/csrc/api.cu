@@ -134,6 +134,8 @@ extern "C" void mrf_ctx_destroy(mrf_ctx *ctx)
     if (ctx->serve) mrf_serve_stop(ctx);
     cudaDeviceSynchronize();
     cudaFree(ctx->err_flag);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
     delete ctx;
 }
 
@@ -254,7 +256,7 @@ extern "C" int mrf_sequence_load(mrf_ctx *ctx, const mrf_sequence_desc *d, mrf_s
         // a rotation about x by beta = -alpha (k even) or +alpha (k odd).
         double beta = cos(ph) > 0 ? -a : a;
         double c = cos(beta), s = sin(beta), sh = sin(0.5 * beta);
-        rfx[j] = make_float4((float)c, (float)s, (float)(2.0 * sh * sh), 0.f);
+        rfx[j] = make_float4((float)c, (float)s, (float)(2.0 * sh * sh), (float)d->te_ms[j]);
         // general matrix: rotation by -alpha about (cos phi, sin phi, 0) (Rodrigues)
         double kx = cos(ph), ky = sin(ph), th = -a;
         double ct = cos(th), st = sin(th), vt = 2.0 * sin(0.5 * th) * sin(0.5 * th);
@@ -490,12 +492,13 @@ extern "C" int mrf_dict_free(mrf_ctx *ctx, mrf_dict *d)
 {
     if (!ctx || !d) return set_error(MRF_E_INVALID, "NULL argument");
     cudaSetDevice(ctx->device);
-    const size_t ebytes = d->dtype == MRF_FP8E4M3 ? 1 : 2;
-    const size_t rows = (size_t)d->entries * d->ld * ebytes;
-    if (d->hi) dev_free(ctx, d->hi, rows);
-    if (d->lo) dev_free(ctx, d->lo, rows);
-    if (d->norm) dev_free(ctx, d->norm, 4 * (size_t)d->entries);
-    if (d->scale) dev_free(ctx, d->scale, 4 * (size_t)d->entries);
+    if (d->block) {
+        // work on any stream may still read the dictionary: wait for the
+        // device, then hand the block back to the pool (no unmapping)
+        cudaDeviceSynchronize();
+        cudaFreeAsync(d->block, 0);
+        budget_release(ctx, d->block_bytes);
+    }
     grid_release(ctx, &d->grid);
     seq_release(ctx, d->seq);
     delete d;
@@ -524,13 +527,28 @@ extern "C" int mrf_dict_generate(mrf_ctx *ctx, const mrf_seq *seq, const mrf_gri
     rc = grid_upload(ctx, grid, &d->grid);
     const size_t ebytes = dtype == MRF_FP8E4M3 ? 1 : 2;
     const size_t rows = (size_t)count * d->ld * ebytes;
-    if (!rc) rc = dev_alloc(ctx, &d->hi, rows, "dictionary");
-    if (!rc && dtype == MRF_F32) rc = dev_alloc(ctx, &d->lo, rows, "dictionary residual");
-    if (!rc) rc = dev_alloc(ctx, (void **)&d->norm, 4 * (size_t)count, "dictionary norms");
-    if (!rc && dtype == MRF_FP8E4M3) rc = dev_alloc(ctx, (void **)&d->scale, 4 * (size_t)count, "dictionary scales");
+    // hi | lo | norm | scale in one block from the stream-ordered pool, so
+    // that generating and freeing dictionaries repeatedly maps no new memory
+    auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+    const size_t b_lo = dtype == MRF_F32 ? al(rows) : 0, b_sc = dtype == MRF_FP8E4M3 ? al(4 * (size_t)count) : 0;
+    const size_t total = al(rows) + b_lo + al(4 * (size_t)count) + b_sc;
+    if (!rc) rc = budget_charge(ctx, total);
+    if (!rc) {
+        cudaError_t e = cudaMallocAsync(&d->block, total, (cudaStream_t)stream);
+        if (e != cudaSuccess) {
+            budget_release(ctx, total);
+            d->block = nullptr;
+            rc = cuda_fail(e, "dictionary");
+        }
+    }
     if (rc) { mrf_dict_free(ctx, d); return rc; }
-    d->bytes = rows * (dtype == MRF_F32 ? 2 : 1) + 4 * (size_t)count * (dtype == MRF_FP8E4M3 ? 2 : 1) +
-               d->grid.bytes + d->seq->bytes;
+    d->block_bytes = total;
+    uint8_t *blk = (uint8_t *)d->block;
+    d->hi = blk;
+    d->lo = dtype == MRF_F32 ? blk + al(rows) : nullptr;
+    d->norm = (float *)(blk + al(rows) + b_lo);
+    d->scale = dtype == MRF_FP8E4M3 ? (float *)(blk + al(rows) + b_lo + al(4 * (size_t)count)) : nullptr;
+    d->bytes = total + d->grid.bytes + d->seq->bytes;
     rc = launch_dict_generate(ctx, d, (cudaStream_t)stream);
     if (rc) { mrf_dict_free(ctx, d); return rc; }
     *out = d;

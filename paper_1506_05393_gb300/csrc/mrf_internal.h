@@ -24,7 +24,7 @@ struct SeqDev {
     int symmetric;      // TE_j == TR_j - TE_j for every j (one evolution factor per step)
     int inversion;
     float inv_delay;    // ms
-    const float4 *rfx;  // xonly: (c, s, 1 - c, 0) of the x-rotation by beta_j
+    const float4 *rfx;  // xonly: (c, s, 1 - c, TE_j) of the x-rotation by beta_j
     const float *rfg;   // general: 12 floats per j: R00..R22 row-major, 1 - R22, 0, 0
     const float2 *tau;  // (TE_j, TR_j - TE_j) in ms
 };
@@ -85,6 +85,8 @@ struct mrf_dict {
     void *lo = nullptr;
     float *norm = nullptr;
     float *scale = nullptr;
+    void *block = nullptr;       // one stream-ordered pool allocation holding hi, lo, norm, scale
+    size_t block_bytes = 0;
     size_t bytes = 0;
 };
 

@@ -25,6 +25,10 @@ namespace {
 
 constexpr int kMaxLevels = MRF_ZOOM_MAX_LEVELS;
 constexpr int kZoomThreads = 256;   // 8 voxels (warps) per CTA
+#ifndef MRF_ZOOM_SCAN_W
+#define MRF_ZOOM_SCAN_W 2
+#endif
+constexpr int kScanW = MRF_ZOOM_SCAN_W;   // df-scan candidates per lane (share T1/T2 factors)
 
 struct ZoomPlan {
     int a0, b0;          // start of the df search
@@ -62,59 +66,186 @@ struct Kahan {
     }
 };
 
-// Evolution factors with the SFU sine/cosine (argument reduced to [-pi, pi]).
-__device__ __forceinline__ void factors_fast(const Relax &r, float tau, float &e1, float &zr, float &zi)
+// 2^x on the SFU (PTX ex2.approx.ftz; relative error about 2^-22).
+__device__ __forceinline__ float ex2_fast(float x)
 {
-    e1 = exp2f(r.k1 * tau);
-    const float e2 = exp2f(r.k2 * tau);
-    float t = r.f * tau;
-    t -= rintf(t);
-    float sn, cs;
-    __sincosf(6.283185307179586f * t, &sn, &cs);
-    zr = e2 * cs;
-    zi = e2 * sn;
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
-// Simulate one candidate and correlate it with x (all lanes call this together).
-template <bool XONLY>
-__device__ __forceinline__ void sim_dot(const SeqDev &s, const float2 *__restrict__ x, float T1, float T2, float df,
-                                        float &ipr, float &ipi, float &dd)
+// e^{i 2 pi f tau} on the SFU, argument first reduced to [-1/2, 1/2] cycles.
+__device__ __forceinline__ void cis_fast(float f, float tau, float &cs, float &sn)
 {
-    const Relax r = relax_make(T1, T2, df);
-    Bloch st;
-    bloch_start(st, s, r);
+    float t = f * tau;
+    t -= rintf(t);
+    __sincosf(6.283185307179586f * t, &sn, &cs);
+}
+
+// Start state of a candidate: equilibrium, or inverted and relaxed over the
+// inversion delay (transverse magnetisation is zero after an ideal inversion).
+__device__ __forceinline__ void start_state(Bloch &st, const SeqDev &s, float k1)
+{
+    bloch_init(st);
+    if (s.inversion) {
+        bloch_invert(st);
+        st.w *= ex2_fast(k1 * s.inv_delay);
+    }
+}
+
+struct Acc {   // x conj(d) and ||d||^2 in 16-timepoint FP32 blocks, Kahan-summed
     Kahan kr, ki, kd;
-    kr.init(); ki.init(); kd.init();
+    float pr, pi, pd;
+    __device__ __forceinline__ void init() { kr.init(); ki.init(); kd.init(); pr = pi = pd = 0.f; }
+    __device__ __forceinline__ void add(float2 z, float sr, float si)
+    {
+        pr = fmaf(z.x, sr, fmaf(z.y, si, pr));
+        pi = fmaf(z.y, sr, fmaf(-z.x, si, pi));
+        pd = fmaf(sr, sr, fmaf(si, si, pd));
+    }
+    __device__ __forceinline__ void flush() { kr.add(pr); ki.add(pi); kd.add(pd); pr = pi = pd = 0.f; }
+};
+
+struct Eval {
+    float v;                  // CC, -inf if the point is not evaluated
+    float ipr, ipi, dd;
+};
+
+// One timepoint of one candidate with per-candidate factors.
+template <bool XONLY>
+__device__ __forceinline__ void step1(Bloch &st, const SeqDev &s, float k1, float k2, float f, int j, float &sr,
+                                      float &si)
+{
+    float ta;
+    if (XONLY) {
+        const float4 r = __ldg(&s.rfx[j]);
+        bloch_rf_x(st, r);
+        ta = r.w;
+    } else {
+        bloch_rf<false>(st, s, j);
+        ta = __ldg(&s.tau[j]).x;
+    }
+    float cs, sn;
+    const float e1 = ex2_fast(k1 * ta), e2 = ex2_fast(k2 * ta);
+    cis_fast(f, ta, cs, sn);
+    bloch_evolve(st, e1, e2 * cs, e2 * sn);
+    sr = st.mx;
+    si = st.my;
+    if (s.symmetric) {
+        bloch_evolve(st, e1, e2 * cs, e2 * sn);
+    } else {
+        const float tb = __ldg(&s.tau[j]).y;
+        const float e1b = ex2_fast(k1 * tb), e2b = ex2_fast(k2 * tb);
+        cis_fast(f, tb, cs, sn);
+        bloch_evolve(st, e1b, e2b * cs, e2b * sn);
+    }
+}
+
+// Simulate one candidate and correlate it with x (all lanes call this
+// together; kept out of line so the hot loop exists once).
+template <bool XONLY>
+__device__ __forceinline__ Eval sim_candidate(const SeqDev &s, const float2 *__restrict__ x, float T1, float T2, float df,
+                                           float inv_xn, bool ok)
+{
+    const float k1 = -1.4426950408889634f / T1, k2 = -1.4426950408889634f / T2, f = df * 1.0e-3f;
+    Bloch st;
+    start_state(st, s, k1);
+    Acc acc;
+    acc.init();
+    const int n = s.n;
+    int j0 = 0;
+    for (; j0 + 16 <= n; j0 += 16) {
+#pragma unroll 4
+        for (int u = 0; u < 16; ++u) {
+            float sr, si;
+            step1<XONLY>(st, s, k1, k2, f, j0 + u, sr, si);
+            acc.add(__ldg(&x[j0 + u]), sr, si);
+        }
+        acc.flush();
+    }
+    for (int j = j0; j < n; ++j) {
+        float sr, si;
+        step1<XONLY>(st, s, k1, k2, f, j, sr, si);
+        acc.add(__ldg(&x[j]), sr, si);
+    }
+    acc.flush();
+    Eval e;
+    e.ipr = acc.kr.s;
+    e.ipi = acc.ki.s;
+    e.dd = acc.kd.s;
+    if (ok) {
+        const float mag = sqrtf(fmaf(e.ipr, e.ipr, e.ipi * e.ipi));
+        e.v = (e.dd > 0.f && inv_xn > 0.f) ? mag * inv_xn * rsqrtf(e.dd) : 0.f;
+    } else {
+        e.v = -INFINITY;
+    }
+    return e;
+}
+
+// kScanW candidates that share (T1, T2) and differ in df (a df scan): the
+// relaxation factors are computed once per timepoint for all of them.
+template <bool XONLY>
+__device__ __forceinline__ void sim_df4(const SeqDev &s, const float2 *__restrict__ x, float T1, float T2,
+                                     const float (&df)[kScanW], float inv_xn, const bool (&ok)[kScanW],
+                                     Eval (&out)[kScanW])
+{
+    const float k1 = -1.4426950408889634f / T1, k2 = -1.4426950408889634f / T2;
+    float f[kScanW];
+    Bloch st[kScanW];
+    Acc acc[kScanW];
+#pragma unroll
+    for (int u = 0; u < kScanW; ++u) {
+        f[u] = df[u] * 1.0e-3f;
+        start_state(st[u], s, k1);
+        acc[u].init();
+    }
     const int n = s.n;
     for (int j0 = 0; j0 < n; j0 += 16) {
-        float pr = 0.f, pi = 0.f, pd = 0.f;
         const int j1 = min(n, j0 + 16);
         for (int j = j0; j < j1; ++j) {
-            bloch_rf<XONLY>(st, s, j);
-            const float2 tau = __ldg(&s.tau[j]);
-            float e1, zr, zi;
-            factors_fast(r, tau.x, e1, zr, zi);
-            bloch_evolve(st, e1, zr, zi);
-            const float sr = st.mx, si = st.my;
-            if (s.symmetric) {
-                bloch_evolve(st, e1, zr, zi);
+            float ta, tb;
+            if (XONLY) {
+                const float4 r = __ldg(&s.rfx[j]);
+#pragma unroll
+                for (int u = 0; u < kScanW; ++u) bloch_rf_x(st[u], r);
+                ta = r.w;
+                tb = s.symmetric ? ta : __ldg(&s.tau[j]).y;
             } else {
-                factors_fast(r, tau.y, e1, zr, zi);
-                bloch_evolve(st, e1, zr, zi);
+#pragma unroll
+                for (int u = 0; u < kScanW; ++u) bloch_rf<false>(st[u], s, j);
+                const float2 t2 = __ldg(&s.tau[j]);
+                ta = t2.x;
+                tb = t2.y;
             }
+            const float e1a = ex2_fast(k1 * ta), e2a = ex2_fast(k2 * ta);
+            const float e1b = s.symmetric ? e1a : ex2_fast(k1 * tb), e2b = s.symmetric ? e2a : ex2_fast(k2 * tb);
             const float2 z = __ldg(&x[j]);
-            // x conj(d)
-            pr = fmaf(z.x, sr, fmaf(z.y, si, pr));
-            pi = fmaf(z.y, sr, fmaf(-z.x, si, pi));
-            pd = fmaf(sr, sr, fmaf(si, si, pd));
+#pragma unroll
+            for (int u = 0; u < kScanW; ++u) {
+                float cs, sn;
+                cis_fast(f[u], ta, cs, sn);
+                bloch_evolve(st[u], e1a, e2a * cs, e2a * sn);
+                acc[u].add(z, st[u].mx, st[u].my);
+                if (!s.symmetric) cis_fast(f[u], tb, cs, sn);
+                bloch_evolve(st[u], e1b, e2b * cs, e2b * sn);
+            }
         }
-        kr.add(pr);
-        ki.add(pi);
-        kd.add(pd);
+#pragma unroll
+        for (int u = 0; u < kScanW; ++u) acc[u].flush();
     }
-    ipr = kr.s;
-    ipi = ki.s;
-    dd = kd.s;
+#pragma unroll
+    for (int u = 0; u < kScanW; ++u) {
+        Eval &e = out[u];
+        e.ipr = acc[u].kr.s;
+        e.ipi = acc[u].ki.s;
+        e.dd = acc[u].kd.s;
+        if (ok[u]) {
+            const float mag = sqrtf(fmaf(e.ipr, e.ipr, e.ipi * e.ipi));
+            e.v = (e.dd > 0.f && inv_xn > 0.f) ? mag * inv_xn * rsqrtf(e.dd) : 0.f;
+        } else {
+            e.v = -INFINITY;
+        }
+    }
 }
 
 __device__ __forceinline__ bool point_valid(const GridDev &g, int a, int b, int c)
@@ -132,11 +263,6 @@ struct Search {
     float inv_xn;
 };
 
-struct Eval {
-    float v;                  // CC, -inf if the point is not evaluated
-    float ipr, ipi, dd;
-};
-
 template <bool XONLY>
 __device__ __forceinline__ Eval eval_point(const ZoomArgs &A, const float2 *x, float inv_xn, bool want, int a, int b,
                                            int c)
@@ -145,15 +271,7 @@ __device__ __forceinline__ Eval eval_point(const ZoomArgs &A, const float2 *x, f
     const float T1 = ok ? __ldg(&A.g.t1[a]) : 1000.f;
     const float T2 = ok ? __ldg(&A.g.t2[b]) : 100.f;
     const float df = ok ? __ldg(&A.g.df[c]) : 0.f;
-    Eval e;
-    sim_dot<XONLY>(A.s, x, T1, T2, df, e.ipr, e.ipi, e.dd);
-    if (ok) {
-        const float mag = sqrtf(fmaf(e.ipr, e.ipr, e.ipi * e.ipi));
-        e.v = (e.dd > 0.f && inv_xn > 0.f) ? mag * inv_xn * rsqrtf(e.dd) : 0.f;
-    } else {
-        e.v = -INFINITY;
-    }
-    return e;
+    return sim_candidate<XONLY>(A.s, x, T1, T2, df, inv_xn, ok);
 }
 
 // Warp argmax: highest value, ties to the smallest position. Returns the lane
@@ -208,25 +326,71 @@ __device__ __forceinline__ void take(Search &S, const Eval &e, int bl, int na, i
     S.centre = bv;
 }
 
-// One scan over an ordered candidate list along df at fixed (a, b): the list
-// position p maps to c = c_start + p * step; `skip` is excluded. The running
-// best (value S.centre at S.c) is replaced only by a strictly better value.
+// Two largest finite values of a per-lane pair (a >= b) across the warp,
+// merged into a running pair.
+__device__ __forceinline__ void warp_top2_pair(float a, float b, float &t1, float &t2)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oa = __shfl_xor_sync(0xffffffffu, a, o);
+        const float ob = __shfl_xor_sync(0xffffffffu, b, o);
+        const float hi = fmaxf(a, oa), lo = fminf(a, oa);
+        b = fmaxf(lo, fmaxf(b, ob));
+        a = hi;
+    }
+    const float hi = fmaxf(t1, a), lo = fminf(t1, a);
+    t2 = fmaxf(lo, fmaxf(t2, b));
+    t1 = hi;
+}
+
+// One scan over an ordered candidate list along df at fixed (a, b): list
+// position p maps to c = c_start + p * step; `skip` is excluded; positions
+// whose c falls off the grid are dropped before batching. Each lane
+// simulates four positions per round. The running best (value S.centre at
+// S.c) is replaced only by a strictly better value, earliest position first.
 template <bool XONLY>
 __device__ void df_scan(const ZoomArgs &A, const float2 *x, Search &S, int count, int c_start, int step, int skip,
                         bool with_centre)
 {
     float t1 = with_centre ? S.centre : -INFINITY, t2 = -INFINITY;
     const int lane = threadIdx.x & 31;
-    for (int base = 0; base < count; base += 32) {
-        const int p = base + lane;
-        const int c = c_start + p * step;
-        const bool want = p < count && c != skip;
-        const Eval e = eval_point<XONLY>(A, x, S.inv_xn, want, S.a, S.b, c);
-        S.evaluated += __popc(__ballot_sync(0xffffffffu, isfinite(e.v)));
-        warp_top2(e.v, t1, t2);
+    // positions with 0 <= c < n_df
+    int p_lo = c_start >= 0 ? 0 : (-c_start + step - 1) / step;
+    int p_hi = min(count - 1, (A.g.n_df - 1 - c_start) >= 0 ? (A.g.n_df - 1 - c_start) / step : -1);
+    const bool ab_ok = point_valid(A.g, S.a, S.b, 0);
+    const float T1 = ab_ok ? __ldg(&A.g.t1[S.a]) : 1000.f, T2 = ab_ok ? __ldg(&A.g.t2[S.b]) : 100.f;
+    for (int base = p_lo; base <= p_hi; base += 32 * kScanW) {
+        float df[kScanW];
+        bool ok[kScanW];
+        int pos[kScanW], cc[kScanW];
+#pragma unroll
+        for (int u = 0; u < kScanW; ++u) {
+            pos[u] = base + 32 * u + lane;
+            cc[u] = c_start + pos[u] * step;
+            ok[u] = ab_ok && pos[u] <= p_hi && cc[u] != skip;
+            df[u] = ok[u] ? __ldg(&A.g.df[cc[u]]) : 0.f;
+        }
+        Eval e[kScanW];
+        sim_df4<XONLY>(A.s, x, T1, T2, df, S.inv_xn, ok, e);
+        // lane-local best (earliest position on ties) and top two
+        int bu = 0;
+        float la = -INFINITY, lb = -INFINITY;
+#pragma unroll
+        for (int u = 0; u < kScanW; ++u) {
+            S.evaluated += __popc(__ballot_sync(0xffffffffu, ok[u]));
+            const float v = e[u].v;
+            if (v > e[bu].v) bu = u;
+            if (isfinite(v)) { if (v > la) { lb = la; la = v; } else if (v > lb) lb = v; }
+        }
+        warp_top2_pair(la, lb, t1, t2);
+        Eval best = e[0];
+        int bpos = pos[0], bc = cc[0];
+#pragma unroll
+        for (int u = 1; u < kScanW; ++u)
+            if (u == bu) { best = e[u]; bpos = pos[u]; bc = cc[u]; }
         float bv;
-        const int bl = warp_best(e.v, p, bv);
-        if (bv > S.centre) take(S, e, bl, S.a, S.b, c, bv);
+        const int bl = warp_best(best.v, bpos, bv);
+        if (bv > S.centre) take(S, best, bl, S.a, S.b, bc, bv);
     }
     close_margin(S, t1, t2);
 }
