@@ -403,63 +403,110 @@ __device__ void df_scan(const ZoomArgs &A, const float2 *x, Search &S, int count
 // one-move-per-round search: values are deterministic, so a point evaluated
 // speculatively has the value the canonical search would compute.
 
-// 2D ZOOM at (h1, h2): each round evaluates the 5x5 block (offsets -2..2 in
-// units of h) around the current centre; the replay visits the 8 neighbours
-// in the fixed order (T1 offset outer, -1 before +1).
+// Points of a 2D speculative batch, in units of (h1, h2) relative to the
+// batch origin, for lane l. Without a predicted direction: the 5x5 block
+// minus its centre (24 points, 2 moves). With direction (da, db): the 3x3
+// neighbourhoods of the origin and of the next positions origin + m (da, db)
+// along it -- 8 points, then 3 new ones per straight step or 5 per diagonal
+// step (9 or 5 moves in one round). Returns false for an unused lane.
+__device__ __forceinline__ bool batch2d_point(int l, int da, int db, int &oa, int &ob)
+{
+    if (da == 0 && db == 0) {
+        if (l >= 24) return false;
+        const int k = l < 12 ? l : l + 1;
+        oa = k / 5 - 2;
+        ob = k % 5 - 2;
+        return true;
+    }
+    if (l < 8) {                              // neighbourhood of the origin
+        const int k = l < 4 ? l : l + 1;
+        oa = k / 3 - 1;
+        ob = k % 3 - 1;
+        return true;
+    }
+    const int r = l - 8;
+    if (da == 0 || db == 0) {                 // straight: 3 new points per step
+        const int m = 1 + r / 3, j = r % 3 - 1;
+        if (da != 0) { oa = (m + 1) * da; ob = j; }
+        else { oa = j; ob = (m + 1) * db; }
+        return true;                          // m <= 8
+    }
+    if (r >= 20) return false;                // diagonal: 5 new points per step
+    const int m = 1 + r / 5, q = r % 5;
+    // around p_m = m (da, db): the far row (u = da, w = -1..1) and the far
+    // column (w = db, u = -da, 0)
+    int u, w;
+    if (q < 3) { u = da; w = q - 1; }
+    else { u = q == 3 ? -da : 0; w = db; }
+    oa = m * da + u;
+    ob = m * db + w;
+    return true;
+}
+
+// 2D ZOOM at (h1, h2): each round evaluates a speculative batch around the
+// current centre (see batch2d_point); the replay visits the 8 neighbours in
+// the fixed order (T1 offset outer, -1 before +1), finds each one's lane
+// with a warp ballot, and stops the round when a neighbour is missing.
 template <bool XONLY>
 __device__ bool move2d(const ZoomArgs &A, const float2 *x, Search &S, int h1, int h2)
 {
     const int lane = threadIdx.x & 31;
-    // lane -> block offset: 24 points of the 5x5 block without its centre
-    const int k = lane < 12 ? lane : lane + 1;
-    const int oa = k / 5 - 2, ob = k % 5 - 2;
-    int moves = 0;
+    int moves = 0, pda = 0, pdb = 0;          // previous move direction
     for (;;) {
-        const int ba = S.a, bb = S.b;                 // block centre
-        const float bc = S.centre;                    // its value (known)
+        const int ba = S.a, bb = S.b;         // batch origin (the centre)
+        const float bc = S.centre;            // its value (known)
         const float bcr = S.cr, bci = S.ci, bcd = S.cd;
+        int oa = 0, ob = 0;
+        const bool have = batch2d_point(lane, pda, pdb, oa, ob);
         const int na = ba + oa * h1, nb = bb + ob * h2;
-        const Eval e = eval_point<XONLY>(A, x, S.inv_xn, lane < 24, na, nb, S.c);
-        int ma = 0, mb = 0;                           // replay position in block units
+        const Eval e = eval_point<XONLY>(A, x, S.inv_xn, have, na, nb, S.c);
+        int ma = 0, mb = 0;                   // replay position in batch units
         for (;;) {
-            if (ma < -1 || ma > 1 || mb < -1 || mb > 1) break;   // neighbours leave the block
             if (++moves > A.max_moves) return false;
-            float best = -INFINITY, t1 = S.centre, t2 = -INFINITY;
-            int bl = -1, bda = 0, bdb = 0, cnt = 0;
+            float vals[8];
+            int srcs[8];
+            bool missing = false;
 #pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                if (q == 4) continue;
-                const int da = q / 3 - 1, db = q % 3 - 1;
-                const int pa = ma + da, pb = mb + db;
-                float v;
-                int src = -1;
+            for (int q = 0; q < 8; ++q) {
+                const int k = q < 4 ? q : q + 1;
+                const int pa = ma + k / 3 - 1, pb = mb + k % 3 - 1;
                 if (pa == 0 && pb == 0) {
-                    v = bc;
+                    vals[q] = bc;
+                    srcs[q] = -1;
                 } else {
-                    const int kk = (pa + 2) * 5 + (pb + 2);
-                    src = kk < 12 ? kk : kk - 1;
-                    v = __shfl_sync(0xffffffffu, e.v, src);
+                    const unsigned hit = __ballot_sync(0xffffffffu, have && oa == pa && ob == pb);
+                    missing |= hit == 0u;
+                    srcs[q] = hit ? __ffs(hit) - 1 : 0;
+                    vals[q] = __shfl_sync(0xffffffffu, e.v, srcs[q]);
                 }
+            }
+            if (missing) { --moves; break; }  // the next decision needs a new batch
+            float best = -INFINITY, t1 = S.centre, t2 = -INFINITY;
+            int bq = -1, cnt = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float v = vals[q];
                 if (isfinite(v)) {
                     ++cnt;
                     if (v > t1) { t2 = t1; t1 = v; } else if (v > t2) t2 = v;
                 }
-                if (v > best) { best = v; bl = src; bda = da; bdb = db; }
+                if (v > best) { best = v; bq = q; }
             }
             S.evaluated += cnt;
             close_margin(S, t1, t2);
             if (!(best > S.centre)) return true;      // the centre wins: this level is done
-            ma += bda;
-            mb += bdb;
-            if (bl >= 0) {
-                take(S, e, bl, na, nb, S.c, best);
-            } else {                                  // back to the block centre (values only rise, so unused)
+            const int k = bq < 4 ? bq : bq + 1;
+            pda = k / 3 - 1;
+            pdb = k % 3 - 1;
+            ma += pda;
+            mb += pdb;
+            if (srcs[bq] >= 0) {
+                take(S, e, srcs[bq], na, nb, S.c, best);
+            } else {                                  // back to the batch origin (values only rise, so unused)
                 S.a = ba; S.b = bb; S.centre = best; S.cr = bcr; S.ci = bci; S.cd = bcd;
             }
         }
-        // the next decision needs points outside this block: re-centre
-        S.a = ba + ma * h1;
-        S.b = bb + mb * h2;
+        // re-plan from the current centre (S.a, S.b were updated by take)
     }
 }
 
