@@ -236,6 +236,20 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
     if ph is not None:
         modes["zoom_same_grid"]["median_abs_error_vs_truth"] = param_errors(res, ph)
 
+    # ZOOM over the resident FP32-equivalent dictionary (Experiment 2's full-dictionary variant)
+    d = M.mrf_dict_generate(ctx, seq_h, g, M.MRF_F32)
+    run = lambda: M.mrf_zoom_search_dict(ctx, d, zo, x_dev, out)
+    run()
+    ms = timed(run, 3)
+    res = M.results_to_numpy(out)[:V]
+    modes["zoom_over_dictionary_same_grid"] = {
+        "grid": GRID, "voxels_per_s": V / ms * 1e3, "ms": ms,
+        "index_agreement_vs_fp32": float(np.mean(res["index"] == fp32_index)),
+        "note": "dictionary resident (generation not timed), candidates read instead of simulated"}
+    if ph is not None:
+        modes["zoom_over_dictionary_same_grid"]["median_abs_error_vs_truth"] = param_errors(res, ph)
+    M.mrf_dict_free(ctx, d)
+
     # finer grids: BF16 / FP8 + re-score on the 12,024,855-entry grid, FP32 there for agreement
     ref = match_mode("fp32_fine_grid", "precision", M.MRF_F32, 4)
     match_mode("bf16_rescore_k8_fine_grid", "precision", M.MRF_BF16, 8, ref["index"])

@@ -266,6 +266,18 @@ void mrf_zoom_opts_default(mrf_zoom_opts *opts);
 int mrf_zoom_search(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, const mrf_zoom_opts *opts,
                     const void *fp_dev, int64_t V, mrf_result *out_dev, void *stream);
 
+/* MRF-ZOOM over a resident dictionary (Methods, Experiment 2: ZOOM "with a
+ * full pre-defined dictionary"): the search of mrf_zoom_search on the
+ * dictionary's own grid and sequence, each candidate's CC read from the
+ * stored normalised entry (one warp streams the row) instead of simulated.
+ * The dictionary must be MRF_F32 (FP32-equivalent CC) or MRF_BF16 (bf16 CC,
+ * decisions may differ from the FP32 search where candidates differ by less
+ * than about 1e-3). M0 and phase use the stored entry norms. Errors:
+ * MRF_E_INVALID, MRF_E_UNSUPPORTED (FP8 dictionary), MRF_E_BUDGET,
+ * MRF_E_CUDA. */
+int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *dict, const mrf_zoom_opts *opts, const void *fp_dev,
+                         int64_t V, mrf_result *out_dev, void *stream);
+
 /* Allocation-free variant of mrf_zoom_search. The paper has no counterpart:
  * it serves callers that cannot let the library allocate device memory
  * during a call -- a framework that already reserved the GPU's memory for

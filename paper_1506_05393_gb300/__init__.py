@@ -114,7 +114,7 @@ EXPORTS = [
     "mrf_dict_generate", "mrf_dict_free", "mrf_dict_query", "mrf_match_bruteforce", "mrf_match_topk",
     "mrf_zoom_opts_default", "mrf_zoom_search", "mrf_serve_start", "mrf_serve_submit", "mrf_serve_poll",
     "mrf_serve_cancel", "mrf_serve_get_stats", "mrf_serve_stop", "mrf_profile_enable", "mrf_profile_read",
-    "mrf_zoom_search_static",
+    "mrf_zoom_search_static", "mrf_zoom_search_dict",
 ]
 
 
@@ -161,6 +161,7 @@ def lib():
         L.mrf_profile_enable.argtypes = [vp, C.c_int]
         L.mrf_profile_read.argtypes = [vp, C.POINTER(Profile), C.c_int]
         L.mrf_zoom_search_static.argtypes = [vp, vp, C.POINTER(GridDesc), C.POINTER(ZoomOpts), vp, i64, vp, vp]
+        L.mrf_zoom_search_dict.argtypes = [vp, vp, C.POINTER(ZoomOpts), vp, i64, vp, vp]
         _lib = L
     return _lib
 
@@ -300,6 +301,12 @@ def mrf_zoom_search(ctx, seq, grid, opts, fp, out, stream=None) -> None:
     g = grid_desc(grid)
     check(lib().mrf_zoom_search(ctx, seq, C.byref(g), C.byref(opts) if opts is not None else None, _ptr(fp),
                                 fp.shape[0], _ptr(out), _stream_ptr(stream)), "mrf_zoom_search")
+
+
+def mrf_zoom_search_dict(ctx, d, opts, fp, out, stream=None) -> None:
+    """MRF-ZOOM with every candidate's CC read from the resident dictionary d."""
+    check(lib().mrf_zoom_search_dict(ctx, d, C.byref(opts) if opts is not None else None, _ptr(fp), fp.shape[0],
+                                     _ptr(out), _stream_ptr(stream)), "mrf_zoom_search_dict")
 
 
 def mrf_zoom_search_static(ctx, seq, grid, opts, fp, out, stream=None) -> None:

@@ -18,6 +18,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "bloch.cuh"
 #include "mrf_internal.h"
 
@@ -45,6 +47,10 @@ struct ZoomPlan {
 struct ZoomArgs {
     SeqDev s;
     GridDev g;
+    // factor mode 3 (resident dictionary): normalised rows, bf16 hi (+ lo)
+    const __nv_bfloat16 *dhi, *dlo;
+    const float *dnorm;      // L2 norm of each un-normalised entry
+    int ld;                  // row stride in elements
     ZoomPlan plan;
     const float2 *x;
     int64_t V;
@@ -263,15 +269,88 @@ struct Search {
     float inv_xn;
 };
 
-template <bool XONLY>
+// Factor mode 3: CC read from a resident dictionary. The lanes' candidates
+// are evaluated one after another by the whole warp: 32 lanes stream the
+// stored row (16-byte loads of 8 bf16) against x and reduce by shuffles.
+__device__ __forceinline__ Eval eval_dict(const ZoomArgs &A, const float2 *x, float inv_xn, bool ok, int a, int b, int c)
+{
+    const int lane = threadIdx.x & 31;
+    const int n2 = 2 * A.s.n;
+    const float *xf = reinterpret_cast<const float *>(x);
+    const long long e = ok ? (long long)(__ldg(&A.g.a_off[a]) + (int64_t)b * A.g.n_df + c) : -1;
+    Eval mine;
+    mine.v = -INFINITY;
+    mine.ipr = mine.ipi = mine.dd = 0.f;
+    unsigned todo = __ballot_sync(0xffffffffu, ok);
+    while (todo) {
+        const int q = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const long long eq = __shfl_sync(0xffffffffu, e, q);
+        const __nv_bfloat16 *hi = A.dhi + (size_t)eq * A.ld;
+        const __nv_bfloat16 *lo = A.dlo ? A.dlo + (size_t)eq * A.ld : nullptr;
+        float re = 0.f, im = 0.f;
+#pragma unroll 4
+        for (int base = lane * 8; base < n2; base += 256) {
+            float d[8];
+            const uint4 h = __ldg(reinterpret_cast<const uint4 *>(hi + base));
+            const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&h);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 f = __bfloat1622float2(h2[k]);
+                d[2 * k] = f.x;
+                d[2 * k + 1] = f.y;
+            }
+            if (lo) {
+                const uint4 l = __ldg(reinterpret_cast<const uint4 *>(lo + base));
+                const __nv_bfloat162 *l2 = reinterpret_cast<const __nv_bfloat162 *>(&l);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 f = __bfloat1622float2(l2[k]);
+                    d[2 * k] += f.x;
+                    d[2 * k + 1] += f.y;
+                }
+            }
+            if (base + 8 <= n2) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 z = __ldg(reinterpret_cast<const float2 *>(xf + base) + k);
+                    // x conj(d)
+                    re = fmaf(z.x, d[2 * k], fmaf(z.y, d[2 * k + 1], re));
+                    im = fmaf(z.y, d[2 * k], fmaf(-z.x, d[2 * k + 1], im));
+                }
+            } else {
+                for (int k = 0; 2 * k + base < n2; ++k) {
+                    const float2 z = __ldg(reinterpret_cast<const float2 *>(xf + base) + k);
+                    re = fmaf(z.x, d[2 * k], fmaf(z.y, d[2 * k + 1], re));
+                    im = fmaf(z.y, d[2 * k], fmaf(-z.x, d[2 * k + 1], im));
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+        }
+        if (lane == q) {
+            // <x, d> of the un-normalised entry is the norm times <x, d_hat>
+            const float nrm = __ldg(&A.dnorm[eq]);
+            mine.ipr = re * nrm;
+            mine.ipi = im * nrm;
+            mine.dd = nrm * nrm;
+            mine.v = sqrtf(fmaf(re, re, im * im)) * inv_xn;
+        }
+    }
+    return mine;
+}
+
+template <int ZM>
 __device__ __forceinline__ Eval eval_point(const ZoomArgs &A, const float2 *x, float inv_xn, bool want, int a, int b,
                                            int c)
 {
     const bool ok = want && point_valid(A.g, a, b, c);
-    const float T1 = ok ? __ldg(&A.g.t1[a]) : 1000.f;
-    const float T2 = ok ? __ldg(&A.g.t2[b]) : 100.f;
-    const float df = ok ? __ldg(&A.g.df[c]) : 0.f;
-    return sim_candidate<XONLY>(A.s, x, T1, T2, df, inv_xn, ok);
+    if (ZM == 3) return eval_dict(A, x, inv_xn, ok, a, b, c);
+    return sim_candidate<(ZM != 0)>(A.s, x, ok ? __ldg(&A.g.t1[a]) : 1000.f, ok ? __ldg(&A.g.t2[b]) : 100.f,
+                             ok ? __ldg(&A.g.df[c]) : 0.f, inv_xn, ok);
 }
 
 // Warp argmax: highest value, ties to the smallest position. Returns the lane
@@ -348,7 +427,7 @@ __device__ __forceinline__ void warp_top2_pair(float a, float b, float &t1, floa
 // whose c falls off the grid are dropped before batching. Each lane
 // simulates four positions per round. The running best (value S.centre at
 // S.c) is replaced only by a strictly better value, earliest position first.
-template <bool XONLY>
+template <int ZM>
 __device__ void df_scan(const ZoomArgs &A, const float2 *x, Search &S, int count, int c_start, int step, int skip,
                         bool with_centre)
 {
@@ -371,7 +450,12 @@ __device__ void df_scan(const ZoomArgs &A, const float2 *x, Search &S, int count
             df[u] = ok[u] ? __ldg(&A.g.df[cc[u]]) : 0.f;
         }
         Eval e[kScanW];
-        sim_df4<XONLY>(A.s, x, T1, T2, df, S.inv_xn, ok, e);
+        if (ZM == 3) {
+#pragma unroll
+            for (int u = 0; u < kScanW; ++u) e[u] = eval_dict(A, x, S.inv_xn, ok[u], S.a, S.b, cc[u]);
+        } else {
+            sim_df4<(ZM != 0)>(A.s, x, T1, T2, df, S.inv_xn, ok, e);
+        }
         // lane-local best (earliest position on ties) and top two
         int bu = 0;
         float la = -INFINITY, lb = -INFINITY;
@@ -447,7 +531,7 @@ __device__ __forceinline__ bool batch2d_point(int l, int da, int db, int &oa, in
 // current centre (see batch2d_point); the replay visits the 8 neighbours in
 // the fixed order (T1 offset outer, -1 before +1), finds each one's lane
 // with a warp ballot, and stops the round when a neighbour is missing.
-template <bool XONLY>
+template <int ZM>
 __device__ bool move2d(const ZoomArgs &A, const float2 *x, Search &S, int h1, int h2)
 {
     const int lane = threadIdx.x & 31;
@@ -459,7 +543,7 @@ __device__ bool move2d(const ZoomArgs &A, const float2 *x, Search &S, int h1, in
         int oa = 0, ob = 0;
         const bool have = batch2d_point(lane, pda, pdb, oa, ob);
         const int na = ba + oa * h1, nb = bb + ob * h2;
-        const Eval e = eval_point<XONLY>(A, x, S.inv_xn, have, na, nb, S.c);
+        const Eval e = eval_point<ZM>(A, x, S.inv_xn, have, na, nb, S.c);
         int ma = 0, mb = 0;                   // replay position in batch units
         for (;;) {
             if (++moves > A.max_moves) return false;
@@ -512,7 +596,7 @@ __device__ bool move2d(const ZoomArgs &A, const float2 *x, Search &S, int h1, in
 
 // 1D ZOOM along T1 (param 0) or T2 (param 1) at half-width h: each round
 // evaluates the points at -16h..16h; the replay compares left then right.
-template <bool XONLY>
+template <int ZM>
 __device__ bool move1d(const ZoomArgs &A, const float2 *x, Search &S, int param, int h)
 {
     const int lane = threadIdx.x & 31;
@@ -523,7 +607,7 @@ __device__ bool move1d(const ZoomArgs &A, const float2 *x, Search &S, int param,
         const float bc = S.centre;
         const float bcr = S.cr, bci = S.ci, bcd = S.cd;
         const int na = ba + (param == 0 ? off * h : 0), nb = bb + (param == 1 ? off * h : 0);
-        const Eval e = eval_point<XONLY>(A, x, S.inv_xn, true, na, nb, S.c);
+        const Eval e = eval_point<ZM>(A, x, S.inv_xn, true, na, nb, S.c);
         int m = 0;
         for (;;) {
             if (m <= -16 || m >= 16) break;
@@ -563,7 +647,7 @@ __device__ bool move1d(const ZoomArgs &A, const float2 *x, Search &S, int param,
     }
 }
 
-template <bool XONLY>
+template <int ZM>
 __global__ void __launch_bounds__(kZoomThreads) zoom_kernel(ZoomArgs A)
 {
     const int lane = threadIdx.x & 31;
@@ -594,31 +678,31 @@ __global__ void __launch_bounds__(kZoomThreads) zoom_kernel(ZoomArgs A)
 
         // step 1a: coarse scan of the whole df range (no prior centre)
         const int nA = (A.g.n_df + P.hA - 1) / P.hA;
-        df_scan<XONLY>(A, x, S, nA, 0, P.hA, -1, false);
+        df_scan<ZM>(A, x, S, nA, 0, P.hA, -1, false);
         // step 1b: window around the optimum
         {
             const int c0 = S.c;
             const int count = 2 * P.K1b + 1;
-            df_scan<XONLY>(A, x, S, count, c0 - P.K1b * P.hB, P.hB, c0, true);
+            df_scan<ZM>(A, x, S, count, c0 - P.K1b * P.hB, P.hB, c0, true);
         }
         // step 1c: probes at whole multiples of omega
         {
             const int c0 = S.c;
             const int start = c0 - (c0 / P.hC) * P.hC;
             const int count = (A.g.n_df - 1 - start) / P.hC + 1;
-            df_scan<XONLY>(A, x, S, count, start, P.hC, c0, true);
+            df_scan<ZM>(A, x, S, count, start, P.hC, c0, true);
         }
         // step 2: 2D ZOOM at the coarse levels
-        for (int l = 0; l < P.n_s2 && ok; ++l) ok = move2d<XONLY>(A, x, S, P.s2_h1[l], P.s2_h2[l]);
+        for (int l = 0; l < P.n_s2 && ok; ++l) ok = move2d<ZM>(A, x, S, P.s2_h1[l], P.s2_h2[l]);
         // step 3: finest-step df window
         {
             const int c0 = S.c;
-            df_scan<XONLY>(A, x, S, 2 * P.W3 + 1, c0 - P.W3, 1, c0, true);
+            df_scan<ZM>(A, x, S, 2 * P.W3 + 1, c0 - P.W3, 1, c0, true);
         }
         // step 4: interleaved 1D ZOOMs
-        for (int l = 0; l < P.n_s4 && ok; ++l) ok = move1d<XONLY>(A, x, S, P.s4_p[l], P.s4_h[l]);
+        for (int l = 0; l < P.n_s4 && ok; ++l) ok = move1d<ZM>(A, x, S, P.s4_p[l], P.s4_h[l]);
         // step 5: final 2D ZOOM at the finest step
-        if (ok) ok = move2d<XONLY>(A, x, S, 1, 1);
+        if (ok) ok = move2d<ZM>(A, x, S, 1, 1);
         if (!ok && lane == 0) atomicExch(A.err, kDeviceErrBounds);
 
         if (lane == 0) {
@@ -709,6 +793,9 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     ZoomArgs A;
     A.s = seq->dev();
     A.g = gdev;
+    A.dhi = A.dlo = nullptr;
+    A.dnorm = nullptr;
+    A.ld = 0;
     A.plan = P;
     A.x = (const float2 *)fp;
     A.V = V;
@@ -717,22 +804,121 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
     int per_sm = 0;
-    if (A.s.xonly) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<true>, kZoomThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<false>, kZoomThreads, 0);
+    if (A.s.xonly) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<1>, kZoomThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<0>, kZoomThreads, 0);
     per_sm = std::max(1, per_sm);
     const int64_t warps_needed = V;
     int64_t blocks = std::min<int64_t>((int64_t)per_sm * ctx->sm_count, (warps_needed + 7) / 8);
     blocks = std::max<int64_t>(blocks, 1);
     {
         ProfScope prof(ctx, kProfZoom, stream);
-        if (A.s.xonly) zoom_kernel<true><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
-        else zoom_kernel<false><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
+        if (A.s.xonly) zoom_kernel<1><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
+        else zoom_kernel<0><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
     }
     e = cudaGetLastError();
     cudaFreeAsync(counter, stream);
     cudaFreeAsync(gblock, stream);
     budget_release(ctx, 256 + gbytes);
     if (e != cudaSuccess) return cuda_fail(e, "zoom launch");
+    return MRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// MRF-ZOOM over a resident dictionary (Experiment 2's "full pre-made
+// dictionary" variant): the same search on the dictionary's grid, every
+// candidate's CC read from the stored normalised entry.
+
+static int plan_zoom(const mrf_seq *seq, const mrf_grid_desc *gd, const mrf_zoom_opts *o, ZoomPlan &P)
+{
+    const double omega = o->omega_hz > 0 ? o->omega_hz : 1000.0 / seq->min_tr;
+    P = ZoomPlan{};
+    int a = (int)floor((o->t1_init_ms - gd->t1_min) / gd->t1_step + 0.5);
+    int b = (int)floor((o->t2_init_ms - gd->t2_min) / gd->t2_step + 0.5);
+    a = std::max(0, std::min(a, gd->n_t1 - 1));
+    b = std::max(0, std::min(b, gd->n_t2 - 1));
+    auto valid = [&](int aa, int bb) {
+        return !gd->require_t2_lt_t1 || gd->t2_min + (double)bb * gd->t2_step < gd->t1_min + (double)aa * gd->t1_step;
+    };
+    while (b > 0 && !valid(a, b)) --b;
+    while (a < gd->n_t1 - 1 && !valid(a, b)) ++a;
+    if (!valid(a, b)) return set_error(MRF_E_INVALID, "zoom: the grid has no valid starting point");
+    P.a0 = a;
+    P.b0 = b;
+    P.hA = snap(o->s1a_step_frac * omega, gd->df_step);
+    P.hB = snap(o->s1b_step_frac * omega, gd->df_step);
+    P.K1b = (int)floor(o->s1b_half_frac * omega / gd->df_step + 0.5) / P.hB;
+    P.hC = snap(omega, gd->df_step);
+    P.W3 = (int)floor(o->s3_half_frac * omega / gd->df_step + 0.5);
+    for (int l = 0, p1 = -1, p2 = -1; l < o->n_s2; ++l) {
+        const int h1 = snap(o->s2_t1_ms[l], gd->t1_step), h2 = snap(o->s2_t2_ms[l], gd->t2_step);
+        if (h1 == p1 && h2 == p2) continue;
+        p1 = h1; p2 = h2;
+        P.s2_h1[P.n_s2] = h1; P.s2_h2[P.n_s2] = h2; P.n_s2++;
+    }
+    for (int l = 0, pp = -1, ph = -1; l < o->n_s4; ++l) {
+        const int p = o->s4_param[l], h = snap(o->s4_ms[l], p == 0 ? gd->t1_step : gd->t2_step);
+        if (p == pp && h == ph) continue;
+        pp = p; ph = h;
+        P.s4_p[P.n_s4] = p; P.s4_h[P.n_s4] = h; P.n_s4++;
+    }
+    return MRF_OK;
+}
+
+extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_zoom_opts *opts, const void *fp,
+                                    int64_t V, mrf_result *out, void *stream_v)
+{
+    if (!ctx || !d) return set_error(MRF_E_INVALID, "NULL argument");
+    if (d->dtype != MRF_F32 && d->dtype != MRF_BF16)
+        return set_error(MRF_E_UNSUPPORTED, "zoom over a dictionary needs an MRF_F32 or MRF_BF16 dictionary");
+    if (V < 0) return set_error(MRF_E_INVALID, "V < 0");
+    mrf_zoom_opts def;
+    if (!opts) { mrf_zoom_opts_default(&def); opts = &def; }
+    if (opts->n_s2 < 0 || opts->n_s2 > MRF_ZOOM_MAX_LEVELS || opts->n_s4 < 0 || opts->n_s4 > MRF_ZOOM_MAX_LEVELS)
+        return set_error(MRF_E_INVALID, "zoom: level counts out of range");
+    for (int i = 0; i < opts->n_s4; ++i)
+        if (opts->s4_param[i] != 0 && opts->s4_param[i] != 1) return set_error(MRF_E_INVALID, "zoom: s4_param must be 0/1");
+    if (!(opts->s1a_step_frac > 0) || !(opts->s1b_step_frac > 0) || opts->s1b_half_frac < 0 || opts->s3_half_frac < 0)
+        return set_error(MRF_E_INVALID, "zoom: bad df search fractions");
+    if (V == 0) return MRF_OK;
+    if (!fp || !out) return set_error(MRF_E_INVALID, "NULL device buffer");
+    cudaSetDevice(ctx->device);
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    ZoomPlan P;
+    int rc = plan_zoom(d->seq, &d->grid.desc, opts, P);
+    if (rc) return rc;
+    rc = budget_charge(ctx, 256);
+    if (rc) return rc;
+    int *counter = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&counter, 256, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+    if (e != cudaSuccess) { budget_release(ctx, 256); return cuda_fail(e, "zoom scratch"); }
+    ZoomArgs A;
+    A.s = d->seq->dev();
+    A.g = d->grid.dev();
+    A.dhi = (const __nv_bfloat16 *)d->hi;
+    A.dlo = (const __nv_bfloat16 *)d->lo;
+    A.dnorm = d->norm;
+    A.ld = d->ld;
+    A.plan = P;
+    A.x = (const float2 *)fp;
+    A.V = V;
+    A.out = out;
+    A.counter = counter;
+    A.err = ctx->err_flag;
+    A.max_moves = 1 << 20;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<3>, kZoomThreads, 0);
+    per_sm = std::max(1, per_sm);
+    int64_t blocks = std::min<int64_t>((int64_t)per_sm * ctx->sm_count, (V + 7) / 8);
+    blocks = std::max<int64_t>(blocks, 1);
+    {
+        ProfScope prof(ctx, kProfZoom, stream);
+        zoom_kernel<3><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
+    }
+    e = cudaGetLastError();
+    cudaFreeAsync(counter, stream);
+    budget_release(ctx, 256);
+    if (e != cudaSuccess) return cuda_fail(e, "zoom (dictionary) launch");
     return MRF_OK;
 }
 
@@ -874,6 +1060,9 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     A.g.a_off = (const int64_t *)(dev + o_ao);
     A.g.nb = (const int32_t *)(dev + o_nb);
     A.g.count = ao[gd->n_t1];
+    A.dhi = A.dlo = nullptr;
+    A.dnorm = nullptr;
+    A.ld = 0;
     A.plan = P;
     A.x = (const float2 *)fp;
     A.V = V;
@@ -882,13 +1071,13 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
     int per_sm = 0;
-    if (A.s.xonly) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<true>, kZoomThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<false>, kZoomThreads, 0);
+    if (A.s.xonly) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<1>, kZoomThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<0>, kZoomThreads, 0);
     per_sm = std::max(1, per_sm);
     int64_t blocks = std::min<int64_t>((int64_t)per_sm * ctx->sm_count, (V + 7) / 8);
     blocks = std::max<int64_t>(blocks, 1);
-    if (A.s.xonly) zoom_kernel<true><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
-    else zoom_kernel<false><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
+    if (A.s.xonly) zoom_kernel<1><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
+    else zoom_kernel<0><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
     count_launch(ctx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "zoom launch (static scratch)");

@@ -138,3 +138,69 @@ def test_zoom_empty_batch(M, ctx):
         assert M.lib().mrf_zoom_search(ctx, h, C.byref(g), None, None, 0, None, None) == M.MRF_OK
     finally:
         M.mrf_sequence_free(ctx, h)
+
+
+def _gpu_zoom_dict(M, ctx, seq, g, x, dtype):
+    h = M.mrf_sequence_load(ctx, seq)
+    d = M.mrf_dict_generate(ctx, h, g, dtype)
+    try:
+        fp = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+        out = M.empty_results(x.shape[0])
+        M.mrf_zoom_search_dict(ctx, d, M.zoom_opts(), fp, out)
+        M.mrf_stream_sync(ctx)
+        return M.results_to_numpy(out)[: x.shape[0]]
+    finally:
+        M.mrf_dict_free(ctx, d)
+        M.mrf_sequence_free(ctx, h)
+
+
+def test_zoom_over_dictionary_tiny(M, ctx, oracle_lib):
+    """Experiment 2's full-dictionary ZOOM: same search, CC read from the
+    resident FP32-equivalent dictionary."""
+    seq = S.sequence(0, 200)
+    g = S.GRIDS["tiny"]
+    ph, x = ongrid_voxels(oracle_lib, seq, g, 256, 30.0, 100)
+    res = _gpu_zoom_dict(M, ctx, seq, g, x, M.MRF_F32)
+    ref = oracle_lib.zoom(seq, g, x)
+    _compare(oracle_lib, g, res, ref, "dict tiny")
+    np.testing.assert_allclose(res["m0"], ref["m0"], rtol=1e-4)
+
+
+def test_zoom_over_dictionary_3d(M, ctx, oracle_lib):
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["fp32_brute"]
+    ph, x = offgrid_voxels(oracle_lib, seq, 96, 20.0, 101)
+    res = _gpu_zoom_dict(M, ctx, seq, g, x, M.MRF_F32)
+    ref = oracle_lib.zoom(seq, g, x)
+    diff, exc = _compare(oracle_lib, g, res, ref, "dict 3d")
+    print(f"zoom dict 3d: differ={diff} excused={exc}")
+
+
+def test_zoom_over_bf16_dictionary_runs(M, ctx, oracle_lib):
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["fp32_brute"]
+    ph, x = offgrid_voxels(oracle_lib, seq, 64, 20.0, 131)
+    res = _gpu_zoom_dict(M, ctx, seq, g, x, M.MRF_BF16)
+    ref = oracle_lib.zoom(seq, g, x)
+    # bf16 CC is within about 1e-3 of the FP64 CC of the same entry
+    t1, t2, df = S.grid_values(g)
+    a, b, c = res["i_t1"], res["i_t2"], res["i_df"]
+    d = oracle_lib.simulate(seq, t1[a], t2[b], df[c])
+    occ = np.abs(np.sum(d.conj() * x, 1)) / (np.linalg.norm(d, axis=1) * np.linalg.norm(x, axis=1))
+    assert np.abs(res["cc"] - occ).max() < 5e-3
+    print(f"zoom bf16 dict: agreement with the FP64 ZOOM {np.mean((np.stack([a, b, c], 1) == ref['abc']).all(1)):.3f}")
+
+
+def test_zoom_dict_rejects_fp8(M, ctx):
+    import ctypes as C
+    seq = S.sequence(0, 64)
+    h = M.mrf_sequence_load(ctx, seq)
+    d = M.mrf_dict_generate(ctx, h, S.GRIDS["tiny"], M.MRF_FP8E4M3)
+    try:
+        fp = torch.zeros((2, 64), dtype=torch.complex64, device="cuda")
+        out = M.empty_results(2)
+        rc = M.lib().mrf_zoom_search_dict(ctx, d, None, C.c_void_p(fp.data_ptr()), 2, C.c_void_p(out.data_ptr()), None)
+        assert rc == M.MRF_E_UNSUPPORTED
+    finally:
+        M.mrf_dict_free(ctx, d)
+        M.mrf_sequence_free(ctx, h)
