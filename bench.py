@@ -45,6 +45,27 @@ FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1
 FLOPS_PER_TP = 32.0
 
 
+def matcher_traffic():
+    """DRAM bytes per full-size matcher launch from the committed ncu summary,
+    or None when the matcher sources changed since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "match_kernel_f32_traffic_614k_4096.txt")
+    try:
+        vals = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        csrc = os.path.join(ROOT, "paper_1506_05393_gb300", "csrc")
+        src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("match.cu", "tc.cuh"))
+        if hashlib.sha256(src).hexdigest() != vals.get("source_sha256"):
+            return None
+        return float(vals["dram_bytes_read"]) + float(vals["dram_bytes_write"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -592,7 +613,8 @@ def main():
     peak = pk["bf16_tflops_sustained"]
     achieved = flops / matcher_ms / 1e9
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "match_kernel<MRF_F32, 4>",
+            "traffic": matcher_traffic(), "traffic_unit": "bytes per launch (ncu dram read + write)",
+            "algorithmic_bytes": 8192 * 2 * 2 * 2112 + D * 2 * 2 * 2112, "kernel": "match_kernel<MRF_F32, 4>",
             "issued_frac": 3.0 * achieved / peak,
             "note": f"achieved = 8*N*D*V algorithmic flops / CUDA-event matcher time ({matcher_ms:.3f} ms); "
                     f"the bf16x3 split issues 3x these flops; peak = bf16 dense sustained "

@@ -80,6 +80,8 @@ struct MatchParams {
     int n_tiles;         // ceil(D / BN)
     int n_vu;            // voxel units (kNB voxel blocks of 64 voxels each)
     int n_chunks;        // dictionary chunks per voxel unit
+    int group_vu;        // voxel units per group: a group's voxel operands stay in L2
+                         // while the dictionary streams past them once
     int k_blocks;        // K blocks of 128 bytes
     int last_ksteps;     // MMA k-steps in the last K block (rest is zero padding)
     const float *colscale;   // FP8: per-entry dequantisation scale, else nullptr
@@ -119,6 +121,19 @@ struct TopK {
         if (pos == 0) { v[0] = c; i[0] = idx; }
     }
 };
+
+// Work unit u -> (dictionary chunk, voxel unit). Units run group by group;
+// inside a group chunk-major, so concurrent CTAs share dictionary tiles.
+__device__ __forceinline__ void decode_unit(const MatchParams &p, int u, int &chunk, int &vu)
+{
+    const int per_group = p.group_vu * p.n_chunks;
+    const int n_groups = (p.n_vu + p.group_vu - 1) / p.group_vu;
+    const int g = min(u / per_group, n_groups - 1);
+    const int r = u - g * per_group;
+    const int gsize = (g == n_groups - 1) ? p.n_vu - g * p.group_vu : p.group_vu;
+    chunk = r / gsize;
+    vu = g * p.group_vu + r % gsize;
+}
 
 __device__ __forceinline__ float sel16(const float (&a)[16], int q)
 {
@@ -187,7 +202,8 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
             uint32_t issued_ph[S];
             for (int q = 0; q < S; ++q) { issued[q] = false; issued_ph[q] = 0; }
             for (int u = blockIdx.x; u < n_units && !abort_flag; u += gridDim.x) {
-                const int chunk = u / p.n_vu, vu = u % p.n_vu;
+                int chunk, vu;
+                decode_unit(p, u, chunk, vu);
                 const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
                 const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
                 for (int t = t0; t < t1; ++t) {
@@ -226,7 +242,9 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
             uint32_t ph = 0, buf_ph = 0;
             bool any = false;
             for (int u = blockIdx.x; u < n_units && !abort_flag; u += gridDim.x) {
-                const int chunk = u / p.n_vu;
+                int chunk, vu;
+                decode_unit(p, u, chunk, vu);
+                (void)vu;
                 const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
                 const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
                 for (int t = t0; t < t1; ++t) {
@@ -287,7 +305,8 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
         TopK<K> tk;
         for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
             if (__any_sync(0xffffffffu, abort_flag != 0)) break;
-            const int chunk = u / p.n_vu, vu = u % p.n_vu;
+            int chunk, vu;
+            decode_unit(p, u, chunk, vu);
             const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
             const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
             tk.reset();
@@ -657,8 +676,14 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     const int64_t V_pad = (int64_t)n_vu * nb * 64;
     const int ebytes = mode == MRF_FP8E4M3 ? 1 : 2;
     const int n_tiles = (int)((d->entries + BN - 1) / BN);
-    // chunks: make units a multiple of the SM count where possible
-    int n_chunks = ctx->sm_count / gcd_i(n_vu, ctx->sm_count);
+    // voxel-unit groups whose operands (all hi/lo parts) fit about 40 MB of L2;
+    // the dictionary streams once per group
+    const size_t unit_bytes = (size_t)nb * 2 * 64 * d->ld * ebytes * (mode == MRF_F32 ? 2 : 1);
+    const int g_max = std::max(1, std::min(n_vu, (int)((size_t)40 * 1024 * 1024 / unit_bytes)));
+    const int n_groups = (n_vu + g_max - 1) / g_max;
+    const int group_vu = (n_vu + n_groups - 1) / n_groups;   // balanced groups
+    // chunks: make each group's units a multiple of the SM count where possible
+    int n_chunks = ctx->sm_count / gcd_i(group_vu, ctx->sm_count);
     n_chunks = std::max(1, std::min(n_chunks, n_tiles));
     const int kbe = mode == MRF_FP8E4M3 ? 128 : 64;    // elements per K block
     const int k_blocks = (2 * d->n + kbe - 1) / kbe;   // K blocks holding at least one real element
@@ -718,6 +743,7 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     p.n_tiles = n_tiles;
     p.n_vu = n_vu;
     p.n_chunks = n_chunks;
+    p.group_vu = group_vu;
     p.k_blocks = k_blocks;
     p.last_ksteps = last_ksteps;
     p.colscale = mode == MRF_FP8E4M3 ? d->scale : nullptr;
