@@ -496,7 +496,10 @@ def ncu_case(which):
         M.mrf_stream_sync(ctx)
         M.mrf_dict_free(ctx, d)
     else:
-        xs = x[: 8 * 152]
+        # the 128x128 slice of the high-precision ZOOM measurement
+        _, x128 = make_slice(M, ctx, h, 103, 128 * 128, 20.0)
+        xs = torch.from_numpy(x128).cuda()
+        out = M.empty_results(xs.shape[0])
         M.mrf_zoom_search(ctx, h, S.GRIDS["zoom_fine"], M.zoom_opts(), xs, out)
         M.mrf_stream_sync(ctx)
     M.mrf_sequence_free(ctx, h)

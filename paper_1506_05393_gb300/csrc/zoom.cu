@@ -1,17 +1,18 @@
 // MRF-ZOOM (Theory: df search steps 1-4, 1D ZOOM of Fig. 1, 2D ZOOM of
-// Fig. 2; Methods, Experiment 2 steps 1-5), every candidate simulated on the
-// fly -- no dictionary.
+// Fig. 2; Methods, Experiment 2 steps 1-5).
 //
-// One warp per voxel; warps pull voxels from an atomic work counter
-// (persistent kernel, a few warps per SM). Each move or scan evaluates its
-// candidate set with one candidate per lane: the lane runs the FP32 Bloch
-// recurrence for its (T1, T2, df) and accumulates <x, d> and ||d||^2 in
-// 16-timepoint FP32 blocks with compensated (Kahan) block sums. The decision
-// (best candidate, ties to the earliest in the canonical scan order; move
-// only when strictly better than the centre) is taken from warp-shuffle
-// reductions, so all lanes follow the same control flow. The host turns
-// physical step sizes into whole grid steps (round half up, at least 1,
-// consecutive duplicates dropped) exactly as the stage machine defines them.
+// Two kernels run the same canonical eager search:
+//  * zoom_pack_kernel simulates every candidate on the fly (no dictionary):
+//    a warp carries eight voxels and gives each lane one candidate per round,
+//    whose FP32 Bloch recurrence accumulates <x, d> and ||d||^2 in
+//    16-timepoint FP32 blocks with compensated (Kahan) block sums;
+//  * zoom_dict_kernel reads candidates from a resident dictionary, one warp
+//    per voxel, the warp streaming each stored row.
+// Decisions take the best candidate with ties to the earliest in the
+// canonical scan order, and move only when strictly better than the centre.
+// The host turns physical step sizes into whole grid steps (round half up, at
+// least 1, consecutive duplicates dropped) exactly as the stage machine
+// defines them.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -26,11 +27,8 @@
 namespace {
 
 constexpr int kMaxLevels = MRF_ZOOM_MAX_LEVELS;
-constexpr int kZoomThreads = 256;   // 8 voxels (warps) per CTA
-#ifndef MRF_ZOOM_SCAN_W
-#define MRF_ZOOM_SCAN_W 2
-#endif
-constexpr int kScanW = MRF_ZOOM_SCAN_W;   // df-scan candidates per lane (share T1/T2 factors)
+constexpr int kZoomThreads = 256;   // dictionary search: 8 voxels (warps) per CTA
+constexpr int kScanW = 2;           // dictionary df scans: positions per lane per round
 
 struct ZoomPlan {
     int a0, b0;          // start of the df search
@@ -117,137 +115,95 @@ struct Eval {
     float ipr, ipi, dd;
 };
 
-// One timepoint of one candidate with per-candidate factors.
-template <bool XONLY>
-__device__ __forceinline__ void step1(Bloch &st, const SeqDev &s, float k1, float k2, float f, int j, float &sr,
-                                      float &si)
+// One timepoint of C candidates (own factors each) sharing the timepoint's RF
+// coefficients. SYM: TE_j equals TR_j - TE_j, so both free evolutions of the
+// step share one set of factors (a compile-time choice: the second set is
+// never computed).
+template <bool XONLY, bool SYM, int C>
+__device__ __forceinline__ void step_multi(const SeqDev &s, int j, const float (&k1)[C], const float (&k2)[C],
+                                           const float (&f)[C], Bloch (&st)[C], Acc (&acc)[C],
+                                           const float2 *const (&x)[C])
 {
-    float ta;
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    float q[10];
+    float ta, tb = 0.f;
     if (XONLY) {
-        const float4 r = __ldg(&s.rfx[j]);
-        bloch_rf_x(st, r);
+        r = __ldg(&s.rfx[j]);
         ta = r.w;
     } else {
-        bloch_rf<false>(st, s, j);
+        const float4 *p = reinterpret_cast<const float4 *>(s.rfg + 12 * j);
+        const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+        q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+        q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w;
+        q[8] = c.x; q[9] = c.y;
         ta = __ldg(&s.tau[j]).x;
     }
-    float cs, sn;
-    const float e1 = ex2_fast(k1 * ta), e2 = ex2_fast(k2 * ta);
-    cis_fast(f, ta, cs, sn);
-    bloch_evolve(st, e1, e2 * cs, e2 * sn);
-    sr = st.mx;
-    si = st.my;
-    if (s.symmetric) {
-        bloch_evolve(st, e1, e2 * cs, e2 * sn);
-    } else {
-        const float tb = __ldg(&s.tau[j]).y;
-        const float e1b = ex2_fast(k1 * tb), e2b = ex2_fast(k2 * tb);
-        cis_fast(f, tb, cs, sn);
-        bloch_evolve(st, e1b, e2b * cs, e2b * sn);
-    }
-}
-
-// Simulate one candidate and correlate it with x (all lanes call this
-// together; kept out of line so the hot loop exists once).
-template <bool XONLY>
-__device__ __forceinline__ Eval sim_candidate(const SeqDev &s, const float2 *__restrict__ x, float T1, float T2, float df,
-                                           float inv_xn, bool ok)
-{
-    const float k1 = -1.4426950408889634f / T1, k2 = -1.4426950408889634f / T2, f = df * 1.0e-3f;
-    Bloch st;
-    start_state(st, s, k1);
-    Acc acc;
-    acc.init();
-    const int n = s.n;
-    int j0 = 0;
-    for (; j0 + 16 <= n; j0 += 16) {
-#pragma unroll 4
-        for (int u = 0; u < 16; ++u) {
-            float sr, si;
-            step1<XONLY>(st, s, k1, k2, f, j0 + u, sr, si);
-            acc.add(__ldg(&x[j0 + u]), sr, si);
-        }
-        acc.flush();
-    }
-    for (int j = j0; j < n; ++j) {
-        float sr, si;
-        step1<XONLY>(st, s, k1, k2, f, j, sr, si);
-        acc.add(__ldg(&x[j]), sr, si);
-    }
-    acc.flush();
-    Eval e;
-    e.ipr = acc.kr.s;
-    e.ipi = acc.ki.s;
-    e.dd = acc.kd.s;
-    if (ok) {
-        const float mag = sqrtf(fmaf(e.ipr, e.ipr, e.ipi * e.ipi));
-        e.v = (e.dd > 0.f && inv_xn > 0.f) ? mag * inv_xn * rsqrtf(e.dd) : 0.f;
-    } else {
-        e.v = -INFINITY;
-    }
-    return e;
-}
-
-// kScanW candidates that share (T1, T2) and differ in df (a df scan): the
-// relaxation factors are computed once per timepoint for all of them.
-template <bool XONLY>
-__device__ __forceinline__ void sim_df4(const SeqDev &s, const float2 *__restrict__ x, float T1, float T2,
-                                     const float (&df)[kScanW], float inv_xn, const bool (&ok)[kScanW],
-                                     Eval (&out)[kScanW])
-{
-    const float k1 = -1.4426950408889634f / T1, k2 = -1.4426950408889634f / T2;
-    float f[kScanW];
-    Bloch st[kScanW];
-    Acc acc[kScanW];
+    if (!SYM) tb = __ldg(&s.tau[j]).y;
 #pragma unroll
-    for (int u = 0; u < kScanW; ++u) {
+    for (int u = 0; u < C; ++u) {
+        if (XONLY) bloch_rf_x(st[u], r);
+        else bloch_rf_general(st[u], q);
+        float cs, sn;
+        const float e1 = ex2_fast(k1[u] * ta), e2 = ex2_fast(k2[u] * ta);
+        cis_fast(f[u], ta, cs, sn);
+        bloch_evolve(st[u], e1, e2 * cs, e2 * sn);
+        acc[u].add(__ldg(&x[u][j]), st[u].mx, st[u].my);
+        if (SYM) {
+            bloch_evolve(st[u], e1, e2 * cs, e2 * sn);
+        } else {
+            const float e1b = ex2_fast(k1[u] * tb), e2b = ex2_fast(k2[u] * tb);
+            cis_fast(f[u], tb, cs, sn);
+            bloch_evolve(st[u], e1b, e2b * cs, e2b * sn);
+        }
+    }
+}
+
+// Simulate C candidates per lane, each against its own voxel x[u], and take
+// their CC: <x, d> and ||d||^2 accumulate in 16-timepoint FP32 blocks with
+// compensated (Kahan) block sums. Every candidate's arithmetic is the same
+// whichever of the C places it occupies, so a point has one value wherever
+// it is simulated.
+template <bool XONLY, bool SYM, int C>
+__device__ __forceinline__ void sim_multi(const SeqDev &s, const float2 *const (&x)[C], const float (&T1)[C],
+                                          const float (&T2)[C], const float (&df)[C], const float (&ixn)[C],
+                                          const bool (&ok)[C], Eval (&out)[C])
+{
+    float k1[C], k2[C], f[C];
+    Bloch st[C];
+    Acc acc[C];
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+        k1[u] = -1.4426950408889634f / T1[u];
+        k2[u] = -1.4426950408889634f / T2[u];
         f[u] = df[u] * 1.0e-3f;
-        start_state(st[u], s, k1);
+        start_state(st[u], s, k1[u]);
         acc[u].init();
     }
     const int n = s.n;
-    for (int j0 = 0; j0 < n; j0 += 16) {
-        const int j1 = min(n, j0 + 16);
-        for (int j = j0; j < j1; ++j) {
-            float ta, tb;
-            if (XONLY) {
-                const float4 r = __ldg(&s.rfx[j]);
+    int j0 = 0;
+    for (; j0 + 16 <= n; j0 += 16) {
+        // each voxel's samples two blocks ahead into L1 (lanes read different voxels)
 #pragma unroll
-                for (int u = 0; u < kScanW; ++u) bloch_rf_x(st[u], r);
-                ta = r.w;
-                tb = s.symmetric ? ta : __ldg(&s.tau[j]).y;
-            } else {
-#pragma unroll
-                for (int u = 0; u < kScanW; ++u) bloch_rf<false>(st[u], s, j);
-                const float2 t2 = __ldg(&s.tau[j]);
-                ta = t2.x;
-                tb = t2.y;
-            }
-            const float e1a = ex2_fast(k1 * ta), e2a = ex2_fast(k2 * ta);
-            const float e1b = s.symmetric ? e1a : ex2_fast(k1 * tb), e2b = s.symmetric ? e2a : ex2_fast(k2 * tb);
-            const float2 z = __ldg(&x[j]);
-#pragma unroll
-            for (int u = 0; u < kScanW; ++u) {
-                float cs, sn;
-                cis_fast(f[u], ta, cs, sn);
-                bloch_evolve(st[u], e1a, e2a * cs, e2a * sn);
-                acc[u].add(z, st[u].mx, st[u].my);
-                if (!s.symmetric) cis_fast(f[u], tb, cs, sn);
-                bloch_evolve(st[u], e1b, e2b * cs, e2b * sn);
-            }
+        for (int u = 0; u < C; ++u) {
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(x[u] + min(j0 + 32, n - 1)));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(x[u] + min(j0 + 47, n - 1)));
         }
+#pragma unroll 4
+        for (int jj = 0; jj < 16; ++jj) step_multi<XONLY, SYM, C>(s, j0 + jj, k1, k2, f, st, acc, x);
 #pragma unroll
-        for (int u = 0; u < kScanW; ++u) acc[u].flush();
+        for (int u = 0; u < C; ++u) acc[u].flush();
     }
+    for (int j = j0; j < n; ++j) step_multi<XONLY, SYM, C>(s, j, k1, k2, f, st, acc, x);
 #pragma unroll
-    for (int u = 0; u < kScanW; ++u) {
+    for (int u = 0; u < C; ++u) {
+        acc[u].flush();
         Eval &e = out[u];
         e.ipr = acc[u].kr.s;
         e.ipi = acc[u].ki.s;
         e.dd = acc[u].kd.s;
         if (ok[u]) {
             const float mag = sqrtf(fmaf(e.ipr, e.ipr, e.ipi * e.ipi));
-            e.v = (e.dd > 0.f && inv_xn > 0.f) ? mag * inv_xn * rsqrtf(e.dd) : 0.f;
+            e.v = (e.dd > 0.f && ixn[u] > 0.f) ? mag * ixn[u] * rsqrtf(e.dd) : 0.f;
         } else {
             e.v = -INFINITY;
         }
@@ -343,16 +299,6 @@ __device__ __forceinline__ Eval eval_dict(const ZoomArgs &A, const float2 *x, fl
     return mine;
 }
 
-template <int ZM>
-__device__ __forceinline__ Eval eval_point(const ZoomArgs &A, const float2 *x, float inv_xn, bool want, int a, int b,
-                                           int c)
-{
-    const bool ok = want && point_valid(A.g, a, b, c);
-    if (ZM == 3) return eval_dict(A, x, inv_xn, ok, a, b, c);
-    return sim_candidate<(ZM != 0)>(A.s, x, ok ? __ldg(&A.g.t1[a]) : 1000.f, ok ? __ldg(&A.g.t2[b]) : 100.f,
-                             ok ? __ldg(&A.g.df[c]) : 0.f, inv_xn, ok);
-}
-
 // Warp argmax: highest value, ties to the smallest position. Returns the lane
 // holding it (valid when the value is finite).
 __device__ __forceinline__ int warp_best(float v, int pos, float &best)
@@ -368,24 +314,6 @@ __device__ __forceinline__ int warp_best(float v, int pos, float &best)
     }
     best = bv;
     return bl;
-}
-
-// Two largest finite values across the warp (plus a running pair).
-__device__ __forceinline__ void warp_top2(float v, float &t1, float &t2)
-{
-    float a = isfinite(v) ? v : -INFINITY, b = -INFINITY;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float oa = __shfl_xor_sync(0xffffffffu, a, o);
-        const float ob = __shfl_xor_sync(0xffffffffu, b, o);
-        const float hi = fmaxf(a, oa), lo = fminf(a, oa);
-        b = fmaxf(lo, fmaxf(b, ob));
-        a = hi;
-    }
-    // merge with the running pair
-    const float hi = fmaxf(t1, a), lo = fminf(t1, a);
-    t2 = fmaxf(lo, fmaxf(t2, b));
-    t1 = hi;
 }
 
 __device__ __forceinline__ void close_margin(Search &S, float t1, float t2)
@@ -427,7 +355,6 @@ __device__ __forceinline__ void warp_top2_pair(float a, float b, float &t1, floa
 // whose c falls off the grid are dropped before batching. Each lane
 // simulates four positions per round. The running best (value S.centre at
 // S.c) is replaced only by a strictly better value, earliest position first.
-template <int ZM>
 __device__ void df_scan(const ZoomArgs &A, const float2 *x, Search &S, int count, int c_start, int step, int skip,
                         bool with_centre)
 {
@@ -437,9 +364,7 @@ __device__ void df_scan(const ZoomArgs &A, const float2 *x, Search &S, int count
     int p_lo = c_start >= 0 ? 0 : (-c_start + step - 1) / step;
     int p_hi = min(count - 1, (A.g.n_df - 1 - c_start) >= 0 ? (A.g.n_df - 1 - c_start) / step : -1);
     const bool ab_ok = point_valid(A.g, S.a, S.b, 0);
-    const float T1 = ab_ok ? __ldg(&A.g.t1[S.a]) : 1000.f, T2 = ab_ok ? __ldg(&A.g.t2[S.b]) : 100.f;
     for (int base = p_lo; base <= p_hi; base += 32 * kScanW) {
-        float df[kScanW];
         bool ok[kScanW];
         int pos[kScanW], cc[kScanW];
 #pragma unroll
@@ -447,15 +372,10 @@ __device__ void df_scan(const ZoomArgs &A, const float2 *x, Search &S, int count
             pos[u] = base + 32 * u + lane;
             cc[u] = c_start + pos[u] * step;
             ok[u] = ab_ok && pos[u] <= p_hi && cc[u] != skip;
-            df[u] = ok[u] ? __ldg(&A.g.df[cc[u]]) : 0.f;
         }
         Eval e[kScanW];
-        if (ZM == 3) {
 #pragma unroll
-            for (int u = 0; u < kScanW; ++u) e[u] = eval_dict(A, x, S.inv_xn, ok[u], S.a, S.b, cc[u]);
-        } else {
-            sim_df4<(ZM != 0)>(A.s, x, T1, T2, df, S.inv_xn, ok, e);
-        }
+        for (int u = 0; u < kScanW; ++u) e[u] = eval_dict(A, x, S.inv_xn, ok[u], S.a, S.b, cc[u]);
         // lane-local best (earliest position on ties) and top two
         int bu = 0;
         float la = -INFINITY, lb = -INFINITY;
@@ -531,7 +451,6 @@ __device__ __forceinline__ bool batch2d_point(int l, int da, int db, int &oa, in
 // current centre (see batch2d_point); the replay visits the 8 neighbours in
 // the fixed order (T1 offset outer, -1 before +1), finds each one's lane
 // with a warp ballot, and stops the round when a neighbour is missing.
-template <int ZM>
 __device__ bool move2d(const ZoomArgs &A, const float2 *x, Search &S, int h1, int h2)
 {
     const int lane = threadIdx.x & 31;
@@ -543,7 +462,7 @@ __device__ bool move2d(const ZoomArgs &A, const float2 *x, Search &S, int h1, in
         int oa = 0, ob = 0;
         const bool have = batch2d_point(lane, pda, pdb, oa, ob);
         const int na = ba + oa * h1, nb = bb + ob * h2;
-        const Eval e = eval_point<ZM>(A, x, S.inv_xn, have, na, nb, S.c);
+        const Eval e = eval_dict(A, x, S.inv_xn, have && point_valid(A.g, na, nb, S.c), na, nb, S.c);
         int ma = 0, mb = 0;                   // replay position in batch units
         for (;;) {
             if (++moves > A.max_moves) return false;
@@ -596,7 +515,6 @@ __device__ bool move2d(const ZoomArgs &A, const float2 *x, Search &S, int h1, in
 
 // 1D ZOOM along T1 (param 0) or T2 (param 1) at half-width h: each round
 // evaluates the points at -16h..16h; the replay compares left then right.
-template <int ZM>
 __device__ bool move1d(const ZoomArgs &A, const float2 *x, Search &S, int param, int h)
 {
     const int lane = threadIdx.x & 31;
@@ -607,7 +525,7 @@ __device__ bool move1d(const ZoomArgs &A, const float2 *x, Search &S, int param,
         const float bc = S.centre;
         const float bcr = S.cr, bci = S.ci, bcd = S.cd;
         const int na = ba + (param == 0 ? off * h : 0), nb = bb + (param == 1 ? off * h : 0);
-        const Eval e = eval_point<ZM>(A, x, S.inv_xn, true, na, nb, S.c);
+        const Eval e = eval_dict(A, x, S.inv_xn, point_valid(A.g, na, nb, S.c), na, nb, S.c);
         int m = 0;
         for (;;) {
             if (m <= -16 || m >= 16) break;
@@ -647,8 +565,7 @@ __device__ bool move1d(const ZoomArgs &A, const float2 *x, Search &S, int param,
     }
 }
 
-template <int ZM>
-__global__ void __launch_bounds__(kZoomThreads) zoom_kernel(ZoomArgs A)
+__global__ void __launch_bounds__(kZoomThreads) zoom_dict_kernel(ZoomArgs A)
 {
     const int lane = threadIdx.x & 31;
     const ZoomPlan &P = A.plan;
@@ -678,31 +595,31 @@ __global__ void __launch_bounds__(kZoomThreads) zoom_kernel(ZoomArgs A)
 
         // step 1a: coarse scan of the whole df range (no prior centre)
         const int nA = (A.g.n_df + P.hA - 1) / P.hA;
-        df_scan<ZM>(A, x, S, nA, 0, P.hA, -1, false);
+        df_scan(A, x, S, nA, 0, P.hA, -1, false);
         // step 1b: window around the optimum
         {
             const int c0 = S.c;
             const int count = 2 * P.K1b + 1;
-            df_scan<ZM>(A, x, S, count, c0 - P.K1b * P.hB, P.hB, c0, true);
+            df_scan(A, x, S, count, c0 - P.K1b * P.hB, P.hB, c0, true);
         }
         // step 1c: probes at whole multiples of omega
         {
             const int c0 = S.c;
             const int start = c0 - (c0 / P.hC) * P.hC;
             const int count = (A.g.n_df - 1 - start) / P.hC + 1;
-            df_scan<ZM>(A, x, S, count, start, P.hC, c0, true);
+            df_scan(A, x, S, count, start, P.hC, c0, true);
         }
         // step 2: 2D ZOOM at the coarse levels
-        for (int l = 0; l < P.n_s2 && ok; ++l) ok = move2d<ZM>(A, x, S, P.s2_h1[l], P.s2_h2[l]);
+        for (int l = 0; l < P.n_s2 && ok; ++l) ok = move2d(A, x, S, P.s2_h1[l], P.s2_h2[l]);
         // step 3: finest-step df window
         {
             const int c0 = S.c;
-            df_scan<ZM>(A, x, S, 2 * P.W3 + 1, c0 - P.W3, 1, c0, true);
+            df_scan(A, x, S, 2 * P.W3 + 1, c0 - P.W3, 1, c0, true);
         }
         // step 4: interleaved 1D ZOOMs
-        for (int l = 0; l < P.n_s4 && ok; ++l) ok = move1d<ZM>(A, x, S, P.s4_p[l], P.s4_h[l]);
+        for (int l = 0; l < P.n_s4 && ok; ++l) ok = move1d(A, x, S, P.s4_p[l], P.s4_h[l]);
         // step 5: final 2D ZOOM at the finest step
-        if (ok) ok = move2d<ZM>(A, x, S, 1, 1);
+        if (ok) ok = move2d(A, x, S, 1, 1);
         if (!ok && lane == 0) atomicExch(A.err, kDeviceErrBounds);
 
         if (lane == 0) {
@@ -721,10 +638,539 @@ __global__ void __launch_bounds__(kZoomThreads) zoom_kernel(ZoomArgs A)
     }
 }
 
+// ---------------------------------------------------------------------------
+// On-the-fly search, packed: a warp carries kSlots voxels and hands out up to
+// 2 x 32 candidates afresh every round.
+//
+// A voxel's next decision lacks only a few values: the unknown points among
+// the eight neighbours of a 2D move (3 or 5 after a move), the unknown end of
+// a 1D line, or any number of positions of a df scan. Each round lane s <
+// kSlots runs the stage machine of slot s as far as the known values allow
+// and lists the points its next decision lacks, then points that later
+// decisions will want if the walk goes on. Lane 0 fills the round's table:
+// first every slot's missing points, then consecutive positions for the
+// slots that scan df, then the speculative points. Each lane simulates one
+// or two table entries (two when more than 32 are listed) with its own
+// (T1, T2, df) and voxel. The values of a move level stay in a per-slot
+// window (8 x 8 points of the level's lattice, or 64 points of a 1D line) so
+// that no point is simulated twice while it is in reach; the evaluation count
+// still counts every visit of the canonical search. The final centre is
+// simulated once more for its <x, d> and ||d||^2 (M0, phase).
+
+constexpr int kSlots = 8;
+constexpr int kPackWarps = 4;
+constexpr int kPackThreads = 32 * kPackWarps;
+constexpr int kPerLane = 2;                  // table entries a lane can simulate in one round
+constexpr int kTable = 32 * kPerLane;
+constexpr int kWin = 64;
+constexpr int kReqMax = 24;                  // listed points per slot and round (8 missing + speculative)
+
+enum Stage : int { kS1a = 0, kS1b, kS1c, kS2, kS3, kS4, kS5, kFinal };
+enum Tag : int { kTagNone = 0, kTagScan, kTagMove, kTagFinal };
+
+struct Slot {
+    int v;                 // voxel, -1 when idle
+    int stage, level;
+    int a, b, c;           // centre
+    float centre;          // its CC (-inf before the first df scan)
+    int evaluated;
+    float mm;              // smallest decision margin so far
+    float inv_xn;
+    int ok;                // 0 once a level exceeded the move limit
+    // df scans: list positions p..p_end, grid point c = start + p * step, `skip` excluded
+    int p, p_end, start, step, skip;
+    float g1, g2;          // running top two of the scan's decision set
+    // move levels: moves so far, lattice origin (la, lb) and steps, the
+    // centre's lattice coordinates, the last move (lattice units)
+    int moves, la, lb, h1, h2, line, param, ia, ib, da, db;
+    // listed points: ra/rb/rw[0..nreq) missing, then nspec speculative (rw: window index)
+    int nreq, nspec;
+    int ra[kReqMax], rb[kReqMax], rw[kReqMax];
+};
+
+struct PackShared {
+    Slot s[kSlots];
+    int wa[kSlots][kWin], wb[kSlots][kWin];
+    float wv[kSlots][kWin];
+    // this round's table and results
+    int t_slot[kTable], t_a[kTable], t_b[kTable], t_c[kTable], t_tag[kTable];
+    float r_v[kTable], r_ipr[kTable], r_ipi[kTable], r_dd[kTable];
+    int used;
+    int norm_mask;         // slots whose new voxel still needs ||x||
+    int drained;
+    int rot;
+};
+
+__device__ __forceinline__ bool is_scan(int st) { return st == kS1a || st == kS1b || st == kS1c || st == kS3; }
+
+__device__ __forceinline__ void top2_add(float v, float &t1, float &t2)
+{
+    if (!isfinite(v)) return;
+    if (v > t1) { t2 = t1; t1 = v; } else if (v > t2) t2 = v;
+}
+
+// List of a df scan at the current (a, b); positions whose c falls off the
+// grid are dropped, and a list holding only the excluded point is empty.
+__device__ __forceinline__ bool scan_setup(Slot &S, int n_df, int count, int start, int step, int skip,
+                                           bool with_centre)
+{
+    S.start = start;
+    S.step = step;
+    S.skip = skip;
+    S.p = start >= 0 ? 0 : (-start + step - 1) / step;
+    S.p_end = min(count - 1, (n_df - 1 - start) >= 0 ? (n_df - 1 - start) / step : -1);
+    S.g1 = with_centre ? S.centre : -INFINITY;
+    S.g2 = -INFINITY;
+    if (S.p == S.p_end && start + S.p * step == skip) return false;
+    return S.p <= S.p_end;
+}
+
+// Window slot of lattice point (i, k): a torus of 8 x 8 for 2D levels (every
+// 7 x 7 block is collision free), 64 along a 1D line.
+__device__ __forceinline__ int win_index(const Slot &S, int i, int k)
+{
+    return S.line ? ((S.param == 0 ? i : k) & (kWin - 1)) : (((i & 7) << 3) | (k & 7));
+}
+
+__device__ __forceinline__ bool win_get(const PackShared &W, int s, int idx, int a, int b, float &v)
+{
+    if (W.wa[s][idx] != a || W.wb[s][idx] != b) return false;
+    v = W.wv[s][idx];
+    return true;
+}
+
+// Enter `stage` (with S.level for the leveled stages), passing over empty
+// scans and exhausted level lists. A move level starts an empty window that
+// holds the centre.
+__device__ void enter(PackShared &W, int s, int stage, const ZoomPlan &P, int n_df)
+{
+    Slot &S = W.s[s];
+    for (;;) {
+        S.stage = stage;
+        bool nonempty;
+        switch (stage) {
+        case kS1a:
+            nonempty = scan_setup(S, n_df, (n_df + P.hA - 1) / P.hA, 0, P.hA, -1, false);
+            break;
+        case kS1b:
+            nonempty = scan_setup(S, n_df, 2 * P.K1b + 1, S.c - P.K1b * P.hB, P.hB, S.c, true);
+            break;
+        case kS1c: {
+            const int st = S.c - (S.c / P.hC) * P.hC;
+            nonempty = scan_setup(S, n_df, (n_df - 1 - st) / P.hC + 1, st, P.hC, S.c, true);
+            break;
+        }
+        case kS3:
+            nonempty = scan_setup(S, n_df, 2 * P.W3 + 1, S.c - P.W3, 1, S.c, true);
+            break;
+        case kS2: case kS4: case kS5:
+            if (stage == kS2 && S.level >= P.n_s2) { stage = kS3; continue; }
+            if (stage == kS4 && S.level >= P.n_s4) { stage = kS5; continue; }
+            S.moves = 0;
+            S.line = stage == kS4;
+            S.param = stage == kS4 ? P.s4_p[S.level] : 0;
+            S.h1 = stage == kS2 ? P.s2_h1[S.level] : stage == kS4 ? P.s4_h[S.level] : 1;
+            S.h2 = stage == kS2 ? P.s2_h2[S.level] : stage == kS4 ? P.s4_h[S.level] : 1;
+            S.la = S.a;
+            S.lb = S.b;
+            S.ia = S.ib = S.da = S.db = 0;
+            for (int i = 0; i < kWin; ++i) W.wa[s][i] = -1;
+            W.wa[s][0] = S.a;
+            W.wb[s][0] = S.b;
+            W.wv[s][0] = S.centre;
+            return;
+        default:
+            return;
+        }
+        if (nonempty) return;
+        // an empty scan: its decision set is the centre alone (no margin)
+        stage = stage == kS1a ? kS1b : stage == kS1b ? kS1c : stage == kS1c ? kS2 : kS4;
+        S.level = 0;
+    }
+}
+
+// List lattice point (i, k) for simulation unless it is off the grid, known,
+// or already listed (bit of its window slot in `listed`).
+__device__ __forceinline__ bool list_point(PackShared &W, int s, const GridDev &g, int i, int k,
+                                           unsigned long long &listed, bool &known, float &v)
+{
+    Slot &S = W.s[s];
+    const int a = S.la + i * S.h1, b = S.lb + k * S.h2;
+    known = false;
+    if (!point_valid(g, a, b, S.c)) { known = true; v = -INFINITY; return false; }
+    const int idx = win_index(S, i, k);
+    if (win_get(W, s, idx, a, b, v)) { known = true; return false; }
+    if ((listed >> idx) & 1ull) return false;
+    if (S.nreq + S.nspec >= kReqMax) return false;
+    listed |= 1ull << idx;
+    const int r = S.nreq + S.nspec;
+    S.ra[r] = a;
+    S.rb[r] = b;
+    S.rw[r] = idx;
+    return true;
+}
+
+// Points that later decisions of a blocked move level will want if the walk
+// goes on: the 3 x 3 neighbourhoods of the next two centres along the last
+// move (before the first move, the 16 points at distance 2), or the next
+// eight points of a 1D line in the direction of travel (both sides before the
+// first move). All lie within 3 lattice steps (9 on a line) of the centre, so
+// the window keeps them until they are needed.
+__device__ void speculate(PackShared &W, int s, const GridDev &g, unsigned long long listed)
+{
+    Slot &S = W.s[s];
+    bool known;
+    float v;
+    auto add = [&](int i, int k) {
+        if (list_point(W, s, g, i, k, listed, known, v)) S.nspec += 1;
+    };
+    if (S.line) {
+        const int d = S.param == 0 ? S.da : S.db;
+        for (int t = 2; t < 10; ++t) {
+            const int m = d != 0 ? d * t : ((t & 1) ? -(t / 2 + 1) : (t / 2 + 1));
+            add(S.ia + (S.param == 0 ? m : 0), S.ib + (S.param == 1 ? m : 0));
+        }
+        return;
+    }
+    if (S.da == 0 && S.db == 0) {
+        for (int i = -2; i <= 2; ++i)
+            for (int k = -2; k <= 2; ++k)
+                if (i == -2 || i == 2 || k == -2 || k == 2) add(S.ia + i, S.ib + k);
+        return;
+    }
+    for (int t = 1; t <= 2; ++t)
+        for (int i = -1; i <= 1; ++i)
+            for (int k = -1; k <= 1; ++k) add(S.ia + t * S.da + i, S.ib + t * S.db + k);
+}
+
+// Run slot s's decisions as far as the known values allow. On return the slot
+// is scanning (positions are handed out elastically), waits for its S.nreq
+// listed points, or is idle.
+__device__ void advance(PackShared &W, int s, const ZoomPlan &P, const GridDev &g, int max_moves)
+{
+    Slot &S = W.s[s];
+    S.nreq = 0;
+    S.nspec = 0;
+    for (;;) {
+        const int st = S.stage;
+        if (S.v < 0) return;
+        if (is_scan(st)) {
+            if (S.p <= S.p_end) return;
+            if (isfinite(S.g2)) S.mm = fminf(S.mm, S.g1 - S.g2);
+            S.level = 0;
+            enter(W, s, st == kS1a ? kS1b : st == kS1b ? kS1c : st == kS1c ? kS2 : kS4, P, g.n_df);
+            continue;
+        }
+        if (st == kFinal) {
+            S.ra[0] = S.a;
+            S.rb[0] = S.b;
+            S.rw[0] = 0;
+            S.nreq = 1;
+            return;
+        }
+        // the points of the next decision, in the canonical order: a 1D line
+        // compares left then right, a 2D move the 8 neighbours with the T1
+        // offset outer and -1 before +1
+        const int npts = S.line ? 2 : 8;
+        float vals[8];
+        int di[8], dk[8];
+        unsigned long long listed = 0;
+        bool missing = false;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            vals[q] = -INFINITY;
+            di[q] = dk[q] = 0;
+            if (q >= npts) continue;
+            if (S.line) {
+                const int m = q == 0 ? -1 : 1;
+                di[q] = S.param == 0 ? m : 0;
+                dk[q] = S.param == 1 ? m : 0;
+            } else {
+                const int k = q < 4 ? q : q + 1;
+                di[q] = k / 3 - 1;
+                dk[q] = k % 3 - 1;
+            }
+            bool known;
+            if (list_point(W, s, g, S.ia + di[q], S.ib + dk[q], listed, known, vals[q])) S.nreq += 1;
+            if (!known) missing = true;
+        }
+        if (missing) {
+            speculate(W, s, g, listed);
+            return;
+        }
+        if (++S.moves > max_moves) { S.ok = 0; S.stage = kFinal; continue; }
+        float t1 = S.centre, t2 = -INFINITY, best = -INFINITY;
+        int bdi = 0, bdk = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float v = vals[q];
+            if (isfinite(v)) { S.evaluated += 1; top2_add(v, t1, t2); }
+            if (v > best) { best = v; bdi = di[q]; bdk = dk[q]; }
+        }
+        if (isfinite(t2)) S.mm = fminf(S.mm, t1 - t2);
+        if (best > S.centre) {
+            S.ia += bdi;
+            S.ib += bdk;
+            S.da = bdi;
+            S.db = bdk;
+            S.a = S.la + S.ia * S.h1;
+            S.b = S.lb + S.ib * S.h2;
+            S.centre = best;
+            continue;
+        }
+        if (st == kS5) { S.stage = kFinal; continue; }
+        S.level += 1;
+        enter(W, s, st, P, g.n_df);
+    }
+}
+
+// Lane 0: the round's table -- every slot's missing points first (rotating
+// slot order), then consecutive df positions for the scanning slots, then the
+// speculative points, one slot at a time.
+__device__ void assign(PackShared &W)
+{
+    int used = 0;
+    const int rot = W.rot;
+    for (int i = 0; i < kSlots; ++i) {
+        const int s = (rot + i) % kSlots;
+        const Slot &S = W.s[s];
+        if (S.v < 0) continue;
+        const int tag = S.stage == kFinal ? kTagFinal : kTagMove;
+        for (int r = 0; r < S.nreq && used < kTable; ++r, ++used) {
+            W.t_slot[used] = s; W.t_a[used] = S.ra[r]; W.t_b[used] = S.rb[r]; W.t_c[used] = S.c;
+            W.t_tag[used] = tag | (S.rw[r] << 8);
+        }
+    }
+    int left[kSlots], give[kSlots];
+    int active = 0;
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+        const Slot &S = W.s[s];
+        left[s] = (S.v >= 0 && is_scan(S.stage)) ? max(0, S.p_end - S.p + 1) : 0;
+        give[s] = 0;
+        active += left[s] > 0;
+    }
+    int free_lanes = kTable - used;
+    while (free_lanes > 0 && active > 0) {
+        const int share = max(1, free_lanes / active);
+        active = 0;
+        for (int i = 0; i < kSlots && free_lanes > 0; ++i) {
+            const int s = (rot + i) % kSlots;
+            if (left[s] <= 0) continue;
+            const int gv = min(share, min(left[s], free_lanes));
+            give[s] += gv;
+            left[s] -= gv;
+            free_lanes -= gv;
+            active += left[s] > 0;
+        }
+    }
+    for (int s = 0; s < kSlots; ++s) {
+        const Slot &S = W.s[s];
+        for (int k = 0; k < give[s]; ++k, ++used) {
+            const int c = S.start + (S.p + k) * S.step;
+            W.t_slot[used] = s;
+            W.t_a[used] = c == S.skip ? -1 : S.a;    // the excluded point is not simulated
+            W.t_b[used] = S.b;
+            W.t_c[used] = c;
+            W.t_tag[used] = kTagScan;
+        }
+    }
+    int taken[kSlots];
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) taken[s] = 0;
+    for (bool any = true; any && used < kTable;) {
+        any = false;
+        for (int i = 0; i < kSlots && used < kTable; ++i) {
+            const int s = (rot + i) % kSlots;
+            const Slot &S = W.s[s];
+            if (S.v < 0 || S.stage == kFinal || is_scan(S.stage) || taken[s] >= S.nspec) continue;
+            const int r = S.nreq + taken[s];
+            taken[s] += 1;
+            W.t_slot[used] = s; W.t_a[used] = S.ra[r]; W.t_b[used] = S.rb[r]; W.t_c[used] = S.c;
+            W.t_tag[used] = kTagMove | (S.rw[r] << 8);
+            ++used;
+            any = true;
+        }
+    }
+    W.used = used;
+    for (; used < kTable; ++used) { W.t_slot[used] = -1; W.t_tag[used] = kTagNone; }
+    W.rot = (rot + 1) % kSlots;
+}
+
+// Slot s takes this round's results: scan positions in order, move points
+// into the window, the final centre's <x, d> into the voxel's result.
+__device__ void ingest(PackShared &W, int s, const GridDev &g, mrf_result *out, int *err)
+{
+    Slot &S = W.s[s];
+    const int used = W.used;
+    for (int t = 0; t < used; ++t) {
+        if (W.t_slot[t] != s) continue;
+        const int tag = W.t_tag[t] & 0xff;
+        const float v = W.r_v[t];
+        if (tag == kTagScan) {
+            if (isfinite(v)) { S.evaluated += 1; top2_add(v, S.g1, S.g2); }
+            if (v > S.centre) { S.centre = v; S.c = W.t_c[t]; }
+            S.p += 1;
+        } else if (tag == kTagMove) {
+            const int idx = W.t_tag[t] >> 8;
+            W.wa[s][idx] = W.t_a[t];
+            W.wb[s][idx] = W.t_b[t];
+            W.wv[s][idx] = v;
+        } else if (tag == kTagFinal) {
+            if (!S.ok) atomicExch(err, kDeviceErrBounds);
+            const float cr = W.r_ipr[t], ci = W.r_ipi[t], cd = W.r_dd[t];
+            mrf_result r;
+            const bool have = isfinite(S.centre);
+            r.index = have ? g.a_off[S.a] + (int64_t)S.b * g.n_df + S.c : -1;
+            r.i_t1 = S.a; r.i_t2 = S.b; r.i_df = S.c;
+            r.t1_ms = g.t1[S.a]; r.t2_ms = g.t2[S.b]; r.df_hz = g.df[S.c];
+            r.cc = have ? S.centre : 0.f;
+            r.m0 = cd > 0.f ? sqrtf(cr * cr + ci * ci) / cd : 0.f;
+            r.phase = atan2f(ci, cr);
+            r.entries_evaluated = S.evaluated;
+            r.min_margin = isfinite(S.mm) ? S.mm : -1.f;
+            out[S.v] = r;
+            S.v = -1;
+        }
+    }
+}
+
+// Simulate table entries lane + 32 u (u < C) and store their results.
+template <bool XONLY, bool SYM, int C>
+__device__ __forceinline__ void eval_entries(PackShared &W, const ZoomArgs &A, int lane)
+{
+    const float2 *x[C];
+    float T1[C], T2[C], df[C], ixn[C];
+    bool ok[C];
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+        const int t = lane + 32 * u;
+        const int s = W.t_slot[t];
+        ok[u] = false;
+        T1[u] = 1000.f; T2[u] = 100.f; df[u] = 0.f; ixn[u] = 0.f;
+        x[u] = A.x;
+        if (s >= 0) {
+            const int a = W.t_a[t], b = W.t_b[t], c = W.t_c[t];
+            ok[u] = point_valid(A.g, a, b, c);
+            if (ok[u]) { T1[u] = __ldg(&A.g.t1[a]); T2[u] = __ldg(&A.g.t2[b]); df[u] = __ldg(&A.g.df[c]); }
+            x[u] = A.x + (size_t)W.s[s].v * A.s.n;
+            ixn[u] = W.s[s].inv_xn;
+        }
+    }
+    __syncwarp();
+    Eval e[C];
+    sim_multi<XONLY, SYM, C>(A.s, x, T1, T2, df, ixn, ok, e);
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+        const int t = lane + 32 * u;
+        W.r_v[t] = e[u].v;
+        W.r_ipr[t] = e[u].ipr;
+        W.r_ipi[t] = e[u].ipi;
+        W.r_dd[t] = e[u].dd;
+    }
+}
+
+template <bool XONLY, bool SYM>
+__global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
+{
+    __shared__ ZoomPlan sP;
+    __shared__ PackShared sW[kPackWarps];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    PackShared &W = sW[threadIdx.x >> 5];
+    if (threadIdx.x == 0) sP = A.plan;
+    if (lane < kSlots) W.s[lane].v = -1;
+    if (lane == 0) { W.drained = 0; W.rot = 0; W.norm_mask = 0; W.used = 0; }
+    __syncthreads();
+    const ZoomPlan &P = sP;
+    const int n = A.s.n;
+
+    for (;;) {
+        // decisions (one lane per slot)
+        if (lane < kSlots) {
+            const int s = lane;
+            ingest(W, s, A.g, A.out, A.err);
+            Slot &S = W.s[s];
+            if (S.v < 0 && !W.drained) {
+                const int nv = atomicAdd(A.counter, 1);
+                if (nv < A.V) {
+                    S.v = nv;
+                    S.a = P.a0; S.b = P.b0; S.c = 0;
+                    S.centre = -INFINITY;
+                    S.evaluated = 0;
+                    S.mm = INFINITY;
+                    S.ok = 1;
+                    S.level = 0;
+                    atomicOr(&W.norm_mask, 1 << s);
+                    enter(W, s, kS1a, P, A.g.n_df);
+                } else {
+                    W.drained = 1;
+                }
+            }
+            advance(W, s, P, A.g, A.max_moves);
+        }
+        __syncwarp();
+        const bool busy = lane < kSlots && W.s[lane].v >= 0;
+        if (!__any_sync(FULL, busy)) break;
+        // ||x|| of the voxels that arrived this round (whole warp)
+        int mask = W.norm_mask;
+        while (mask) {
+            const int s = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const float2 *x = A.x + (size_t)W.s[s].v * n;
+            float xx = 0.f;
+            for (int j = lane; j < n; j += 32) {
+                const float2 z = __ldg(&x[j]);
+                xx = fmaf(z.x, z.x, fmaf(z.y, z.y, xx));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) xx += __shfl_xor_sync(FULL, xx, o);
+            if (lane == 0) W.s[s].inv_xn = xx > 0.f ? rsqrtf(xx) : 0.f;
+        }
+        if (lane == 0) {
+            W.norm_mask = 0;
+            assign(W);
+        }
+        __syncwarp();
+        // busy slots always list at least one point; a round with none would
+        // repeat forever, so it ends the warp with an error instead
+        const int used = W.used;
+        if (used == 0) {
+            if (lane == 0) atomicExch(A.err, kDeviceErrBounds);
+            break;
+        }
+        if (used > 32) eval_entries<XONLY, SYM, 2>(W, A, lane);
+        else eval_entries<XONLY, SYM, 1>(W, A, lane);
+        __syncwarp();
+    }
+}
+
 int snap(double h_phys, double step)
 {
     const int h = (int)floor(h_phys / step + 0.5);
     return h < 1 ? 1 : h;
+}
+
+// Grid of the packed kernel: every resident CTA slot of the device, but no
+// more CTAs than the voxels need (kSlots voxels in flight per warp). The four
+// instantiations share one resource footprint up to a few registers.
+unsigned pack_blocks(const mrf_ctx *ctx, int64_t V)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_pack_kernel<true, true>, kPackThreads, 0);
+    per_sm = std::max(1, per_sm);
+    const int64_t per_cta = (int64_t)kSlots * kPackWarps;
+    const int64_t blocks = std::min<int64_t>((int64_t)per_sm * ctx->sm_count, (V + per_cta - 1) / per_cta);
+    return (unsigned)std::max<int64_t>(blocks, 1);
+}
+
+// Launch the packed kernel instantiated for the sequence's RF form and symmetry.
+void launch_pack(const ZoomArgs &A, unsigned blocks, cudaStream_t stream)
+{
+    if (A.s.xonly && A.s.symmetric) zoom_pack_kernel<true, true><<<blocks, kPackThreads, 0, stream>>>(A);
+    else if (A.s.xonly) zoom_pack_kernel<true, false><<<blocks, kPackThreads, 0, stream>>>(A);
+    else if (A.s.symmetric) zoom_pack_kernel<false, true><<<blocks, kPackThreads, 0, stream>>>(A);
+    else zoom_pack_kernel<false, false><<<blocks, kPackThreads, 0, stream>>>(A);
 }
 
 }  // namespace
@@ -803,17 +1249,10 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     A.counter = counter;
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
-    int per_sm = 0;
-    if (A.s.xonly) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<1>, kZoomThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<0>, kZoomThreads, 0);
-    per_sm = std::max(1, per_sm);
-    const int64_t warps_needed = V;
-    int64_t blocks = std::min<int64_t>((int64_t)per_sm * ctx->sm_count, (warps_needed + 7) / 8);
-    blocks = std::max<int64_t>(blocks, 1);
+    const unsigned blocks = pack_blocks(ctx, V);
     {
         ProfScope prof(ctx, kProfZoom, stream);
-        if (A.s.xonly) zoom_kernel<1><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
-        else zoom_kernel<0><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
+        launch_pack(A, blocks, stream);
     }
     e = cudaGetLastError();
     cudaFreeAsync(counter, stream);
@@ -907,13 +1346,13 @@ extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_z
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<3>, kZoomThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_dict_kernel, kZoomThreads, 0);
     per_sm = std::max(1, per_sm);
     int64_t blocks = std::min<int64_t>((int64_t)per_sm * ctx->sm_count, (V + 7) / 8);
     blocks = std::max<int64_t>(blocks, 1);
     {
         ProfScope prof(ctx, kProfZoom, stream);
-        zoom_kernel<3><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
+        zoom_dict_kernel<<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
     }
     e = cudaGetLastError();
     cudaFreeAsync(counter, stream);
@@ -1070,14 +1509,8 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     A.counter = (int *)dev;
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
-    int per_sm = 0;
-    if (A.s.xonly) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<1>, kZoomThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_kernel<0>, kZoomThreads, 0);
-    per_sm = std::max(1, per_sm);
-    int64_t blocks = std::min<int64_t>((int64_t)per_sm * ctx->sm_count, (V + 7) / 8);
-    blocks = std::max<int64_t>(blocks, 1);
-    if (A.s.xonly) zoom_kernel<1><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
-    else zoom_kernel<0><<<(unsigned)blocks, kZoomThreads, 0, stream>>>(A);
+    const unsigned blocks = pack_blocks(ctx, V);
+    launch_pack(A, blocks, stream);
     count_launch(ctx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "zoom launch (static scratch)");
