@@ -22,15 +22,25 @@ namespace {
 
 constexpr int kGenThreads = 128;
 
+// Factor tables. General sequences keep both intervals of a step, TE_j and
+// TR_j - TE_j; a symmetric sequence (TE_j = TR_j - TE_j) keeps one, and its
+// tables are half the size (e1s, e2s, ciss).
 struct Tables {
     const float2 *e1;    // [n_t1][n]: (E1 over TE_j, E1 over TR_j - TE_j)
     const float2 *e2;    // [n_t2][n]
     const float4 *cis;   // [n][n_df]: (cos, sin) over TE_j, then over TR_j - TE_j
+    const float *e1s;    // symmetric: [n_t1][n] E1 over TE_j
+    const float *e2s;    // symmetric: [n_t2][n]
+    const float2 *ciss;  // symmetric: [n][n_df] (cos, sin) over TE_j
     const float *e1_inv; // [n_t1]: E1 over the inversion delay
 };
 
 __global__ void tables_kernel(SeqDev s, GridDev g, float2 *e1, float2 *e2, float4 *cis, float *e1_inv)
 {
+    // symmetric sequences: the same storage holds the one-interval tables
+    float *e1s = reinterpret_cast<float *>(e1), *e2s = reinterpret_cast<float *>(e2);
+    float2 *ciss = reinterpret_cast<float2 *>(cis);
+    const bool sym = s.symmetric;
     const int64_t n = s.n;
     const int64_t n1 = (int64_t)g.n_t1 * n, n2 = (int64_t)g.n_t2 * n, n3 = n * g.n_df;
     const int64_t total = n1 + n2 + n3 + g.n_t1;
@@ -39,13 +49,15 @@ __global__ void tables_kernel(SeqDev s, GridDev g, float2 *e1, float2 *e2, float
             const int a = (int)(i / n), j = (int)(i % n);
             const float2 t = s.tau[j];
             const float T1 = g.t1[a];
-            e1[i] = make_float2(expf(-t.x / T1), expf(-t.y / T1));
+            if (sym) e1s[i] = expf(-t.x / T1);
+            else e1[i] = make_float2(expf(-t.x / T1), expf(-t.y / T1));
         } else if (i < n1 + n2) {
             const int64_t k = i - n1;
             const int b = (int)(k / n), j = (int)(k % n);
             const float2 t = s.tau[j];
             const float T2 = g.t2[b];
-            e2[k] = make_float2(expf(-t.x / T2), expf(-t.y / T2));
+            if (sym) e2s[k] = expf(-t.x / T2);
+            else e2[k] = make_float2(expf(-t.x / T2), expf(-t.y / T2));
         } else if (i < n1 + n2 + n3) {
             const int64_t k = i - n1 - n2;
             const int j = (int)(k / g.n_df), c = (int)(k % g.n_df);
@@ -56,8 +68,12 @@ __global__ void tables_kernel(SeqDev s, GridDev g, float2 *e1, float2 *e2, float
             tb -= rintf(tb);
             float sa, ca, sb, cb;
             sincospif(2.0f * ta, &sa, &ca);
-            sincospif(2.0f * tb, &sb, &cb);
-            cis[k] = make_float4(ca, sa, cb, sb);
+            if (sym) {
+                ciss[k] = make_float2(ca, sa);
+            } else {
+                sincospif(2.0f * tb, &sb, &cb);
+                cis[k] = make_float4(ca, sa, cb, sb);
+            }
         } else {
             const int a = (int)(i - n1 - n2 - n3);
             e1_inv[a] = expf(-s.inv_delay / g.t1[a]);
@@ -79,19 +95,65 @@ __device__ __forceinline__ void unravel(const GridDev &g, int64_t e, int &a, int
     c = (int)(rem % g.n_df);
 }
 
-// One timepoint with tabulated factors.
-template <bool XONLY>
+// One timepoint with tabulated factors (SYM: one factor set for both
+// intervals of the step).
+template <bool XONLY, bool SYM>
 __device__ __forceinline__ void step_tab(Bloch &st, const SeqDev &s, const Tables &t, int n, int n_df, int a, int b,
                                          int c, int j, float &sr, float &si)
 {
     bloch_rf<XONLY>(st, s, j);
-    const float2 e1 = __ldg(&t.e1[(int64_t)a * n + j]);
-    const float2 e2 = __ldg(&t.e2[(int64_t)b * n + j]);
-    const float4 z = __ldg(&t.cis[(int64_t)j * n_df + c]);
-    bloch_evolve(st, e1.x, e2.x * z.x, e2.x * z.y);
+    if (SYM) {
+        const float e1 = __ldg(&t.e1s[(int64_t)a * n + j]);
+        const float e2 = __ldg(&t.e2s[(int64_t)b * n + j]);
+        const float2 z = __ldg(&t.ciss[(int64_t)j * n_df + c]);
+        const float zr = e2 * z.x, zi = e2 * z.y;
+        bloch_evolve(st, e1, zr, zi);
+        sr = st.mx;
+        si = st.my;
+        bloch_evolve(st, e1, zr, zi);
+    } else {
+        const float2 e1 = __ldg(&t.e1[(int64_t)a * n + j]);
+        const float2 e2 = __ldg(&t.e2[(int64_t)b * n + j]);
+        const float4 z = __ldg(&t.cis[(int64_t)j * n_df + c]);
+        bloch_evolve(st, e1.x, e2.x * z.x, e2.x * z.y);
+        sr = st.mx;
+        si = st.my;
+        bloch_evolve(st, e1.y, e2.y * z.z, e2.y * z.w);
+    }
+}
+
+// Symmetric sequences: the factors of kFacG consecutive timepoints, fetched a
+// group ahead of their use so that one group's table loads overlap the
+// previous group's recurrence (indices past the end are clamped).
+constexpr int kFacG = 8;
+
+struct FacGroup {
+    float e1[kFacG], e2[kFacG];
+    float2 z[kFacG];
+};
+
+__device__ __forceinline__ void fac_load(FacGroup &f, const Tables &t, int n, int n_df, int a, int b, int c, int jb)
+{
+#pragma unroll
+    for (int g = 0; g < kFacG; ++g) {
+        const int j = min(jb + g, n - 1);
+        f.e1[g] = __ldg(&t.e1s[(int64_t)a * n + j]);
+        f.e2[g] = __ldg(&t.e2s[(int64_t)b * n + j]);
+        f.z[g] = __ldg(&t.ciss[(int64_t)j * n_df + c]);
+    }
+}
+
+// One timepoint from preloaded symmetric factors (the same arithmetic as step_tab).
+template <bool XONLY>
+__device__ __forceinline__ void step_fac(Bloch &st, const SeqDev &s, const FacGroup &f, int g, int j, float &sr,
+                                         float &si)
+{
+    bloch_rf<XONLY>(st, s, j);
+    const float zr = f.e2[g] * f.z[g].x, zi = f.e2[g] * f.z[g].y;
+    bloch_evolve(st, f.e1[g], zr, zi);
     sr = st.mx;
     si = st.my;
-    bloch_evolve(st, e1.y, e2.y * z.z, e2.y * z.w);
+    bloch_evolve(st, f.e1[g], zr, zi);
 }
 
 // Packs timepoint values into 16-byte vectors for the staged row writer.
@@ -138,7 +200,7 @@ struct Packer<MRF_FP8E4M3> {
     }
 };
 
-template <int OUT, bool XONLY>
+template <int OUT, bool XONLY, bool SYM>
 __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev g, Tables t, int64_t D, int ld,
                                                                uint8_t *out_hi, uint8_t *out_lo, float *norm_out,
                                                                float *scale_out)
@@ -167,19 +229,47 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
     if (live) {
         bloch_init(st);
         if (s.inversion) { bloch_invert(st); st.w *= e1inv; }
-        for (int j0 = 0; j0 < n; j0 += 32) {
+        if constexpr (SYM) {
+            FacGroup cur, nxt;
+            fac_load(cur, t, n, g.n_df, a, b, c, 0);
             float part = 0.f;
-            const int j1 = min(n, j0 + 32);
-            for (int j = j0; j < j1; ++j) {
-                float sr, si;
-                step_tab<XONLY>(st, s, t, n, g.n_df, a, b, c, j, sr, si);
-                part = fmaf(sr, sr, fmaf(si, si, part));
-                if (OUT == MRF_FP8E4M3) amax = fmaxf(amax, fmaxf(fabsf(sr), fabsf(si)));
+            for (int j0 = 0; j0 < n; j0 += kFacG) {
+                fac_load(nxt, t, n, g.n_df, a, b, c, j0 + kFacG);
+#pragma unroll
+                for (int q = 0; q < kFacG; ++q) {
+                    const int j = j0 + q;
+                    if (j < n) {
+                        float sr, si;
+                        step_fac<XONLY>(st, s, cur, q, j, sr, si);
+                        part = fmaf(sr, sr, fmaf(si, si, part));
+                        if (OUT == MRF_FP8E4M3) amax = fmaxf(amax, fmaxf(fabsf(sr), fabsf(si)));
+                    }
+                }
+                if ((j0 + kFacG) % 32 == 0 || j0 + kFacG >= n) {   // 32-timepoint blocks
+                    const float y = part - comp;
+                    const float tt = tot + y;
+                    comp = (tt - tot) - y;
+                    tot = tt;
+                    part = 0.f;
+                }
+                cur = nxt;
             }
-            const float y = part - comp;
-            const float tt = tot + y;
-            comp = (tt - tot) - y;
-            tot = tt;
+        } else {
+            for (int j0 = 0; j0 < n; j0 += 32) {
+                float part = 0.f;
+                const int j1 = min(n, j0 + 32);
+#pragma unroll 8
+                for (int j = j0; j < j1; ++j) {
+                    float sr, si;
+                    step_tab<XONLY, SYM>(st, s, t, n, g.n_df, a, b, c, j, sr, si);
+                    part = fmaf(sr, sr, fmaf(si, si, part));
+                    if (OUT == MRF_FP8E4M3) amax = fmaxf(amax, fmaxf(fabsf(sr), fabsf(si)));
+                }
+                const float y = part - comp;
+                const float tt = tot + y;
+                comp = (tt - tot) - y;
+                tot = tt;
+            }
         }
     }
     const float nrm = sqrtf(tot);
@@ -204,28 +294,65 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
     }
     const int row_bytes = ld * (OUT == MRF_FP8E4M3 ? 1 : 2);
     const int tp_row = row_bytes / kBpt;      // timepoint slots per row (incl. padding)
+    FacGroup cur, nxt;
+    if constexpr (SYM) fac_load(cur, t, n, g.n_df, a, b, c, 0);
     for (int j0 = 0; j0 < tp_row; j0 += kJ) {
+        if constexpr (SYM) {
+            // groups of kFacG timepoints: 8 / kPerVec vectors each
+            constexpr int kVecs = kFacG / kPerVec;
 #pragma unroll 1
-        for (int q = 0; q < 8; ++q) {
-            P pk;
+            for (int gq = 0; gq < kJ / kFacG; ++gq) {
+                const int jg = j0 + gq * kFacG;
+                fac_load(nxt, t, n, g.n_df, a, b, c, jg + kFacG);
+                float vr[kFacG], vi[kFacG];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) { pk.hi[u] = 0u; pk.lo[u] = 0u; }
-#pragma unroll
-            for (int u = 0; u < kPerVec; ++u) {
-                const int j = j0 + q * kPerVec + u;
-                float vr = 0.f, vi = 0.f;
-                if (live && j < n) {
-                    float sr, si;
-                    step_tab<XONLY>(st, s, t, n, g.n_df, a, b, c, j, sr, si);
-                    vr = sr;
-                    vi = si;
+                for (int q = 0; q < kFacG; ++q) {
+                    const int j = jg + q;
+                    vr[q] = 0.f;
+                    vi[q] = 0.f;
+                    if (live && j < n) step_fac<XONLY>(st, s, cur, q, j, vr[q], vi[q]);
                 }
-                pk.put(u, vr * (OUT == MRF_FP8E4M3 ? 1.f : qs), vi * (OUT == MRF_FP8E4M3 ? 1.f : qs),
-                       OUT == MRF_FP8E4M3 ? qs : 1.f);
+#pragma unroll
+                for (int vq = 0; vq < kVecs; ++vq) {
+                    P pk;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) { pk.hi[u] = 0u; pk.lo[u] = 0u; }
+#pragma unroll
+                    for (int u = 0; u < kPerVec; ++u) {
+                        const float xr = vr[vq * kPerVec + u], xi = vi[vq * kPerVec + u];
+                        pk.put(u, xr * (OUT == MRF_FP8E4M3 ? 1.f : qs), xi * (OUT == MRF_FP8E4M3 ? 1.f : qs),
+                               OUT == MRF_FP8E4M3 ? qs : 1.f);
+                    }
+                    const int q = gq * kVecs + vq;
+                    const int pq = q ^ (lane & 7);
+                    stage_hi[warp][lane][pq] = make_uint4(pk.hi[0], pk.hi[1], pk.hi[2], pk.hi[3]);
+                    if (kTwo) stage_lo[kTwo ? warp : 0][lane][pq] = make_uint4(pk.lo[0], pk.lo[1], pk.lo[2], pk.lo[3]);
+                }
+                cur = nxt;
             }
-            const int pq = q ^ (lane & 7);
-            stage_hi[warp][lane][pq] = make_uint4(pk.hi[0], pk.hi[1], pk.hi[2], pk.hi[3]);
-            if (kTwo) stage_lo[kTwo ? warp : 0][lane][pq] = make_uint4(pk.lo[0], pk.lo[1], pk.lo[2], pk.lo[3]);
+        } else {
+#pragma unroll 2
+            for (int q = 0; q < 8; ++q) {
+                P pk;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) { pk.hi[u] = 0u; pk.lo[u] = 0u; }
+#pragma unroll
+                for (int u = 0; u < kPerVec; ++u) {
+                    const int j = j0 + q * kPerVec + u;
+                    float vr = 0.f, vi = 0.f;
+                    if (live && j < n) {
+                        float sr, si;
+                        step_tab<XONLY, SYM>(st, s, t, n, g.n_df, a, b, c, j, sr, si);
+                        vr = sr;
+                        vi = si;
+                    }
+                    pk.put(u, vr * (OUT == MRF_FP8E4M3 ? 1.f : qs), vi * (OUT == MRF_FP8E4M3 ? 1.f : qs),
+                           OUT == MRF_FP8E4M3 ? qs : 1.f);
+                }
+                const int pq = q ^ (lane & 7);
+                stage_hi[warp][lane][pq] = make_uint4(pk.hi[0], pk.hi[1], pk.hi[2], pk.hi[3]);
+                if (kTwo) stage_lo[kTwo ? warp : 0][lane][pq] = make_uint4(pk.lo[0], pk.lo[1], pk.lo[2], pk.lo[3]);
+            }
         }
         __syncwarp();
         const int qq = lane & 7;
@@ -322,22 +449,24 @@ int launch_dict_generate(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream)
     float *e1i = (float *)(tab + al(b1) + al(b2) + al(b3));
     tables_kernel<<<4 * ctx->sm_count, 256, 0, stream>>>(s, g, e1, e2, cis, e1i);
     count_launch(ctx);
-    Tables t{e1, e2, cis, e1i};
+    Tables t{e1, e2, cis, (const float *)e1, (const float *)e2, (const float2 *)cis, e1i};
     const int64_t blocks = (d->entries + kGenThreads - 1) / kGenThreads;
     uint8_t *hi = (uint8_t *)d->hi, *lo = (uint8_t *)d->lo;
-#define MRF_GEN(OUT, XO) dict_gen_kernel<OUT, XO><<<(unsigned)blocks, kGenThreads, 0, stream>>>(s, g, t, d->entries, d->ld, hi, lo, d->norm, d->scale)
+#define MRF_GEN(OUT, XO, SY) dict_gen_kernel<OUT, XO, SY><<<(unsigned)blocks, kGenThreads, 0, stream>>>(s, g, t, d->entries, d->ld, hi, lo, d->norm, d->scale)
+#define MRF_GEN_DT(XO, SY)                                        \
+    do {                                                          \
+        if (d->dtype == MRF_F32) MRF_GEN(MRF_F32, XO, SY);        \
+        else if (d->dtype == MRF_BF16) MRF_GEN(MRF_BF16, XO, SY); \
+        else MRF_GEN(MRF_FP8E4M3, XO, SY);                        \
+    } while (0)
     {
     ProfScope prof(ctx, kProfDictGen, stream);
-    if (s.xonly) {
-        if (d->dtype == MRF_F32) MRF_GEN(MRF_F32, true);
-        else if (d->dtype == MRF_BF16) MRF_GEN(MRF_BF16, true);
-        else MRF_GEN(MRF_FP8E4M3, true);
-    } else {
-        if (d->dtype == MRF_F32) MRF_GEN(MRF_F32, false);
-        else if (d->dtype == MRF_BF16) MRF_GEN(MRF_BF16, false);
-        else MRF_GEN(MRF_FP8E4M3, false);
+    if (s.xonly && s.symmetric) MRF_GEN_DT(true, true);
+    else if (s.xonly) MRF_GEN_DT(true, false);
+    else if (s.symmetric) MRF_GEN_DT(false, true);
+    else MRF_GEN_DT(false, false);
     }
-    }
+#undef MRF_GEN_DT
 #undef MRF_GEN
     e = cudaGetLastError();
     cudaFreeAsync(tab, stream);

@@ -182,11 +182,12 @@ __device__ __forceinline__ void sim_multi(const SeqDev &s, const float2 *const (
     const int n = s.n;
     int j0 = 0;
     for (; j0 + 16 <= n; j0 += 16) {
-        // each voxel's samples two blocks ahead into L1 (lanes read different voxels)
+        // each voxel's samples four blocks ahead into L1 (lanes read different
+        // voxels, whose rows need not stay in L2 while all are in flight)
 #pragma unroll
         for (int u = 0; u < C; ++u) {
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(x[u] + min(j0 + 32, n - 1)));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(x[u] + min(j0 + 47, n - 1)));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(x[u] + min(j0 + 64, n - 1)));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(x[u] + min(j0 + 79, n - 1)));
         }
 #pragma unroll 4
         for (int jj = 0; jj < 16; ++jj) step_multi<XONLY, SYM, C>(s, j0 + jj, k1, k2, f, st, acc, x);
