@@ -85,6 +85,10 @@ struct MatchParams {
     int k_blocks;        // K blocks of 128 bytes
     int last_ksteps;     // MMA k-steps in the last K block (rest is zero padding)
     const float *colscale;   // FP8: per-entry dequantisation scale, else nullptr
+    int col_stride;      // dictionary entry of tile column c is c * col_stride (sampled pre-pass)
+    const float *thr0;   // per-voxel lower bound on the K-th best CC^2 (thr0[v * thr0_stride]), or nullptr
+    int thr0_stride;
+    float *thr_live;     // per-voxel bound shared by the CTAs of one pass (atomic max of their K-th bests), or nullptr
     float2 *part;        // [V][n_chunks][K]: (cc2, idx bits)
     int *err;
 };
@@ -310,7 +314,19 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
             const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
             const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
             tk.reset();
-            float thr = -1.0f;                     // current K-th best
+            // Values below a lower bound on the voxel's K-th best CC^2 over the
+            // whole dictionary (the K-th best of a subset of it, slightly
+            // lowered for rounding) cannot be among its K best: they are
+            // filtered before the list ever sees them.
+            float seed = -1.0f;
+            if (p.thr0) {
+                const int64_t vs = (int64_t)(vu * NB + blk) * (BM / 2) + (row >> 1);
+                const float lb = vs < p.V ? __ldg(&p.thr0[vs * p.thr0_stride]) : -1.0f;
+                if (lb > 0.f) seed = lb * (1.0f - 1.0e-6f);
+            }
+            float thr = seed;                      // current K-th best (or the bound)
+            const int64_t vrow = (int64_t)(vu * NB + blk) * (BM / 2) + (row >> 1);
+            const bool vlive = vrow < p.V;
             for (int t = t0; t < t1; ++t) {
                 const bool ok = mbar_wait_bounded(&tfull_bar[buf], buf_ph, &abort_flag, p.err, kWaitLimitNs);
                 if (!__all_sync(0xffffffffu, ok)) goto epi_done;   // leave as a whole warp
@@ -324,6 +340,24 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                     tmem_wait_ld();
                     const int col0 = t * BN + ch * 32 + (par ? 16 : 0);
                     float c2v[16];
+                    float sc16[16];
+                    if (MODE == MRF_FP8E4M3) {
+                        if (p.col_stride == 1 && col0 + 16 <= p.D) {
+                            // 16 consecutive scales from a 16-byte aligned offset
+                            const float4 *s4 = reinterpret_cast<const float4 *>(p.colscale + col0);
+#pragma unroll
+                            for (int q4 = 0; q4 < 4; ++q4) {
+                                const float4 f = __ldg(s4 + q4);
+                                sc16[4 * q4] = f.x; sc16[4 * q4 + 1] = f.y; sc16[4 * q4 + 2] = f.z; sc16[4 * q4 + 3] = f.w;
+                            }
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                const int col = col0 + q;
+                                sc16[q] = col < p.D ? __ldg(&p.colscale[(int64_t)col * p.col_stride]) : 0.f;
+                            }
+                        }
+                    }
                     uint32_t mask = 0;
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
@@ -335,10 +369,7 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                         const float im = par ? mine_hi : recv;
                         float c2 = fmaf(re, re, im * im);
                         const int col = col0 + q;
-                        if (MODE == MRF_FP8E4M3) {
-                            const float sc = col < p.D ? __ldg(&p.colscale[col]) : 0.f;
-                            c2 *= sc * sc;
-                        }
+                        if (MODE == MRF_FP8E4M3) c2 *= sc16[q] * sc16[q];
                         c2v[q] = c2;
                         mask |= (col < p.D && c2 > thr) ? (1u << q) : 0u;
                     }
@@ -347,13 +378,23 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                         const int q = __ffs(mask) - 1;
                         mask &= mask - 1;
                         tk.insert(sel16(c2v, q), col0 + q);
-                        thr = tk.v[K - 1];
+                        thr = fmaxf(seed, tk.v[K - 1]);
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty_bar[buf]);
                 if (++buf == NBUF) { buf = 0; buf_ph ^= 1; }
+                if (p.thr_live && vlive) {
+                    // this lane's K-th best covers a subset of the dictionary, so it
+                    // bounds the voxel's K-th best; share it with the other chunks
+                    // (non-negative floats order like their bit patterns)
+                    int *cell = reinterpret_cast<int *>(p.thr_live + vrow);
+                    if (tk.v[K - 1] > 0.f) atomicMax(cell, __float_as_int(tk.v[K - 1]));
+                    const float lb = __int_as_float(__ldcg(cell));
+                    if (lb > 0.f) seed = fmaxf(seed, lb * (1.0f - 1.0e-6f));
+                    thr = fmaxf(seed, tk.v[K - 1]);
+                }
             }
             // merge the Re/Im pair's lists (each covered half of the columns):
             // only the even lane inserts, so the odd lane's list stays intact
@@ -609,13 +650,15 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 }
 
 // 2D K-major map: rows x ld elements, box = (128 bytes of K) x box_rows, 128-byte swizzle.
-int make_map(CUtensorMap *m, const void *base, int64_t rows, int ld, int elem_bytes, int box_rows)
+// 2D tensor map over `rows` rows of `ld` elements; consecutive map rows are
+// `row_step` stored rows apart (1: dense; > 1: a strided sample).
+int make_map(CUtensorMap *m, const void *base, int64_t rows, int ld, int elem_bytes, int box_rows, int row_step = 1)
 {
     auto enc = get_encode();
     if (!enc) return set_error(MRF_E_CUDA, "cuTensorMapEncodeTiled unavailable");
     const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
     cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * elem_bytes};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * elem_bytes * (cuuint64_t)row_step};
     cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -640,7 +683,6 @@ int launch_match_k(mrf_ctx *ctx, const CUtensorMap &mA, const CUtensorMap &mA2, 
     }
     const int units = p.n_vu * p.n_chunks;
     const int grid = std::min(units, ctx->sm_count);
-    ProfScope prof(ctx, kProfMatcher, stream);
     match_kernel<MODE, K><<<grid, threads_of<MODE>(), smem_bytes<MODE>(), stream>>>(mA, mA2, mB, mB2, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "matcher launch");
@@ -691,7 +733,18 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     const int kstep = mode == MRF_FP8E4M3 ? 32 : 16;
     const int last_ksteps = (k_valid + kstep - 1) / kstep;
 
-    // scratch: A operands, row scales, partial lists, candidates
+    // Threshold pre-pass (K >= 8 on large dictionaries): the same matcher
+    // over every kSample-th entry gives each voxel the K-th best CC^2 of that
+    // subset, a lower bound on its K-th best over the whole dictionary. The
+    // full pass starts every top-k list at that bound, so far fewer columns
+    // reach the insertion; the merged result is the same.
+    constexpr int kSample = 64;
+    const int64_t D_s = (d->entries + kSample - 1) / kSample;
+    const int n_tiles_s = (int)((D_s + BN - 1) / BN);
+    const bool seeded = K >= 8 && n_tiles_s >= 4;
+    const int n_chunks_s = seeded ? std::max(1, std::min(n_tiles_s, ctx->sm_count / std::max(1, n_vu))) : 0;
+
+    // scratch: A operands, row scales, partial lists, candidates, pre-pass lists and bounds
     auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
     const size_t bA = (size_t)(2 * V_pad) * d->ld * ebytes;
     const size_t bA2 = mode == MRF_F32 ? bA : 0;
@@ -699,7 +752,11 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     const size_t bP = sizeof(float2) * (size_t)V * n_chunks * K;
     const size_t bI = idx_out ? 0 : sizeof(int64_t) * (size_t)V * K;
     const size_t bC = cc2_out ? 0 : sizeof(float) * (size_t)V * K;
-    const size_t total = al(bA) + al(bA2) + al(bRS) + al(bP) + al(bI) + al(bC);
+    const size_t bPs = seeded ? sizeof(float2) * (size_t)V * n_chunks_s * K : 0;
+    const size_t bIs = seeded ? sizeof(int64_t) * (size_t)V * K : 0;
+    const size_t bCs = seeded ? sizeof(float) * (size_t)V * K : 0;
+    const size_t bL = K >= 8 ? sizeof(float) * (size_t)V : 0;
+    const size_t total = al(bA) + al(bA2) + al(bRS) + al(bP) + al(bI) + al(bC) + al(bPs) + al(bIs) + al(bCs) + al(bL);
     int rc = budget_charge(ctx, total);
     if (rc) return rc;
     uint8_t *ws = nullptr;
@@ -711,6 +768,11 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     float2 *pP = (float2 *)((uint8_t *)pRS + al(bRS));
     int64_t *pI = idx_out ? idx_out : (int64_t *)((uint8_t *)pP + al(bP));
     float *pC = cc2_out ? cc2_out : (float *)((uint8_t *)pP + al(bP) + al(bI));
+    uint8_t *pS = (uint8_t *)pP + al(bP) + al(bI) + al(bC);
+    float2 *pPs = (float2 *)pS;
+    int64_t *pIs = (int64_t *)(pS + al(bPs));
+    float *pCs = (float *)(pS + al(bPs) + al(bIs));
+    float *pL = bL ? (float *)(pS + al(bPs) + al(bIs) + al(bCs)) : nullptr;
 
     auto finish = [&](int code) {
         cudaFreeAsync(ws, stream);
@@ -747,28 +809,68 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     p.k_blocks = k_blocks;
     p.last_ksteps = last_ksteps;
     p.colscale = mode == MRF_FP8E4M3 ? d->scale : nullptr;
+    p.col_stride = 1;
+    p.thr0 = nullptr;
+    p.thr0_stride = 0;
+    p.thr_live = nullptr;
     p.part = pP;
     p.err = ctx->err_flag;
-    {
+
+    const unsigned mblocks = (unsigned)((V + 3) / 4);
+    auto merge = [&](const float2 *part, int chunks, const float *row_scale, int64_t *io, float *co) {
+        switch (K) {
+        case 1: merge_kernel<1><<<mblocks, 128, 0, stream>>>(part, V, chunks, row_scale, io, co); break;
+        case 2: merge_kernel<2><<<mblocks, 128, 0, stream>>>(part, V, chunks, row_scale, io, co); break;
+        case 4: merge_kernel<4><<<mblocks, 128, 0, stream>>>(part, V, chunks, row_scale, io, co); break;
+        case 8: merge_kernel<8><<<mblocks, 128, 0, stream>>>(part, V, chunks, row_scale, io, co); break;
+        case 16: merge_kernel<16><<<mblocks, 128, 0, stream>>>(part, V, chunks, row_scale, io, co); break;
+        case 32: merge_kernel<32><<<mblocks, 128, 0, stream>>>(part, V, chunks, row_scale, io, co); break;
+        }
+        count_launch(ctx);
+        return cudaGetLastError();
+    };
+    auto launch_all = [&](const CUtensorMap &b, const CUtensorMap &b2, const MatchParams &pp) {
         std::lock_guard<std::mutex> lk(g_match_attr_mu);
-        if (mode == MRF_F32) rc = launch_match_mode<MRF_F32>(ctx, K, mA, mA2, mB, mB2, p, stream);
-        else if (mode == MRF_BF16) rc = launch_match_mode<MRF_BF16>(ctx, K, mA, mA2, mB, mB2, p, stream);
-        else rc = launch_match_mode<MRF_FP8E4M3>(ctx, K, mA, mA2, mB, mB2, p, stream);
+        if (mode == MRF_F32) return launch_match_mode<MRF_F32>(ctx, K, mA, mA2, b, b2, pp, stream);
+        if (mode == MRF_BF16) return launch_match_mode<MRF_BF16>(ctx, K, mA, mA2, b, b2, pp, stream);
+        return launch_match_mode<MRF_FP8E4M3>(ctx, K, mA, mA2, b, b2, pp, stream);
+    };
+    {
+        // one timed region: pre-pass, its merge and the full pass
+        ProfScope prof(ctx, kProfMatcher, stream);
+        if (seeded) {
+            CUtensorMap mBs, mB2s;
+            rc = make_map(&mBs, d->hi, D_s, d->ld, ebytes, BN, kSample);
+            if (!rc && mode == MRF_F32) rc = make_map(&mB2s, d->lo, D_s, d->ld, ebytes, BN, kSample);
+            if (rc) return finish(rc);
+            if (mode != MRF_F32) mB2s = mBs;
+            MatchParams ps = p;
+            ps.D = D_s;
+            ps.n_tiles = n_tiles_s;
+            ps.n_chunks = n_chunks_s;
+            ps.group_vu = n_vu;
+            ps.col_stride = kSample;
+            ps.part = pPs;
+            rc = launch_all(mBs, mB2s, ps);
+            if (rc) return finish(rc);
+            count_launch(ctx);
+            // bounds in the kernel's units (no FP8 row scale)
+            e = merge(pPs, n_chunks_s, nullptr, pIs, pCs);
+            if (e != cudaSuccess) return finish(cuda_fail(e, "pre-pass merge launch"));
+            p.thr0 = pCs + (K - 1);
+            p.thr0_stride = K;
+        }
+        if (pL) {
+            e = cudaMemsetAsync(pL, 0, bL, stream);
+            if (e != cudaSuccess) return finish(cuda_fail(e, "bound scratch"));
+            p.thr_live = pL;
+        }
+        rc = launch_all(mB, mB2, p);
     }
     if (rc) return finish(rc);
 
     // 3. merge chunk lists
-    const unsigned mblocks = (unsigned)((V + 3) / 4);
-    switch (K) {
-    case 1: merge_kernel<1><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
-    case 2: merge_kernel<2><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
-    case 4: merge_kernel<4><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
-    case 8: merge_kernel<8><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
-    case 16: merge_kernel<16><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
-    case 32: merge_kernel<32><<<mblocks, 128, 0, stream>>>(pP, V, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC); break;
-    }
-    count_launch(ctx);
-    e = cudaGetLastError();
+    e = merge(pP, n_chunks, mode == MRF_FP8E4M3 ? pRS : nullptr, pI, pC);
     if (e != cudaSuccess) return finish(cuda_fail(e, "merge launch"));
 
     // 4. re-score / finalize

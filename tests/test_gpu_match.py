@@ -162,6 +162,32 @@ def test_ragged_no_rescore_keeps_tensor_core_rank1(M, ctx, ragged):
     assert (res["index"] == idx[:, 0]).all()
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_seeded_topk_head_equals_unseeded_list(M, ctx, oracle_lib, precision):
+    """Top-k lists with k >= 8 over a dictionary of at least 4 x 256 x 64
+    entries start from a per-voxel bound, the k-th best CC^2 of every 64th
+    entry; values below it cannot be among the k best. The head of such a
+    list must therefore equal, bit for bit, the top-4 list that the same
+    arithmetic gives without a bound."""
+    seq = S.sequence(3, 200)
+    g = S.Grid(100.0, 20.0, 96, 10.0, 10.0, 40, -20.0, 2.0, 21)
+    assert oracle_lib.grid_count(g) >= 4 * 256 * 64
+    ph, x = offgrid_voxels(oracle_lib, seq, 200, 20.0, 17, t1_range=(150.0, 1900.0), t2_range=(15.0, 380.0),
+                           df_range=(-18.0, 18.0))
+    h = M.mrf_sequence_load(ctx, seq)
+    d = M.mrf_dict_generate(ctx, h, g, precision)
+    try:
+        i32, c32 = _topk(M, ctx, d, x, precision, 32)
+        i4, c4 = _topk(M, ctx, d, x, precision, 4)
+        np.testing.assert_array_equal(i32[:, :4], i4)
+        np.testing.assert_array_equal(c32[:, :4], c4)
+        assert (np.diff(c32, axis=1) <= 0).all()
+        assert all(len(set(r)) == 32 for r in i32)
+    finally:
+        M.mrf_dict_free(ctx, d)
+        M.mrf_sequence_free(ctx, h)
+
+
 def test_topk_larger_than_dictionary(M, ctx, oracle_lib):
     seq = S.sequence(3, 64)
     g = S.Grid(300.0, 100.0, 4, 20.0, 40.0, 3, 0.0, 1.0, 1)   # 12 entries
