@@ -95,6 +95,8 @@ def lib():
                                       ip, dp, ip, dp, C.c_int32, ip, ip, dp]
         L.or_zoom.argtypes = [C.POINTER(OrSeq), C.POINTER(OrGrid), C.POINTER(OrZoomOpts), dp, C.c_int64,
                               ip, dp, dp, dp, ip, dp]
+        L.or_refine_generic.argtypes = [C.POINTER(OrGrid), C.c_int32, SCORE_FN, C.c_void_p, ip, dp, ip, dp]
+        L.or_refine.argtypes = [C.POINTER(OrSeq), C.POINTER(OrGrid), dp, C.c_int64, C.c_int32, ip, dp, dp, dp, ip, dp]
         L.or_default_omega.argtypes = [C.POINTER(OrSeq)]
         L.or_default_omega.restype = C.c_double
         L.or_num_threads.restype = C.c_int
@@ -275,3 +277,35 @@ def zoom_generic(g, score, omega, opts=None, trace_cap=100000):
     n = min(int(tn[0]), trace_cap)
     return dict(abc=tuple(int(v) for v in abc), cc=float(ccv[0]), evaluated=int(ev[0]),
                 min_margin=float(mm[0]), trace=tr[:n].copy(), trace_cc=tcc[:n].copy())
+
+
+def refine_generic(g, score, start, max_moves=1 << 20):
+    """Windowed refinement over a Python score(a, b, c) -> float (test hook)."""
+    cb = SCORE_FN(lambda _ctx, a, b, c: float(score(a, b, c)))
+    abc = np.array(start, np.int32)
+    ccv = np.zeros(1)
+    ev = np.zeros(1, np.int32)
+    mm = np.zeros(1)
+    rc = lib().or_refine_generic(C.byref(_grid(g)), int(max_moves), cb, None, _ip(abc), _dp(ccv), _ip(ev), _dp(mm))
+    if rc != 0:
+        raise RuntimeError(f"or_refine_generic failed: {rc}")
+    return dict(abc=tuple(int(v) for v in abc), cc=float(ccv[0]), evaluated=int(ev[0]), min_margin=float(mm[0]))
+
+
+def refine(seq, g, x, start_abc, max_moves=1 << 20):
+    """Windowed refinement per voxel from start_abc (V, 3). Returns dict(abc,
+    cc, m0, phase, evaluated, min_margin)."""
+    h = _SeqHandle(seq)
+    xi = _interleave(np.atleast_2d(x))
+    V = xi.shape[0]
+    abc = np.ascontiguousarray(np.asarray(start_abc, np.int32).reshape(V, 3)).copy()
+    ccs = np.zeros(V)
+    m0 = np.zeros(V)
+    ph = np.zeros(V)
+    ev = np.zeros(V, np.int32)
+    mm = np.zeros(V)
+    rc = lib().or_refine(C.byref(h.c), C.byref(_grid(g)), _dp(xi), V, int(max_moves), _ip(abc), _dp(ccs), _dp(m0),
+                         _dp(ph), _ip(ev), _dp(mm))
+    if rc != 0:
+        raise RuntimeError(f"or_refine failed: {rc}")
+    return dict(abc=abc, cc=ccs, m0=m0, phase=ph, evaluated=ev, min_margin=mm)

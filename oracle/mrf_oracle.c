@@ -18,6 +18,8 @@
  *     Experiment 2 step 1, the 2D ZOOM of Fig. 2, the df refinement of step 3,
  *     the interleaved 1D ZOOMs of Fig. 1 / step 4 and the final 2D ZOOM of
  *     step 5.
+ *   - Windowed refinement: the windowed brute-force check around a ZOOM
+ *     answer (Results, Experiment 2), repeated as a hill climb on the grid.
  *
  * Precision: IEEE double throughout, libm exp/sin/cos, no FMA contraction
  * (built with -ffp-contract=off). OpenMP parallelises over independent
@@ -642,6 +644,103 @@ int or_zoom(const or_seq *s, const or_grid *g, const or_zoom_opts *o, const doub
                 }
                 evaluated[v] = z.evaluated;
                 min_margin[v] = z.min_margin;
+                simulate_one(s, t1_of(g, r[0]), t2_of(g, r[1]), df_of(g, r[2]), NULL, d, NULL);
+                double re, im;
+                inner(n, k.x, d, &re, &im);
+                double dd = norm2(n, d);
+                if (m0) m0[v] = dd > 0.0 ? sqrt(re * re + im * im) / dd : 0.0;
+                if (phase) phase[v] = atan2(im, re);
+            }
+            free(d);
+        }
+    }
+    return err;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Windowed refinement. Results (Experiment 2) checks ZOOM answers with a
+ * brute-force search in a small window around them; applied repeatedly it is
+ * a hill climb on the full grid: compare the centre with the 26 points of its
+ * 3 x 3 x 3 neighbourhood (T1 offset outer, then T2, then df; -1 before +1),
+ * move to the best of them when it is strictly better than the centre (the
+ * first in that order on ties), and stop when the centre wins. The starting
+ * centre is evaluated too. Points off the grid or with T2 >= T1 (when the
+ * grid requires T2 < T1) are never evaluated. min_margin: the smallest gap
+ * between the two largest finite values of a decision set.                 */
+
+static int refine_run(const or_grid *g, or_score_fn fn, void *ctx, int32_t max_moves, int32_t *a, int32_t *b,
+                      int32_t *c, double *centre, int32_t *evaluated, double *min_margin)
+{
+    if (*c < 0 || *c >= g->n_df || !valid_ab(g, *a, *b)) return -1;
+    double cv = fn(ctx, *a, *b, *c);
+    ++*evaluated;
+    int32_t it;
+    for (it = 0; it < max_moves; ++it) {
+        double t1 = cv, t2 = -INFINITY, best = -INFINITY;
+        int32_t ba = *a, bb = *b, bc = *c;
+        for (int da = -1; da <= 1; ++da)
+            for (int db = -1; db <= 1; ++db)
+                for (int dc = -1; dc <= 1; ++dc) {
+                    if (da == 0 && db == 0 && dc == 0) continue;
+                    const int32_t na = *a + da, nb = *b + db, nc = *c + dc;
+                    if (nc < 0 || nc >= g->n_df || !valid_ab(g, na, nb)) continue;
+                    const double v = fn(ctx, na, nb, nc);
+                    ++*evaluated;
+                    if (v > t1) { t2 = t1; t1 = v; } else if (v > t2) t2 = v;
+                    if (v > best) { best = v; ba = na; bb = nb; bc = nc; }
+                }
+        if (isfinite(t2) && t1 - t2 < *min_margin) *min_margin = t1 - t2;
+        if (!(best > cv)) break;
+        *a = ba; *b = bb; *c = bc; cv = best;
+    }
+    *centre = cv;
+    return it < max_moves ? 0 : -3;
+}
+
+/* Refinement on an arbitrary score function (test hook). abc: in/out. */
+int or_refine_generic(const or_grid *g, int32_t max_moves, or_score_fn fn, void *ctx, int32_t *abc, double *cc,
+                      int32_t *evaluated, double *min_margin)
+{
+    if (!grid_ok(g) || !fn || max_moves < 0) return -1;
+    int32_t ev = 0;
+    double mm = INFINITY;
+    int rc = refine_run(g, fn, ctx, max_moves, &abc[0], &abc[1], &abc[2], cc, &ev, &mm);
+    if (evaluated) *evaluated = ev;
+    if (min_margin) *min_margin = mm;
+    return rc;
+}
+
+/* Refinement for V voxels (x: V x n interleaved) from the starting points in
+ * abc (V x 3, in/out). Outputs per voxel: CC, M0, phase of the final point,
+ * candidates evaluated, smallest decision margin (+inf when no decision had
+ * two finite values). OpenMP over voxels. */
+int or_refine(const or_seq *s, const or_grid *g, const double *x, int64_t V, int32_t max_moves, int32_t *abc,
+              double *cc, double *m0, double *phase, int32_t *evaluated, double *min_margin)
+{
+    if (!s || s->n < 1 || !grid_ok(g) || V < 0 || max_moves < 0) return -1;
+    const int32_t n = s->n;
+    int err = 0;
+    #pragma omp parallel
+    {
+        double *d = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+        if (!d) {
+            #pragma omp atomic write
+            err = -2;
+        } else {
+            #pragma omp for schedule(dynamic, 1)
+            for (int64_t v = 0; v < V; ++v) {
+                cc_ctx k = {s, g, x + (size_t)v * 2 * n, sqrt(norm2(n, x + (size_t)v * 2 * n)), d};
+                int32_t *r = abc + 3 * v;
+                int32_t ev = 0;
+                double mm = INFINITY;
+                int rc = refine_run(g, score_cc, &k, max_moves, &r[0], &r[1], &r[2], &cc[v], &ev, &mm);
+                if (rc != 0) {
+                    #pragma omp atomic write
+                    err = rc;
+                    continue;
+                }
+                evaluated[v] = ev;
+                min_margin[v] = mm;
                 simulate_one(s, t1_of(g, r[0]), t2_of(g, r[1]), df_of(g, r[2]), NULL, d, NULL);
                 double re, im;
                 inner(n, k.x, d, &re, &im);

@@ -340,3 +340,83 @@ def test_bruteforce_exact_ties_go_to_smaller_index(oracle_lib):
     # entries (a, b=1, c=1) for a = 0, 1, 2 are identical -> indices 4, 10, 16
     assert list(r["idx"][0, :3]) == [4, 10, 16]
     assert r["cc"][0, 0] == r["cc"][0, 1] == r["cc"][0, 2]
+
+
+# ------------------------------------------------------- windowed refinement
+
+def test_refine_l1_score_closed_form(oracle_lib):
+    """Score -(|a-a*| + |b-b*| + |c-c*|): the best of the 26 neighbours steps
+    every unsettled coordinate one towards the target, so the climb takes
+    max |delta| moves, ends at the target, and (away from the grid's edges)
+    evaluates 1 + 26 (moves + 1) points; integer scores give a margin of 1."""
+    g = S.Grid(0.0, 1.0, 40, 0.0, 1.0, 40, 0.0, 1.0, 30, 0)
+    target = (25, 14, 9)
+    f = lambda a, b, c: -(abs(a - target[0]) + abs(b - target[1]) + abs(c - target[2]))
+    for start in [(10, 20, 3), (25, 14, 9), (30, 5, 20), (24, 15, 9)]:
+        r = oracle_lib.refine_generic(g, f, start)
+        moves = max(abs(s - t) for s, t in zip(start, target))
+        assert r["abc"] == target
+        assert r["cc"] == 0.0
+        assert r["evaluated"] == 1 + 26 * (moves + 1)
+        assert r["min_margin"] == 1.0
+
+
+def test_refine_ties_follow_neighbour_order(oracle_lib):
+    """Two neighbours tie for best: the first in the order (T1 offset outer,
+    then T2, then df, -1 before +1) wins; (+1, -1, 0) comes before (+1, 0, -1)."""
+    g = S.Grid(0.0, 1.0, 9, 0.0, 1.0, 9, 0.0, 1.0, 9, 0)
+    top = {(5, 3, 4): 1.0, (5, 4, 3): 1.0}
+    f = lambda a, b, c: top.get((a, b, c), 0.0) - (0.5 if (a, b, c) not in top and (a, b, c) != (4, 4, 4) else 0.0)
+    r = oracle_lib.refine_generic(g, f, (4, 4, 4))
+    assert r["abc"] == (5, 3, 4) and r["cc"] == 1.0
+    assert r["min_margin"] == 0.0
+
+
+def test_refine_skips_invalid_points_and_stops_at_max_moves(oracle_lib):
+    g = S.Grid(0.0, 1.0, 12, 0.0, 1.0, 12, 0.0, 1.0, 4, 1)
+    seen = []
+
+    def f(a, b, c):
+        seen.append((a, b, c))
+        return -abs(a - 3) - abs(b - 2) - abs(c - 0)
+
+    r = oracle_lib.refine_generic(g, f, (8, 6, 3))
+    assert all(0 <= b < a < 12 and 0 <= c < 4 for a, b, c in seen)
+    assert r["abc"] == (3, 2, 0) and r["evaluated"] == len(seen)
+    with pytest.raises(RuntimeError):
+        oracle_lib.refine_generic(g, f, (8, 6, 3), max_moves=2)
+
+
+def test_refine_keeps_brute_force_optimum_and_reaches_local_optima(oracle_lib):
+    """From the exhaustive optimum the climb does not move (the global maximum
+    is a local one). From perturbed starts it ends at a point whose FP64 CC is
+    at least that of each of its 26 neighbours (checked here with numpy)."""
+    seq = S.sequence(4, 120)
+    g = S.Grid(200.0, 40.0, 30, 20.0, 15.0, 20, -12.0, 3.0, 9)
+    ph = S.phantom_offgrid(44, 12, t1_range=(400.0, 1300.0), t2_range=(50.0, 250.0), df_range=(-8.0, 8.0))
+    clean = oracle_lib.simulate(seq, ph["t1"], ph["t2"], ph["df"])
+    x = S.compose_voxels(clean, ph["m0"], ph["phase"], *S.noise_draws(44, 12, seq.n), 25.0)
+    bf = oracle_lib.bruteforce(seq, g, x, k=1)
+    a, b, c = oracle_lib.grid_params(g)
+    best = np.stack([a[bf["idx"][:, 0]], b[bf["idx"][:, 0]], c[bf["idx"][:, 0]]], 1)
+    r0 = oracle_lib.refine(seq, g, x, best)
+    assert (r0["abc"] == best).all()
+    np.testing.assert_allclose(r0["cc"], bf["cc"][:, 0], rtol=0, atol=1e-14)
+    rng = np.random.default_rng(9)
+    start = np.clip(best + rng.integers(-4, 5, best.shape), 0, [g.n_t1 - 1, g.n_t2 - 1, g.n_df - 1])
+    t1, t2, df = S.grid_values(g)
+    start[:, 1] = np.minimum(start[:, 1], np.searchsorted(t2, t1[start[:, 0]]) - 1)
+    r = oracle_lib.refine(seq, g, x, start)
+    d0 = oracle_lib.simulate(seq, t1[start[:, 0]], t2[start[:, 1]], df[start[:, 2]])
+    cc0 = np.abs(np.sum(d0.conj() * x, 1)) / (np.linalg.norm(d0, axis=1) * np.linalg.norm(x, axis=1))
+    assert (r["cc"] >= cc0 - 1e-12).all()
+    for v in range(len(x)):
+        ca, cb, cc0 = r["abc"][v]
+        pts = [(ca + i, cb + j, cc0 + k) for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)]
+        pts = [p for p in pts if 0 <= p[0] < g.n_t1 and 0 <= p[1] < g.n_t2 and 0 <= p[2] < g.n_df
+               and t2[p[1]] < t1[p[0]]]
+        pts = np.array(pts)
+        d = oracle_lib.simulate(seq, t1[pts[:, 0]], t2[pts[:, 1]], df[pts[:, 2]])
+        cc = np.abs(d.conj() @ x[v]) / (np.linalg.norm(d, axis=1) * np.linalg.norm(x[v]))
+        assert cc.max() <= r["cc"][v] + 1e-12
+        assert len(pts) == 27 or r["evaluated"][v] >= len(pts)
