@@ -208,7 +208,7 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
     g = S.GRIDS[GRID]
     D = M.mrf_grid_count(g)
 
-    def match_mode(name, grid_name, dtype, k, ref_index=None):
+    def match_mode(name, grid_name, dtype, k, ref_index=None, refine=False):
         gg = S.GRIDS[grid_name]
         Dg = M.mrf_grid_count(gg)
         t0 = time.time()
@@ -216,7 +216,11 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
         torch.cuda.synchronize()
         gen_s = time.time() - t0
         out = M.empty_results(V)
-        run = lambda: M.mrf_match_bruteforce(ctx, d, x_dev, M.match_opts(dtype, k, 1), out)
+
+        def run():
+            M.mrf_match_bruteforce(ctx, d, x_dev, M.match_opts(dtype, k, 1), out)
+            if refine:
+                M.mrf_refine(ctx, seq_h, gg, x_dev, out)
         run()
         M.mrf_profile_read(ctx, reset=True)
         M.mrf_profile_enable(ctx, True)
@@ -232,6 +236,8 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
                  "matcher_tflops_algorithmic": flops / mm / 1e9,
                  "matcher_frac_of_peak": flops / mm / 1e9 / peak,
                  "peak_tflops": peak, "peak_note": "bf16 measured" + (" x 2 (fp8 nominal ratio)" if dtype == 2 else "")}
+        if refine:
+            entry["refined"] = "windowed refinement (26-point hill climb, FP64 CC) after the re-score, timed"
         if ref_index is not None:
             entry["index_agreement_vs_fp32"] = float(np.mean(res["index"] == ref_index))
         if ph is not None:
@@ -243,6 +249,8 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
     match_mode("bf16_rescore_k8", GRID, M.MRF_BF16, 8, fp32_index)
     match_mode("bf16_rescore_k32", GRID, M.MRF_BF16, 32, fp32_index)
     match_mode("fp8_rescore_k32", GRID, M.MRF_FP8E4M3, 32, fp32_index)
+    match_mode("bf16_rescore_k8_refine", GRID, M.MRF_BF16, 8, fp32_index, refine=True)
+    match_mode("fp8_rescore_k8_refine", GRID, M.MRF_FP8E4M3, 8, fp32_index, refine=True)
 
     # ZOOM on the same grid and voxels (agreement with brute force)
     out = M.empty_results(V)
@@ -256,6 +264,17 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
                                "index_agreement_vs_fp32": float(np.mean(res["index"] == fp32_index))}
     if ph is not None:
         modes["zoom_same_grid"]["median_abs_error_vs_truth"] = param_errors(res, ph)
+
+    # ZOOM, then the windowed refinement from its answer
+    def zoom_refined():
+        M.mrf_zoom_search(ctx, seq_h, g, zo, x_dev, out)
+        M.mrf_refine(ctx, seq_h, g, x_dev, out)
+    zoom_refined()
+    ms = timed(zoom_refined, 2)
+    res = M.results_to_numpy(out)[:V]
+    modes["zoom_refine_same_grid"] = {"grid": GRID, "voxels_per_s": V / ms * 1e3, "ms": ms,
+                                      "mean_entries_evaluated": float(res["entries_evaluated"].mean()),
+                                      "index_agreement_vs_fp32": float(np.mean(res["index"] == fp32_index))}
 
     # ZOOM over the resident FP32-equivalent dictionary (Experiment 2's full-dictionary variant)
     d = M.mrf_dict_generate(ctx, seq_h, g, M.MRF_F32)
@@ -275,6 +294,8 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
     ref = match_mode("fp32_fine_grid", "precision", M.MRF_F32, 4)
     match_mode("bf16_rescore_k8_fine_grid", "precision", M.MRF_BF16, 8, ref["index"])
     match_mode("fp8_rescore_k32_fine_grid", "precision", M.MRF_FP8E4M3, 32, ref["index"])
+    match_mode("bf16_rescore_k8_refine_fine_grid", "precision", M.MRF_BF16, 8, ref["index"], refine=True)
+    match_mode("fp8_rescore_k8_refine_fine_grid", "precision", M.MRF_FP8E4M3, 8, ref["index"], refine=True)
     zf = M.zoom_opts()
     gz = S.GRIDS["precision"]
     run = lambda: M.mrf_zoom_search(ctx, seq_h, gz, zf, x_dev, out)
@@ -283,6 +304,15 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
     res = M.results_to_numpy(out)[:V]
     modes["zoom_fine_grid"] = {"grid": "precision", "voxels_per_s": V / ms * 1e3, "ms": ms,
                                "index_agreement_vs_fp32": float(np.mean(res["index"] == ref["index"]))}
+
+    def zoom_fine_refined():
+        M.mrf_zoom_search(ctx, seq_h, gz, zf, x_dev, out)
+        M.mrf_refine(ctx, seq_h, gz, x_dev, out)
+    zoom_fine_refined()
+    ms = timed(zoom_fine_refined, 2)
+    res = M.results_to_numpy(out)[:V]
+    modes["zoom_refine_fine_grid"] = {"grid": "precision", "voxels_per_s": V / ms * 1e3, "ms": ms,
+                                      "index_agreement_vs_fp32": float(np.mean(res["index"] == ref["index"]))}
 
     # high-precision ZOOM: 128x128 slice on the 2.4e9-entry grid (never materialised)
     ph, x128 = make_slice(M, ctx, seq_h, 103, 128 * 128, 20.0)

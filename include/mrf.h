@@ -278,6 +278,28 @@ int mrf_zoom_search(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid,
 int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *dict, const mrf_zoom_opts *opts, const void *fp_dev,
                          int64_t V, mrf_result *out_dev, void *stream);
 
+/* Windowed refinement of per-voxel grid points (Results, Experiment 2: a
+ * brute-force search in a small window around a ZOOM answer, here repeated
+ * as a hill climb). res_dev holds V results; on entry each voxel's start is
+ * (i_t1, i_t2, i_df), and a voxel whose index is < 0 or whose start is not a
+ * valid grid point is left unchanged. From the start, the centre is compared
+ * with the 26 points of its 3 x 3 x 3 grid neighbourhood (T1 offset outer,
+ * then T2, then df, -1 before +1; points off the grid or with T2 >= T1 when
+ * the grid requires T2 < T1 are not evaluated) and moves to the best of them
+ * when it is strictly better (the first in that order on ties), until the
+ * centre wins. CC uses the re-score's arithmetic (FP32 simulation, FP64
+ * accumulation). On return the result describes the final point (index,
+ * indices, values, cc, m0, phase); entries_evaluated is increased by the
+ * points simulated (the start included) and min_margin becomes the smaller
+ * of its entry value (when >= 0) and the climb's smallest gap between the
+ * two best values of a decision. seq and grid must be those the starting
+ * points refer to; fp_dev: V x n complex64. max_moves >= 1 bounds the moves
+ * per voxel; a voxel that reaches it keeps its point and raises a device
+ * error reported by mrf_stream_sync. Errors: MRF_E_INVALID, MRF_E_BUDGET,
+ * MRF_E_CUDA. */
+int mrf_refine(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, const void *fp_dev, int64_t V,
+               int32_t max_moves, mrf_result *res_dev, void *stream);
+
 /* Allocation-free variant of mrf_zoom_search. The paper has no counterpart:
  * it serves callers that cannot let the library allocate device memory
  * during a call -- a framework that already reserved the GPU's memory for

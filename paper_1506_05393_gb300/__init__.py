@@ -114,7 +114,7 @@ EXPORTS = [
     "mrf_dict_generate", "mrf_dict_free", "mrf_dict_query", "mrf_match_bruteforce", "mrf_match_topk",
     "mrf_zoom_opts_default", "mrf_zoom_search", "mrf_serve_start", "mrf_serve_submit", "mrf_serve_poll",
     "mrf_serve_cancel", "mrf_serve_get_stats", "mrf_serve_stop", "mrf_profile_enable", "mrf_profile_read",
-    "mrf_zoom_search_static", "mrf_zoom_search_dict",
+    "mrf_zoom_search_static", "mrf_zoom_search_dict", "mrf_refine",
 ]
 
 
@@ -152,6 +152,7 @@ def lib():
         L.mrf_zoom_opts_default.argtypes = [C.POINTER(ZoomOpts)]
         L.mrf_zoom_opts_default.restype = None
         L.mrf_zoom_search.argtypes = [vp, vp, C.POINTER(GridDesc), C.POINTER(ZoomOpts), vp, i64, vp, vp]
+        L.mrf_refine.argtypes = [vp, vp, C.POINTER(GridDesc), vp, i64, i32, vp, vp]
         L.mrf_serve_start.argtypes = [vp, C.POINTER(ServeConfig)]
         L.mrf_serve_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
         L.mrf_serve_poll.argtypes = [vp, C.c_uint64, i32, vp]
@@ -301,6 +302,13 @@ def mrf_zoom_search(ctx, seq, grid, opts, fp, out, stream=None) -> None:
     g = grid_desc(grid)
     check(lib().mrf_zoom_search(ctx, seq, C.byref(g), C.byref(opts) if opts is not None else None, _ptr(fp),
                                 fp.shape[0], _ptr(out), _stream_ptr(stream)), "mrf_zoom_search")
+
+
+def mrf_refine(ctx, seq, grid, fp, res, max_moves=1 << 20, stream=None) -> None:
+    """Windowed refinement of the results in res (in place) from their grid points."""
+    g = grid_desc(grid)
+    check(lib().mrf_refine(ctx, seq, C.byref(g), _ptr(fp), fp.shape[0], int(max_moves), _ptr(res),
+                           _stream_ptr(stream)), "mrf_refine")
 
 
 def mrf_zoom_search_dict(ctx, d, opts, fp, out, stream=None) -> None:
