@@ -95,6 +95,9 @@ def lib():
                                       ip, dp, ip, dp, C.c_int32, ip, ip, dp]
         L.or_zoom.argtypes = [C.POINTER(OrSeq), C.POINTER(OrGrid), C.POINTER(OrZoomOpts), dp, C.c_int64,
                               ip, dp, dp, dp, ip, dp]
+        L.or_smooth.argtypes = [C.c_int32, C.c_int64, dp, C.c_int32, C.c_double, dp]
+        L.or_bruteforce_smooth.argtypes = [C.POINTER(OrSeq), C.POINTER(OrGrid), dp, C.c_int64, C.c_int32, C.c_int32,
+                                           C.c_double, lp, dp, dp, dp]
         L.or_refine_generic.argtypes = [C.POINTER(OrGrid), C.c_int32, SCORE_FN, C.c_void_p, ip, dp, ip, dp]
         L.or_refine.argtypes = [C.POINTER(OrSeq), C.POINTER(OrGrid), dp, C.c_int64, C.c_int32, ip, dp, dp, dp, ip, dp]
         L.or_default_omega.argtypes = [C.POINTER(OrSeq)]
@@ -220,8 +223,9 @@ def grid_params(g):
     return a, b, c
 
 
-def bruteforce(seq, g, x, k: int = 1):
-    """Top-k by Eq. 1 for each voxel. Returns dict(idx (V,k), cc (V,k), m0 (V,), phase (V,))."""
+def bruteforce(seq, g, x, k: int = 1, smooth=None):
+    """Top-k by Eq. 1 for each voxel. Returns dict(idx (V,k), cc (V,k), m0 (V,), phase (V,)).
+    smooth = (width, sigma): the dictionary entries are smoothed first (x is used as given)."""
     h = _SeqHandle(seq)
     xi = _interleave(np.atleast_2d(x))
     V = xi.shape[0]
@@ -229,11 +233,28 @@ def bruteforce(seq, g, x, k: int = 1):
     ccs = np.zeros((V, k))
     m0 = np.zeros(V)
     ph = np.zeros(V)
-    rc = lib().or_bruteforce(C.byref(h.c), C.byref(_grid(g)), _dp(xi), V, k,
-                             idx.ctypes.data_as(C.POINTER(C.c_int64)), _dp(ccs), _dp(m0), _dp(ph))
+    lp = C.POINTER(C.c_int64)
+    if smooth is None:
+        rc = lib().or_bruteforce(C.byref(h.c), C.byref(_grid(g)), _dp(xi), V, k, idx.ctypes.data_as(lp), _dp(ccs),
+                                 _dp(m0), _dp(ph))
+    else:
+        rc = lib().or_bruteforce_smooth(C.byref(h.c), C.byref(_grid(g)), _dp(xi), V, k, int(smooth[0]),
+                                        float(smooth[1]), idx.ctypes.data_as(lp), _dp(ccs), _dp(m0), _dp(ph))
     if rc != 0:
         raise RuntimeError(f"or_bruteforce failed: {rc}")
     return dict(idx=idx, cc=ccs, m0=m0, phase=ph)
+
+
+def smooth(x, width: int, sigma: float = 1.0):
+    """Temporal smoothing of V x n complex timecourses (Experiment 4)."""
+    x2 = np.atleast_2d(np.asarray(x, np.complex128))
+    V, n = x2.shape
+    xi = _interleave(x2)
+    out = np.zeros_like(xi)
+    rc = lib().or_smooth(n, V, _dp(xi), int(width), float(sigma), _dp(out))
+    if rc != 0:
+        raise RuntimeError(f"or_smooth failed: {rc}")
+    return out[..., 0] + 1j * out[..., 1]
 
 
 def default_omega(seq) -> float:

@@ -20,6 +20,8 @@
  *     step 5.
  *   - Windowed refinement: the windowed brute-force check around a ZOOM
  *     answer (Results, Experiment 2), repeated as a hill climb on the grid.
+ *   - Temporal smoothing of fingerprints and dictionary entries (Methods,
+ *     Experiment 4), and brute force against a smoothed dictionary.
  *
  * Precision: IEEE double throughout, libm exp/sin/cos, no FMA contraction
  * (built with -ffp-contract=off). OpenMP parallelises over independent
@@ -256,6 +258,39 @@ int64_t or_grid_params(const or_grid *g, int64_t cap, int32_t *a_out, int32_t *b
 }
 
 /* ------------------------------------------------------------------------- */
+/* Temporal smoothing (Methods, Experiment 4: "3 points and 5 points moving
+ * Gaussian smoothing" of the fingerprints and of the dictionary). Each sample
+ * becomes the weighted mean of the samples within h = (width - 1) / 2 of it,
+ * weights exp(-k^2 / (2 sigma^2)), renormalised over the samples that exist
+ * at the ends of the timecourse; Re and Im alike. width = 1: the identity.
+ * x and out: n interleaved complex samples, distinct arrays.              */
+
+static void smooth_one(int32_t n, const double *x, int32_t width, double sigma, double *out)
+{
+    const int32_t h = (width - 1) / 2;
+    for (int32_t j = 0; j < n; ++j) {
+        double wr = 0.0, sr = 0.0, si = 0.0;
+        for (int32_t k = -h; k <= h; ++k) {
+            const int32_t i = j + k;
+            if (i < 0 || i >= n) continue;
+            const double w = exp(-(double)(k * k) / (2.0 * sigma * sigma));
+            wr += w;
+            sr += w * x[2 * i];
+            si += w * x[2 * i + 1];
+        }
+        out[2 * j] = sr / wr;
+        out[2 * j + 1] = si / wr;
+    }
+}
+
+int or_smooth(int32_t n, int64_t V, const double *x, int32_t width, double sigma, double *out)
+{
+    if (n < 1 || V < 0 || width < 1 || (width & 1) == 0 || !(sigma > 0.0)) return -1;
+    for (int64_t v = 0; v < V; ++v) smooth_one(n, x + (size_t)v * 2 * n, width, sigma, out + (size_t)v * 2 * n);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Brute-force DGS: for every voxel, the top-k entries by Eq. 1 (descending
  * CC, ties to the smaller linear index), plus M0 = |<x,d>| / ||d||^2 and
  * phase = arg <x,d> of the best entry (Theory: proton density from scale). */
@@ -275,10 +310,15 @@ static void topk_insert(or_cand *list, int32_t k, double cc, int64_t idx)
     list[p].cc = cc; list[p].idx = idx;
 }
 
-int or_bruteforce(const or_seq *s, const or_grid *g, const double *x, int64_t V, int32_t k,
-                  int64_t *top_idx, double *top_cc, double *m0, double *phase)
+/* Brute force against a dictionary whose entries are smoothed (width, sigma)
+ * before their norm and CC are taken; width = 1 is the plain dictionary. The
+ * fingerprints x are used as given (smooth them with or_smooth to smooth both
+ * sides). */
+static int bruteforce_impl(const or_seq *s, const or_grid *g, const double *x, int64_t V, int32_t k,
+                           int32_t width, double sigma, int64_t *top_idx, double *top_cc, double *m0, double *phase)
 {
     if (!s || s->n < 1 || !grid_ok(g) || V < 0 || k < 1) return -1;
+    if (width < 1 || (width & 1) == 0 || !(sigma > 0.0)) return -1;
     if (V == 0) return 0;
     const int32_t n = s->n;
     double *xn = (double *)malloc(sizeof(double) * (size_t)V);
@@ -304,18 +344,24 @@ int or_bruteforce(const or_seq *s, const or_grid *g, const double *x, int64_t V,
         tid = omp_get_thread_num();
 #endif
         or_cand *mine = all + (size_t)tid * (size_t)V * (size_t)k;
-        double *d = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+        double *d = (double *)malloc(sizeof(double) * 4 * (size_t)n);
         if (!d) {
             #pragma omp atomic write
             err = 1;
         } else {
+            double *raw = d + 2 * (size_t)n;
             #pragma omp for schedule(dynamic, 1)
             for (int32_t a = 0; a < g->n_t1; ++a) {
                 int64_t idx = a_off[a];
                 int32_t nb = nb_valid(g, a);
                 for (int32_t b = 0; b < nb; ++b)
                     for (int32_t c = 0; c < g->n_df; ++c, ++idx) {
-                        simulate_one(s, t1_of(g, a), t2_of(g, b), df_of(g, c), NULL, d, NULL);
+                        if (width == 1) {
+                            simulate_one(s, t1_of(g, a), t2_of(g, b), df_of(g, c), NULL, d, NULL);
+                        } else {
+                            simulate_one(s, t1_of(g, a), t2_of(g, b), df_of(g, c), NULL, raw, NULL);
+                            smooth_one(n, raw, width, sigma, d);
+                        }
                         double nd = sqrt(norm2(n, d));
                         for (int64_t v = 0; v < V; ++v) {
                             double re, im, cc = 0.0;
@@ -331,7 +377,7 @@ int or_bruteforce(const or_seq *s, const or_grid *g, const double *x, int64_t V,
     if (err) { free(all); free(xn); free(a_off); return -2; }
 
     /* merge the per-thread lists, then M0 and phase of each voxel's best */
-    double *d = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+    double *d = (double *)malloc(sizeof(double) * 4 * (size_t)n);
     for (int64_t v = 0; v < V; ++v) {
         or_cand *dst = all + (size_t)v * k;   /* thread 0's list */
         for (int t = 1; t < nthreads; ++t) {
@@ -349,7 +395,12 @@ int or_bruteforce(const or_seq *s, const or_grid *g, const double *x, int64_t V,
             while (a + 1 <= g->n_t1 && a_off[a + 1] <= best) ++a;
             int64_t rem = best - a_off[a];
             int32_t b = (int32_t)(rem / g->n_df), c = (int32_t)(rem % g->n_df);
-            simulate_one(s, t1_of(g, a), t2_of(g, b), df_of(g, c), NULL, d, NULL);
+            if (width == 1) {
+                simulate_one(s, t1_of(g, a), t2_of(g, b), df_of(g, c), NULL, d, NULL);
+            } else {
+                simulate_one(s, t1_of(g, a), t2_of(g, b), df_of(g, c), NULL, d + 2 * (size_t)n, NULL);
+                smooth_one(n, d + 2 * (size_t)n, width, sigma, d);
+            }
             double re, im;
             inner(n, x + (size_t)v * 2 * n, d, &re, &im);
             double dd = norm2(n, d);
@@ -359,6 +410,18 @@ int or_bruteforce(const or_seq *s, const or_grid *g, const double *x, int64_t V,
     }
     free(d); free(all); free(xn); free(a_off);
     return 0;
+}
+
+int or_bruteforce(const or_seq *s, const or_grid *g, const double *x, int64_t V, int32_t k,
+                  int64_t *top_idx, double *top_cc, double *m0, double *phase)
+{
+    return bruteforce_impl(s, g, x, V, k, 1, 1.0, top_idx, top_cc, m0, phase);
+}
+
+int or_bruteforce_smooth(const or_seq *s, const or_grid *g, const double *x, int64_t V, int32_t k, int32_t width,
+                         double sigma, int64_t *top_idx, double *top_cc, double *m0, double *phase)
+{
+    return bruteforce_impl(s, g, x, V, k, width, sigma, top_idx, top_cc, m0, phase);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -420,3 +420,52 @@ def test_refine_keeps_brute_force_optimum_and_reaches_local_optima(oracle_lib):
         cc = np.abs(d.conj() @ x[v]) / (np.linalg.norm(d, axis=1) * np.linalg.norm(x[v]))
         assert cc.max() <= r["cc"][v] + 1e-12
         assert len(pts) == 27 or r["evaluated"][v] >= len(pts)
+
+
+# ---------------------------------------------------------- temporal smoothing
+
+def test_smoothing_closed_forms(oracle_lib):
+    """Gaussian weights exp(-k^2 / 2 sigma^2), renormalised where the window
+    leaves the timecourse: constants are unchanged, an interior linear ramp is
+    unchanged (symmetric weights), an impulse returns the normalised weights,
+    and width 1 is the identity."""
+    n = 40
+    c = np.full((1, n), 0.3 - 0.7j)
+    for w in (3, 5):
+        np.testing.assert_allclose(oracle_lib.smooth(c, w), c, rtol=0, atol=1e-15)
+    ramp = (np.arange(n) * (0.25 + 0.5j))[None, :]
+    out = oracle_lib.smooth(ramp, 5, 1.3)
+    np.testing.assert_allclose(out[0, 2:-2], ramp[0, 2:-2], rtol=0, atol=1e-13)
+    imp = np.zeros((1, n), complex)
+    imp[0, 20] = 1.0
+    for w, s in ((3, 1.0), (5, 1.0), (5, 0.7)):
+        h = (w - 1) // 2
+        wts = np.exp(-np.arange(-h, h + 1) ** 2 / (2 * s * s))
+        out = oracle_lib.smooth(imp, w, s)[0]
+        # sample 20 + k receives weight w_{-k} of the impulse over the full window sum
+        np.testing.assert_allclose(out[20 - h: 21 + h].real, wts[::-1] / wts.sum(), rtol=1e-14)
+        assert np.abs(np.delete(out, np.arange(20 - h, 21 + h))).max() == 0.0
+    # the first sample's window is cut to samples 0..h, renormalised there
+    x = np.arange(1, n + 1, dtype=float)[None, :] + 0j
+    wts = np.exp(-np.arange(0, 3) ** 2 / 2.0)
+    np.testing.assert_allclose(oracle_lib.smooth(x, 5)[0, 0].real, (wts * x[0, :3].real).sum() / wts.sum(), rtol=1e-14)
+    rng = np.random.default_rng(3)
+    z = rng.normal(size=(2, n)) + 1j * rng.normal(size=(2, n))
+    np.testing.assert_array_equal(oracle_lib.smooth(z, 1), z)
+
+
+def test_smoothed_bruteforce_recovers_on_grid_voxels(oracle_lib):
+    """Smoothing is linear and applied alike to both sides, so a noise-free
+    on-grid fingerprint, smoothed, still matches its own smoothed entry with
+    CC = 1 and the applied scale as M0."""
+    seq, g, ph, x = _tiny_voxels(oracle_lib, 24, None, seed=300)
+    for w in (3, 5):
+        xs = oracle_lib.smooth(x, w)
+        r = oracle_lib.bruteforce(seq, g, xs, k=1, smooth=(w, 1.0))
+        a, b, c = oracle_lib.grid_params(g)
+        assert (a[r["idx"][:, 0]] == ph["a"]).all() and (b[r["idx"][:, 0]] == ph["b"]).all()
+        np.testing.assert_allclose(r["cc"][:, 0], 1.0, atol=1e-12)
+        np.testing.assert_allclose(r["m0"], ph["m0"], rtol=1e-12)
+    # smoothing the dictionary alone changes the scores: the plain entry no longer matches exactly
+    r1 = oracle_lib.bruteforce(seq, g, x, k=1, smooth=(5, 1.0))
+    assert (r1["cc"][:, 0] < 1.0 - 1e-6).all()
