@@ -183,8 +183,34 @@ typedef struct {
     const float *norm_dev; /* D: L2 norm of the un-normalised FP32 signal */
     const float *scale_dev;/* D: FP8 dequantisation scale (FP8 only), else NULL */
     size_t bytes;          /* device bytes charged to the budget */
+    int32_t smooth_width;  /* temporal smoothing applied by mrf_dict_smooth (1: none) */
+    double smooth_sigma;
 } mrf_dict_info;
 int mrf_dict_query(const mrf_dict *dict, mrf_dict_info *info);
+
+/* Temporal smoothing (Methods, Experiment 4: 3- and 5-point moving Gaussian
+ * smoothing of the fingerprints and of the dictionary). Each sample becomes
+ * the weighted mean of the samples within h = (width - 1) / 2 of it, weights
+ * exp(-k^2 / (2 sigma^2)) renormalised over the samples that exist at the
+ * ends of the timecourse; Re and Im alike. width is 1 (identity), 3 or 5;
+ * sigma > 0 in samples (1 is the usual choice).
+ *
+ * mrf_smooth: in_dev and out_dev are distinct V x n complex64 device arrays
+ * (caller-owned), out = smooth(in); runs on `stream`.
+ *
+ * mrf_dict_smooth: smooths a generated MRF_F32 or MRF_BF16 dictionary's
+ * entries in place and renormalises them to unit norm; the stored norms
+ * become those of the smoothed un-normalised entries, and the dictionary
+ * remembers the smoothing, so that its top-k re-score smooths the
+ * re-simulated candidates alike (mrf_match_bruteforce then matches smoothed
+ * fingerprints, which the caller smooths with mrf_smooth, against smoothed
+ * entries, as in the paper's test of smoothing "both" sides). A dictionary
+ * is smoothed at most once. ZOOM on the fly and mrf_refine simulate
+ * unsmoothed candidates. Errors: MRF_E_INVALID (width, sigma, aliasing,
+ * already smoothed), MRF_E_UNSUPPORTED (FP8 dictionary), MRF_E_CUDA. */
+int mrf_smooth(mrf_ctx *ctx, const void *in_dev, void *out_dev, int64_t V, int32_t n, int32_t width, double sigma,
+               void *stream);
+int mrf_dict_smooth(mrf_ctx *ctx, mrf_dict *dict, int32_t width, double sigma, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Matching                                                                 */

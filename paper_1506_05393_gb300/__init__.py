@@ -59,7 +59,8 @@ class GridDesc(C.Structure):
 class DictInfo(C.Structure):
     _fields_ = [("entries", C.c_int64), ("n", C.c_int32), ("ld", C.c_int32), ("dtype", C.c_int32),
                 ("hi_dev", C.c_void_p), ("lo_dev", C.c_void_p), ("norm_dev", C.c_void_p),
-                ("scale_dev", C.c_void_p), ("bytes", C.c_size_t)]
+                ("scale_dev", C.c_void_p), ("bytes", C.c_size_t), ("smooth_width", C.c_int32),
+                ("smooth_sigma", C.c_double)]
 
 
 class MatchOpts(C.Structure):
@@ -114,7 +115,7 @@ EXPORTS = [
     "mrf_dict_generate", "mrf_dict_free", "mrf_dict_query", "mrf_match_bruteforce", "mrf_match_topk",
     "mrf_zoom_opts_default", "mrf_zoom_search", "mrf_serve_start", "mrf_serve_submit", "mrf_serve_poll",
     "mrf_serve_cancel", "mrf_serve_get_stats", "mrf_serve_stop", "mrf_profile_enable", "mrf_profile_read",
-    "mrf_zoom_search_static", "mrf_zoom_search_dict", "mrf_refine",
+    "mrf_zoom_search_static", "mrf_zoom_search_dict", "mrf_refine", "mrf_smooth", "mrf_dict_smooth",
 ]
 
 
@@ -153,6 +154,8 @@ def lib():
         L.mrf_zoom_opts_default.restype = None
         L.mrf_zoom_search.argtypes = [vp, vp, C.POINTER(GridDesc), C.POINTER(ZoomOpts), vp, i64, vp, vp]
         L.mrf_refine.argtypes = [vp, vp, C.POINTER(GridDesc), vp, i64, i32, vp, vp]
+        L.mrf_smooth.argtypes = [vp, vp, vp, i64, i32, i32, C.c_double, vp]
+        L.mrf_dict_smooth.argtypes = [vp, vp, i32, C.c_double, vp]
         L.mrf_serve_start.argtypes = [vp, C.POINTER(ServeConfig)]
         L.mrf_serve_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
         L.mrf_serve_poll.argtypes = [vp, C.c_uint64, i32, vp]
@@ -272,6 +275,18 @@ def mrf_dict_generate(ctx, seq, grid, dtype: int, stream=None):
 
 def mrf_dict_free(ctx, d) -> None:
     check(lib().mrf_dict_free(ctx, d), "mrf_dict_free")
+
+
+def mrf_smooth(ctx, fp_in, fp_out, width: int, sigma: float = 1.0, stream=None) -> None:
+    """Temporal smoothing of V x n complex64 CUDA tensors (distinct in and out)."""
+    V, n = fp_in.shape
+    check(lib().mrf_smooth(ctx, _ptr(fp_in), _ptr(fp_out), V, n, int(width), float(sigma), _stream_ptr(stream)),
+          "mrf_smooth")
+
+
+def mrf_dict_smooth(ctx, d, width: int, sigma: float = 1.0, stream=None) -> None:
+    """Smooth a generated FP32-equivalent or BF16 dictionary in place."""
+    check(lib().mrf_dict_smooth(ctx, d, int(width), float(sigma), _stream_ptr(stream)), "mrf_dict_smooth")
 
 
 def mrf_dict_query(d) -> DictInfo:

@@ -567,6 +567,8 @@ extern "C" int mrf_dict_query(const mrf_dict *d, mrf_dict_info *info)
     info->norm_dev = d->norm;
     info->scale_dev = d->scale;
     info->bytes = d->bytes;
+    info->smooth_width = d->smooth_width;
+    info->smooth_sigma = d->smooth_sigma;
     return MRF_OK;
 }
 

@@ -545,9 +545,16 @@ __device__ __forceinline__ void unravel_dev(const GridDev &g, int64_t e, int &a,
     c = (int)(rem % g.n_df);
 }
 
+// Temporal smoothing of the re-simulated candidates (the dictionary's own,
+// see mrf_dict_smooth): half-width h and weights w[k], k = 0..h.
+struct RescoreSmooth {
+    int h;
+    float w[3];
+};
+
 template <bool XONLY>
 __global__ void rescore_kernel(SeqDev s, GridDev g, const float2 *x, int64_t V, int K, const int64_t *cand,
-                               const float *cand_cc2, int rank, int64_t D, mrf_result *out)
+                               const float *cand_cc2, int rank, int64_t D, RescoreSmooth sm, mrf_result *out)
 {
     const int64_t v = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -572,18 +579,63 @@ __global__ void rescore_kernel(SeqDev s, GridDev g, const float2 *x, int64_t V, 
     Bloch st;
     bloch_start(st, s, r);
     double ipr = 0.0, ipi = 0.0, dd = 0.0;
-    for (int j0 = 0; j0 < n; j0 += 8) {
+    if (sm.h == 0) {
+        for (int j0 = 0; j0 < n; j0 += 8) {
+            float pr = 0.f, pi = 0.f, pd = 0.f;
+            const int j1 = min(n, j0 + 8);
+            for (int j = j0; j < j1; ++j) {
+                float sr, si;
+                bloch_step_otf<XONLY>(st, s, r, j, sr, si);
+                const float2 z = __ldg(&xv[j]);
+                // x conj(d) = (xr dr + xi di) + i (xi dr - xr di)
+                pr = fmaf(z.x, sr, fmaf(z.y, si, pr));
+                pi = fmaf(z.y, sr, fmaf(-z.x, si, pi));
+                pd = fmaf(sr, sr, fmaf(si, si, pd));
+            }
+            ipr += (double)pr;
+            ipi += (double)pi;
+            dd += (double)pd;
+        }
+    } else {
+        // raw samples pass through a five-sample ring (ring[4] newest); sample t
+        // is smoothed once s_{t+h} exists, with weights renormalised at the ends
+        float2 ring[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) ring[k] = make_float2(0.f, 0.f);
         float pr = 0.f, pi = 0.f, pd = 0.f;
-        const int j1 = min(n, j0 + 8);
-        for (int j = j0; j < j1; ++j) {
-            float sr, si;
-            bloch_step_otf<XONLY>(st, s, r, j, sr, si);
-            const float2 z = __ldg(&xv[j]);
-            // x conj(d) = (xr dr + xi di) + i (xi dr - xr di)
+        int cnt = 0;
+        auto emit = [&](int t, int newest) {
+            float sr = 0.f, si = 0.f, ws = 0.f;
+            for (int k = -sm.h; k <= sm.h; ++k) {
+                const int tk = t + k;
+                if (tk < 0 || tk > newest) continue;
+                const float2 zz = ring[4 - (newest - tk)];
+                const float w = sm.w[k < 0 ? -k : k];
+                sr = fmaf(w, zz.x, sr);
+                si = fmaf(w, zz.y, si);
+                ws += w;
+            }
+            sr /= ws;
+            si /= ws;
+            const float2 z = __ldg(&xv[t]);
             pr = fmaf(z.x, sr, fmaf(z.y, si, pr));
             pi = fmaf(z.y, sr, fmaf(-z.x, si, pi));
             pd = fmaf(sr, sr, fmaf(si, si, pd));
+            if (++cnt == 8) {
+                ipr += (double)pr; ipi += (double)pi; dd += (double)pd;
+                pr = pi = pd = 0.f;
+                cnt = 0;
+            }
+        };
+        for (int j = 0; j < n; ++j) {
+            float sr, si;
+            bloch_step_otf<XONLY>(st, s, r, j, sr, si);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ring[k] = ring[k + 1];
+            ring[4] = make_float2(sr, si);
+            if (j >= sm.h) emit(j - sm.h, j);
         }
+        for (int t = max(0, n - sm.h); t < n; ++t) emit(t, n - 1);
         ipr += (double)pr;
         ipi += (double)pi;
         dd += (double)pd;
@@ -877,10 +929,13 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     if (out) {
         const SeqDev s = d->seq->dev();
         const GridDev g = d->grid.dev();
+        RescoreSmooth sm;
+        sm.h = d->smooth_h;
+        for (int k = 0; k < 3; ++k) sm.w[k] = d->smooth_w[k];
         if (s.xonly)
-            rescore_kernel<true><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, out);
+            rescore_kernel<true><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, sm, out);
         else
-            rescore_kernel<false><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, out);
+            rescore_kernel<false><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, sm, out);
         count_launch(ctx);
         e = cudaGetLastError();
         if (e != cudaSuccess) return finish(cuda_fail(e, "re-score launch"));

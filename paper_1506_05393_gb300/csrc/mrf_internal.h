@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -88,6 +89,12 @@ struct mrf_dict {
     void *block = nullptr;       // one stream-ordered pool allocation holding hi, lo, norm, scale
     size_t block_bytes = 0;
     size_t bytes = 0;
+    // temporal smoothing applied to the stored entries (mrf_dict_smooth): half-width and
+    // the weights w[k] = exp(-k^2 / (2 sigma^2)); the re-score smooths alike
+    int smooth_h = 0;
+    float smooth_w[3] = {1.f, 0.f, 0.f};
+    int32_t smooth_width = 1;
+    double smooth_sigma = 1.0;
 };
 
 struct ServeState;   // serve.cpp
