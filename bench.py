@@ -640,11 +640,13 @@ def main():
     opts = M.match_opts(M.MRF_F32, 4, 1)
 
     def step():
+        # every use of d and h is on `stream`: release them in its order, so the
+        # host queues the next step while this one runs
         h = M.mrf_sequence_load(ctx, seq)
         d = M.mrf_dict_generate(ctx, h, g, M.MRF_F32, stream)
         M.mrf_match_bruteforce(ctx, d, x_dev, opts, out, stream)
-        M.mrf_dict_free(ctx, d)
-        M.mrf_sequence_free(ctx, h)
+        M.mrf_dict_free_async(ctx, d, stream)
+        M.mrf_sequence_free_async(ctx, h, stream)
 
     for _ in range(args.warmup):
         step()
@@ -685,8 +687,8 @@ def main():
         d = M.mrf_dict_generate(ctx, h, g, M.MRF_F32, stream)
         M.mrf_match_bruteforce(ctx, d, x_e2e, opts, out, stream)
         out_pin.copy_(out, non_blocking=True)
-        M.mrf_dict_free(ctx, d)
-        M.mrf_sequence_free(ctx, h)
+        M.mrf_dict_free_async(ctx, d, stream)
+        M.mrf_sequence_free_async(ctx, h, stream)
         torch.cuda.current_stream().synchronize()
 
     for _ in range(2):

@@ -122,10 +122,17 @@ typedef struct {
 
 /* Copy a host sequence to the device (FP64 host values; per-timepoint RF
  * rotation coefficients are formed in FP64 on the host and stored as FP32).
- * Synchronous. Errors: MRF_E_INVALID (n < 1, non-finite values, TE outside
- * [0, TR], TR <= 0), MRF_E_BUDGET, MRF_E_CUDA. */
+ * Synchronous for the upload only: it runs on the library's own stream and
+ * does not wait for work queued on the caller's streams. Errors:
+ * MRF_E_INVALID (n < 1, non-finite values, TE outside [0, TR], TR <= 0),
+ * MRF_E_BUDGET, MRF_E_CUDA.
+ * mrf_sequence_free waits for all work on the device, then releases the
+ * sequence. mrf_sequence_free_async releases it in the order of `stream`
+ * without waiting: every use of the sequence must already be enqueued on
+ * that stream (or have finished). */
 int mrf_sequence_load(mrf_ctx *ctx, const mrf_sequence_desc *desc, mrf_seq **out);
 int mrf_sequence_free(mrf_ctx *ctx, mrf_seq *seq);
+int mrf_sequence_free_async(mrf_ctx *ctx, mrf_seq *seq, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Parameter grid (Theory: ranges R, S, Q of T1, T2, df)                    */
@@ -169,7 +176,13 @@ int mrf_simulate(mrf_ctx *ctx, const mrf_seq *seq, int64_t count, const float *t
  * MRF_E_BUDGET, MRF_E_NOMEM, MRF_E_CUDA. */
 int mrf_dict_generate(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, mrf_dtype dtype,
                       void *stream, mrf_dict **out);
+/* mrf_dict_free waits for all work on the device, then releases the
+ * dictionary. mrf_dict_free_async releases it in the order of `stream`
+ * without waiting: every use of the dictionary (generation, matching, ZOOM)
+ * must already be enqueued on that stream (or have finished); the memory
+ * returns to the stream-ordered pool. */
 int mrf_dict_free(mrf_ctx *ctx, mrf_dict *dict);
+int mrf_dict_free_async(mrf_ctx *ctx, mrf_dict *dict, void *stream);
 
 /* Read-only view of a dictionary's device storage (for inspection/tests). */
 typedef struct {

@@ -116,6 +116,7 @@ EXPORTS = [
     "mrf_zoom_opts_default", "mrf_zoom_search", "mrf_serve_start", "mrf_serve_submit", "mrf_serve_poll",
     "mrf_serve_cancel", "mrf_serve_get_stats", "mrf_serve_stop", "mrf_profile_enable", "mrf_profile_read",
     "mrf_zoom_search_static", "mrf_zoom_search_dict", "mrf_refine", "mrf_smooth", "mrf_dict_smooth",
+    "mrf_dict_free_async", "mrf_sequence_free_async",
 ]
 
 
@@ -155,6 +156,8 @@ def lib():
         L.mrf_zoom_search.argtypes = [vp, vp, C.POINTER(GridDesc), C.POINTER(ZoomOpts), vp, i64, vp, vp]
         L.mrf_refine.argtypes = [vp, vp, C.POINTER(GridDesc), vp, i64, i32, vp, vp]
         L.mrf_smooth.argtypes = [vp, vp, vp, i64, i32, i32, C.c_double, vp]
+        L.mrf_dict_free_async.argtypes = [vp, vp, vp]
+        L.mrf_sequence_free_async.argtypes = [vp, vp, vp]
         L.mrf_dict_smooth.argtypes = [vp, vp, i32, C.c_double, vp]
         L.mrf_serve_start.argtypes = [vp, C.POINTER(ServeConfig)]
         L.mrf_serve_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
@@ -287,6 +290,16 @@ def mrf_smooth(ctx, fp_in, fp_out, width: int, sigma: float = 1.0, stream=None) 
 def mrf_dict_smooth(ctx, d, width: int, sigma: float = 1.0, stream=None) -> None:
     """Smooth a generated FP32-equivalent or BF16 dictionary in place."""
     check(lib().mrf_dict_smooth(ctx, d, int(width), float(sigma), _stream_ptr(stream)), "mrf_dict_smooth")
+
+
+def mrf_dict_free_async(ctx, d, stream=None) -> None:
+    """Release a dictionary in the order of `stream` (its uses must be enqueued there)."""
+    check(lib().mrf_dict_free_async(ctx, d, _stream_ptr(stream)), "mrf_dict_free_async")
+
+
+def mrf_sequence_free_async(ctx, seq, stream=None) -> None:
+    """Release a sequence in the order of `stream` (its uses must be enqueued there)."""
+    check(lib().mrf_sequence_free_async(ctx, seq, _stream_ptr(stream)), "mrf_sequence_free_async")
 
 
 def mrf_dict_query(d) -> DictInfo:

@@ -46,25 +46,33 @@ int budget_charge(mrf_ctx *ctx, size_t bytes)
 
 void budget_release(mrf_ctx *ctx, size_t bytes) { ctx->used.fetch_sub(bytes); }
 
-int dev_alloc(mrf_ctx *ctx, void **p, size_t bytes, const char *what)
+int upload_block(mrf_ctx *ctx, const void *host, size_t bytes, void **dev, const char *what)
 {
-    *p = nullptr;
+    *dev = nullptr;
     if (bytes == 0) return MRF_OK;
     int rc = budget_charge(ctx, bytes);
     if (rc) return rc;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = cudaMallocAsync(dev, bytes, ctx->aux);
+    if (e == cudaSuccess && host) e = cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, ctx->aux);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->aux);
     if (e != cudaSuccess) {
+        if (*dev) cudaFreeAsync(*dev, ctx->aux);
+        *dev = nullptr;
         budget_release(ctx, bytes);
-        *p = nullptr;
         return cuda_fail(e, what);
     }
     return MRF_OK;
 }
 
-void dev_free(mrf_ctx *ctx, void *p, size_t bytes)
+void release_block(mrf_ctx *ctx, void *p, size_t bytes, cudaStream_t stream, bool sync)
 {
     if (!p) return;
-    cudaFree(p);
+    if (sync) {
+        cudaDeviceSynchronize();
+        cudaFreeAsync(p, ctx->aux);
+    } else {
+        cudaFreeAsync(p, stream);
+    }
     budget_release(ctx, bytes);
 }
 
@@ -114,6 +122,8 @@ extern "C" int mrf_ctx_create(int device, size_t hbm_budget_bytes, mrf_ctx **out
     c->budget = hbm_budget_bytes ? hbm_budget_bytes : free_b;
     e = cudaMalloc(&c->err_flag, sizeof(int));
     if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(err flag)"); }
+    e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { cudaFree(c->err_flag); delete c; return cuda_fail(e, "cudaStreamCreate"); }
     cudaMemset(c->err_flag, 0, sizeof(int));
     // keep stream-ordered scratch in the pool between calls
     cudaMemPool_t pool;
@@ -134,6 +144,7 @@ extern "C" void mrf_ctx_destroy(mrf_ctx *ctx)
     if (ctx->serve) mrf_serve_stop(ctx);
     cudaDeviceSynchronize();
     cudaFree(ctx->err_flag);
+    cudaStreamDestroy(ctx->aux);
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
     delete ctx;
@@ -272,42 +283,44 @@ extern "C" int mrf_sequence_load(mrf_ctx *ctx, const mrf_sequence_desc *d, mrf_s
     mrf_seq *s = new mrf_seq();
     s->n = n; s->xonly = xonly; s->symmetric = symmetric; s->inversion = d->inversion;
     s->inv_delay = d->inv_delay_ms; s->min_tr = min_tr;
-    size_t b1 = sizeof(float4) * n, b2 = sizeof(float) * 12 * (size_t)n, b3 = sizeof(float2) * n;
-    int rc = dev_alloc(ctx, (void **)&s->rfx, b1, "sequence rfx");
-    if (!rc) rc = dev_alloc(ctx, (void **)&s->rfg, b2, "sequence rfg");
-    if (!rc) rc = dev_alloc(ctx, (void **)&s->tau, b3, "sequence tau");
-    if (rc) { seq_release(ctx, s); return rc; }
-    s->bytes = b1 + b2 + b3;
-    cudaError_t e = cudaMemcpy(s->rfx, rfx.data(), b1, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(s->rfg, rfg.data(), b2, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(s->tau, tau.data(), b3, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { seq_release(ctx, s); return cuda_fail(e, "sequence upload"); }
+    // rfx | rfg | tau in one block, 256-byte aligned pieces
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t b1 = sizeof(float4) * n, b2 = sizeof(float) * 12 * (size_t)n, b3 = sizeof(float2) * n;
+    const size_t o2 = al(b1), o3 = o2 + al(b2), total = o3 + al(b3);
+    std::vector<uint8_t> h(total, 0);
+    memcpy(h.data(), rfx.data(), b1);
+    memcpy(h.data() + o2, rfg.data(), b2);
+    memcpy(h.data() + o3, tau.data(), b3);
+    int rc = upload_block(ctx, h.data(), total, &s->block, "sequence upload");
+    if (rc) { delete s; return rc; }
+    s->bytes = total;
+    s->rfx = (float4 *)s->block;
+    s->rfg = (float *)((uint8_t *)s->block + o2);
+    s->tau = (float2 *)((uint8_t *)s->block + o3);
     *out = s;
     return MRF_OK;
 }
 
-void seq_release(mrf_ctx *ctx, mrf_seq *s)
+void seq_release(mrf_ctx *ctx, mrf_seq *s, cudaStream_t stream, bool sync)
 {
     if (!s) return;
-    if (s->rfx) dev_free(ctx, s->rfx, sizeof(float4) * s->n);
-    if (s->rfg) dev_free(ctx, s->rfg, sizeof(float) * 12 * (size_t)s->n);
-    if (s->tau) dev_free(ctx, s->tau, sizeof(float2) * s->n);
+    release_block(ctx, s->block, s->bytes, stream, sync);
     delete s;
 }
 
 int seq_clone(mrf_ctx *ctx, const mrf_seq *src, mrf_seq **out)
 {
     mrf_seq *s = new mrf_seq(*src);
-    s->rfx = nullptr; s->rfg = nullptr; s->tau = nullptr;
-    size_t b1 = sizeof(float4) * src->n, b2 = sizeof(float) * 12 * (size_t)src->n, b3 = sizeof(float2) * src->n;
-    int rc = dev_alloc(ctx, (void **)&s->rfx, b1, "sequence rfx");
-    if (!rc) rc = dev_alloc(ctx, (void **)&s->rfg, b2, "sequence rfg");
-    if (!rc) rc = dev_alloc(ctx, (void **)&s->tau, b3, "sequence tau");
-    if (rc) { seq_release(ctx, s); return rc; }
-    cudaError_t e = cudaMemcpy(s->rfx, src->rfx, b1, cudaMemcpyDeviceToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(s->rfg, src->rfg, b2, cudaMemcpyDeviceToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(s->tau, src->tau, b3, cudaMemcpyDeviceToDevice);
-    if (e != cudaSuccess) { seq_release(ctx, s); return cuda_fail(e, "sequence copy"); }
+    s->block = nullptr;
+    int rc = upload_block(ctx, nullptr, src->bytes, &s->block, "sequence copy");
+    if (rc) { delete s; return rc; }
+    cudaError_t e = cudaMemcpyAsync(s->block, src->block, src->bytes, cudaMemcpyDeviceToDevice, ctx->aux);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->aux);
+    if (e != cudaSuccess) { seq_release(ctx, s, ctx->aux, false); return cuda_fail(e, "sequence copy"); }
+    const ptrdiff_t d = (uint8_t *)s->block - (uint8_t *)src->block;
+    s->rfx = (float4 *)((uint8_t *)src->rfx + d);
+    s->rfg = (float *)((uint8_t *)src->rfg + d);
+    s->tau = (float2 *)((uint8_t *)src->tau + d);
     *out = s;
     return MRF_OK;
 }
@@ -316,7 +329,15 @@ extern "C" int mrf_sequence_free(mrf_ctx *ctx, mrf_seq *seq)
 {
     if (!ctx || !seq) return set_error(MRF_E_INVALID, "NULL argument");
     cudaSetDevice(ctx->device);
-    seq_release(ctx, seq);
+    seq_release(ctx, seq, nullptr, true);
+    return MRF_OK;
+}
+
+extern "C" int mrf_sequence_free_async(mrf_ctx *ctx, mrf_seq *seq, void *stream)
+{
+    if (!ctx || !seq) return set_error(MRF_E_INVALID, "NULL argument");
+    cudaSetDevice(ctx->device);
+    seq_release(ctx, seq, (cudaStream_t)stream, false);
     return MRF_OK;
 }
 
@@ -378,56 +399,27 @@ extern "C" int mrf_grid_unravel(const mrf_grid_desc *g, int64_t index, int32_t *
     return set_error(MRF_E_INVALID, "index beyond the grid");
 }
 
-int grid_upload(mrf_ctx *ctx, const mrf_grid_desc *g, GridBuf *out)
-{
-    int rc = grid_validate(g);
-    if (rc) return rc;
-    GridBuf gb;
-    gb.desc = *g;
-    std::vector<float> t1(g->n_t1), t2(g->n_t2), df(g->n_df);
-    std::vector<int64_t> aoff(g->n_t1 + 1);
-    std::vector<int32_t> nb(g->n_t1);
-    for (int a = 0; a < g->n_t1; ++a) t1[a] = (float)t1v(g, a);
-    for (int b = 0; b < g->n_t2; ++b) t2[b] = (float)t2v(g, b);
-    for (int c = 0; c < g->n_df; ++c) df[c] = (float)(g->df_min + (double)c * g->df_step);
-    aoff[0] = 0;
-    for (int a = 0; a < g->n_t1; ++a) {
-        nb[a] = nb_valid(g, a);
-        aoff[a + 1] = aoff[a] + (int64_t)nb[a] * g->n_df;
-    }
-    gb.count = aoff[g->n_t1];
-    size_t bt1 = 4 * (size_t)g->n_t1, bt2 = 4 * (size_t)g->n_t2, bdf = 4 * (size_t)g->n_df;
-    size_t bao = 8 * (size_t)(g->n_t1 + 1), bnb = 4 * (size_t)g->n_t1;
-    rc = dev_alloc(ctx, (void **)&gb.t1, bt1, "grid t1");
-    if (!rc) rc = dev_alloc(ctx, (void **)&gb.t2, bt2, "grid t2");
-    if (!rc) rc = dev_alloc(ctx, (void **)&gb.df, bdf, "grid df");
-    if (!rc) rc = dev_alloc(ctx, (void **)&gb.a_off, bao, "grid offsets");
-    if (!rc) rc = dev_alloc(ctx, (void **)&gb.nb, bnb, "grid nb");
-    gb.bytes = bt1 + bt2 + bdf + bao + bnb;
-    if (rc) { grid_release(ctx, &gb); return rc; }
-    cudaError_t e = cudaMemcpy(gb.t1, t1.data(), bt1, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(gb.t2, t2.data(), bt2, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(gb.df, df.data(), bdf, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(gb.a_off, aoff.data(), bao, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(gb.nb, nb.data(), bnb, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { grid_release(ctx, &gb); return cuda_fail(e, "grid upload"); }
-    *out = gb;
-    return MRF_OK;
-}
+// Host tables of a grid (axis values, T1-block offsets, valid-T2 counts) in
+// one 256-byte aligned layout.
+struct GridHost {
+    std::vector<uint8_t> h;
+    size_t o_t2, o_df, o_ao, o_nb, total;
+    int64_t count;
+};
 
-int grid_upload_async(mrf_ctx *ctx, const mrf_grid_desc *g, cudaStream_t stream, GridDev *out, void **block,
-                      size_t *bytes)
+static void grid_tables(const mrf_grid_desc *g, GridHost &G)
 {
-    int rc = grid_validate(g);
-    if (rc) return rc;
     const size_t nt1 = g->n_t1, nt2 = g->n_t2, ndf = g->n_df;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t o_t2 = al(4 * nt1), o_df = o_t2 + al(4 * nt2), o_ao = o_df + al(4 * ndf);
-    const size_t o_nb = o_ao + al(8 * (nt1 + 1)), total = o_nb + al(4 * nt1);
-    std::vector<uint8_t> h(total, 0);
-    float *t1 = (float *)h.data(), *t2 = (float *)(h.data() + o_t2), *df = (float *)(h.data() + o_df);
-    int64_t *ao = (int64_t *)(h.data() + o_ao);
-    int32_t *nb = (int32_t *)(h.data() + o_nb);
+    G.o_t2 = al(4 * nt1);
+    G.o_df = G.o_t2 + al(4 * nt2);
+    G.o_ao = G.o_df + al(4 * ndf);
+    G.o_nb = G.o_ao + al(8 * (nt1 + 1));
+    G.total = G.o_nb + al(4 * nt1);
+    G.h.assign(G.total, 0);
+    float *t1 = (float *)G.h.data(), *t2 = (float *)(G.h.data() + G.o_t2), *df = (float *)(G.h.data() + G.o_df);
+    int64_t *ao = (int64_t *)(G.h.data() + G.o_ao);
+    int32_t *nb = (int32_t *)(G.h.data() + G.o_nb);
     for (int a = 0; a < g->n_t1; ++a) t1[a] = (float)t1v(g, a);
     for (int b = 0; b < g->n_t2; ++b) t2[b] = (float)t2v(g, b);
     for (int c = 0; c < g->n_df; ++c) df[c] = (float)(g->df_min + (double)c * g->df_step);
@@ -436,37 +428,58 @@ int grid_upload_async(mrf_ctx *ctx, const mrf_grid_desc *g, cudaStream_t stream,
         nb[a] = nb_valid(g, a);
         ao[a + 1] = ao[a] + (int64_t)nb[a] * g->n_df;
     }
-    rc = budget_charge(ctx, total);
+    G.count = ao[g->n_t1];
+}
+
+int grid_upload(mrf_ctx *ctx, const mrf_grid_desc *g, GridBuf *out)
+{
+    int rc = grid_validate(g);
     if (rc) return rc;
-    uint8_t *d = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&d, total, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), total, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) {
-        if (d) cudaFreeAsync(d, stream);
-        budget_release(ctx, total);
-        return cuda_fail(e, "grid upload");
-    }
-    out->n_t1 = g->n_t1; out->n_t2 = g->n_t2; out->n_df = g->n_df;
-    out->t1 = (const float *)d;
-    out->t2 = (const float *)(d + o_t2);
-    out->df = (const float *)(d + o_df);
-    out->a_off = (const int64_t *)(d + o_ao);
-    out->nb = (const int32_t *)(d + o_nb);
-    out->count = ao[g->n_t1];
-    *block = d;
-    *bytes = total;
-    // pageable source: cudaMemcpyAsync has staged it before returning, so h may go
+    GridHost G;
+    grid_tables(g, G);
+    GridBuf gb;
+    gb.desc = *g;
+    rc = upload_block(ctx, G.h.data(), G.total, &gb.block, "grid upload");
+    if (rc) return rc;
+    uint8_t *d = (uint8_t *)gb.block;
+    gb.t1 = (float *)d;
+    gb.t2 = (float *)(d + G.o_t2);
+    gb.df = (float *)(d + G.o_df);
+    gb.a_off = (int64_t *)(d + G.o_ao);
+    gb.nb = (int32_t *)(d + G.o_nb);
+    gb.count = G.count;
+    gb.bytes = G.total;
+    *out = gb;
     return MRF_OK;
 }
 
-void grid_release(mrf_ctx *ctx, GridBuf *g)
+int grid_upload_async(mrf_ctx *ctx, const mrf_grid_desc *g, cudaStream_t stream, GridDev *out, void **block,
+                      size_t *bytes)
 {
-    const mrf_grid_desc &d = g->desc;
-    if (g->t1) dev_free(ctx, g->t1, 4 * (size_t)d.n_t1);
-    if (g->t2) dev_free(ctx, g->t2, 4 * (size_t)d.n_t2);
-    if (g->df) dev_free(ctx, g->df, 4 * (size_t)d.n_df);
-    if (g->a_off) dev_free(ctx, g->a_off, 8 * (size_t)(d.n_t1 + 1));
-    if (g->nb) dev_free(ctx, g->nb, 4 * (size_t)d.n_t1);
+    (void)stream;   // uploaded on the library's own stream; the caller frees it in stream order
+    int rc = grid_validate(g);
+    if (rc) return rc;
+    GridHost G;
+    grid_tables(g, G);
+    void *dv = nullptr;
+    rc = upload_block(ctx, G.h.data(), G.total, &dv, "grid upload");
+    if (rc) return rc;
+    uint8_t *d = (uint8_t *)dv;
+    out->n_t1 = g->n_t1; out->n_t2 = g->n_t2; out->n_df = g->n_df;
+    out->t1 = (const float *)d;
+    out->t2 = (const float *)(d + G.o_t2);
+    out->df = (const float *)(d + G.o_df);
+    out->a_off = (const int64_t *)(d + G.o_ao);
+    out->nb = (const int32_t *)(d + G.o_nb);
+    out->count = G.count;
+    *block = d;
+    *bytes = G.total;
+    return MRF_OK;
+}
+
+void grid_release(mrf_ctx *ctx, GridBuf *g, cudaStream_t stream, bool sync)
+{
+    release_block(ctx, g->block, g->bytes, stream, sync);
     *g = GridBuf();
 }
 
@@ -492,15 +505,23 @@ extern "C" int mrf_dict_free(mrf_ctx *ctx, mrf_dict *d)
 {
     if (!ctx || !d) return set_error(MRF_E_INVALID, "NULL argument");
     cudaSetDevice(ctx->device);
-    if (d->block) {
-        // work on any stream may still read the dictionary: wait for the
-        // device, then hand the block back to the pool (no unmapping)
-        cudaDeviceSynchronize();
-        cudaFreeAsync(d->block, 0);
-        budget_release(ctx, d->block_bytes);
-    }
-    grid_release(ctx, &d->grid);
-    seq_release(ctx, d->seq);
+    // work on any stream may still read the dictionary: wait for the device,
+    // then hand the blocks back to the pool (no unmapping)
+    if (d->block) release_block(ctx, d->block, d->block_bytes, nullptr, true);
+    grid_release(ctx, &d->grid, ctx->aux, false);
+    seq_release(ctx, d->seq, ctx->aux, false);
+    delete d;
+    return MRF_OK;
+}
+
+extern "C" int mrf_dict_free_async(mrf_ctx *ctx, mrf_dict *d, void *stream_v)
+{
+    if (!ctx || !d) return set_error(MRF_E_INVALID, "NULL argument");
+    cudaSetDevice(ctx->device);
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    if (d->block) release_block(ctx, d->block, d->block_bytes, stream, false);
+    grid_release(ctx, &d->grid, stream, false);
+    seq_release(ctx, d->seq, stream, false);
     delete d;
     return MRF_OK;
 }

@@ -48,9 +48,10 @@ struct mrf_seq {
     int xonly = 0, symmetric = 0, inversion = 0;
     double inv_delay = 0.0;
     double min_tr = 0.0;
-    float4 *rfx = nullptr;
+    float4 *rfx = nullptr;      // rfx, rfg and tau live in one block from the stream-ordered pool
     float *rfg = nullptr;
     float2 *tau = nullptr;
+    void *block = nullptr;
     size_t bytes = 0;
     SeqDev dev() const {
         SeqDev s;
@@ -67,6 +68,7 @@ struct GridBuf {
     int64_t *a_off = nullptr;
     int32_t *nb = nullptr;
     int64_t count = 0;
+    void *block = nullptr;      // t1, t2, df, a_off, nb in one block from the stream-ordered pool
     size_t bytes = 0;
     GridDev dev() const {
         GridDev g;
@@ -108,6 +110,7 @@ struct ProfEvent {
 
 struct mrf_ctx {
     int device = 0;
+    cudaStream_t aux = nullptr;  // the library's own non-blocking stream for small uploads
     int sm_count = 0;
     int cc_major = 0, cc_minor = 0;
     size_t budget = 0;
@@ -144,16 +147,21 @@ int set_error(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 int budget_charge(mrf_ctx *ctx, size_t bytes);
 void budget_release(mrf_ctx *ctx, size_t bytes);
-int dev_alloc(mrf_ctx *ctx, void **p, size_t bytes, const char *what);
-void dev_free(mrf_ctx *ctx, void *p, size_t bytes);
+// Small host-to-device uploads: one block from the stream-ordered pool, copied
+// on the context's own non-blocking stream; the host waits for that copy only,
+// never for work queued on the caller's streams.
+int upload_block(mrf_ctx *ctx, const void *host, size_t bytes, void **dev, const char *what);
+// Release a block: after every enqueued use (device-wide synchronisation) when
+// `stream` is null and `sync` set, else in the order of `stream`.
+void release_block(mrf_ctx *ctx, void *p, size_t bytes, cudaStream_t stream, bool sync);
 int grid_validate(const mrf_grid_desc *g);
 int grid_upload(mrf_ctx *ctx, const mrf_grid_desc *g, GridBuf *out);
-void grid_release(mrf_ctx *ctx, GridBuf *g);
+void grid_release(mrf_ctx *ctx, GridBuf *g, cudaStream_t stream, bool sync);
 // stream-ordered upload into one pool block; free with cudaFreeAsync + budget_release
 int grid_upload_async(mrf_ctx *ctx, const mrf_grid_desc *g, cudaStream_t stream, GridDev *out, void **block,
                       size_t *bytes);
 int seq_clone(mrf_ctx *ctx, const mrf_seq *src, mrf_seq **out);
-void seq_release(mrf_ctx *ctx, mrf_seq *s);
+void seq_release(mrf_ctx *ctx, mrf_seq *s, cudaStream_t stream, bool sync);
 int check_device_error(mrf_ctx *ctx, cudaStream_t stream);   // synchronises; reads err_flag
 
 // ---------------------------------------------------------------------------
