@@ -124,7 +124,7 @@ __device__ __forceinline__ void step_tab(Bloch &st, const SeqDev &s, const Table
 
 // Symmetric sequences: the factors of kFacG consecutive timepoints, fetched a
 // group ahead of their use so that one group's table loads overlap the
-// previous group's recurrence (indices past the end are clamped).
+// previous group's recurrence.
 constexpr int kFacG = 8;
 
 struct FacGroup {
@@ -132,14 +132,23 @@ struct FacGroup {
     float2 z[kFacG];
 };
 
-__device__ __forceinline__ void fac_load(FacGroup &f, const Tables &t, int n, int n_df, int a, int b, int c, int jb)
+// An entry's rows of the symmetric tables; the tables carry kFacG samples of
+// padding past their end, so a group may run past the last timepoint.
+struct FacRows {
+    const float *e1, *e2;    // E1 / E2 of this entry's T1 / T2, by timepoint
+    const float2 *z;         // e^{i theta} of this entry's df at timepoint 0; stride n_df
+    int n_df;
+};
+
+__device__ __forceinline__ void fac_load(FacGroup &f, const FacRows &r, int jb)
 {
+    const float2 *z = r.z + (size_t)jb * r.n_df;
 #pragma unroll
     for (int g = 0; g < kFacG; ++g) {
-        const int j = min(jb + g, n - 1);
-        f.e1[g] = __ldg(&t.e1s[(int64_t)a * n + j]);
-        f.e2[g] = __ldg(&t.e2s[(int64_t)b * n + j]);
-        f.z[g] = __ldg(&t.ciss[(int64_t)j * n_df + c]);
+        f.e1[g] = __ldg(r.e1 + jb + g);
+        f.e2[g] = __ldg(r.e2 + jb + g);
+        f.z[g] = __ldg(z);
+        z += r.n_df;
     }
 }
 
@@ -222,6 +231,13 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
     int a = 0, b = 0, c = 0;
     if (live) unravel(g, e, a, b, c);
     const float e1inv = live && s.inversion ? __ldg(&t.e1_inv[a]) : 1.f;
+    FacRows fr;
+    if (SYM) {
+        fr.e1 = t.e1s + (size_t)a * n;
+        fr.e2 = t.e2s + (size_t)b * n;
+        fr.z = t.ciss + c;
+        fr.n_df = g.n_df;
+    }
 
     // pass 1: norm (blocked FP32 partial sums, Kahan-compensated total)
     float tot = 0.f, comp = 0.f, amax = 0.f;
@@ -231,10 +247,10 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
         if (s.inversion) { bloch_invert(st); st.w *= e1inv; }
         if constexpr (SYM) {
             FacGroup cur, nxt;
-            fac_load(cur, t, n, g.n_df, a, b, c, 0);
+            fac_load(cur, fr, 0);
             float part = 0.f;
             for (int j0 = 0; j0 < n; j0 += kFacG) {
-                fac_load(nxt, t, n, g.n_df, a, b, c, j0 + kFacG);
+                fac_load(nxt, fr, j0 + kFacG);
 #pragma unroll
                 for (int q = 0; q < kFacG; ++q) {
                     const int j = j0 + q;
@@ -295,7 +311,7 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
     const int row_bytes = ld * (OUT == MRF_FP8E4M3 ? 1 : 2);
     const int tp_row = row_bytes / kBpt;      // timepoint slots per row (incl. padding)
     FacGroup cur, nxt;
-    if constexpr (SYM) fac_load(cur, t, n, g.n_df, a, b, c, 0);
+    if constexpr (SYM) fac_load(cur, fr, 0);
     for (int j0 = 0; j0 < tp_row; j0 += kJ) {
         if constexpr (SYM) {
             // groups of kFacG timepoints: 8 / kPerVec vectors each
@@ -303,7 +319,7 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
 #pragma unroll 1
             for (int gq = 0; gq < kJ / kFacG; ++gq) {
                 const int jg = j0 + gq * kFacG;
-                fac_load(nxt, t, n, g.n_df, a, b, c, jg + kFacG);
+                fac_load(nxt, fr, jg + kFacG);
                 float vr[kFacG], vi[kFacG];
 #pragma unroll
                 for (int q = 0; q < kFacG; ++q) {
@@ -434,8 +450,11 @@ int launch_dict_generate(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream)
     const GridDev g = d->grid.dev();
     const int n = s.n;
     // evolution-factor tables in stream-ordered scratch
-    const size_t b1 = sizeof(float2) * (size_t)g.n_t1 * n, b2 = sizeof(float2) * (size_t)g.n_t2 * n;
-    const size_t b3 = sizeof(float4) * (size_t)n * g.n_df, b4 = sizeof(float) * (size_t)g.n_t1;
+    // each table is followed by room for 2 x kFacG timepoints of padding (a
+    // look-ahead group of the last entry reads past its end)
+    const size_t b1 = sizeof(float2) * ((size_t)g.n_t1 * n + 2 * kFacG);
+    const size_t b2 = sizeof(float2) * ((size_t)g.n_t2 * n + 2 * kFacG);
+    const size_t b3 = sizeof(float4) * ((size_t)n + 2 * kFacG) * g.n_df, b4 = sizeof(float) * (size_t)g.n_t1;
     const size_t tb = b1 + b2 + b3 + b4 + 256 * 4;
     int rc = budget_charge(ctx, tb);
     if (rc) return rc;
