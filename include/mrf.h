@@ -50,9 +50,10 @@ enum {
 };
 
 typedef enum {
-    MRF_F32 = 0,      /* FP32-equivalent: normalised entries split into bf16 hi + lo,
-                         three tensor-core products (hi.hi + hi.lo + lo.hi) */
-    MRF_BF16 = 1,     /* normalised entries rounded to bf16 (nearest even) */
+    MRF_F32 = 0,      /* FP32-equivalent: the raw FP32 entries split into bf16 hi + lo
+                         with a per-entry scale 1 / ||d||, three tensor-core products
+                         (hi.hi + hi.lo + lo.hi) */
+    MRF_BF16 = 1,     /* normalised entries rounded to bf16 (nearest even), scale 1 */
     MRF_FP8E4M3 = 2   /* normalised entries scaled to max |value| = 448 per entry,
                          stored as fp8 e4m3 with an fp32 per-entry scale */
 } mrf_dtype;
@@ -168,9 +169,10 @@ int mrf_simulate(mrf_ctx *ctx, const mrf_seq *seq, int64_t count, const float *t
 /* Dictionary (Theory: unit-norm entries so that CC is |inner product|)     */
 
 /* Generate the whole grid's dictionary on the device: Bloch recurrence per
- * entry in FP32, then normalisation to unit L2 norm and storage in `dtype`
- * (see mrf_dtype). Entry e's row is the interleaved (re, im) signal,
- * zero-padded to `ld` elements. The library owns the dictionary memory,
+ * entry in FP32 and storage in `dtype` (see mrf_dtype) with a per-entry
+ * scale such that stored value x scale is the unit-L2-norm entry (Theory:
+ * unit-norm entries make CC the inner product). Entry e's row is the
+ * interleaved (re, im) signal, zero-padded to `ld` elements. The library owns the dictionary memory,
  * charged to the budget. Runs on `stream`; the dictionary is usable by later
  * work on that stream. Errors: MRF_E_INVALID (bad grid, zero entries),
  * MRF_E_BUDGET, MRF_E_NOMEM, MRF_E_CUDA. */
@@ -194,7 +196,8 @@ typedef struct {
     const void *hi_dev;    /* D x ld: bf16 (F32 hi, BF16) or e4m3 bytes (FP8) */
     const void *lo_dev;    /* D x ld bf16 residual (F32 only), else NULL */
     const float *norm_dev; /* D: L2 norm of the un-normalised FP32 signal */
-    const float *scale_dev;/* D: FP8 dequantisation scale (FP8 only), else NULL */
+    const float *scale_dev;/* D: per-entry scale, stored value x scale = unit-norm entry
+                              (F32: 1 / norm; BF16: 1; FP8: the dequantisation scale) */
     size_t bytes;          /* device bytes charged to the budget */
     int32_t smooth_width;  /* temporal smoothing applied by mrf_dict_smooth (1: none) */
     double smooth_sigma;

@@ -551,7 +551,7 @@ extern "C" int mrf_dict_generate(mrf_ctx *ctx, const mrf_seq *seq, const mrf_gri
     // hi | lo | norm | scale in one block from the stream-ordered pool, so
     // that generating and freeing dictionaries repeatedly maps no new memory
     auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
-    const size_t b_lo = dtype == MRF_F32 ? al(rows) : 0, b_sc = dtype == MRF_FP8E4M3 ? al(4 * (size_t)count) : 0;
+    const size_t b_lo = dtype == MRF_F32 ? al(rows) : 0, b_sc = al(4 * (size_t)count);
     const size_t total = al(rows) + b_lo + al(4 * (size_t)count) + b_sc;
     if (!rc) rc = budget_charge(ctx, total);
     if (!rc) {
@@ -568,7 +568,7 @@ extern "C" int mrf_dict_generate(mrf_ctx *ctx, const mrf_seq *seq, const mrf_gri
     d->hi = blk;
     d->lo = dtype == MRF_F32 ? blk + al(rows) : nullptr;
     d->norm = (float *)(blk + al(rows) + b_lo);
-    d->scale = dtype == MRF_FP8E4M3 ? (float *)(blk + al(rows) + b_lo + al(4 * (size_t)count)) : nullptr;
+    d->scale = (float *)(blk + al(rows) + b_lo + al(4 * (size_t)count));
     d->bytes = total + d->grid.bytes + d->seq->bytes;
     rc = launch_dict_generate(ctx, d, (cudaStream_t)stream);
     if (rc) { mrf_dict_free(ctx, d); return rc; }

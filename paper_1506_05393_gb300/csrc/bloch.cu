@@ -4,8 +4,11 @@
 // Dictionary generation (Theory: brute-force DGS simulates every grid entry;
 // entries normalised to unit norm so CC is |inner product|):
 //   one thread per entry, FP32 recurrence in registers (bloch.cuh);
-//   pass 1 accumulates ||d||^2 (and max |d| for FP8);
-//   pass 2 re-runs the recurrence and writes the normalised, quantised row.
+//   FP32-equivalent (bf16 hi + lo): one pass writes the raw signal and
+//   accumulates ||d||^2; the entry's scale 1 / ||d|| makes it unit norm;
+//   BF16 / FP8: pass 1 accumulates ||d||^2 (and max |d| for FP8), pass 2
+//   re-runs the recurrence and writes the normalised (BF16, scale 1) or
+//   scaled e4m3 (FP8) row.
 // Rows are staged per warp in shared memory (32 entries x 128 bytes, XOR
 // swizzled on 16-byte chunks) and leave as fully coalesced 16-byte stores, so
 // the kernel streams HBM writes at one pass of the output.
@@ -239,10 +242,15 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
         fr.n_df = g.n_df;
     }
 
+    // MRF_F32 stores the raw signal and the scale 1 / ||d||, so it needs a
+    // single pass (the norm accumulates while the row is written); BF16 and
+    // FP8 store normalised or scaled values and take the norm first.
+    constexpr bool kOnePass = (OUT == MRF_F32);
+
     // pass 1: norm (blocked FP32 partial sums, Kahan-compensated total)
     float tot = 0.f, comp = 0.f, amax = 0.f;
     Bloch st;
-    if (live) {
+    if (live && !kOnePass) {
         bloch_init(st);
         if (s.inversion) { bloch_invert(st); st.w *= e1inv; }
         if constexpr (SYM) {
@@ -288,10 +296,10 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
             }
         }
     }
-    const float nrm = sqrtf(tot);
-    const float inv = nrm > 0.f ? 1.0f / nrm : 0.f;
     float qs = 1.f;
-    if (live) {
+    if (live && !kOnePass) {
+        const float nrm = sqrtf(tot);
+        const float inv = nrm > 0.f ? 1.0f / nrm : 0.f;
         norm_out[e] = nrm;
         if (OUT == MRF_FP8E4M3) {
             const float mx = amax * inv;                      // max |normalised component|
@@ -299,11 +307,12 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
             qs = inv / scale;                                 // raw value -> e4m3 code scale
             scale_out[e] = scale;
         } else {
-            qs = inv;
+            qs = inv;                                         // BF16: normalised values
+            scale_out[e] = 1.0f;
         }
     }
 
-    // pass 2: re-run, write normalised rows through the warp stage
+    // pass 2: (re-)run and write the rows through the warp stage
     if (live) {
         bloch_init(st);
         if (s.inversion) { bloch_invert(st); st.w *= e1inv; }
@@ -312,6 +321,7 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
     const int tp_row = row_bytes / kBpt;      // timepoint slots per row (incl. padding)
     FacGroup cur, nxt;
     if constexpr (SYM) fac_load(cur, fr, 0);
+    float part1 = 0.f;                        // one-pass norm: this chunk's partial sum
     for (int j0 = 0; j0 < tp_row; j0 += kJ) {
         if constexpr (SYM) {
             // groups of kFacG timepoints: 8 / kPerVec vectors each
@@ -326,7 +336,10 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
                     const int j = jg + q;
                     vr[q] = 0.f;
                     vi[q] = 0.f;
-                    if (live && j < n) step_fac<XONLY>(st, s, cur, q, j, vr[q], vi[q]);
+                    if (live && j < n) {
+                        step_fac<XONLY>(st, s, cur, q, j, vr[q], vi[q]);
+                        if (kOnePass) part1 = fmaf(vr[q], vr[q], fmaf(vi[q], vi[q], part1));
+                    }
                 }
 #pragma unroll
                 for (int vq = 0; vq < kVecs; ++vq) {
@@ -361,6 +374,7 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
                         step_tab<XONLY, SYM>(st, s, t, n, g.n_df, a, b, c, j, sr, si);
                         vr = sr;
                         vi = si;
+                        if (kOnePass) part1 = fmaf(sr, sr, fmaf(si, si, part1));
                     }
                     pk.put(u, vr * (OUT == MRF_FP8E4M3 ? 1.f : qs), vi * (OUT == MRF_FP8E4M3 ? 1.f : qs),
                            OUT == MRF_FP8E4M3 ? qs : 1.f);
@@ -369,6 +383,13 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
                 stage_hi[warp][lane][pq] = make_uint4(pk.hi[0], pk.hi[1], pk.hi[2], pk.hi[3]);
                 if (kTwo) stage_lo[kTwo ? warp : 0][lane][pq] = make_uint4(pk.lo[0], pk.lo[1], pk.lo[2], pk.lo[3]);
             }
+        }
+        if (kOnePass) {   // 32-timepoint blocks (kJ = 32 for 4-byte timepoints)
+            const float y = part1 - comp;
+            const float tt = tot + y;
+            comp = (tt - tot) - y;
+            tot = tt;
+            part1 = 0.f;
         }
         __syncwarp();
         const int qq = lane & 7;
@@ -387,6 +408,11 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
             }
         }
         __syncwarp();
+    }
+    if (kOnePass && live) {
+        const float nrm = sqrtf(tot);
+        norm_out[e] = nrm;
+        scale_out[e] = nrm > 0.f ? 1.0f / nrm : 0.f;
     }
 }
 

@@ -19,9 +19,10 @@
 // leaves the SM; each (voxel block, dictionary chunk) work unit writes only
 // its top-k, merged across chunks afterwards.
 //
-// Precisions: MRF_F32 = bf16 hi/lo split with three products
-// (hi.hi + hi.lo + lo.hi, ~2^-16 relative per term); MRF_BF16 = one bf16
-// product; MRF_FP8E4M3 = one e4m3 product (kind::f8f6f4) with per-entry and
+// Precisions: MRF_F32 = bf16 hi/lo split of the raw entries with three
+// products (hi.hi + hi.lo + lo.hi, ~2^-16 relative per term), the entry's
+// scale 1 / ||d|| applied to CC^2; MRF_BF16 = one bf16 product of unit-norm
+// entries; MRF_FP8E4M3 = one e4m3 product (kind::f8f6f4) with per-entry and
 // per-voxel scales applied to CC^2.
 //
 // Re-score (Discussion: normalised-CC errors fixed by a non-normalised final
@@ -84,7 +85,7 @@ struct MatchParams {
                          // while the dictionary streams past them once
     int k_blocks;        // K blocks of 128 bytes
     int last_ksteps;     // MMA k-steps in the last K block (rest is zero padding)
-    const float *colscale;   // FP8: per-entry dequantisation scale, else nullptr
+    const float *colscale;   // per-entry scale (stored value x scale = unit-norm entry), nullptr when 1
     int col_stride;      // dictionary entry of tile column c is c * col_stride (sampled pre-pass)
     const float *thr0;   // per-voxel lower bound on the K-th best CC^2 (thr0[v * thr0_stride]), or nullptr
     int thr0_stride;
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                     const int col0 = t * BN + ch * 32 + (par ? 16 : 0);
                     float c2v[16];
                     float sc16[16];
-                    if (MODE == MRF_FP8E4M3) {
+                    if (MODE != MRF_BF16) {
                         if (p.col_stride == 1 && col0 + 16 <= p.D) {
                             // 16 consecutive scales from a 16-byte aligned offset
                             const float4 *s4 = reinterpret_cast<const float4 *>(p.colscale + col0);
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                         const float im = par ? mine_hi : recv;
                         float c2 = fmaf(re, re, im * im);
                         const int col = col0 + q;
-                        if (MODE == MRF_FP8E4M3) c2 *= sc16[q] * sc16[q];
+                        if (MODE != MRF_BF16) c2 *= sc16[q] * sc16[q];
                         c2v[q] = c2;
                         mask |= (col < p.D && c2 > thr) ? (1u << q) : 0u;
                     }
@@ -860,7 +861,7 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     p.group_vu = group_vu;
     p.k_blocks = k_blocks;
     p.last_ksteps = last_ksteps;
-    p.colscale = mode == MRF_FP8E4M3 ? d->scale : nullptr;
+    p.colscale = mode == MRF_BF16 ? nullptr : d->scale;
     p.col_stride = 1;
     p.thr0 = nullptr;
     p.thr0_stride = 0;

@@ -8,7 +8,8 @@
 // mrf_dict_smooth: a generated FP32-equivalent or BF16 dictionary in place,
 // one thread per entry re-simulating it from the dictionary's own sequence
 // and grid (FP32 recurrence, accurate factors) twice: the norm of the
-// smoothed entry, then the normalised write, rounded to storage once. The
+// smoothed entry, then the write in the dictionary's convention, rounded to
+// storage once. The
 // dictionary remembers the smoothing so that its top-k re-score smooths the
 // re-simulated candidates alike.
 #include <cuda_bf16.h>
@@ -107,7 +108,7 @@ struct RawStream {
 // factors), smooths it, and writes the normalised result with one rounding.
 template <bool XONLY>
 __global__ void dict_smooth_kernel(SeqDev s, GridDev g, __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *norm,
-                                   int64_t D, int ld, SmoothW sw)
+                                   float *scale, int64_t D, int ld, SmoothW sw)
 {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= D) return;
@@ -134,13 +135,16 @@ __global__ void dict_smooth_kernel(SeqDev s, GridDev g, __nv_bfloat16 *hi, __nv_
     }
     ss += part;
     const float inv = ss > 0.0 ? (float)(1.0 / sqrt(ss)) : 0.f;
-    // pass 2: the normalised smoothed entry
+    // pass 2: the smoothed entry, stored as the dictionary stores entries: the
+    // raw signal with scale 1 / ||d|| (FP32-equivalent, lo present), or the
+    // unit-norm signal with scale 1 (BF16)
+    const float wmul = lo ? 1.f : inv;
     __nv_bfloat16 *h = hi + (size_t)e * ld;
     __nv_bfloat16 *l = lo ? lo + (size_t)e * ld : nullptr;
     rs.start(s, rr);
     for (int t = 0; t < n; ++t) {
         const float2 z = smoothed(rs.win, t, n, sw);
-        const float zr = z.x * inv, zi = z.y * inv;
+        const float zr = z.x * wmul, zi = z.y * wmul;
         const __nv_bfloat162 hv = __floats2bfloat162_rn(zr, zi);
         *reinterpret_cast<__nv_bfloat162 *>(h + 2 * t) = hv;
         if (l) {
@@ -150,6 +154,7 @@ __global__ void dict_smooth_kernel(SeqDev s, GridDev g, __nv_bfloat16 *hi, __nv_
         rs.advance(s);
     }
     norm[e] = (float)sqrt(ss);
+    scale[e] = lo ? inv : 1.f;
 }
 
 }  // namespace
@@ -193,10 +198,10 @@ extern "C" int mrf_dict_smooth(mrf_ctx *ctx, mrf_dict *d, int32_t width, double 
     count_launch(ctx);
     if (s.xonly)
         dict_smooth_kernel<true><<<blocks, 128, 0, (cudaStream_t)stream>>>(
-            s, g, (__nv_bfloat16 *)d->hi, (__nv_bfloat16 *)d->lo, d->norm, d->entries, d->ld, sw);
+            s, g, (__nv_bfloat16 *)d->hi, (__nv_bfloat16 *)d->lo, d->norm, d->scale, d->entries, d->ld, sw);
     else
         dict_smooth_kernel<false><<<blocks, 128, 0, (cudaStream_t)stream>>>(
-            s, g, (__nv_bfloat16 *)d->hi, (__nv_bfloat16 *)d->lo, d->norm, d->entries, d->ld, sw);
+            s, g, (__nv_bfloat16 *)d->hi, (__nv_bfloat16 *)d->lo, d->norm, d->scale, d->entries, d->ld, sw);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "dictionary smoothing launch");
     d->smooth_h = sw.h;

@@ -48,6 +48,7 @@ struct ZoomArgs {
     // factor mode 3 (resident dictionary): normalised rows, bf16 hi (+ lo)
     const __nv_bfloat16 *dhi, *dlo;
     const float *dnorm;      // L2 norm of each un-normalised entry
+    const float *dscale;     // per-entry scale: stored row x scale = unit-norm entry
     int ld;                  // row stride in elements
     ZoomPlan plan;
     const float2 *x;
@@ -289,12 +290,15 @@ __device__ __forceinline__ Eval eval_dict(const ZoomArgs &A, const float2 *x, fl
             im += __shfl_xor_sync(0xffffffffu, im, o);
         }
         if (lane == q) {
-            // <x, d> of the un-normalised entry is the norm times <x, d_hat>
+            // the stored row times its scale is the unit-norm entry d_hat; <x, d>
+            // of the un-normalised entry is the norm times <x, d_hat>
+            const float sc = __ldg(&A.dscale[eq]);
+            const float hr = re * sc, hi_ = im * sc;
             const float nrm = __ldg(&A.dnorm[eq]);
-            mine.ipr = re * nrm;
-            mine.ipi = im * nrm;
+            mine.ipr = hr * nrm;
+            mine.ipi = hi_ * nrm;
             mine.dd = nrm * nrm;
-            mine.v = sqrtf(fmaf(re, re, im * im)) * inv_xn;
+            mine.v = sqrtf(fmaf(hr, hr, hi_ * hi_)) * inv_xn;
         }
     }
     return mine;
@@ -1242,6 +1246,7 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     A.g = gdev;
     A.dhi = A.dlo = nullptr;
     A.dnorm = nullptr;
+    A.dscale = nullptr;
     A.ld = 0;
     A.plan = P;
     A.x = (const float2 *)fp;
@@ -1338,6 +1343,7 @@ extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_z
     A.dhi = (const __nv_bfloat16 *)d->hi;
     A.dlo = (const __nv_bfloat16 *)d->lo;
     A.dnorm = d->norm;
+    A.dscale = d->scale;
     A.ld = d->ld;
     A.plan = P;
     A.x = (const float2 *)fp;
@@ -1502,6 +1508,7 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     A.g.count = ao[gd->n_t1];
     A.dhi = A.dlo = nullptr;
     A.dnorm = nullptr;
+    A.dscale = nullptr;
     A.ld = 0;
     A.plan = P;
     A.x = (const float2 *)fp;

@@ -65,15 +65,17 @@ def _dict_rows(M, d, dtype):
     eb = 1 if dtype == M.MRF_FP8E4M3 else 2
     hi = device_bytes(info.hi_dev, D * ld * eb).cpu().numpy()
     norm = device_bytes(info.norm_dev, 4 * D).cpu().numpy().view(np.float32)
+    # stored value x per-entry scale = unit-norm entry, for every dtype
+    sc = device_bytes(info.scale_dev, 4 * D).cpu().numpy().view(np.float32).astype(np.float64)
     if dtype == M.MRF_FP8E4M3:
         q = torch.from_numpy(hi).view(torch.float8_e4m3fn).float().numpy().reshape(D, ld)
-        sc = device_bytes(info.scale_dev, 4 * D).cpu().numpy().view(np.float32)
         vals = q * sc[:, None]
     else:
         vals = torch.from_numpy(hi).view(torch.bfloat16).float().numpy().reshape(D, ld).astype(np.float64)
         if dtype == M.MRF_F32:
             lo = device_bytes(info.lo_dev, D * ld * 2).cpu()
             vals = vals + lo.view(torch.bfloat16).float().numpy().reshape(D, ld)
+        vals = vals * sc[:, None]
     n = info.n
     return vals[:, 0:2 * n:2] + 1j * vals[:, 1:2 * n:2], vals[:, 2 * n:], norm, info
 
@@ -116,8 +118,10 @@ def test_dictionary_full_size_sampled(M, ctx, oracle_lib):
         idx = np.unique(np.concatenate([rng.integers(0, D, 250), [0, D - 1]]))
         hi = device_bytes(info.hi_dev, D * ld * 2).view(torch.bfloat16).view(D, ld)
         lo = device_bytes(info.lo_dev, D * ld * 2).view(torch.bfloat16).view(D, ld)
+        sc = device_bytes(info.scale_dev, 4 * D).view(torch.float32)
         it = torch.from_numpy(idx).cuda()
-        vals = (hi[it].double() + lo[it].double()).cpu().numpy()
+        # stored value x per-entry scale = unit-norm entry
+        vals = ((hi[it].double() + lo[it].double()) * sc[it].double()[:, None]).cpu().numpy()
         rows = vals[:, 0:2000:2] + 1j * vals[:, 1:2000:2]
         params = [M.mrf_grid_unravel(g, int(i)) for i in idx]
         t1, t2, df = S.grid_values(g)
