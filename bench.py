@@ -336,19 +336,56 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
     prof = M.mrf_profile_read(ctx, reset=True)
     res = M.results_to_numpy(out)[: x128d.shape[0]]
     zk = prof.zoom_ms / max(prof.zoom_timed, 1)
+    lk = prof.zoomline_ms / max(prof.zoomline_timed, 1)
+    nrun = max(prof.zoom_timed, 1)
+    pairs = prof.zoomline_pairs / nrun          # step-3 positions evaluated per search
+    cands = prof.zoomline_entries / nrun        # candidates the line kernel simulated per search
     ev = float(res["entries_evaluated"].sum())
-    flops = ev * N_TP * FLOPS_PER_TP
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     clk = clock_mhz or pk.get("sm_max_mhz", 2070.0)
     fp32_peak = sms * 128 * 2 * clk * 1e6 / 1e12
+    # per-voxel kernels (steps 1, 2, 4, 5): FLOPS_PER_TP per evaluated candidate;
+    # line kernel (step 3): 8 flops per (voxel, position) and timepoint for
+    # <x, d>, FLOPS_PER_TP - 8 per simulated candidate and timepoint
+    pack_ms = zk - lk
+    pack_flops = (ev - pairs) * N_TP * FLOPS_PER_TP
+    line_flops = (pairs * 8.0 + cands * (FLOPS_PER_TP - 8.0)) * N_TP
+    peak_note = f"peak = {sms} SMs x 128 FMA/clk x 2 x {clk:.0f} MHz"
+
+    def roof(flops, ms, note):
+        return {"bound": "alu", "achieved": flops / ms / 1e9, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": flops / ms / 1e9 / fp32_peak, "note": note + "; " + peak_note}
+
+    # the same search in one kernel (every step per voxel, as the allocation-free entry point runs it)
+    import ctypes as C
+    gzd = M.grid_desc(gz)
+    L = M.lib()
+    out1 = M.empty_results(x128d.shape[0])
+
+    def run_single():
+        M.check(L.mrf_zoom_search_static(ctx, seq_h, C.byref(gzd), C.byref(zf), C.c_void_p(x128d.data_ptr()),
+                                         x128d.shape[0], C.c_void_p(out1.data_ptr()),
+                                         C.c_void_p(torch.cuda.current_stream().cuda_stream)), "zoom static")
+    run_single()
+    ms1 = timed(run_single, 1)
+    res1 = M.results_to_numpy(out1)[: x128d.shape[0]]
     modes["zoom_128x128_fine"] = {
         "grid": "zoom_fine (T1 1 ms, T2 0.5 ms, df 0.1 Hz; 2,367,820,080 entries)", "voxels": int(x128d.shape[0]),
         "voxels_per_s": x128d.shape[0] / ms * 1e3, "ms": ms, "kernel_ms": zk,
         "mean_entries_evaluated": ev / x128d.shape[0],
-        "roofline": {"bound": "alu", "achieved": flops / zk / 1e9, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": flops / zk / 1e9 / fp32_peak,
-                     "note": f"{FLOPS_PER_TP:.0f} FP32 flops per timepoint per evaluated candidate; peak = "
-                             f"{sms} SMs x 128 FMA/clk x 2 x {clk:.0f} MHz"}}
+        "step3_positions_per_voxel": pairs / x128d.shape[0],
+        "line_kernel_ms": lk, "per_voxel_kernels_ms": pack_ms,
+        "roofline": roof(pack_flops + line_flops, zk, "whole search: the two rows below summed"),
+        "roofline_line_kernel": roof(line_flops, lk, "step 3 batched by (T1, T2) line: 8 FP32 flops per "
+                                     "(voxel, position, timepoint), "
+                                     f"{FLOPS_PER_TP - 8:.0f} per simulated candidate and timepoint"),
+        "roofline_per_voxel_kernels": roof(pack_flops, pack_ms, f"{FLOPS_PER_TP:.0f} FP32 flops per timepoint per "
+                                           "evaluated candidate of steps 1, 2, 4, 5 (time includes the grouping "
+                                           "kernels)"),
+        "single_kernel_ms": ms1, "single_kernel_voxels_per_s": x128d.shape[0] / ms1 * 1e3,
+        "single_kernel_identical": bool(np.array_equal(res1["index"], res["index"]) and
+                                        np.array_equal(res1["cc"].view(np.uint32), res["cc"].view(np.uint32)) and
+                                        np.array_equal(res1["entries_evaluated"], res["entries_evaluated"]))}
     return modes
 
 

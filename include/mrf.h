@@ -92,15 +92,23 @@ int mrf_stream_sync(mrf_ctx *ctx, void *stream);
  * kernels against their rooflines). Launch counts are always kept. With
  * profiling enabled, CUDA events are recorded on the launching stream around
  * the dictionary-generation, matcher and ZOOM kernels, and their durations
- * accumulate into the *_ms fields. */
+ * accumulate into the *_ms fields. zoom_* covers a whole on-the-fly ZOOM
+ * search (all its kernels); zoomline_* the batched step-3 kernel within it. */
 typedef struct {
     uint64_t launches;            /* every kernel this context launched */
     uint64_t dictgen_launches, matcher_launches, zoom_launches;
     double dictgen_ms, matcher_ms, zoom_ms;   /* event-timed launches only */
     uint64_t dictgen_timed, matcher_timed, zoom_timed;
+    uint64_t zoomline_launches;
+    double zoomline_ms;
+    uint64_t zoomline_timed;
+    /* work of the batched step-3 kernel, always counted: df positions
+     * evaluated (voxel, candidate pairs) and candidates simulated */
+    uint64_t zoomline_pairs, zoomline_entries;
 } mrf_profile;
 int mrf_profile_enable(mrf_ctx *ctx, int on);
-/* Synchronises on pending profile events. reset != 0 zeroes all counters. */
+/* Synchronises the device (pending profile events, work counters). reset != 0
+ * zeroes all counters. */
 int mrf_profile_read(mrf_ctx *ctx, mrf_profile *out, int reset);
 
 /* ------------------------------------------------------------------------ */

@@ -97,7 +97,8 @@ class Profile(C.Structure):
     _fields_ = [("launches", C.c_uint64), ("dictgen_launches", C.c_uint64), ("matcher_launches", C.c_uint64),
                 ("zoom_launches", C.c_uint64), ("dictgen_ms", C.c_double), ("matcher_ms", C.c_double),
                 ("zoom_ms", C.c_double), ("dictgen_timed", C.c_uint64), ("matcher_timed", C.c_uint64),
-                ("zoom_timed", C.c_uint64)]
+                ("zoom_timed", C.c_uint64), ("zoomline_launches", C.c_uint64), ("zoomline_ms", C.c_double),
+                ("zoomline_timed", C.c_uint64), ("zoomline_pairs", C.c_uint64), ("zoomline_entries", C.c_uint64)]
 
 
 # one mrf_result (56 bytes, 8-byte aligned)

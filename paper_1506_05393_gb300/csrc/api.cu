@@ -120,11 +120,13 @@ extern "C" int mrf_ctx_create(int device, size_t hbm_budget_bytes, mrf_ctx **out
     c->cc_major = prop.major;
     c->cc_minor = prop.minor;
     c->budget = hbm_budget_bytes ? hbm_budget_bytes : free_b;
-    e = cudaMalloc(&c->err_flag, sizeof(int));
+    // device words: the error flag, then the work counters of the profile
+    e = cudaMalloc(&c->err_flag, 64);
     if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(err flag)"); }
+    c->dev_stats = (unsigned long long *)((char *)c->err_flag + 8);
     e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
     if (e != cudaSuccess) { cudaFree(c->err_flag); delete c; return cuda_fail(e, "cudaStreamCreate"); }
-    cudaMemset(c->err_flag, 0, sizeof(int));
+    cudaMemset(c->err_flag, 0, 64);
     // keep stream-ordered scratch in the pool between calls
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
@@ -221,7 +223,17 @@ extern "C" int mrf_profile_read(mrf_ctx *ctx, mrf_profile *out, int reset)
     out->dictgen_timed = ctx->prof_timed[kProfDictGen];
     out->matcher_timed = ctx->prof_timed[kProfMatcher];
     out->zoom_timed = ctx->prof_timed[kProfZoom];
+    out->zoomline_launches = ctx->kind_launches[kProfZoomLine].load();
+    out->zoomline_ms = ctx->prof_ms[kProfZoomLine];
+    out->zoomline_timed = ctx->prof_timed[kProfZoomLine];
+    unsigned long long st[2] = {0, 0};
+    cudaDeviceSynchronize();
+    if (cudaMemcpy(st, ctx->dev_stats, sizeof(st), cudaMemcpyDeviceToHost) == cudaSuccess) {
+        out->zoomline_pairs = st[0];
+        out->zoomline_entries = st[1];
+    }
     if (reset) {
+        cudaMemset(ctx->dev_stats, 0, sizeof(st));
         ctx->launches = 0;
         for (int k = 0; k < kProfKinds; ++k) {
             ctx->kind_launches[k] = 0;

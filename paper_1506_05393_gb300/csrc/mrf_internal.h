@@ -101,7 +101,7 @@ struct mrf_dict {
 
 struct ServeState;   // serve.cpp
 
-enum ProfKind { kProfDictGen = 0, kProfMatcher = 1, kProfZoom = 2, kProfKinds = 3 };
+enum ProfKind { kProfDictGen = 0, kProfMatcher = 1, kProfZoom = 2, kProfZoomLine = 3, kProfKinds = 4 };
 
 struct ProfEvent {
     int kind;
@@ -116,6 +116,7 @@ struct mrf_ctx {
     size_t budget = 0;
     std::atomic<size_t> used{0};
     int *err_flag = nullptr;     // device int: set by kernels whose bounded waits run out
+    unsigned long long *dev_stats = nullptr;   // device work counters (same allocation as err_flag)
     std::mutex mu;
     ServeState *serve = nullptr;
     // kernel accounting
@@ -124,8 +125,8 @@ struct mrf_ctx {
     std::atomic<bool> profiling{false};
     std::mutex prof_mu;
     std::vector<ProfEvent> prof_pending;
-    double prof_ms[kProfKinds] = {0, 0, 0};
-    uint64_t prof_timed[kProfKinds] = {0, 0, 0};
+    double prof_ms[kProfKinds] = {0, 0, 0, 0};
+    uint64_t prof_timed[kProfKinds] = {0, 0, 0, 0};
     mrf_ctx() { for (auto &k : kind_launches) k = 0; }
 };
 

@@ -1,11 +1,16 @@
 // MRF-ZOOM (Theory: df search steps 1-4, 1D ZOOM of Fig. 1, 2D ZOOM of
 // Fig. 2; Methods, Experiment 2 steps 1-5).
 //
-// Two kernels run the same canonical eager search:
-//  * zoom_pack_kernel simulates every candidate on the fly (no dictionary):
-//    a warp carries eight voxels and gives each lane one candidate per round,
-//    whose FP32 Bloch recurrence accumulates <x, d> and ||d||^2 in
-//    16-timepoint FP32 blocks with compensated (Kahan) block sums;
+// Two searches run the same canonical eager stage machine:
+//  * on the fly (no dictionary): zoom_pack_kernel carries eight voxels per
+//    warp and gives each lane one candidate per round, whose FP32 Bloch
+//    recurrence accumulates <x, d> and ||d||^2 in 16-timepoint FP32 blocks
+//    with compensated (Kahan) block sums. mrf_zoom_search splits it in three:
+//    the packed kernel runs steps 1-2 and parks each voxel at step 3; the df
+//    refinement of step 3 runs batched over the voxels that stopped at the
+//    same (T1, T2) (zoom_line_kernel, same arithmetic per candidate and
+//    voxel, so the same decisions); the packed kernel then resumes steps 4-5.
+//    mrf_zoom_search_static runs all steps in the packed kernel;
 //  * zoom_dict_kernel reads candidates from a resident dictionary, one warp
 //    per voxel, the warp streaming each stored row.
 // Decisions take the best candidate with ties to the earliest in the
@@ -42,6 +47,21 @@ struct ZoomPlan {
     int s4_p[kMaxLevels], s4_h[kMaxLevels];
 };
 
+// A voxel's search state between the phases of the split on-the-fly search
+// (the stages up to the 2D ZOOM, the df refinement of step 3 batched over the
+// voxels that share its (T1, T2), then the rest).
+struct ZState {
+    int a, b, c, evaluated;
+    float centre, mm, inv_xn;
+    int flags;
+};
+constexpr int kZOk = 1;      // no level exceeded the move limit
+constexpr int kZDone = 2;    // the search ended before step 3; its result is written
+
+// Packed-kernel phases: the whole search, or the stages before step 3 (state
+// saved there), or the stages after it (state restored).
+enum ZPhase : int { kPhaseAll = 0, kPhaseHead = 1, kPhaseTail = 2 };
+
 struct ZoomArgs {
     SeqDev s;
     GridDev g;
@@ -57,6 +77,8 @@ struct ZoomArgs {
     int *counter;
     int *err;
     int max_moves;
+    ZState *state;           // split search only
+    int phase;               // ZPhase
 };
 
 struct Kahan {
@@ -670,7 +692,7 @@ constexpr int kTable = 32 * kPerLane;
 constexpr int kWin = 64;
 constexpr int kReqMax = 24;                  // listed points per slot and round (8 missing + speculative)
 
-enum Stage : int { kS1a = 0, kS1b, kS1c, kS2, kS3, kS4, kS5, kFinal };
+enum Stage : int { kS1a = 0, kS1b, kS1c, kS2, kS3, kS4, kS5, kFinal, kStop };
 enum Tag : int { kTagNone = 0, kTagScan, kTagMove, kTagFinal };
 
 struct Slot {
@@ -746,12 +768,13 @@ __device__ __forceinline__ bool win_get(const PackShared &W, int s, int idx, int
 
 // Enter `stage` (with S.level for the leveled stages), passing over empty
 // scans and exhausted level lists. A move level starts an empty window that
-// holds the centre.
-__device__ void enter(PackShared &W, int s, int stage, const ZoomPlan &P, int n_df)
+// holds the centre. With `stop3`, reaching step 3 parks the slot (kStop).
+__device__ void enter(PackShared &W, int s, int stage, const ZoomPlan &P, int n_df, bool stop3)
 {
     Slot &S = W.s[s];
     for (;;) {
         S.stage = stage;
+        if (stop3 && stage == kS3) { S.stage = kStop; return; }
         bool nonempty;
         switch (stage) {
         case kS1a:
@@ -851,19 +874,30 @@ __device__ void speculate(PackShared &W, int s, const GridDev &g, unsigned long 
 // Run slot s's decisions as far as the known values allow. On return the slot
 // is scanning (positions are handed out elastically), waits for its S.nreq
 // listed points, or is idle.
-__device__ void advance(PackShared &W, int s, const ZoomPlan &P, const GridDev &g, int max_moves)
+__device__ void advance(PackShared &W, int s, const ZoomPlan &P, const GridDev &g, int max_moves, ZState *state)
 {
     Slot &S = W.s[s];
     S.nreq = 0;
     S.nspec = 0;
+    const bool stop3 = state != nullptr;
     for (;;) {
         const int st = S.stage;
         if (S.v < 0) return;
+        if (st == kStop) {
+            // the stages before step 3 are done: save the search and free the slot
+            ZState z;
+            z.a = S.a; z.b = S.b; z.c = S.c; z.evaluated = S.evaluated;
+            z.centre = S.centre; z.mm = S.mm; z.inv_xn = S.inv_xn;
+            z.flags = S.ok ? kZOk : 0;
+            state[S.v] = z;
+            S.v = -1;
+            return;
+        }
         if (is_scan(st)) {
             if (S.p <= S.p_end) return;
             if (isfinite(S.g2)) S.mm = fminf(S.mm, S.g1 - S.g2);
             S.level = 0;
-            enter(W, s, st == kS1a ? kS1b : st == kS1b ? kS1c : st == kS1c ? kS2 : kS4, P, g.n_df);
+            enter(W, s, st == kS1a ? kS1b : st == kS1b ? kS1c : st == kS1c ? kS2 : kS4, P, g.n_df, stop3);
             continue;
         }
         if (st == kFinal) {
@@ -925,7 +959,7 @@ __device__ void advance(PackShared &W, int s, const ZoomPlan &P, const GridDev &
         }
         if (st == kS5) { S.stage = kFinal; continue; }
         S.level += 1;
-        enter(W, s, st, P, g.n_df);
+        enter(W, s, st, P, g.n_df, stop3);
     }
 }
 
@@ -1004,7 +1038,7 @@ __device__ void assign(PackShared &W)
 
 // Slot s takes this round's results: scan positions in order, move points
 // into the window, the final centre's <x, d> into the voxel's result.
-__device__ void ingest(PackShared &W, int s, const GridDev &g, mrf_result *out, int *err)
+__device__ void ingest(PackShared &W, int s, const GridDev &g, mrf_result *out, int *err, ZState *state)
 {
     Slot &S = W.s[s];
     const int used = W.used;
@@ -1035,6 +1069,7 @@ __device__ void ingest(PackShared &W, int s, const GridDev &g, mrf_result *out, 
             r.entries_evaluated = S.evaluated;
             r.min_margin = isfinite(S.mm) ? S.mm : -1.f;
             out[S.v] = r;
+            if (state) state[S.v].flags = kZDone;
             S.v = -1;
         }
     }
@@ -1089,30 +1124,48 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
     __syncthreads();
     const ZoomPlan &P = sP;
     const int n = A.s.n;
+    ZState *head = A.phase == kPhaseHead ? A.state : nullptr;   // saves at step 3
 
     for (;;) {
         // decisions (one lane per slot)
         if (lane < kSlots) {
             const int s = lane;
-            ingest(W, s, A.g, A.out, A.err);
+            ingest(W, s, A.g, A.out, A.err, head);
             Slot &S = W.s[s];
-            if (S.v < 0 && !W.drained) {
-                const int nv = atomicAdd(A.counter, 1);
-                if (nv < A.V) {
-                    S.v = nv;
-                    S.a = P.a0; S.b = P.b0; S.c = 0;
-                    S.centre = -INFINITY;
-                    S.evaluated = 0;
-                    S.mm = INFINITY;
-                    S.ok = 1;
-                    S.level = 0;
-                    atomicOr(&W.norm_mask, 1 << s);
-                    enter(W, s, kS1a, P, A.g.n_df);
-                } else {
-                    W.drained = 1;
+            // a slot parked at step 3 is free at once: refill it until it has
+            // work or the voxels run out, so no warp leaves with voxels left
+            for (;;) {
+                while (S.v < 0 && !W.drained) {
+                    const int nv = atomicAdd(A.counter, 1);
+                    if (nv >= A.V) { W.drained = 1; break; }
+                    if (A.phase == kPhaseTail) {
+                        // resume after step 3 (voxels finished earlier are skipped)
+                        const ZState z = A.state[nv];
+                        if (z.flags & kZDone) continue;
+                        S.v = nv;
+                        S.a = z.a; S.b = z.b; S.c = z.c;
+                        S.centre = z.centre;
+                        S.evaluated = z.evaluated;
+                        S.mm = z.mm;
+                        S.ok = z.flags & kZOk;
+                        S.inv_xn = z.inv_xn;
+                        S.level = 0;
+                        enter(W, s, kS4, P, A.g.n_df, false);
+                    } else {
+                        S.v = nv;
+                        S.a = P.a0; S.b = P.b0; S.c = 0;
+                        S.centre = -INFINITY;
+                        S.evaluated = 0;
+                        S.mm = INFINITY;
+                        S.ok = 1;
+                        S.level = 0;
+                        atomicOr(&W.norm_mask, 1 << s);
+                        enter(W, s, kS1a, P, A.g.n_df, head != nullptr);
+                    }
                 }
+                advance(W, s, P, A.g, A.max_moves, head);
+                if (S.v >= 0 || W.drained) break;
             }
-            advance(W, s, P, A.g, A.max_moves);
         }
         __syncwarp();
         const bool busy = lane < kSlots && W.s[lane].v >= 0;
@@ -1150,6 +1203,331 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Step 3 batched over the voxels that share (T1, T2).
+//
+// Step 3 scans df at the (T1, T2) where the 2D ZOOM of step 2 stopped, over
+// the window c0 - W3 .. c0 + W3 around the voxel's df index c0. Every voxel
+// that stopped at the same (a, b) scans the same line of candidates, and the
+// coarse lattice of step 2 has few points, so the voxels group into few
+// lines with many voxels each. zoom_line_kernel simulates each line's
+// candidates once per tile of kLineVox voxels and correlates each simulated
+// sample with all of them: a candidate's recurrence is shared by 16 voxels,
+// and the inner loop is four FMAs per voxel and timepoint.
+//
+// Every (voxel, candidate) value is computed with the same FP32 operations
+// in the same order as the packed kernel (16-timepoint blocks, Kahan block
+// sums, the voxel's own 1/||x||), so the scan decides what the voxel's own
+// scan would. A voxel's scan outcome -- the first position with the largest
+// CC, the top two CC values with the centre, the number of evaluated
+// positions -- is reduced per 128-position chunk and then merged over the
+// chunks in scan order.
+
+constexpr int kLineVox = 16;        // voxels of a tile
+constexpr int kLineEntries = 128;   // df positions of a chunk (one per thread)
+constexpr int kLineTJ = 64;         // timepoints of a staged block of samples
+constexpr int kLineThreads = kLineEntries;
+
+struct LinePart {                   // one voxel's scan outcome over one chunk
+    float t1;                       // largest CC (-inf when none)
+    int c1;                         // its first position
+    float t2;                       // second largest (as a multiset)
+    int cnt;                        // finite values
+};
+
+struct LineArgs {
+    SeqDev s;
+    GridDev g;
+    const float2 *x;
+    const ZState *state;
+    const int *order;               // voxels grouped by line
+    const int2 *tiles;              // (first position in `order`, voxels)
+    const int *n_tiles;
+    int *item_counter;
+    int n_chunks, W3;
+    LinePart *part;                 // [voxel][chunk]
+    unsigned long long *stats;      // [1] += candidates simulated
+};
+
+__device__ __forceinline__ void s3_window(int c0, int W3, int n_df, int &lo, int &hi)
+{
+    lo = max(0, c0 - W3);
+    hi = min(n_df - 1, c0 + W3);
+}
+
+// First-position-of-the-maximum and top-two merge of two partial outcomes,
+// (t1, c1, t2, cnt) <- (t1, c1, t2, cnt) + (u1, d1, u2, dn).
+__device__ __forceinline__ void part_merge(float &t1, int &c1, float &t2, int &cnt, float u1, int d1, float u2, int dn)
+{
+    t2 = fmaxf(fmaxf(t2, u2), fminf(t1, u1));
+    if (u1 > t1 || (u1 == t1 && d1 < c1)) { t1 = u1; c1 = d1; }
+    cnt += dn;
+}
+
+// Voxels grouped by the (a, b) of their step 3: an open-addressing table of
+// H (a power of two, at least twice the voxels) keys; each voxel learns its
+// line's slot and its rank among the line's voxels.
+__global__ void line_hash_kernel(const ZState *state, int64_t V, int W3, int n_df, int n_t2, int H,
+                                 unsigned long long *hkey, int *hcnt, int *vslot, int *vrank, int *err)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const ZState z = state[v];
+    int lo, hi;
+    s3_window(z.c, W3, n_df, lo, hi);
+    vslot[v] = -1;
+    if ((z.flags & kZDone) || lo >= hi) return;   // finished, or a scan of the centre alone
+    const unsigned long long key = (unsigned long long)z.a * (unsigned long long)n_t2 + (unsigned long long)z.b;
+    unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 32) & (unsigned)(H - 1);
+    for (int probe = 0; probe < H; ++probe) {
+        const unsigned long long prev = atomicCAS(&hkey[h], ~0ull, key);
+        if (prev == ~0ull || prev == key) {
+            vslot[v] = (int)h;
+            vrank[v] = atomicAdd(&hcnt[h], 1);
+            return;
+        }
+        h = (h + 1) & (unsigned)(H - 1);
+    }
+    atomicExch(err, kDeviceErrBounds);   // cannot happen: the table has room for every voxel
+}
+
+// One CTA: each line's first position in `order` and its tiles of at most
+// kLineVox voxels. Thread t owns slots [t H / T, (t + 1) H / T).
+constexpr int kPlanThreads = 1024;
+
+__global__ void __launch_bounds__(kPlanThreads) line_plan_kernel(int H, const int *hcnt, int *hbase, int2 *tiles,
+                                                                 int *n_tiles)
+{
+    __shared__ int sv[kPlanThreads], st[kPlanThreads];
+    const int t = threadIdx.x;
+    const int per = (H + kPlanThreads - 1) / kPlanThreads;
+    const int h0 = min(H, t * per), h1 = min(H, h0 + per);
+    int nv = 0, nt = 0;
+    for (int h = h0; h < h1; ++h) {
+        const int c = hcnt[h];
+        nv += c;
+        nt += (c + kLineVox - 1) / kLineVox;
+    }
+    sv[t] = nv;
+    st[t] = nt;
+    __syncthreads();
+    // inclusive scan (Hillis-Steele)
+    for (int o = 1; o < kPlanThreads; o <<= 1) {
+        const int av = t >= o ? sv[t - o] : 0, at = t >= o ? st[t - o] : 0;
+        __syncthreads();
+        sv[t] += av;
+        st[t] += at;
+        __syncthreads();
+    }
+    int vb = sv[t] - nv, tb = st[t] - nt;
+    for (int h = h0; h < h1; ++h) {
+        const int c = hcnt[h];
+        hbase[h] = vb;
+        for (int i = 0; i < c; i += kLineVox) tiles[tb++] = make_int2(vb + i, min(kLineVox, c - i));
+        vb += c;
+    }
+    if (t == kPlanThreads - 1) *n_tiles = st[t];
+}
+
+__global__ void line_scatter_kernel(int64_t V, const int *vslot, const int *vrank, const int *hbase, int *order)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const int h = vslot[v];
+    if (h >= 0) order[hbase[h] + vrank[v]] = (int)v;
+}
+
+// Work items are (tile, chunk) pairs taken from a counter; the chunks of one
+// tile are consecutive items, so its voxels' samples are read from L2.
+template <bool XONLY, bool SYM>
+__global__ void __launch_bounds__(kLineThreads, 3) zoom_line_kernel(LineArgs L)
+{
+    __shared__ __align__(16) float2 xs[kLineTJ][kLineVox];
+    __shared__ int s_item, s_vid[kLineVox], s_c0[kLineVox];
+    __shared__ float s_ixn[kLineVox];
+    __shared__ LinePart s_red[kLineThreads / 32][kLineVox];
+    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = L.s.n, n_df = L.g.n_df;
+    const int n_items = *L.n_tiles * L.n_chunks;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(L.item_counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items) break;
+        const int t = item / L.n_chunks, k = item - t * L.n_chunks;
+        const int2 tl = L.tiles[t];
+        const int nv = tl.y;
+        if (tid < kLineVox) {
+            int v = -1, c0 = 0;
+            float ixn = 0.f;
+            if (tid < nv) {
+                v = L.order[tl.x + tid];
+                c0 = L.state[v].c;
+                ixn = L.state[v].inv_xn;
+            }
+            s_vid[tid] = v;
+            s_c0[tid] = c0;
+            s_ixn[tid] = ixn;
+        }
+        __syncthreads();
+        int lo = n_df, hi = -1;
+        for (int i = 0; i < nv; ++i) {
+            int l, h;
+            s3_window(s_c0[i], L.W3, n_df, l, h);
+            lo = min(lo, l);
+            hi = max(hi, h);
+        }
+        const int cbase = k * kLineEntries;
+        if (cbase > hi || cbase + kLineEntries - 1 < lo) {   // the chunk misses every window of the tile
+            __syncthreads();
+            continue;
+        }
+        const int c = cbase + tid;
+        const bool act = c >= lo && c <= hi;
+        if (tid == 0)
+            atomicAdd(&L.stats[1], (unsigned long long)(min(hi, cbase + kLineEntries - 1) - max(lo, cbase) + 1));
+        const int a = L.state[s_vid[0]].a, b = L.state[s_vid[0]].b;
+        const float T1 = __ldg(&L.g.t1[a]), T2 = __ldg(&L.g.t2[b]);
+        const float df = act ? __ldg(&L.g.df[c]) : 0.f;
+        const float k1 = -1.4426950408889634f / T1, k2 = -1.4426950408889634f / T2, f = df * 1.0e-3f;
+        Bloch st;
+        start_state(st, L.s, k1);
+        Kahan kr[kLineVox], ki[kLineVox], kd;
+        float pr[kLineVox], pi[kLineVox], pd = 0.f;
+#pragma unroll
+        for (int i = 0; i < kLineVox; ++i) { kr[i].init(); ki[i].init(); pr[i] = 0.f; pi[i] = 0.f; }
+        kd.init();
+        auto flush = [&]() {
+#pragma unroll
+            for (int i = 0; i < kLineVox; ++i) { kr[i].add(pr[i]); ki[i].add(pi[i]); pr[i] = 0.f; pi[i] = 0.f; }
+            kd.add(pd);
+            pd = 0.f;
+        };
+        for (int j0 = 0; j0 < n; j0 += kLineTJ) {
+            const int len = min(kLineTJ, n - j0);
+            __syncthreads();   // the previous block of samples is consumed
+            for (int q = tid; q < kLineVox * kLineTJ; q += kLineThreads) {
+                const int i = q & (kLineVox - 1), jj = q / kLineVox;
+                float2 z = make_float2(0.f, 0.f);
+                if (i < nv && jj < len) z = __ldg(&L.x[(size_t)s_vid[i] * n + j0 + jj]);
+                xs[jj][i] = z;
+            }
+            __syncthreads();
+            const float4 *xv = reinterpret_cast<const float4 *>(&xs[0][0]);
+            for (int jj = 0; jj < len; ++jj) {
+                const int j = j0 + jj;
+                // one timepoint, the operations of step_multi for one candidate
+                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+                float q[10];
+                float ta, tb = 0.f;
+                if (XONLY) {
+                    r = __ldg(&L.s.rfx[j]);
+                    ta = r.w;
+                } else {
+                    const float4 *p = reinterpret_cast<const float4 *>(L.s.rfg + 12 * j);
+                    const float4 a4 = __ldg(p), b4 = __ldg(p + 1), c4 = __ldg(p + 2);
+                    q[0] = a4.x; q[1] = a4.y; q[2] = a4.z; q[3] = a4.w;
+                    q[4] = b4.x; q[5] = b4.y; q[6] = b4.z; q[7] = b4.w;
+                    q[8] = c4.x; q[9] = c4.y;
+                    ta = __ldg(&L.s.tau[j]).x;
+                }
+                if (!SYM) tb = __ldg(&L.s.tau[j]).y;
+                if (XONLY) bloch_rf_x(st, r);
+                else bloch_rf_general(st, q);
+                float cs, sn;
+                const float e1 = ex2_fast(k1 * ta), e2 = ex2_fast(k2 * ta);
+                cis_fast(f, ta, cs, sn);
+                bloch_evolve(st, e1, e2 * cs, e2 * sn);
+                const float sr = st.mx, si = st.my;
+#pragma unroll
+                for (int i2 = 0; i2 < kLineVox / 2; ++i2) {
+                    const float4 z = xv[jj * (kLineVox / 2) + i2];
+                    pr[2 * i2] = fmaf(z.x, sr, fmaf(z.y, si, pr[2 * i2]));
+                    pi[2 * i2] = fmaf(z.y, sr, fmaf(-z.x, si, pi[2 * i2]));
+                    pr[2 * i2 + 1] = fmaf(z.z, sr, fmaf(z.w, si, pr[2 * i2 + 1]));
+                    pi[2 * i2 + 1] = fmaf(z.w, sr, fmaf(-z.z, si, pi[2 * i2 + 1]));
+                }
+                pd = fmaf(sr, sr, fmaf(si, si, pd));
+                if (SYM) {
+                    bloch_evolve(st, e1, e2 * cs, e2 * sn);
+                } else {
+                    const float e1b = ex2_fast(k1 * tb), e2b = ex2_fast(k2 * tb);
+                    cis_fast(f, tb, cs, sn);
+                    bloch_evolve(st, e1b, e2b * cs, e2b * sn);
+                }
+                if (((j + 1) & 15) == 0) flush();
+            }
+        }
+        flush();   // the tail block (the packed kernel flushes once more after its last full block)
+        // each voxel's CC at this position, -inf outside its window or at its centre
+        const float dd = kd.s;
+#pragma unroll
+        for (int i = 0; i < kLineVox; ++i) {
+            float v = -INFINITY;
+            if (act && i < nv) {
+                int l, h;
+                s3_window(s_c0[i], L.W3, n_df, l, h);
+                if (c >= l && c <= h && c != s_c0[i]) {
+                    const float ipr = kr[i].s, ipi = ki[i].s, ixn = s_ixn[i];
+                    const float mag = sqrtf(fmaf(ipr, ipr, ipi * ipi));
+                    v = (dd > 0.f && ixn > 0.f) ? mag * ixn * rsqrtf(dd) : 0.f;
+                }
+            }
+            float t1 = v, t2 = -INFINITY;
+            int c1 = c, cnt = isfinite(v) ? 1 : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float u1 = __shfl_xor_sync(FULL, t1, o), u2 = __shfl_xor_sync(FULL, t2, o);
+                const int d1 = __shfl_xor_sync(FULL, c1, o), dn = __shfl_xor_sync(FULL, cnt, o);
+                part_merge(t1, c1, t2, cnt, u1, d1, u2, dn);
+            }
+            if (lane == 0) s_red[warp][i] = LinePart{t1, c1, t2, cnt};
+        }
+        __syncthreads();
+        if (tid < nv) {
+            LinePart r = s_red[0][tid];
+#pragma unroll
+            for (int w = 1; w < kLineThreads / 32; ++w) {
+                const LinePart u = s_red[w][tid];
+                part_merge(r.t1, r.c1, r.t2, r.cnt, u.t1, u.c1, u.t2, u.cnt);
+            }
+            L.part[(size_t)s_vid[tid] * L.n_chunks + k] = r;
+        }
+        __syncthreads();
+    }
+}
+
+// Each voxel's step 3 from its chunks, in scan order: the first position of
+// the largest CC moves the centre if strictly better; the decision set's top
+// two (with the centre) give the margin.
+__global__ void line_merge_kernel(int64_t V, int W3, int n_df, int n_chunks, const int *vslot, const LinePart *part,
+                                  ZState *state, unsigned long long *stats)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V || vslot[v] < 0) return;
+    ZState z = state[v];
+    int lo, hi;
+    s3_window(z.c, W3, n_df, lo, hi);
+    float best = z.centre, g1 = z.centre, g2 = -INFINITY;
+    int bc = z.c, cnt = 0;
+    for (int k = lo / kLineEntries; k <= hi / kLineEntries; ++k) {
+        const LinePart p = part[(size_t)v * n_chunks + k];
+        if (p.t1 > best) { best = p.t1; bc = p.c1; }
+        top2_add(p.t1, g1, g2);
+        top2_add(p.t2, g1, g2);
+        cnt += p.cnt;
+    }
+    if (isfinite(g2)) z.mm = fminf(z.mm, g1 - g2);
+    z.evaluated += cnt;
+    const unsigned m = __activemask();
+    const unsigned tot = __reduce_add_sync(m, (unsigned)cnt);
+    if ((threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&stats[0], (unsigned long long)tot);
+    z.centre = best;
+    z.c = bc;
+    state[v] = z;
+}
+
 int snap(double h_phys, double step)
 {
     const int h = (int)floor(h_phys / step + 0.5);
@@ -1176,6 +1554,20 @@ void launch_pack(const ZoomArgs &A, unsigned blocks, cudaStream_t stream)
     else if (A.s.xonly) zoom_pack_kernel<true, false><<<blocks, kPackThreads, 0, stream>>>(A);
     else if (A.s.symmetric) zoom_pack_kernel<false, true><<<blocks, kPackThreads, 0, stream>>>(A);
     else zoom_pack_kernel<false, false><<<blocks, kPackThreads, 0, stream>>>(A);
+}
+
+// Line kernel: a persistent grid over the (tile, chunk) items, no more CTAs
+// than the items can need.
+void launch_line(const mrf_ctx *ctx, const LineArgs &L, int64_t max_items, cudaStream_t stream)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_line_kernel<true, true>, kLineThreads, 0);
+    per_sm = std::max(1, per_sm);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * ctx->sm_count, max_items));
+    if (L.s.xonly && L.s.symmetric) zoom_line_kernel<true, true><<<blocks, kLineThreads, 0, stream>>>(L);
+    else if (L.s.xonly) zoom_line_kernel<true, false><<<blocks, kLineThreads, 0, stream>>>(L);
+    else if (L.s.symmetric) zoom_line_kernel<false, true><<<blocks, kLineThreads, 0, stream>>>(L);
+    else zoom_line_kernel<false, false><<<blocks, kLineThreads, 0, stream>>>(L);
 }
 
 }  // namespace
@@ -1230,17 +1622,35 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     size_t gbytes = 0;
     int rc = grid_upload_async(ctx, gd, stream, &gdev, &gblock, &gbytes);
     if (rc) return rc;
-    int *counter = nullptr;
-    rc = budget_charge(ctx, 256);
+
+    // Split search (step 3 batched by line) unless step 3 never scans. Scratch,
+    // one block: counters + line counts | state | keys | line bases | per-voxel
+    // slot, rank, order | tiles | chunk outcomes.
+    const int n_chunks = (gd->n_df + kLineEntries - 1) / kLineEntries;
+    const bool split = P.W3 > 0 && gd->n_df > 1 && V * (int64_t)n_chunks < (int64_t)INT32_MAX / 2;
+    int H = 1024;
+    while (split && (int64_t)H < 2 * V) H <<= 1;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t Vs = (size_t)V;
+    const size_t o_hcnt = 256, o_state = o_hcnt + al(4 * (size_t)H), o_hkey = o_state + al(sizeof(ZState) * Vs);
+    const size_t o_hbase = o_hkey + al(8 * (size_t)H), o_vslot = o_hbase + al(4 * (size_t)H);
+    const size_t o_vrank = o_vslot + al(4 * Vs), o_order = o_vrank + al(4 * Vs), o_tiles = o_order + al(4 * Vs);
+    const size_t o_part = o_tiles + al(8 * Vs), total = o_part + al(sizeof(LinePart) * Vs * n_chunks);
+    const size_t scratch = split ? total : 256;
+    rc = budget_charge(ctx, scratch);
     if (rc) { cudaFreeAsync(gblock, stream); budget_release(ctx, gbytes); return rc; }
-    cudaError_t e = cudaMallocAsync((void **)&counter, 256, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), stream);
+    uint8_t *sb = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&sb, scratch, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sb, 0, split ? o_state : 256, stream);
+    if (e == cudaSuccess && split) e = cudaMemsetAsync(sb + o_hkey, 0xFF, 8 * (size_t)H, stream);
     if (e != cudaSuccess) {
-        budget_release(ctx, 256);
+        if (sb) cudaFreeAsync(sb, stream);
+        budget_release(ctx, scratch);
         cudaFreeAsync(gblock, stream);
         budget_release(ctx, gbytes);
         return cuda_fail(e, "zoom scratch");
     }
+    int *counters = (int *)sb;   // [0] head / whole search, [1] tail, [2] tiles, [3] line items
     ZoomArgs A;
     A.s = seq->dev();
     A.g = gdev;
@@ -1252,18 +1662,56 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     A.x = (const float2 *)fp;
     A.V = V;
     A.out = out;
-    A.counter = counter;
+    A.counter = counters;
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
+    A.state = split ? (ZState *)(sb + o_state) : nullptr;
+    A.phase = split ? kPhaseHead : kPhaseAll;
     const unsigned blocks = pack_blocks(ctx, V);
     {
         ProfScope prof(ctx, kProfZoom, stream);
         launch_pack(A, blocks, stream);
+        if (split) {
+            ZState *state = (ZState *)(sb + o_state);
+            unsigned long long *hkey = (unsigned long long *)(sb + o_hkey);
+            int *hcnt = (int *)(sb + o_hcnt), *hbase = (int *)(sb + o_hbase);
+            int *vslot = (int *)(sb + o_vslot), *vrank = (int *)(sb + o_vrank), *order = (int *)(sb + o_order);
+            int2 *tiles = (int2 *)(sb + o_tiles);
+            LinePart *part = (LinePart *)(sb + o_part);
+            const unsigned vb = (unsigned)((V + 255) / 256);
+            line_hash_kernel<<<vb, 256, 0, stream>>>(state, V, P.W3, gd->n_df, gd->n_t2, H, hkey, hcnt, vslot,
+                                                     vrank, ctx->err_flag);
+            line_plan_kernel<<<1, kPlanThreads, 0, stream>>>(H, hcnt, hbase, tiles, counters + 2);
+            line_scatter_kernel<<<vb, 256, 0, stream>>>(V, vslot, vrank, hbase, order);
+            LineArgs L;
+            L.s = A.s;
+            L.g = gdev;
+            L.x = A.x;
+            L.state = state;
+            L.order = order;
+            L.tiles = tiles;
+            L.n_tiles = counters + 2;
+            L.item_counter = counters + 3;
+            L.n_chunks = n_chunks;
+            L.W3 = P.W3;
+            L.part = part;
+            L.stats = ctx->dev_stats;
+            {
+                ProfScope lp(ctx, kProfZoomLine, stream);
+                launch_line(ctx, L, V * (int64_t)n_chunks, stream);
+            }
+            line_merge_kernel<<<vb, 256, 0, stream>>>(V, P.W3, gd->n_df, n_chunks, vslot, part, state,
+                                                      ctx->dev_stats);
+            A.counter = counters + 1;
+            A.phase = kPhaseTail;
+            launch_pack(A, blocks, stream);
+            count_launch(ctx, 5);   // hash, plan, scatter, merge, tail (head and line kernels counted above)
+        }
     }
     e = cudaGetLastError();
-    cudaFreeAsync(counter, stream);
+    cudaFreeAsync(sb, stream);
     cudaFreeAsync(gblock, stream);
-    budget_release(ctx, 256 + gbytes);
+    budget_release(ctx, scratch + gbytes);
     if (e != cudaSuccess) return cuda_fail(e, "zoom launch");
     return MRF_OK;
 }
@@ -1352,6 +1800,8 @@ extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_z
     A.counter = counter;
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
+    A.state = nullptr;
+    A.phase = kPhaseAll;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_dict_kernel, kZoomThreads, 0);
     per_sm = std::max(1, per_sm);
@@ -1517,6 +1967,8 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     A.counter = (int *)dev;
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
+    A.state = nullptr;
+    A.phase = kPhaseAll;   // one kernel: the split search's scratch grows with V
     const unsigned blocks = pack_blocks(ctx, V);
     launch_pack(A, blocks, stream);
     count_launch(ctx);

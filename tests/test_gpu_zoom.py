@@ -204,3 +204,75 @@ def test_zoom_dict_rejects_fp8(M, ctx):
     finally:
         M.mrf_dict_free(ctx, d)
         M.mrf_sequence_free(ctx, h)
+
+
+def _zoom_both(M, ctx, seq, grid, x, **kw):
+    """mrf_zoom_search (step 3 batched by (T1, T2) line) and the single-kernel
+    search of mrf_zoom_search_static on the same voxels."""
+    import ctypes as C
+    L = M.lib()
+    h = M.mrf_sequence_load(ctx, seq)
+    try:
+        fp = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+        g = M.grid_desc(grid)
+        o = M.zoom_opts(**kw)
+        res = []
+        for fn in (L.mrf_zoom_search, L.mrf_zoom_search_static):
+            out = M.empty_results(x.shape[0])
+            rc = fn(ctx, h, C.byref(g), C.byref(o), C.c_void_p(fp.data_ptr()), x.shape[0],
+                    C.c_void_p(out.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+            assert rc == M.MRF_OK, M.last_error()
+            M.mrf_stream_sync(ctx)
+            res.append(M.results_to_numpy(out)[: x.shape[0]])
+        return res
+    finally:
+        M.mrf_sequence_free(ctx, h)
+
+
+@pytest.mark.parametrize("grid,v,seed", [("fp32_brute", 600, 11), ("zoom_fine", 160, 12), ("fp32_brute", 1, 13),
+                                         ("fp32_brute", 17, 14)])
+def test_zoom_batched_step3_equals_per_voxel_scan(M, ctx, oracle_lib, grid, v, seed):
+    """Step 3 batched over the voxels sharing (T1, T2) computes every CC with
+    the per-voxel kernel's FP32 operations in the same order, so the two
+    searches agree bit for bit: same decisions, evaluation counts, margins and
+    CC. Covers several lines, lines of more than one 16-voxel tile, a single
+    voxel, windows clipped at both ends of the df axis and the 7 chunks of
+    the 801-point df axis."""
+    seq = S.sequence(1, 1000)
+    ph, x = offgrid_voxels(oracle_lib, seq, v, 20.0, seed)
+    split, single = _zoom_both(M, ctx, seq, S.GRIDS[grid], x)
+    for f in ("index", "i_t1", "i_t2", "i_df", "entries_evaluated"):
+        assert np.array_equal(split[f], single[f]), f
+    for f in ("cc", "min_margin", "m0", "phase"):
+        assert np.array_equal(split[f].view(np.uint32), single[f].view(np.uint32)), f
+
+
+def test_zoom_batched_step3_general_rf_against_oracle(M, ctx, oracle_lib):
+    """The other instantiations of the line kernel (general RF rotation, TE not
+    half of TR) on a grid whose windows cover 3 chunks, against the oracle and
+    against the per-voxel kernel."""
+    import math
+    base = S.sequence(5, 300)
+    rng = np.random.default_rng(21)
+    seq = S.Sequence(base.flip_rad, rng.uniform(0, 2 * math.pi, 300), base.tr_ms, base.tr_ms * 0.4, 1, 20.0)
+    g = S.Grid(200.0, 20.0, 60, 20.0, 8.0, 30, -40.0, 0.25, 321)
+    ph, x = offgrid_voxels(oracle_lib, seq, 48, 30.0, 57, t1_range=(300.0, 1200.0), t2_range=(30.0, 200.0),
+                           df_range=(-38.0, 38.0))
+    split, single = _zoom_both(M, ctx, seq, g, x)
+    for f in ("index", "entries_evaluated"):
+        assert np.array_equal(split[f], single[f]), f
+    assert np.array_equal(split["cc"].view(np.uint32), single["cc"].view(np.uint32))
+    ref = oracle_lib.zoom(seq, g, x)
+    _compare(oracle_lib, g, split, ref, "general rf, 321 df")
+
+
+@pytest.mark.parametrize("s3", [0.0, 0.02])
+def test_zoom_step3_narrow_or_empty_window(M, ctx, oracle_lib, s3):
+    """A step-3 window of the centre alone (s3_half_frac 0: no scan, the
+    single-kernel path) and one of a few positions, against the oracle."""
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["fp32_brute"]
+    ph, x = offgrid_voxels(oracle_lib, seq, 64, 20.0, 202)
+    res = _gpu_zoom(M, ctx, seq, g, x, s3_half_frac=s3)
+    ref = oracle_lib.zoom(seq, g, x, oracle_lib.default_zoom_opts(s3_half_frac=s3))
+    _compare(oracle_lib, g, res, ref, f"s3_half_frac={s3}")
