@@ -1246,6 +1246,7 @@ struct LineArgs {
     int *item_counter;
     int n_chunks, W3;
     LinePart *part;                 // [voxel][chunk]
+    int *vlo;                       // [voxel] first position of its tile's chunk 0
     unsigned long long *stats;      // [1] += candidates simulated
 };
 
@@ -1266,9 +1267,18 @@ __device__ __forceinline__ void part_merge(float &t1, int &c1, float &t2, int &c
 
 // Voxels grouped by the (a, b) of their step 3: an open-addressing table of
 // H (a power of two, at least twice the voxels) keys; each voxel learns its
-// line's slot and its rank among the line's voxels.
+// line's slot, and its rank within one of kLineBuckets df bands of the line
+// (c0 binned), so that a line's voxels are laid out by df and a tile's
+// windows overlap.
+constexpr int kLineBuckets = 32;
+
+__device__ __forceinline__ int line_bucket(int c0, int n_df)
+{
+    return (int)(((int64_t)c0 * kLineBuckets) / n_df);
+}
+
 __global__ void line_hash_kernel(const ZState *state, int64_t V, int W3, int n_df, int n_t2, int H,
-                                 unsigned long long *hkey, int *hcnt, int *vslot, int *vrank, int *err)
+                                 unsigned long long *hkey, int *hcnt, int *hist, int *vslot, int *vrank, int *err)
 {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
@@ -1283,7 +1293,9 @@ __global__ void line_hash_kernel(const ZState *state, int64_t V, int W3, int n_d
         const unsigned long long prev = atomicCAS(&hkey[h], ~0ull, key);
         if (prev == ~0ull || prev == key) {
             vslot[v] = (int)h;
-            vrank[v] = atomicAdd(&hcnt[h], 1);
+            atomicAdd(&hcnt[h], 1);
+            const int bk = line_bucket(z.c, n_df);
+            vrank[v] = atomicAdd(&hist[(size_t)h * kLineBuckets + bk], 1) | (bk << 24);
             return;
         }
         h = (h + 1) & (unsigned)(H - 1);
@@ -1329,12 +1341,17 @@ __global__ void __launch_bounds__(kPlanThreads) line_plan_kernel(int H, const in
     if (t == kPlanThreads - 1) *n_tiles = st[t];
 }
 
-__global__ void line_scatter_kernel(int64_t V, const int *vslot, const int *vrank, const int *hbase, int *order)
+__global__ void line_scatter_kernel(int64_t V, const int *vslot, const int *vrank, const int *hbase, const int *hist,
+                                    int *order)
 {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
     const int h = vslot[v];
-    if (h >= 0) order[hbase[h] + vrank[v]] = (int)v;
+    if (h < 0) return;
+    const int r = vrank[v] & 0xffffff, bk = vrank[v] >> 24;
+    int off = hbase[h] + r;
+    for (int b = 0; b < bk; ++b) off += hist[(size_t)h * kLineBuckets + b];
+    order[off] = (int)v;
 }
 
 // Work items are (tile, chunk) pairs taken from a counter; the chunks of one
@@ -1343,6 +1360,8 @@ template <bool XONLY, bool SYM>
 __global__ void __launch_bounds__(kLineThreads, 3) zoom_line_kernel(LineArgs L)
 {
     __shared__ __align__(16) float2 xs[kLineTJ][kLineVox];
+    __shared__ float4 s_rf[3 * kLineTJ];   // x rotation (c, s, 1 - c, TE), or 12 floats of a general rotation
+    __shared__ float2 s_tau[kLineTJ];
     __shared__ int s_item, s_vid[kLineVox], s_c0[kLineVox];
     __shared__ float s_ixn[kLineVox];
     __shared__ LinePart s_red[kLineThreads / 32][kLineVox];
@@ -1378,15 +1397,16 @@ __global__ void __launch_bounds__(kLineThreads, 3) zoom_line_kernel(LineArgs L)
             lo = min(lo, l);
             hi = max(hi, h);
         }
-        const int cbase = k * kLineEntries;
-        if (cbase > hi || cbase + kLineEntries - 1 < lo) {   // the chunk misses every window of the tile
+        const int cbase = lo + k * kLineEntries;   // chunks tile the union of the tile's windows
+        if (cbase > hi) {
             __syncthreads();
             continue;
         }
+        if (k == 0 && tid < nv) L.vlo[s_vid[tid]] = lo;
         const int c = cbase + tid;
         const bool act = c >= lo && c <= hi;
         if (tid == 0)
-            atomicAdd(&L.stats[1], (unsigned long long)(min(hi, cbase + kLineEntries - 1) - max(lo, cbase) + 1));
+            atomicAdd(&L.stats[1], (unsigned long long)(min(hi, cbase + kLineEntries - 1) - cbase + 1));
         const int a = L.state[s_vid[0]].a, b = L.state[s_vid[0]].b;
         const float T1 = __ldg(&L.g.t1[a]), T2 = __ldg(&L.g.t2[b]);
         const float df = act ? __ldg(&L.g.df[c]) : 0.f;
@@ -1404,6 +1424,48 @@ __global__ void __launch_bounds__(kLineThreads, 3) zoom_line_kernel(LineArgs L)
             kd.add(pd);
             pd = 0.f;
         };
+        // one timepoint, the operations of step_multi for one candidate; the
+        // block's samples and RF coefficients come from shared memory
+        auto step = [&](int jj) {
+            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+            float q[10];
+            float ta, tb = 0.f;
+            if (XONLY) {
+                r = s_rf[jj];
+                ta = r.w;
+            } else {
+                const float4 a4 = s_rf[3 * jj], b4 = s_rf[3 * jj + 1], c4 = s_rf[3 * jj + 2];
+                q[0] = a4.x; q[1] = a4.y; q[2] = a4.z; q[3] = a4.w;
+                q[4] = b4.x; q[5] = b4.y; q[6] = b4.z; q[7] = b4.w;
+                q[8] = c4.x; q[9] = c4.y;
+                ta = s_tau[jj].x;
+            }
+            if (!SYM) tb = s_tau[jj].y;
+            if (XONLY) bloch_rf_x(st, r);
+            else bloch_rf_general(st, q);
+            float cs, sn;
+            const float e1 = ex2_fast(k1 * ta), e2 = ex2_fast(k2 * ta);
+            cis_fast(f, ta, cs, sn);
+            bloch_evolve(st, e1, e2 * cs, e2 * sn);
+            const float sr = st.mx, si = st.my;
+            const float4 *xv = reinterpret_cast<const float4 *>(&xs[jj][0]);
+#pragma unroll
+            for (int i2 = 0; i2 < kLineVox / 2; ++i2) {
+                const float4 z = xv[i2];
+                pr[2 * i2] = fmaf(z.x, sr, fmaf(z.y, si, pr[2 * i2]));
+                pi[2 * i2] = fmaf(z.y, sr, fmaf(-z.x, si, pi[2 * i2]));
+                pr[2 * i2 + 1] = fmaf(z.z, sr, fmaf(z.w, si, pr[2 * i2 + 1]));
+                pi[2 * i2 + 1] = fmaf(z.w, sr, fmaf(-z.z, si, pi[2 * i2 + 1]));
+            }
+            pd = fmaf(sr, sr, fmaf(si, si, pd));
+            if (SYM) {
+                bloch_evolve(st, e1, e2 * cs, e2 * sn);
+            } else {
+                const float e1b = ex2_fast(k1 * tb), e2b = ex2_fast(k2 * tb);
+                cis_fast(f, tb, cs, sn);
+                bloch_evolve(st, e1b, e2b * cs, e2b * sn);
+            }
+        };
         for (int j0 = 0; j0 < n; j0 += kLineTJ) {
             const int len = min(kLineTJ, n - j0);
             __syncthreads();   // the previous block of samples is consumed
@@ -1413,50 +1475,29 @@ __global__ void __launch_bounds__(kLineThreads, 3) zoom_line_kernel(LineArgs L)
                 if (i < nv && jj < len) z = __ldg(&L.x[(size_t)s_vid[i] * n + j0 + jj]);
                 xs[jj][i] = z;
             }
-            __syncthreads();
-            const float4 *xv = reinterpret_cast<const float4 *>(&xs[0][0]);
-            for (int jj = 0; jj < len; ++jj) {
-                const int j = j0 + jj;
-                // one timepoint, the operations of step_multi for one candidate
-                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-                float q[10];
-                float ta, tb = 0.f;
+            if (tid < len) {
                 if (XONLY) {
-                    r = __ldg(&L.s.rfx[j]);
-                    ta = r.w;
+                    s_rf[tid] = __ldg(&L.s.rfx[j0 + tid]);
                 } else {
-                    const float4 *p = reinterpret_cast<const float4 *>(L.s.rfg + 12 * j);
-                    const float4 a4 = __ldg(p), b4 = __ldg(p + 1), c4 = __ldg(p + 2);
-                    q[0] = a4.x; q[1] = a4.y; q[2] = a4.z; q[3] = a4.w;
-                    q[4] = b4.x; q[5] = b4.y; q[6] = b4.z; q[7] = b4.w;
-                    q[8] = c4.x; q[9] = c4.y;
-                    ta = __ldg(&L.s.tau[j]).x;
+                    const float4 *p = reinterpret_cast<const float4 *>(L.s.rfg + 12 * (j0 + tid));
+                    s_rf[3 * tid] = __ldg(p);
+                    s_rf[3 * tid + 1] = __ldg(p + 1);
+                    s_rf[3 * tid + 2] = __ldg(p + 2);
                 }
-                if (!SYM) tb = __ldg(&L.s.tau[j]).y;
-                if (XONLY) bloch_rf_x(st, r);
-                else bloch_rf_general(st, q);
-                float cs, sn;
-                const float e1 = ex2_fast(k1 * ta), e2 = ex2_fast(k2 * ta);
-                cis_fast(f, ta, cs, sn);
-                bloch_evolve(st, e1, e2 * cs, e2 * sn);
-                const float sr = st.mx, si = st.my;
-#pragma unroll
-                for (int i2 = 0; i2 < kLineVox / 2; ++i2) {
-                    const float4 z = xv[jj * (kLineVox / 2) + i2];
-                    pr[2 * i2] = fmaf(z.x, sr, fmaf(z.y, si, pr[2 * i2]));
-                    pi[2 * i2] = fmaf(z.y, sr, fmaf(-z.x, si, pi[2 * i2]));
-                    pr[2 * i2 + 1] = fmaf(z.z, sr, fmaf(z.w, si, pr[2 * i2 + 1]));
-                    pi[2 * i2 + 1] = fmaf(z.w, sr, fmaf(-z.z, si, pi[2 * i2 + 1]));
-                }
-                pd = fmaf(sr, sr, fmaf(si, si, pd));
-                if (SYM) {
-                    bloch_evolve(st, e1, e2 * cs, e2 * sn);
+                s_tau[tid] = __ldg(&L.s.tau[j0 + tid]);
+            }
+            __syncthreads();
+            // 16-timepoint blocks (block boundaries at multiples of 16, as in
+            // the packed kernel); a block cut by the end of the sequence is
+            // flushed once after the loop
+            for (int jb = 0; jb < len; jb += 16) {
+                if (jb + 16 <= len) {
+#pragma unroll 4
+                    for (int u = 0; u < 16; ++u) step(jb + u);
+                    flush();
                 } else {
-                    const float e1b = ex2_fast(k1 * tb), e2b = ex2_fast(k2 * tb);
-                    cis_fast(f, tb, cs, sn);
-                    bloch_evolve(st, e1b, e2b * cs, e2b * sn);
+                    for (int u = jb; u < len; ++u) step(u);
                 }
-                if (((j + 1) & 15) == 0) flush();
             }
         }
         flush();   // the tail block (the packed kernel flushes once more after its last full block)
@@ -1502,7 +1543,7 @@ __global__ void __launch_bounds__(kLineThreads, 3) zoom_line_kernel(LineArgs L)
 // the largest CC moves the centre if strictly better; the decision set's top
 // two (with the centre) give the margin.
 __global__ void line_merge_kernel(int64_t V, int W3, int n_df, int n_chunks, const int *vslot, const LinePart *part,
-                                  ZState *state, unsigned long long *stats)
+                                  const int *vlo, ZState *state, unsigned long long *stats)
 {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V || vslot[v] < 0) return;
@@ -1511,7 +1552,8 @@ __global__ void line_merge_kernel(int64_t V, int W3, int n_df, int n_chunks, con
     s3_window(z.c, W3, n_df, lo, hi);
     float best = z.centre, g1 = z.centre, g2 = -INFINITY;
     int bc = z.c, cnt = 0;
-    for (int k = lo / kLineEntries; k <= hi / kLineEntries; ++k) {
+    const int tlo = vlo[v];
+    for (int k = (lo - tlo) / kLineEntries; k <= (hi - tlo) / kLineEntries; ++k) {
         const LinePart p = part[(size_t)v * n_chunks + k];
         if (p.t1 > best) { best = p.t1; bc = p.c1; }
         top2_add(p.t1, g1, g2);
@@ -1627,15 +1669,19 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     // one block: counters + line counts | state | keys | line bases | per-voxel
     // slot, rank, order | tiles | chunk outcomes.
     const int n_chunks = (gd->n_df + kLineEntries - 1) / kLineEntries;
-    const bool split = P.W3 > 0 && gd->n_df > 1 && V * (int64_t)n_chunks < (int64_t)INT32_MAX / 2;
+    // (a window of fewer than 64 positions leaves the line kernel's lanes mostly idle)
+    const bool split = std::min(2 * P.W3 + 1, gd->n_df) >= 64 && V * (int64_t)n_chunks < (int64_t)INT32_MAX / 2 &&
+                       V < (1 << 24);
     int H = 1024;
     while (split && (int64_t)H < 2 * V) H <<= 1;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t Vs = (size_t)V;
-    const size_t o_hcnt = 256, o_state = o_hcnt + al(4 * (size_t)H), o_hkey = o_state + al(sizeof(ZState) * Vs);
+    const size_t o_hcnt = 256, o_hist = o_hcnt + al(4 * (size_t)H);
+    const size_t o_state = o_hist + al(4 * (size_t)H * kLineBuckets), o_hkey = o_state + al(sizeof(ZState) * Vs);
     const size_t o_hbase = o_hkey + al(8 * (size_t)H), o_vslot = o_hbase + al(4 * (size_t)H);
     const size_t o_vrank = o_vslot + al(4 * Vs), o_order = o_vrank + al(4 * Vs), o_tiles = o_order + al(4 * Vs);
-    const size_t o_part = o_tiles + al(8 * Vs), total = o_part + al(sizeof(LinePart) * Vs * n_chunks);
+    const size_t o_vlo = o_tiles + al(8 * Vs), o_part = o_vlo + al(4 * Vs);
+    const size_t total = o_part + al(sizeof(LinePart) * Vs * n_chunks);
     const size_t scratch = split ? total : 256;
     rc = budget_charge(ctx, scratch);
     if (rc) { cudaFreeAsync(gblock, stream); budget_release(ctx, gbytes); return rc; }
@@ -1674,15 +1720,16 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
         if (split) {
             ZState *state = (ZState *)(sb + o_state);
             unsigned long long *hkey = (unsigned long long *)(sb + o_hkey);
-            int *hcnt = (int *)(sb + o_hcnt), *hbase = (int *)(sb + o_hbase);
+            int *hcnt = (int *)(sb + o_hcnt), *hbase = (int *)(sb + o_hbase), *hist = (int *)(sb + o_hist);
+            int *vlo = (int *)(sb + o_vlo);
             int *vslot = (int *)(sb + o_vslot), *vrank = (int *)(sb + o_vrank), *order = (int *)(sb + o_order);
             int2 *tiles = (int2 *)(sb + o_tiles);
             LinePart *part = (LinePart *)(sb + o_part);
             const unsigned vb = (unsigned)((V + 255) / 256);
-            line_hash_kernel<<<vb, 256, 0, stream>>>(state, V, P.W3, gd->n_df, gd->n_t2, H, hkey, hcnt, vslot,
-                                                     vrank, ctx->err_flag);
+            line_hash_kernel<<<vb, 256, 0, stream>>>(state, V, P.W3, gd->n_df, gd->n_t2, H, hkey, hcnt, hist,
+                                                     vslot, vrank, ctx->err_flag);
             line_plan_kernel<<<1, kPlanThreads, 0, stream>>>(H, hcnt, hbase, tiles, counters + 2);
-            line_scatter_kernel<<<vb, 256, 0, stream>>>(V, vslot, vrank, hbase, order);
+            line_scatter_kernel<<<vb, 256, 0, stream>>>(V, vslot, vrank, hbase, hist, order);
             LineArgs L;
             L.s = A.s;
             L.g = gdev;
@@ -1695,12 +1742,13 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
             L.n_chunks = n_chunks;
             L.W3 = P.W3;
             L.part = part;
+            L.vlo = vlo;
             L.stats = ctx->dev_stats;
             {
                 ProfScope lp(ctx, kProfZoomLine, stream);
                 launch_line(ctx, L, V * (int64_t)n_chunks, stream);
             }
-            line_merge_kernel<<<vb, 256, 0, stream>>>(V, P.W3, gd->n_df, n_chunks, vslot, part, state,
+            line_merge_kernel<<<vb, 256, 0, stream>>>(V, P.W3, gd->n_df, n_chunks, vslot, part, vlo, state,
                                                       ctx->dev_stats);
             A.counter = counters + 1;
             A.phase = kPhaseTail;

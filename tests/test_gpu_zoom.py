@@ -229,8 +229,8 @@ def _zoom_both(M, ctx, seq, grid, x, **kw):
         M.mrf_sequence_free(ctx, h)
 
 
-@pytest.mark.parametrize("grid,v,seed", [("fp32_brute", 600, 11), ("zoom_fine", 160, 12), ("fp32_brute", 1, 13),
-                                         ("fp32_brute", 17, 14)])
+@pytest.mark.parametrize("grid,v,seed", [("precision", 600, 11), ("zoom_fine", 160, 12), ("precision", 1, 13),
+                                         ("precision", 17, 14)])
 def test_zoom_batched_step3_equals_per_voxel_scan(M, ctx, oracle_lib, grid, v, seed):
     """Step 3 batched over the voxels sharing (T1, T2) computes every CC with
     the per-voxel kernel's FP32 operations in the same order, so the two
@@ -266,12 +266,14 @@ def test_zoom_batched_step3_general_rf_against_oracle(M, ctx, oracle_lib):
     _compare(oracle_lib, g, split, ref, "general rf, 321 df")
 
 
-@pytest.mark.parametrize("s3", [0.0, 0.02])
-def test_zoom_step3_narrow_or_empty_window(M, ctx, oracle_lib, s3):
-    """A step-3 window of the centre alone (s3_half_frac 0: no scan, the
-    single-kernel path) and one of a few positions, against the oracle."""
+@pytest.mark.parametrize("grid,s3", [("fp32_brute", 0.0), ("fp32_brute", 0.02), ("precision", 0.4)])
+def test_zoom_step3_narrow_or_empty_window(M, ctx, oracle_lib, grid, s3):
+    """Step-3 windows of the centre alone (s3_half_frac 0: no scan) and of a
+    few positions (both on the single-kernel path: fewer than 64 positions),
+    and windows of 71 positions clipped by the df axis on the batched path,
+    against the oracle."""
     seq = S.sequence(1, 1000)
-    g = S.GRIDS["fp32_brute"]
+    g = S.GRIDS[grid]
     ph, x = offgrid_voxels(oracle_lib, seq, 64, 20.0, 202)
     res = _gpu_zoom(M, ctx, seq, g, x, s3_half_frac=s3)
     ref = oracle_lib.zoom(seq, g, x, oracle_lib.default_zoom_opts(s3_half_frac=s3))
