@@ -105,6 +105,9 @@ typedef struct {
     /* work of the batched step-3 kernel, always counted: df positions
      * evaluated (voxel, candidate pairs) and candidates simulated */
     uint64_t zoomline_pairs, zoomline_entries;
+    /* the packed on-the-fly ZOOM kernel: warp rounds, candidates simulated,
+     * and the most rounds one voxel spent in flight within a launch */
+    uint64_t zoom_rounds, zoom_candidates, zoom_max_voxel_rounds;
 } mrf_profile;
 int mrf_profile_enable(mrf_ctx *ctx, int on);
 /* Synchronises the device (pending profile events, work counters). reset != 0

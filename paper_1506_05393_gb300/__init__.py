@@ -98,7 +98,8 @@ class Profile(C.Structure):
                 ("zoom_launches", C.c_uint64), ("dictgen_ms", C.c_double), ("matcher_ms", C.c_double),
                 ("zoom_ms", C.c_double), ("dictgen_timed", C.c_uint64), ("matcher_timed", C.c_uint64),
                 ("zoom_timed", C.c_uint64), ("zoomline_launches", C.c_uint64), ("zoomline_ms", C.c_double),
-                ("zoomline_timed", C.c_uint64), ("zoomline_pairs", C.c_uint64), ("zoomline_entries", C.c_uint64)]
+                ("zoomline_timed", C.c_uint64), ("zoomline_pairs", C.c_uint64), ("zoomline_entries", C.c_uint64),
+                ("zoom_rounds", C.c_uint64), ("zoom_candidates", C.c_uint64), ("zoom_max_voxel_rounds", C.c_uint64)]
 
 
 # one mrf_result (56 bytes, 8-byte aligned)

@@ -226,11 +226,14 @@ extern "C" int mrf_profile_read(mrf_ctx *ctx, mrf_profile *out, int reset)
     out->zoomline_launches = ctx->kind_launches[kProfZoomLine].load();
     out->zoomline_ms = ctx->prof_ms[kProfZoomLine];
     out->zoomline_timed = ctx->prof_timed[kProfZoomLine];
-    unsigned long long st[2] = {0, 0};
+    unsigned long long st[5] = {0, 0, 0, 0, 0};
     cudaDeviceSynchronize();
     if (cudaMemcpy(st, ctx->dev_stats, sizeof(st), cudaMemcpyDeviceToHost) == cudaSuccess) {
         out->zoomline_pairs = st[0];
         out->zoomline_entries = st[1];
+        out->zoom_rounds = st[2];
+        out->zoom_candidates = st[3];
+        out->zoom_max_voxel_rounds = st[4];
     }
     if (reset) {
         cudaMemset(ctx->dev_stats, 0, sizeof(st));

@@ -79,6 +79,7 @@ struct ZoomArgs {
     int max_moves;
     ZState *state;           // split search only
     int phase;               // ZPhase
+    unsigned long long *stats;   // work counters: [2] warp rounds, [3] candidates simulated, [4] most rounds of a voxel
 };
 
 struct Kahan {
@@ -691,6 +692,7 @@ constexpr int kPerLane = 2;                  // table entries a lane can simulat
 constexpr int kTable = 32 * kPerLane;
 constexpr int kWin = 64;
 constexpr int kReqMax = 24;                  // listed points per slot and round (8 missing + speculative)
+constexpr int kSpecCentres = 5;              // 2D walks: future centres whose neighbourhoods are speculated
 
 enum Stage : int { kS1a = 0, kS1b, kS1c, kS2, kS3, kS4, kS5, kFinal, kStop };
 enum Tag : int { kTagNone = 0, kTagScan, kTagMove, kTagFinal };
@@ -704,6 +706,7 @@ struct Slot {
     float mm;              // smallest decision margin so far
     float inv_xn;
     int ok;                // 0 once a level exceeded the move limit
+    int rounds;            // rounds the voxel has been in flight (work counter)
     // df scans: list positions p..p_end, grid point c = start + p * step, `skip` excluded
     int p, p_end, start, step, skip;
     float g1, g2;          // running top two of the scan's decision set
@@ -839,11 +842,15 @@ __device__ __forceinline__ bool list_point(PackShared &W, int s, const GridDev &
 }
 
 // Points that later decisions of a blocked move level will want if the walk
-// goes on: the 3 x 3 neighbourhoods of the next two centres along the last
-// move (before the first move, the 16 points at distance 2), or the next
-// eight points of a 1D line in the direction of travel (both sides before the
-// first move). All lie within 3 lattice steps (9 on a line) of the centre, so
-// the window keeps them until they are needed.
+// goes on: the 3 x 3 neighbourhoods of the next kSpecCentres centres along the
+// last move, nearest first (before the first move, the 16 points at distance
+// 2), or the next eight points of a 1D line in the direction of travel (both
+// sides before the first move). The long walks of the final 2D ZOOM run
+// straight for tens of moves, so a round can settle up to kSpecCentres + 1
+// moves. With the current 3 x 3 block these points span at most 8 lattice
+// steps along each axis (9 on a line), which the window holds without
+// collisions, so every decision a round's results allow finds its values.
+// Speculative points fill only lanes that required points leave idle.
 __device__ void speculate(PackShared &W, int s, const GridDev &g, unsigned long long listed)
 {
     Slot &S = W.s[s];
@@ -866,7 +873,7 @@ __device__ void speculate(PackShared &W, int s, const GridDev &g, unsigned long 
                 if (i == -2 || i == 2 || k == -2 || k == 2) add(S.ia + i, S.ib + k);
         return;
     }
-    for (int t = 1; t <= 2; ++t)
+    for (int t = 1; t <= kSpecCentres; ++t)
         for (int i = -1; i <= 1; ++i)
             for (int k = -1; k <= 1; ++k) add(S.ia + t * S.da + i, S.ib + t * S.db + k);
 }
@@ -888,7 +895,7 @@ __device__ void advance(PackShared &W, int s, const ZoomPlan &P, const GridDev &
             ZState z;
             z.a = S.a; z.b = S.b; z.c = S.c; z.evaluated = S.evaluated;
             z.centre = S.centre; z.mm = S.mm; z.inv_xn = S.inv_xn;
-            z.flags = S.ok ? kZOk : 0;
+            z.flags = (S.ok ? kZOk : 0) | (S.rounds << 8);
             state[S.v] = z;
             S.v = -1;
             return;
@@ -1038,7 +1045,8 @@ __device__ void assign(PackShared &W)
 
 // Slot s takes this round's results: scan positions in order, move points
 // into the window, the final centre's <x, d> into the voxel's result.
-__device__ void ingest(PackShared &W, int s, const GridDev &g, mrf_result *out, int *err, ZState *state)
+__device__ void ingest(PackShared &W, int s, const GridDev &g, mrf_result *out, int *err, ZState *state,
+                       unsigned long long *stats)
 {
     Slot &S = W.s[s];
     const int used = W.used;
@@ -1070,6 +1078,7 @@ __device__ void ingest(PackShared &W, int s, const GridDev &g, mrf_result *out, 
             r.min_margin = isfinite(S.mm) ? S.mm : -1.f;
             out[S.v] = r;
             if (state) state[S.v].flags = kZDone;
+            if (stats) atomicMax(&stats[4], (unsigned long long)S.rounds);
             S.v = -1;
         }
     }
@@ -1125,12 +1134,13 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
     const ZoomPlan &P = sP;
     const int n = A.s.n;
     ZState *head = A.phase == kPhaseHead ? A.state : nullptr;   // saves at step 3
+    unsigned long long w_rounds = 0, w_entries = 0;
 
     for (;;) {
         // decisions (one lane per slot)
         if (lane < kSlots) {
             const int s = lane;
-            ingest(W, s, A.g, A.out, A.err, head);
+            ingest(W, s, A.g, A.out, A.err, head, A.stats);
             Slot &S = W.s[s];
             // a slot parked at step 3 is free at once: refill it until it has
             // work or the voxels run out, so no warp leaves with voxels left
@@ -1148,6 +1158,7 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
                         S.evaluated = z.evaluated;
                         S.mm = z.mm;
                         S.ok = z.flags & kZOk;
+                        S.rounds = z.flags >> 8;
                         S.inv_xn = z.inv_xn;
                         S.level = 0;
                         enter(W, s, kS4, P, A.g.n_df, false);
@@ -1158,6 +1169,7 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
                         S.evaluated = 0;
                         S.mm = INFINITY;
                         S.ok = 1;
+                        S.rounds = 0;
                         S.level = 0;
                         atomicOr(&W.norm_mask, 1 << s);
                         enter(W, s, kS1a, P, A.g.n_df, head != nullptr);
@@ -1166,6 +1178,7 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
                 advance(W, s, P, A.g, A.max_moves, head);
                 if (S.v >= 0 || W.drained) break;
             }
+            if (S.v >= 0) S.rounds += 1;
         }
         __syncwarp();
         const bool busy = lane < kSlots && W.s[lane].v >= 0;
@@ -1197,9 +1210,15 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
             if (lane == 0) atomicExch(A.err, kDeviceErrBounds);
             break;
         }
+        w_rounds += 1;
+        w_entries += used;
         if (used > 32) eval_entries<XONLY, SYM, 2>(W, A, lane);
         else eval_entries<XONLY, SYM, 1>(W, A, lane);
         __syncwarp();
+    }
+    if (lane == 0 && A.stats) {
+        atomicAdd(&A.stats[2], w_rounds);
+        atomicAdd(&A.stats[3], w_entries);
     }
 }
 
@@ -1713,6 +1732,7 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     A.max_moves = 1 << 20;
     A.state = split ? (ZState *)(sb + o_state) : nullptr;
     A.phase = split ? kPhaseHead : kPhaseAll;
+    A.stats = ctx->dev_stats;
     const unsigned blocks = pack_blocks(ctx, V);
     {
         ProfScope prof(ctx, kProfZoom, stream);
@@ -1850,6 +1870,7 @@ extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_z
     A.max_moves = 1 << 20;
     A.state = nullptr;
     A.phase = kPhaseAll;
+    A.stats = nullptr;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_dict_kernel, kZoomThreads, 0);
     per_sm = std::max(1, per_sm);
@@ -2017,6 +2038,7 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     A.max_moves = 1 << 20;
     A.state = nullptr;
     A.phase = kPhaseAll;   // one kernel: the split search's scratch grows with V
+    A.stats = ctx->dev_stats;
     const unsigned blocks = pack_blocks(ctx, V);
     launch_pack(A, blocks, stream);
     count_launch(ctx);
