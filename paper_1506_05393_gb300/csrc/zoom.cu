@@ -709,6 +709,7 @@ struct Slot {
     int rounds;            // rounds the voxel has been in flight (work counter)
     // df scans: list positions p..p_end, grid point c = start + p * step, `skip` excluded
     int p, p_end, start, step, skip;
+    int scan_first, scan_n;  // this round's df positions in the table
     float g1, g2;          // running top two of the scan's decision set
     // move levels: moves so far, lattice origin (la, lb) and steps, the
     // centre's lattice coordinates, the last move (lattice units)
@@ -970,23 +971,12 @@ __device__ void advance(PackShared &W, int s, const ZoomPlan &P, const GridDev &
     }
 }
 
-// Lane 0: the round's table -- every slot's missing points first (rotating
-// slot order), then consecutive df positions for the scanning slots, then the
-// speculative points, one slot at a time.
-__device__ void assign(PackShared &W)
+// Lane 0, rounds with a df scan: consecutive positions for the scanning slots
+// from table entry `used` on, shared out elastically over the free entries;
+// returns the next free entry.
+__device__ int assign_scans(PackShared &W, int used)
 {
-    int used = 0;
     const int rot = W.rot;
-    for (int i = 0; i < kSlots; ++i) {
-        const int s = (rot + i) % kSlots;
-        const Slot &S = W.s[s];
-        if (S.v < 0) continue;
-        const int tag = S.stage == kFinal ? kTagFinal : kTagMove;
-        for (int r = 0; r < S.nreq && used < kTable; ++r, ++used) {
-            W.t_slot[used] = s; W.t_a[used] = S.ra[r]; W.t_b[used] = S.rb[r]; W.t_c[used] = S.c;
-            W.t_tag[used] = tag | (S.rw[r] << 8);
-        }
-    }
     int left[kSlots], give[kSlots];
     int active = 0;
 #pragma unroll
@@ -1011,7 +1001,9 @@ __device__ void assign(PackShared &W)
         }
     }
     for (int s = 0; s < kSlots; ++s) {
-        const Slot &S = W.s[s];
+        Slot &S = W.s[s];
+        S.scan_first = used;
+        S.scan_n = give[s];
         for (int k = 0; k < give[s]; ++k, ++used) {
             const int c = S.start + (S.p + k) * S.step;
             W.t_slot[used] = s;
@@ -1021,49 +1013,92 @@ __device__ void assign(PackShared &W)
             W.t_tag[used] = kTagScan;
         }
     }
-    int taken[kSlots];
-#pragma unroll
-    for (int s = 0; s < kSlots; ++s) taken[s] = 0;
-    for (bool any = true; any && used < kTable;) {
-        any = false;
-        for (int i = 0; i < kSlots && used < kTable; ++i) {
-            const int s = (rot + i) % kSlots;
-            const Slot &S = W.s[s];
-            if (S.v < 0 || S.stage == kFinal || is_scan(S.stage) || taken[s] >= S.nspec) continue;
-            const int r = S.nreq + taken[s];
-            taken[s] += 1;
-            W.t_slot[used] = s; W.t_a[used] = S.ra[r]; W.t_b[used] = S.rb[r]; W.t_c[used] = S.c;
-            W.t_tag[used] = kTagMove | (S.rw[r] << 8);
-            ++used;
-            any = true;
-        }
-    }
-    W.used = used;
-    for (; used < kTable; ++used) { W.t_slot[used] = -1; W.t_tag[used] = kTagNone; }
-    W.rot = (rot + 1) % kSlots;
+    return used;
 }
 
-// Slot s takes this round's results: scan positions in order, move points
-// into the window, the final centre's <x, d> into the voxel's result.
-__device__ void ingest(PackShared &W, int s, const GridDev &g, mrf_result *out, int *err, ZState *state,
+// The round's table, built by the whole warp: every slot's missing points
+// first (rotating slot order), then consecutive df positions for the scanning
+// slots, then the speculative points one slot at a time (pass r takes the r-th
+// point of each slot that has one, in rotating order), cut at kTable. Each
+// slot lane computes where its own points go in that order.
+__device__ void assign(PackShared &W, int lane)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int rot = W.rot;
+    int nreq = 0, nsp = 0, scanning = 0, tag = kTagMove, ord = kSlots;
+    if (lane < kSlots) {
+        Slot &S = W.s[lane];
+        ord = (lane - rot + kSlots) % kSlots;
+        S.scan_n = 0;
+        if (S.v >= 0) {
+            nreq = S.nreq;
+            tag = S.stage == kFinal ? kTagFinal : kTagMove;
+            if (is_scan(S.stage)) scanning = S.p <= S.p_end;
+            else if (S.stage != kFinal) nsp = S.nspec;
+        }
+    }
+    int base = 0, nreq_total = 0, nsp_total = 0;
+    int nsp_all[kSlots], ord_all[kSlots];
+#pragma unroll
+    for (int t = 0; t < kSlots; ++t) {
+        const int nr = __shfl_sync(FULL, nreq, t);
+        ord_all[t] = __shfl_sync(FULL, ord, t);
+        nsp_all[t] = __shfl_sync(FULL, nsp, t);
+        nreq_total += nr;
+        nsp_total += nsp_all[t];
+        if (ord_all[t] < ord) base += nr;
+    }
+    if (lane < kSlots) {
+        const Slot &S = W.s[lane];
+        for (int r = 0; r < nreq; ++r) {
+            const int u = base + r;   // at most 8 points per slot: never past kTable
+            W.t_slot[u] = lane; W.t_a[u] = S.ra[r]; W.t_b[u] = S.rb[r]; W.t_c[u] = S.c;
+            W.t_tag[u] = tag | (S.rw[r] << 8);
+        }
+    }
+    int used = nreq_total;
+    if (__any_sync(FULL, scanning)) {
+        __syncwarp();
+        if (lane == 0) used = assign_scans(W, used);
+        used = __shfl_sync(FULL, used, 0);
+    }
+    if (lane < kSlots && nsp > 0) {
+        const Slot &S = W.s[lane];
+        for (int r = 0; r < nsp; ++r) {
+            int u = used;
+#pragma unroll
+            for (int t = 0; t < kSlots; ++t) u += min(r, nsp_all[t]) + ((ord_all[t] < ord && nsp_all[t] > r) ? 1 : 0);
+            if (u >= kTable) break;
+            const int q = S.nreq + r;
+            W.t_slot[u] = lane; W.t_a[u] = S.ra[q]; W.t_b[u] = S.rb[q]; W.t_c[u] = S.c;
+            W.t_tag[u] = kTagMove | (S.rw[q] << 8);
+        }
+    }
+    const int fin = min(kTable, used + nsp_total);
+    for (int u = fin + lane; u < kTable; u += 32) { W.t_slot[u] = -1; W.t_tag[u] = kTagNone; }
+    if (lane == 0) {
+        W.used = fin;
+        W.rot = (rot + 1) % kSlots;
+    }
+}
+
+// The round's results, all lanes: move points into their slot's window, a
+// final centre's <x, d> into its voxel's result (the slot is then free).
+__device__ void ingest(PackShared &W, int lane, const GridDev &g, mrf_result *out, int *err, ZState *state,
                        unsigned long long *stats)
 {
-    Slot &S = W.s[s];
     const int used = W.used;
-    for (int t = 0; t < used; ++t) {
-        if (W.t_slot[t] != s) continue;
+    for (int t = lane; t < used; t += 32) {
+        const int s = W.t_slot[t];
+        if (s < 0) continue;
         const int tag = W.t_tag[t] & 0xff;
-        const float v = W.r_v[t];
-        if (tag == kTagScan) {
-            if (isfinite(v)) { S.evaluated += 1; top2_add(v, S.g1, S.g2); }
-            if (v > S.centre) { S.centre = v; S.c = W.t_c[t]; }
-            S.p += 1;
-        } else if (tag == kTagMove) {
+        if (tag == kTagMove) {
             const int idx = W.t_tag[t] >> 8;
             W.wa[s][idx] = W.t_a[t];
             W.wb[s][idx] = W.t_b[t];
-            W.wv[s][idx] = v;
+            W.wv[s][idx] = W.r_v[t];
         } else if (tag == kTagFinal) {
+            Slot &S = W.s[s];
             if (!S.ok) atomicExch(err, kDeviceErrBounds);
             const float cr = W.r_ipr[t], ci = W.r_ipi[t], cd = W.r_dd[t];
             mrf_result r;
@@ -1082,6 +1117,19 @@ __device__ void ingest(PackShared &W, int s, const GridDev &g, mrf_result *out, 
             S.v = -1;
         }
     }
+}
+
+// Slot s's df-scan positions of the round, in scan order.
+__device__ void ingest_scan(PackShared &W, int s)
+{
+    Slot &S = W.s[s];
+    for (int t = S.scan_first; t < S.scan_first + S.scan_n; ++t) {
+        const float v = W.r_v[t];
+        if (isfinite(v)) { S.evaluated += 1; top2_add(v, S.g1, S.g2); }
+        if (v > S.centre) { S.centre = v; S.c = W.t_c[t]; }
+        S.p += 1;
+    }
+    S.scan_n = 0;
 }
 
 // Simulate table entries lane + 32 u (u < C) and store their results.
@@ -1128,7 +1176,7 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
     const int lane = threadIdx.x & 31;
     PackShared &W = sW[threadIdx.x >> 5];
     if (threadIdx.x == 0) sP = A.plan;
-    if (lane < kSlots) W.s[lane].v = -1;
+    if (lane < kSlots) { W.s[lane].v = -1; W.s[lane].scan_n = 0; }
     if (lane == 0) { W.drained = 0; W.rot = 0; W.norm_mask = 0; W.used = 0; }
     __syncthreads();
     const ZoomPlan &P = sP;
@@ -1138,9 +1186,11 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
 
     for (;;) {
         // decisions (one lane per slot)
+        ingest(W, lane, A.g, A.out, A.err, head, A.stats);
+        __syncwarp();
         if (lane < kSlots) {
             const int s = lane;
-            ingest(W, s, A.g, A.out, A.err, head, A.stats);
+            ingest_scan(W, s);
             Slot &S = W.s[s];
             // a slot parked at step 3 is free at once: refill it until it has
             // work or the voxels run out, so no warp leaves with voxels left
@@ -1198,10 +1248,8 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
             for (int o = 16; o > 0; o >>= 1) xx += __shfl_xor_sync(FULL, xx, o);
             if (lane == 0) W.s[s].inv_xn = xx > 0.f ? rsqrtf(xx) : 0.f;
         }
-        if (lane == 0) {
-            W.norm_mask = 0;
-            assign(W);
-        }
+        if (lane == 0) W.norm_mask = 0;
+        assign(W, lane);
         __syncwarp();
         // busy slots always list at least one point; a round with none would
         // repeat forever, so it ends the warp with an error instead
