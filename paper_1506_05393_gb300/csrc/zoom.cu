@@ -758,11 +758,6 @@ __device__ __forceinline__ bool scan_setup(Slot &S, int n_df, int count, int sta
 
 // Window slot of lattice point (i, k): a torus of 8 x 8 for 2D levels (every
 // 7 x 7 block is collision free), 64 along a 1D line.
-__device__ __forceinline__ int win_index(const Slot &S, int i, int k)
-{
-    return S.line ? ((S.param == 0 ? i : k) & (kWin - 1)) : (((i & 7) << 3) | (k & 7));
-}
-
 __device__ __forceinline__ bool win_get(const PackShared &W, int s, int idx, int a, int b, float &v)
 {
     if (W.wa[s][idx] != a || W.wb[s][idx] != b) return false;
@@ -821,24 +816,38 @@ __device__ void enter(PackShared &W, int s, int stage, const ZoomPlan &P, int n_
     }
 }
 
-// List lattice point (i, k) for simulation unless it is off the grid, known,
-// or already listed (bit of its window slot in `listed`).
-__device__ __forceinline__ bool list_point(PackShared &W, int s, const GridDev &g, int i, int k,
-                                           unsigned long long &listed, bool &known, float &v)
+// A move level's lattice (fixed between level entries), held in registers
+// while a slot's decisions run.
+struct Lattice {
+    int la, lb, h1, h2, c, line, param;
+};
+
+__device__ __forceinline__ Lattice lattice_of(const Slot &S)
 {
-    Slot &S = W.s[s];
-    const int a = S.la + i * S.h1, b = S.lb + k * S.h2;
+    Lattice L;
+    L.la = S.la; L.lb = S.lb; L.h1 = S.h1; L.h2 = S.h2; L.c = S.c; L.line = S.line; L.param = S.param;
+    return L;
+}
+
+// List lattice point (i, k) for simulation unless it is off the grid, known,
+// or already listed (bit of its window slot in `listed`); `cnt` counts the
+// slot's listed points (S.ra/rb/rw[0..cnt)).
+__device__ __forceinline__ bool list_point(PackShared &W, int s, const GridDev &g, const Lattice &L, int &cnt, int i,
+                                           int k, unsigned long long &listed, bool &known, float &v)
+{
+    const int a = L.la + i * L.h1, b = L.lb + k * L.h2;
     known = false;
-    if (!point_valid(g, a, b, S.c)) { known = true; v = -INFINITY; return false; }
-    const int idx = win_index(S, i, k);
+    if (!point_valid(g, a, b, L.c)) { known = true; v = -INFINITY; return false; }
+    const int idx = L.line ? ((L.param == 0 ? i : k) & (kWin - 1)) : (((i & 7) << 3) | (k & 7));
     if (win_get(W, s, idx, a, b, v)) { known = true; return false; }
     if ((listed >> idx) & 1ull) return false;
-    if (S.nreq + S.nspec >= kReqMax) return false;
+    if (cnt >= kReqMax) return false;
     listed |= 1ull << idx;
-    const int r = S.nreq + S.nspec;
-    S.ra[r] = a;
-    S.rb[r] = b;
-    S.rw[r] = idx;
+    Slot &S = W.s[s];
+    S.ra[cnt] = a;
+    S.rb[cnt] = b;
+    S.rw[cnt] = idx;
+    ++cnt;
     return true;
 }
 
@@ -852,31 +861,29 @@ __device__ __forceinline__ bool list_point(PackShared &W, int s, const GridDev &
 // steps along each axis (9 on a line), which the window holds without
 // collisions, so every decision a round's results allow finds its values.
 // Speculative points fill only lanes that required points leave idle.
-__device__ void speculate(PackShared &W, int s, const GridDev &g, unsigned long long listed)
+__device__ void speculate(PackShared &W, int s, const GridDev &g, const Lattice &L, int ia, int ib, int da, int db,
+                          int &cnt, unsigned long long listed)
 {
-    Slot &S = W.s[s];
     bool known;
     float v;
-    auto add = [&](int i, int k) {
-        if (list_point(W, s, g, i, k, listed, known, v)) S.nspec += 1;
-    };
-    if (S.line) {
-        const int d = S.param == 0 ? S.da : S.db;
+    auto add = [&](int i, int k) { list_point(W, s, g, L, cnt, i, k, listed, known, v); };
+    if (L.line) {
+        const int d = L.param == 0 ? da : db;
         for (int t = 2; t < 10; ++t) {
             const int m = d != 0 ? d * t : ((t & 1) ? -(t / 2 + 1) : (t / 2 + 1));
-            add(S.ia + (S.param == 0 ? m : 0), S.ib + (S.param == 1 ? m : 0));
+            add(ia + (L.param == 0 ? m : 0), ib + (L.param == 1 ? m : 0));
         }
         return;
     }
-    if (S.da == 0 && S.db == 0) {
+    if (da == 0 && db == 0) {
         for (int i = -2; i <= 2; ++i)
             for (int k = -2; k <= 2; ++k)
-                if (i == -2 || i == 2 || k == -2 || k == 2) add(S.ia + i, S.ib + k);
+                if (i == -2 || i == 2 || k == -2 || k == 2) add(ia + i, ib + k);
         return;
     }
     for (int t = 1; t <= kSpecCentres; ++t)
         for (int i = -1; i <= 1; ++i)
-            for (int k = -1; k <= 1; ++k) add(S.ia + t * S.da + i, S.ib + t * S.db + k);
+            for (int k = -1; k <= 1; ++k) add(ia + t * da + i, ib + t * db + k);
 }
 
 // Run slot s's decisions as far as the known values allow. On return the slot
@@ -918,31 +925,37 @@ __device__ void advance(PackShared &W, int s, const ZoomPlan &P, const GridDev &
         // the points of the next decision, in the canonical order: a 1D line
         // compares left then right, a 2D move the 8 neighbours with the T1
         // offset outer and -1 before +1
-        const int npts = S.line ? 2 : 8;
+        const Lattice L = lattice_of(S);
+        const int ia = S.ia, ib = S.ib;
+        const int npts = L.line ? 2 : 8;
         float vals[8];
         int di[8], dk[8];
         unsigned long long listed = 0;
         bool missing = false;
+        int cnt = 0;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             vals[q] = -INFINITY;
             di[q] = dk[q] = 0;
             if (q >= npts) continue;
-            if (S.line) {
+            if (L.line) {
                 const int m = q == 0 ? -1 : 1;
-                di[q] = S.param == 0 ? m : 0;
-                dk[q] = S.param == 1 ? m : 0;
+                di[q] = L.param == 0 ? m : 0;
+                dk[q] = L.param == 1 ? m : 0;
             } else {
                 const int k = q < 4 ? q : q + 1;
                 di[q] = k / 3 - 1;
                 dk[q] = k % 3 - 1;
             }
             bool known;
-            if (list_point(W, s, g, S.ia + di[q], S.ib + dk[q], listed, known, vals[q])) S.nreq += 1;
+            list_point(W, s, g, L, cnt, ia + di[q], ib + dk[q], listed, known, vals[q]);
             if (!known) missing = true;
         }
         if (missing) {
-            speculate(W, s, g, listed);
+            const int nreq = cnt;
+            speculate(W, s, g, L, ia, ib, S.da, S.db, cnt, listed);
+            S.nreq = nreq;
+            S.nspec = cnt - nreq;
             return;
         }
         if (++S.moves > max_moves) { S.ok = 0; S.stage = kFinal; continue; }
@@ -956,12 +969,12 @@ __device__ void advance(PackShared &W, int s, const ZoomPlan &P, const GridDev &
         }
         if (isfinite(t2)) S.mm = fminf(S.mm, t1 - t2);
         if (best > S.centre) {
-            S.ia += bdi;
-            S.ib += bdk;
+            S.ia = ia + bdi;
+            S.ib = ib + bdk;
             S.da = bdi;
             S.db = bdk;
-            S.a = S.la + S.ia * S.h1;
-            S.b = S.lb + S.ib * S.h2;
+            S.a = L.la + (ia + bdi) * L.h1;
+            S.b = L.lb + (ib + bdk) * L.h2;
             S.centre = best;
             continue;
         }
