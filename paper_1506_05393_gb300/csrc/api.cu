@@ -420,6 +420,7 @@ struct GridHost {
     std::vector<uint8_t> h;
     size_t o_t2, o_df, o_ao, o_nb, total;
     int64_t count;
+    int a_full;
 };
 
 static void grid_tables(const mrf_grid_desc *g, GridHost &G)
@@ -444,6 +445,8 @@ static void grid_tables(const mrf_grid_desc *g, GridHost &G)
         ao[a + 1] = ao[a] + (int64_t)nb[a] * g->n_df;
     }
     G.count = ao[g->n_t1];
+    G.a_full = g->n_t1;
+    while (G.a_full > 0 && nb[G.a_full - 1] == g->n_t2) --G.a_full;
 }
 
 int grid_upload(mrf_ctx *ctx, const mrf_grid_desc *g, GridBuf *out)
@@ -463,6 +466,7 @@ int grid_upload(mrf_ctx *ctx, const mrf_grid_desc *g, GridBuf *out)
     gb.a_off = (int64_t *)(d + G.o_ao);
     gb.nb = (int32_t *)(d + G.o_nb);
     gb.count = G.count;
+    gb.a_full = G.a_full;
     gb.bytes = G.total;
     *out = gb;
     return MRF_OK;
@@ -487,6 +491,7 @@ int grid_upload_async(mrf_ctx *ctx, const mrf_grid_desc *g, cudaStream_t stream,
     out->a_off = (const int64_t *)(d + G.o_ao);
     out->nb = (const int32_t *)(d + G.o_nb);
     out->count = G.count;
+    out->a_full = G.a_full;
     *block = d;
     *bytes = G.total;
     return MRF_OK;

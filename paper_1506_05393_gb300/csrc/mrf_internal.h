@@ -38,6 +38,7 @@ struct GridDev {
     const int64_t *a_off;   // n_t1 + 1: linear index of the first entry with T1 index a
     const int32_t *nb;      // n_t1: number of valid T2 indices for T1 index a
     int64_t count;
+    int a_full;             // from this T1 index on every T2 index is valid (nb[a] == n_t2)
 };
 
 // ---------------------------------------------------------------------------
@@ -68,12 +69,13 @@ struct GridBuf {
     int64_t *a_off = nullptr;
     int32_t *nb = nullptr;
     int64_t count = 0;
+    int a_full = 1 << 30;       // set by grid_upload; the default never skips the table
     void *block = nullptr;      // t1, t2, df, a_off, nb in one block from the stream-ordered pool
     size_t bytes = 0;
     GridDev dev() const {
         GridDev g;
         g.n_t1 = desc.n_t1; g.n_t2 = desc.n_t2; g.n_df = desc.n_df;
-        g.t1 = t1; g.t2 = t2; g.df = df; g.a_off = a_off; g.nb = nb; g.count = count;
+        g.t1 = t1; g.t2 = t2; g.df = df; g.a_off = a_off; g.nb = nb; g.count = count; g.a_full = a_full;
         return g;
     }
 };

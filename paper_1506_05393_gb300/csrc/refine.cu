@@ -25,7 +25,8 @@ constexpr int kRefineThreads = 128;   // 4 voxels (warps) per CTA
 
 __device__ __forceinline__ bool refine_valid(const GridDev &g, int a, int b, int c)
 {
-    return a >= 0 && a < g.n_t1 && b >= 0 && c >= 0 && c < g.n_df && b < __ldg(&g.nb[a]);
+    return a >= 0 && a < g.n_t1 && b >= 0 && b < g.n_t2 && c >= 0 && c < g.n_df &&
+           (a >= g.a_full || b < __ldg(&g.nb[a]));
 }
 
 // <x, d>, ||d||^2 of one point in FP64 (FP32 partial sums over 8 timepoints).

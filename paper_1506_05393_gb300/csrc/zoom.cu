@@ -237,7 +237,9 @@ __device__ __forceinline__ void sim_multi(const SeqDev &s, const float2 *const (
 
 __device__ __forceinline__ bool point_valid(const GridDev &g, int a, int b, int c)
 {
-    return a >= 0 && a < g.n_t1 && b >= 0 && c >= 0 && c < g.n_df && b < __ldg(&g.nb[a]);
+    // T1 indices from a_full on admit every T2 index: no table read there
+    return a >= 0 && a < g.n_t1 && b >= 0 && b < g.n_t2 && c >= 0 && c < g.n_df &&
+           (a >= g.a_full || b < __ldg(&g.nb[a]));
 }
 
 // Per-voxel search state shared (identically) by all lanes of the warp.
@@ -2086,6 +2088,8 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     A.g.a_off = (const int64_t *)(dev + o_ao);
     A.g.nb = (const int32_t *)(dev + o_nb);
     A.g.count = ao[gd->n_t1];
+    A.g.a_full = gd->n_t1;
+    while (A.g.a_full > 0 && nb[A.g.a_full - 1] == gd->n_t2) --A.g.a_full;
     A.dhi = A.dlo = nullptr;
     A.dnorm = nullptr;
     A.dscale = nullptr;
