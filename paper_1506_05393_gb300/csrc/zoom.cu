@@ -695,6 +695,7 @@ constexpr int kTable = 32 * kPerLane;
 constexpr int kWin = 64;
 constexpr int kReqMax = 24;                  // listed points per slot and round (8 missing + speculative)
 constexpr int kSpecCentres = 5;              // 2D walks: future centres whose neighbourhoods are speculated
+constexpr int kRunPrio = 3;                  // straight 2D run length whose speculation goes first
 
 enum Stage : int { kS1a = 0, kS1b, kS1c, kS2, kS3, kS4, kS5, kFinal, kStop };
 enum Tag : int { kTagNone = 0, kTagScan, kTagMove, kTagFinal };
@@ -716,6 +717,7 @@ struct Slot {
     // move levels: moves so far, lattice origin (la, lb) and steps, the
     // centre's lattice coordinates, the last move (lattice units)
     int moves, la, lb, h1, h2, line, param, ia, ib, da, db;
+    int run;               // consecutive moves in the direction (da, db)
     // listed points: ra/rb/rw[0..nreq) missing, then nspec speculative (rw: window index)
     int nreq, nspec;
     int ra[kReqMax], rb[kReqMax], rw[kReqMax];
@@ -803,6 +805,7 @@ __device__ void enter(PackShared &W, int s, int stage, const ZoomPlan &P, int n_
             S.la = S.a;
             S.lb = S.b;
             S.ia = S.ib = S.da = S.db = 0;
+            S.run = 0;
             for (int i = 0; i < kWin; ++i) W.wa[s][i] = -1;
             W.wa[s][0] = S.a;
             W.wb[s][0] = S.b;
@@ -971,6 +974,7 @@ __device__ void advance(PackShared &W, int s, const ZoomPlan &P, const GridDev &
         }
         if (isfinite(t2)) S.mm = fminf(S.mm, t1 - t2);
         if (best > S.centre) {
+            S.run = (bdi == S.da && bdk == S.db) ? S.run + 1 : 1;
             S.ia = ia + bdi;
             S.ib = ib + bdk;
             S.da = bdi;
@@ -1034,13 +1038,16 @@ __device__ int assign_scans(PackShared &W, int used)
 // The round's table, built by the whole warp: every slot's missing points
 // first (rotating slot order), then consecutive df positions for the scanning
 // slots, then the speculative points one slot at a time (pass r takes the r-th
-// point of each slot that has one, in rotating order), cut at kTable. Each
-// slot lane computes where its own points go in that order.
+// point of each slot that has one, in rotating order), cut at kTable -- first
+// for the slots on a straight 2D walk (kRunPrio moves or more in one
+// direction, the long final walks that set the search's duration), then for
+// the others. Each slot lane computes where its own points go in that order.
+// Speculation decides nothing, so the order changes no result.
 __device__ void assign(PackShared &W, int lane)
 {
     const unsigned FULL = 0xffffffffu;
     const int rot = W.rot;
-    int nreq = 0, nsp = 0, scanning = 0, tag = kTagMove, ord = kSlots;
+    int nreq = 0, nsp = 0, scanning = 0, tag = kTagMove, ord = kSlots, prio = 0;
     if (lane < kSlots) {
         Slot &S = W.s[lane];
         ord = (lane - rot + kSlots) % kSlots;
@@ -1049,18 +1056,23 @@ __device__ void assign(PackShared &W, int lane)
             nreq = S.nreq;
             tag = S.stage == kFinal ? kTagFinal : kTagMove;
             if (is_scan(S.stage)) scanning = S.p <= S.p_end;
-            else if (S.stage != kFinal) nsp = S.nspec;
+            else if (S.stage != kFinal) {
+                nsp = S.nspec;
+                prio = !S.line && S.run >= kRunPrio;
+            }
         }
     }
-    int base = 0, nreq_total = 0, nsp_total = 0;
-    int nsp_all[kSlots], ord_all[kSlots];
+    int base = 0, nreq_total = 0, nsp_total = 0, nsp_prio = 0;
+    int nsp_all[kSlots], ord_all[kSlots], prio_all[kSlots];
 #pragma unroll
     for (int t = 0; t < kSlots; ++t) {
         const int nr = __shfl_sync(FULL, nreq, t);
         ord_all[t] = __shfl_sync(FULL, ord, t);
         nsp_all[t] = __shfl_sync(FULL, nsp, t);
+        prio_all[t] = __shfl_sync(FULL, prio, t);
         nreq_total += nr;
         nsp_total += nsp_all[t];
+        nsp_prio += prio_all[t] ? nsp_all[t] : 0;
         if (ord_all[t] < ord) base += nr;
     }
     if (lane < kSlots) {
@@ -1079,10 +1091,12 @@ __device__ void assign(PackShared &W, int lane)
     }
     if (lane < kSlots && nsp > 0) {
         const Slot &S = W.s[lane];
+        const int gbase = used + (prio ? 0 : nsp_prio);
         for (int r = 0; r < nsp; ++r) {
-            int u = used;
+            int u = gbase;
 #pragma unroll
-            for (int t = 0; t < kSlots; ++t) u += min(r, nsp_all[t]) + ((ord_all[t] < ord && nsp_all[t] > r) ? 1 : 0);
+            for (int t = 0; t < kSlots; ++t)
+                if (prio_all[t] == prio) u += min(r, nsp_all[t]) + ((ord_all[t] < ord && nsp_all[t] > r) ? 1 : 0);
             if (u >= kTable) break;
             const int q = S.nreq + r;
             W.t_slot[u] = lane; W.t_a[u] = S.ra[q]; W.t_b[u] = S.rb[q]; W.t_c[u] = S.c;
