@@ -166,6 +166,9 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
     __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], tfull_bar[NBUF], tempty_bar[NBUF], drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
+    // per epilogue warp: the column scales of its current tile, fetched while
+    // the tile's MMAs run
+    __shared__ __align__(16) float sc_tile[NEPI][MODE == MRF_BF16 ? 1 : BN];
 
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     // stage s: [A(block 0..NB-1, hi) | A lo? | B hi | B lo?]
@@ -329,6 +332,14 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
             const int64_t vrow = (int64_t)(vu * NB + blk) * (BM / 2) + (row >> 1);
             const bool vlive = vrow < p.V;
             for (int t = t0; t < t1; ++t) {
+                if (MODE != MRF_BF16) {
+                    float *sct = sc_tile[warp - 2];
+                    for (int q = lane; q < BN; q += 32) {
+                        const int col = t * BN + q;
+                        sct[q] = col < p.D ? __ldg(&p.colscale[(int64_t)col * p.col_stride]) : 0.f;
+                    }
+                    __syncwarp();
+                }
                 const bool ok = mbar_wait_bounded(&tfull_bar[buf], buf_ph, &abort_flag, p.err, kWaitLimitNs);
                 if (!__all_sync(0xffffffffu, ok)) goto epi_done;   // leave as a whole warp
                 tc_fence_after();
@@ -343,20 +354,11 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                     float c2v[16];
                     float sc16[16];
                     if (MODE != MRF_BF16) {
-                        if (p.col_stride == 1 && col0 + 16 <= p.D) {
-                            // 16 consecutive scales from a 16-byte aligned offset
-                            const float4 *s4 = reinterpret_cast<const float4 *>(p.colscale + col0);
+                        const float4 *s4 = reinterpret_cast<const float4 *>(&sc_tile[warp - 2][ch * 32 + (par ? 16 : 0)]);
 #pragma unroll
-                            for (int q4 = 0; q4 < 4; ++q4) {
-                                const float4 f = __ldg(s4 + q4);
-                                sc16[4 * q4] = f.x; sc16[4 * q4 + 1] = f.y; sc16[4 * q4 + 2] = f.z; sc16[4 * q4 + 3] = f.w;
-                            }
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) {
-                                const int col = col0 + q;
-                                sc16[q] = col < p.D ? __ldg(&p.colscale[(int64_t)col * p.col_stride]) : 0.f;
-                            }
+                        for (int q4 = 0; q4 < 4; ++q4) {
+                            const float4 f = s4[q4];
+                            sc16[4 * q4] = f.x; sc16[4 * q4 + 1] = f.y; sc16[4 * q4 + 2] = f.z; sc16[4 * q4 + 3] = f.w;
                         }
                     }
                     uint32_t mask = 0;
