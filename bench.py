@@ -389,6 +389,57 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
     return modes
 
 
+def run_cc_landscape(M, ctx, seq_h, seq, target=(1400.0, 200.0, 20.0)):
+    """The CC landscape around one fingerprint on this sequence (Theory,
+    Properties I-III; Experiment 1 as a shape): GPU-simulated candidates
+    along df, T1 and T2 lines through (and beside) the target, CC on the host."""
+    import torch
+
+    def sim(t1, t2, df):
+        t = [torch.tensor(np.asarray(v, np.float32)).cuda() for v in (t1, t2, df)]
+        out = torch.empty((t[0].numel(), seq.n), dtype=torch.complex64, device="cuda")
+        M.mrf_simulate(ctx, seq_h, t[0], t[1], t[2], out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy().astype(np.complex128)
+
+    x = sim([target[0]], [target[1]], [target[2]])[0]
+    x /= np.linalg.norm(x)
+
+    def cc(d):
+        return np.abs(d.conj() @ x) / np.linalg.norm(d, axis=1)
+
+    def local_maxima(c):
+        return int(sum(1 for i in range(1, c.size - 1) if c[i] > c[i - 1] and c[i] > c[i + 1]))
+
+    dfs = np.arange(-300.0, 301.0, 1.0)
+    pairs, at_target = [], 0
+    for t1 in (700.0, 1000.0, 1400.0, 2000.0, 3000.0):
+        for t2 in (50.0, 100.0, 200.0, 300.0):
+            c = cc(sim(np.full(dfs.size, t1), np.full(dfs.size, t2), dfs))
+            am = float(dfs[np.argmax(c)])
+            at_target += am == target[2]
+            pairs.append({"t1_ms": t1, "t2_ms": t2, "df_argmax_hz": am, "cc_max": float(c.max())})
+    c0 = cc(sim(np.full(dfs.size, target[0]), np.full(dfs.size, target[1]), dfs))
+    lm = sorted(((float(dfs[i] - target[2]), float(c0[i])) for i in range(1, dfs.size - 1)
+                 if c0[i] > c0[i - 1] and c0[i] > c0[i + 1]), key=lambda t: -t[1])
+    t1s, t2s = np.arange(100.0, 4001.0, 20.0), np.arange(10.0, 401.0, 5.0)
+    t1_lines, t2_lines = [], []
+    for t2 in (50.0, 100.0, 200.0, 300.0):
+        ok = t1s > t2
+        c = cc(sim(t1s[ok], np.full(ok.sum(), t2), np.full(ok.sum(), target[2])))
+        t1_lines.append({"t2_ms": t2, "t1_argmax_ms": float(t1s[ok][np.argmax(c)]), "local_maxima": local_maxima(c)})
+    for t1 in (700.0, 1400.0, 3000.0):
+        ok = t2s < t1
+        c = cc(sim(np.full(ok.sum(), t1), t2s[ok], np.full(ok.sum(), target[2])))
+        t2_lines.append({"t1_ms": t1, "t2_argmax_ms": float(t2s[ok][np.argmax(c)]), "local_maxima": local_maxima(c)})
+    return {"target": {"t1_ms": target[0], "t2_ms": target[1], "df_hz": target[2]},
+            "property_I": {"df_argmax_at_target": f"{at_target} of {len(pairs)} (T1, T2) pairs", "pairs": pairs},
+            "property_II": {"cc_df_local_maxima_top": [{"offset_hz": o, "cc": c} for o, c in lm[:6]],
+                            "hz_1000_over_mean_tr": float(1000.0 / np.mean(seq.tr_ms)),
+                            "hz_1000_over_min_tr": float(1000.0 / np.min(seq.tr_ms))},
+            "property_III": {"t1_lines": t1_lines, "t2_lines": t2_lines}}
+
+
 def run_noise_study(M, ctx, seq_h, seed=151, levels=(0.04, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 0.98)):
     """Methods, Experiment 4: white noise on Re and Im at levels given by the
     CC between the noise-free and the noisy fingerprint (0.04 .. 0.98); per
@@ -776,6 +827,7 @@ def main():
         line["modes"] = run_modes(M, ctx, seq, seq_h, x_dev, fp32_res["index"], pk, clk.get("sm_mhz"), ph)
     if not args.no_modes:
         line["noise_study"] = run_noise_study(M, ctx, seq_h)
+        line["cc_landscape"] = run_cc_landscape(M, ctx, seq_h, seq)
     M.mrf_sequence_free(ctx, seq_h)
     M.mrf_ctx_destroy(ctx)
     if not args.no_serving and not args.no_modes:

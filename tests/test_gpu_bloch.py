@@ -133,3 +133,47 @@ def test_dictionary_full_size_sampled(M, ctx, oracle_lib):
     finally:
         M.mrf_dict_free(ctx, d)
         M.mrf_sequence_free(ctx, h)
+
+
+def test_cc_landscape_around_a_fingerprint(M, ctx):
+    """The CC landscape of GPU fingerprints around a target on this sequence
+    (Theory, Properties I-III; Experiment 1 as a shape). What must hold: the
+    df line through the target peaks at the target with CC = 1, and the T1
+    and T2 lines through it are unimodal with their maximum at the target.
+    What the paper postulates beyond that (df argmax at the target for every
+    T1/T2 pair, periodic df side lobes) is measured and printed: on this
+    sequence the alternating-sign train gives every candidate a competing df
+    peak at 0 Hz, and the random TRs leave no clean 1/TR period."""
+    seq = S.sequence(1, 1000)
+    h = M.mrf_sequence_load(ctx, seq)
+    try:
+        def sim(t1, t2, df):
+            t = [torch.tensor(np.asarray(v, np.float32)).cuda() for v in (t1, t2, df)]
+            out = torch.empty((t[0].numel(), seq.n), dtype=torch.complex64, device="cuda")
+            M.mrf_simulate(ctx, h, t[0], t[1], t[2], out)
+            torch.cuda.synchronize()
+            return out.cpu().numpy().astype(np.complex128)
+
+        target = (1400.0, 200.0, 20.0)
+        x = sim([target[0]], [target[1]], [target[2]])[0]
+        x /= np.linalg.norm(x)
+        cc = lambda d: np.abs(d.conj() @ x) / np.linalg.norm(d, axis=1)
+        dfs = np.arange(-300.0, 301.0, 1.0)
+        c = cc(sim(np.full(dfs.size, target[0]), np.full(dfs.size, target[1]), dfs))
+        assert dfs[np.argmax(c)] == target[2] and abs(c.max() - 1.0) < 1e-5
+        t1s = np.arange(100.0, 4001.0, 20.0)
+        c1 = cc(sim(t1s, np.full(t1s.size, target[1]), np.full(t1s.size, target[2])))
+        t2s = np.arange(10.0, 401.0, 5.0)
+        c2 = cc(sim(np.full(t2s.size, target[0]), t2s, np.full(t2s.size, target[2])))
+        for line, axis, want in ((c1, t1s, target[0]), (c2, t2s, target[1])):
+            maxima = [i for i in range(1, line.size - 1) if line[i] > line[i - 1] and line[i] > line[i + 1]]
+            assert len(maxima) == 1 and axis[maxima[0]] == want
+        hits = 0
+        for t1 in (700.0, 1400.0, 3000.0):
+            for t2 in (50.0, 100.0, 300.0):
+                cd = cc(sim(np.full(dfs.size, t1), np.full(dfs.size, t2), dfs))
+                hits += dfs[np.argmax(cd)] == target[2]
+        print(f"CC landscape: df argmax at the target for {hits} of 9 off-target (T1, T2) pairs; "
+              f"CC at df = 0 Hz on the target's T1/T2: {c[dfs == 0.0][0]:.4f}")
+    finally:
+        M.mrf_sequence_free(ctx, h)
