@@ -30,7 +30,7 @@ from dataclasses import dataclass, asdict
 import numpy as np
 
 __all__ = [
-    "Sequence", "Grid", "GRIDS", "sequence", "grid_values", "grid_valid_params",
+    "Sequence", "Grid", "GRIDS", "sequence", "grid_values", "grid_valid_params", "phantom_piecewise",
     "phantom_offgrid", "phantom_ongrid", "noise_draws", "compose_voxels",
     "write_sequence", "read_sequence",
 ]
@@ -164,6 +164,35 @@ def phantom_offgrid(seed: int, v: int, t1_range=(200.0, 3000.0), t2_range=(20.0,
     m0 = rng.uniform(0.5, 1.0, v)
     ph = rng.uniform(0.0, 2.0 * math.pi, v)
     return dict(t1=t1, t2=t2, df=df, m0=m0, phase=ph, rng_state=rng.bit_generator.state)
+
+
+def phantom_piecewise(seed: int, rows: int, cols: int, classes: int = 5, t1_range=(200.0, 3000.0),
+                      t2_range=(20.0, 300.0), df_range=(-40.0, 40.0)):
+    """A piecewise-smooth slice (row-major, rows x cols voxels), for searches
+    that use spatial neighbours: `classes` tissue classes with T1, T2
+    log-uniform (T2 < T1) and df uniform, laid out by the largest of smooth
+    random fields (one per class, a sum of Gaussian blobs), then 2 % jitter on
+    T1 and T2 and a +-3 Hz df gradient across the slice; M0 ~ U(0.5, 1) and
+    global phase ~ U(0, 2 pi) per voxel. Draw order is fixed."""
+    rng = np.random.default_rng(seed)
+    ct1 = np.exp(rng.uniform(math.log(t1_range[0]), math.log(t1_range[1]), classes))
+    ct2 = np.minimum(np.exp(rng.uniform(math.log(t2_range[0]), math.log(t2_range[1]), classes)), 0.8 * ct1)
+    cdf = rng.uniform(df_range[0] + 3.0, df_range[1] - 3.0, classes)
+    yy, xx = np.mgrid[0:rows, 0:cols].astype(np.float64)
+    field = np.zeros((classes, rows, cols))
+    for k in range(classes):
+        for _ in range(8):
+            cy, cx = rng.uniform(0, rows), rng.uniform(0, cols)
+            r = rng.uniform(0.08, 0.25) * max(rows, cols)
+            field[k] += rng.uniform(0.5, 1.0) * np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (2 * r * r))
+    label = field.argmax(0).ravel()
+    v = rows * cols
+    t1 = ct1[label] * (1.0 + 0.02 * rng.uniform(-1, 1, v))
+    t2 = ct2[label] * (1.0 + 0.02 * rng.uniform(-1, 1, v))
+    df = cdf[label] + 3.0 * (xx.ravel() / max(cols - 1, 1) * 2.0 - 1.0)
+    m0 = rng.uniform(0.5, 1.0, v)
+    ph = rng.uniform(0.0, 2.0 * math.pi, v)
+    return dict(t1=t1, t2=t2, df=df, m0=m0, phase=ph, label=label)
 
 
 def phantom_ongrid(seed: int, v: int, g: Grid):

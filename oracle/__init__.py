@@ -21,6 +21,8 @@ import os
 import subprocess
 import threading
 
+import math
+
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -278,6 +280,63 @@ def zoom(seq, g, x, opts=None):
     if rc != 0:
         raise RuntimeError(f"or_zoom failed: {rc}")
     return dict(abc=abc, cc=ccs, m0=m0, phase=ph, evaluated=ev, min_margin=mm)
+
+
+class _SubGrid:
+    """A grid restricted to index boxes [a_lo, a_hi] x [b_lo, b_hi] x [c_lo, c_hi]
+    of `g` (same steps; first values those of the box's first points)."""
+
+    def __init__(self, g, a_lo, a_hi, b_lo, b_hi, c_lo, c_hi):
+        self.t1_min, self.t1_step, self.n_t1 = g.t1_min + a_lo * g.t1_step, g.t1_step, a_hi - a_lo + 1
+        self.t2_min, self.t2_step, self.n_t2 = g.t2_min + b_lo * g.t2_step, g.t2_step, b_hi - b_lo + 1
+        self.df_min, self.df_step, self.n_df = g.df_min + c_lo * g.df_step, g.df_step, c_hi - c_lo + 1
+        self.require_t2_lt_t1 = g.require_t2_lt_t1
+
+
+def prior_neighbours(V: int, width: int, stride: int):
+    """First-pass voxels (every stride-th row and column of a row-major slice
+    `width` voxels wide) and, for every voxel, the first-pass voxel whose
+    result bounds its search (itself for first-pass voxels)."""
+    v = np.arange(V)
+    r, c = v // width, v % width
+    first = (r % stride == 0) & (c % stride == 0)
+    nb = (r - r % stride) * width + (c - c % stride)
+    return first, nb
+
+
+def prior_box(g, abc_p, half):
+    """Index box of the grid points within `half` = (T1, T2, df) half-widths of
+    the neighbour's grid point abc_p, overlapped with the grid."""
+    h = [int(math.floor(w / st + 1e-9)) for w, st in zip(half, (g.t1_step, g.t2_step, g.df_step))]
+    n = (g.n_t1, g.n_t2, g.n_df)
+    return [(max(0, int(abc_p[k]) - h[k]), min(n[k] - 1, int(abc_p[k]) + h[k])) for k in range(3)]
+
+
+def zoom_prior(seq, g, x, width: int, stride: int = 4, half=(3000.0, 800.0, 150.0), opts=None):
+    """MRF-ZOOM with the spatial-neighbour prior (Methods, Experiment 3): each
+    voxel's search runs on the original ranges overlapped with T1p +- 3000 ms,
+    T2p +- 800 ms, dfp +- 150 Hz around a neighbour's result (T1p, T2p, dfp).
+    The neighbour is a first-pass voxel (prior_neighbours): first-pass voxels
+    are searched on the whole grid, every other voxel on its box, as a search
+    on that sub-grid. Returns zoom()'s dict (global indices) plus `box`."""
+    x = np.atleast_2d(x)
+    V = x.shape[0]
+    first, nb = prior_neighbours(V, width, stride)
+    out = dict(abc=np.zeros((V, 3), np.int32), cc=np.zeros(V), m0=np.zeros(V), phase=np.zeros(V),
+               evaluated=np.zeros(V, np.int32), min_margin=np.zeros(V), box=np.zeros((V, 6), np.int32))
+    idx1 = np.nonzero(first)[0]
+    r1 = zoom(seq, g, x[idx1], opts)
+    for k in ("abc", "cc", "m0", "phase", "evaluated", "min_margin"):
+        out[k][idx1] = r1[k]
+    out["box"][idx1] = [0, g.n_t1 - 1, 0, g.n_t2 - 1, 0, g.n_df - 1]
+    for v in np.nonzero(~first)[0]:
+        (a0, a1), (b0, b1), (c0, c1) = prior_box(g, out["abc"][nb[v]], half)
+        r = zoom(seq, _SubGrid(g, a0, a1, b0, b1, c0, c1), x[v:v + 1], opts)
+        out["abc"][v] = r["abc"][0] + np.array([a0, b0, c0], np.int32)
+        for k in ("cc", "m0", "phase", "evaluated", "min_margin"):
+            out[k][v] = r[k][0]
+        out["box"][v] = [a0, a1, b0, b1, c0, c1]
+    return out
 
 
 def zoom_generic(g, score, omega, opts=None, trace_cap=100000):

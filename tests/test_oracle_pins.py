@@ -469,3 +469,61 @@ def test_smoothed_bruteforce_recovers_on_grid_voxels(oracle_lib):
     # smoothing the dictionary alone changes the scores: the plain entry no longer matches exactly
     r1 = oracle_lib.bruteforce(seq, g, x, k=1, smooth=(5, 1.0))
     assert (r1["cc"][:, 0] < 1.0 - 1e-6).all()
+
+
+# ---------------------------------------------------------------------------
+# Spatial-neighbour prior (Methods, Experiment 3)
+
+def test_prior_neighbours_and_box_by_hand(oracle_lib):
+    """First-pass voxels of a 4 x 4 slice at stride 2 and their neighbours,
+    and the index box of T1p +- 100 ms on a 20 ms axis (5 steps each way,
+    cut by the axis ends)."""
+    first, nb = oracle_lib.prior_neighbours(16, 4, 2)
+    assert list(np.nonzero(first)[0]) == [0, 2, 8, 10]
+    assert [int(nb[v]) for v in (0, 1, 4, 5, 7, 13, 15)] == [0, 0, 0, 0, 2, 8, 10]
+    g = S.GRIDS["fp32_brute"]   # T1 step 20 ms (196), T2 step 5 ms (79), df step 2 Hz (41)
+    assert oracle_lib.prior_box(g, (10, 40, 20), (100.0, 50.0, 6.0)) == [(5, 15), (30, 50), (17, 23)]
+    assert oracle_lib.prior_box(g, (2, 77, 0), (100.0, 50.0, 6.0)) == [(0, 7), (67, 78), (0, 3)]
+    assert oracle_lib.prior_box(g, (2, 77, 0), (3000.0, 800.0, 150.0)) == [(0, 152), (0, 78), (0, 40)]
+
+
+def test_prior_covering_the_grid_changes_nothing(oracle_lib):
+    """With windows wider than every axis the sub-grid is the grid: the prior
+    search returns exactly the plain search's results."""
+    seq = S.sequence(0, 200)
+    g = S.GRIDS["fp32_brute"]
+    ph = S.phantom_piecewise(5, 4, 4)
+    clean = oracle_lib.simulate(seq, ph["t1"], ph["t2"], ph["df"])
+    g_re, g_im = S.noise_draws(5, 16, seq.n)
+    x = S.compose_voxels(clean, ph["m0"], ph["phase"], g_re, g_im, 30.0)
+    plain = oracle_lib.zoom(seq, g, x)
+    pri = oracle_lib.zoom_prior(seq, g, x, 4, 2, (1e6, 1e6, 1e6))
+    for k in ("abc", "evaluated"):
+        assert np.array_equal(plain[k], pri[k]), k
+    assert np.array_equal(plain["cc"], pri["cc"])
+
+
+def test_prior_results_lie_in_their_boxes(oracle_lib):
+    """Narrow windows (T1p +- 200 ms, T2p +- 30 ms, dfp +- 6 Hz): every
+    second-pass result lies in the box of its neighbour's result, and equals
+    the plain search on that box's sub-grid."""
+    seq = S.sequence(0, 200)
+    g = S.GRIDS["fp32_brute"]
+    ph = S.phantom_piecewise(6, 4, 4)
+    clean = oracle_lib.simulate(seq, ph["t1"], ph["t2"], ph["df"])
+    g_re, g_im = S.noise_draws(6, 16, seq.n)
+    x = S.compose_voxels(clean, ph["m0"], ph["phase"], g_re, g_im, 30.0)
+    half = (200.0, 30.0, 6.0)
+    pri = oracle_lib.zoom_prior(seq, g, x, 4, 2, half)
+    first, nb = oracle_lib.prior_neighbours(16, 4, 2)
+    for v in np.nonzero(~first)[0]:
+        box = oracle_lib.prior_box(g, pri["abc"][nb[v]], half)
+        assert list(pri["box"][v]) == [box[0][0], box[0][1], box[1][0], box[1][1], box[2][0], box[2][1]]
+        for k in range(3):
+            assert box[k][0] <= pri["abc"][v][k] <= box[k][1]
+    v = int(np.nonzero(~first)[0][0])
+    (a0, a1), (b0, b1), (c0, c1) = oracle_lib.prior_box(g, pri["abc"][nb[v]], half)
+    sub = S.Grid(g.t1_min + a0 * g.t1_step, g.t1_step, a1 - a0 + 1, g.t2_min + b0 * g.t2_step, g.t2_step, b1 - b0 + 1,
+                 g.df_min + c0 * g.df_step, g.df_step, c1 - c0 + 1)
+    r = oracle_lib.zoom(seq, sub, x[v:v + 1])
+    assert list(r["abc"][0] + np.array([a0, b0, c0])) == list(pri["abc"][v])
