@@ -306,6 +306,18 @@ typedef struct {
     int32_t n_s4;           /* step 4: interleaved 1D ZOOMs */
     int32_t s4_param[MRF_ZOOM_MAX_LEVELS];   /* 0: T1, 1: T2 */
     double s4_ms[MRF_ZOOM_MAX_LEVELS];
+    /* Spatial-neighbour prior (Methods, Experiment 3), mrf_zoom_search only:
+     * prior_width > 0 treats the V voxels as a row-major slice prior_width
+     * voxels wide. Voxels on every prior_stride-th row and column are searched
+     * first on the whole grid; every other voxel is then searched on the grid
+     * overlapped with T1p +- prior_t1_ms, T2p +- prior_t2_ms, dfp +-
+     * prior_df_hz around the result of the first-pass voxel at (r - r mod
+     * stride, c - c mod stride): the index box |i - i_p| <= floor(half /
+     * step), searched as a grid of its own. Defaults 0 (off), 4, 3000, 800,
+     * 150. */
+    int32_t prior_width;
+    int32_t prior_stride;
+    double prior_t1_ms, prior_t2_ms, prior_df_hz;
 } mrf_zoom_opts;
 
 /* Fill `opts` with the schedule of Experiment 2 (T1@100, T2@100, T1@50/20/10,

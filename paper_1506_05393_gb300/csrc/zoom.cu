@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -37,6 +38,7 @@ constexpr int kScanW = 2;           // dictionary df scans: positions per lane p
 
 struct ZoomPlan {
     int a0, b0;          // start of the df search
+    int a_raw, b_raw;    // the nearest grid indices of the start before clipping (per-voxel boxes clip them)
     int hA;              // step 1a: coarse df step
     int K1b, hB;         // step 1b: k = -K1b..K1b (k != 0), step hB
     int hC;              // step 1c: probe spacing (omega)
@@ -79,6 +81,8 @@ struct ZoomArgs {
     int max_moves;
     ZState *state;           // split search only
     int phase;               // ZPhase
+    const int *vmap;         // voxel of each work item (nullptr: item = voxel)
+    const int *box;          // per work item: a_lo, a_hi, b_lo, b_hi, c_lo, c_hi of its search (nullptr: the grid)
     unsigned long long *stats;   // work counters: [2] warp rounds, [3] candidates simulated, [4] most rounds of a voxel
 };
 
@@ -718,6 +722,7 @@ struct Slot {
     // centre's lattice coordinates, the last move (lattice units)
     int moves, la, lb, h1, h2, line, param, ia, ib, da, db;
     int run;               // consecutive moves in the direction (da, db)
+    int alo, ahi, blo, bhi, clo, chi;   // the voxel's search box (the whole grid unless a prior bounds it)
     // listed points: ra/rb/rw[0..nreq) missing, then nspec speculative (rw: window index)
     int nreq, nspec;
     int ra[kReqMax], rb[kReqMax], rw[kReqMax];
@@ -746,14 +751,13 @@ __device__ __forceinline__ void top2_add(float v, float &t1, float &t2)
 
 // List of a df scan at the current (a, b); positions whose c falls off the
 // grid are dropped, and a list holding only the excluded point is empty.
-__device__ __forceinline__ bool scan_setup(Slot &S, int n_df, int count, int start, int step, int skip,
-                                           bool with_centre)
+__device__ __forceinline__ bool scan_setup(Slot &S, int count, int start, int step, int skip, bool with_centre)
 {
     S.start = start;
     S.step = step;
     S.skip = skip;
-    S.p = start >= 0 ? 0 : (-start + step - 1) / step;
-    S.p_end = min(count - 1, (n_df - 1 - start) >= 0 ? (n_df - 1 - start) / step : -1);
+    S.p = start >= S.clo ? 0 : (S.clo - start + step - 1) / step;
+    S.p_end = min(count - 1, (S.chi - start) >= 0 ? (S.chi - start) / step : -1);
     S.g1 = with_centre ? S.centre : -INFINITY;
     S.g2 = -INFINITY;
     if (S.p == S.p_end && start + S.p * step == skip) return false;
@@ -780,19 +784,22 @@ __device__ void enter(PackShared &W, int s, int stage, const ZoomPlan &P, int n_
         if (stop3 && stage == kS3) { S.stage = kStop; return; }
         bool nonempty;
         switch (stage) {
-        case kS1a:
-            nonempty = scan_setup(S, n_df, (n_df + P.hA - 1) / P.hA, 0, P.hA, -1, false);
+        case kS1a: {
+            const int n = S.chi - S.clo + 1;
+            nonempty = scan_setup(S, (n + P.hA - 1) / P.hA, S.clo, P.hA, -1, false);
             break;
+        }
         case kS1b:
-            nonempty = scan_setup(S, n_df, 2 * P.K1b + 1, S.c - P.K1b * P.hB, P.hB, S.c, true);
+            nonempty = scan_setup(S, 2 * P.K1b + 1, S.c - P.K1b * P.hB, P.hB, S.c, true);
             break;
         case kS1c: {
-            const int st = S.c - (S.c / P.hC) * P.hC;
-            nonempty = scan_setup(S, n_df, (n_df - 1 - st) / P.hC + 1, st, P.hC, S.c, true);
+            const int r = S.c - S.clo;
+            const int st = S.clo + (r - (r / P.hC) * P.hC);
+            nonempty = scan_setup(S, (S.chi - st) / P.hC + 1, st, P.hC, S.c, true);
             break;
         }
         case kS3:
-            nonempty = scan_setup(S, n_df, 2 * P.W3 + 1, S.c - P.W3, 1, S.c, true);
+            nonempty = scan_setup(S, 2 * P.W3 + 1, S.c - P.W3, 1, S.c, true);
             break;
         case kS2: case kS4: case kS5:
             if (stage == kS2 && S.level >= P.n_s2) { stage = kS3; continue; }
@@ -825,12 +832,14 @@ __device__ void enter(PackShared &W, int s, int stage, const ZoomPlan &P, int n_
 // while a slot's decisions run.
 struct Lattice {
     int la, lb, h1, h2, c, line, param;
+    int alo, ahi, blo, bhi;
 };
 
 __device__ __forceinline__ Lattice lattice_of(const Slot &S)
 {
     Lattice L;
     L.la = S.la; L.lb = S.lb; L.h1 = S.h1; L.h2 = S.h2; L.c = S.c; L.line = S.line; L.param = S.param;
+    L.alo = S.alo; L.ahi = S.ahi; L.blo = S.blo; L.bhi = S.bhi;
     return L;
 }
 
@@ -842,7 +851,11 @@ __device__ __forceinline__ bool list_point(PackShared &W, int s, const GridDev &
 {
     const int a = L.la + i * L.h1, b = L.lb + k * L.h2;
     known = false;
-    if (!point_valid(g, a, b, L.c)) { known = true; v = -INFINITY; return false; }
+    if (a < L.alo || a > L.ahi || b < L.blo || b > L.bhi || !point_valid(g, a, b, L.c)) {
+        known = true;
+        v = -INFINITY;
+        return false;
+    }
     const int idx = L.line ? ((L.param == 0 ? i : k) & (kWin - 1)) : (((i & 7) << 3) | (k & 7));
     if (win_get(W, s, idx, a, b, v)) { known = true; return false; }
     if ((listed >> idx) & 1ull) return false;
@@ -1230,6 +1243,8 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
                     if (A.phase == kPhaseTail) {
                         // resume after step 3 (voxels finished earlier are skipped)
                         const ZState z = A.state[nv];
+                        S.alo = 0; S.ahi = A.g.n_t1 - 1; S.blo = 0; S.bhi = A.g.n_t2 - 1;
+                        S.clo = 0; S.chi = A.g.n_df - 1;
                         if (z.flags & kZDone) continue;
                         S.v = nv;
                         S.a = z.a; S.b = z.b; S.c = z.c;
@@ -1242,8 +1257,24 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
                         S.level = 0;
                         enter(W, s, kS4, P, A.g.n_df, false);
                     } else {
-                        S.v = nv;
-                        S.a = P.a0; S.b = P.b0; S.c = 0;
+                        S.v = A.vmap ? __ldg(&A.vmap[nv]) : nv;
+                        if (A.box) {
+                            // a search bounded by a prior: the start clipped into
+                            // the box, then moved to a valid point inside it
+                            const int *bx = A.box + 6 * (size_t)nv;
+                            S.alo = __ldg(&bx[0]); S.ahi = __ldg(&bx[1]); S.blo = __ldg(&bx[2]);
+                            S.bhi = __ldg(&bx[3]); S.clo = __ldg(&bx[4]); S.chi = __ldg(&bx[5]);
+                            int a = min(max(P.a_raw, S.alo), S.ahi), b = min(max(P.b_raw, S.blo), S.bhi);
+                            while (b > S.blo && !point_valid(A.g, a, b, S.clo)) --b;
+                            while (a < S.ahi && !point_valid(A.g, a, b, S.clo)) ++a;
+                            if (!point_valid(A.g, a, b, S.clo)) atomicExch(A.err, kDeviceErrBounds);
+                            S.a = a; S.b = b;
+                        } else {
+                            S.alo = 0; S.ahi = A.g.n_t1 - 1; S.blo = 0; S.bhi = A.g.n_t2 - 1;
+                            S.clo = 0; S.chi = A.g.n_df - 1;
+                            S.a = P.a0; S.b = P.b0;
+                        }
+                        S.c = S.clo;
                         S.centre = -INFINITY;
                         S.evaluated = 0;
                         S.mm = INFINITY;
@@ -1710,6 +1741,114 @@ void launch_line(const mrf_ctx *ctx, const LineArgs &L, int64_t max_items, cudaS
 
 }  // namespace
 
+namespace {
+
+// Boxes of the second pass of the spatial-neighbour prior: the grid points
+// within h1, h2, h3 steps of the first-pass neighbour's result, cut by the
+// grid.
+__global__ void prior_box_kernel(const mrf_result *out, const int *nbr, int n2, int h1, int h2, int h3, int n_t1,
+                                 int n_t2, int n_df, int *box)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n2) return;
+    const mrf_result r = out[nbr[i]];
+    int *bx = box + 6 * (size_t)i;
+    bx[0] = max(0, r.i_t1 - h1); bx[1] = min(n_t1 - 1, r.i_t1 + h1);
+    bx[2] = max(0, r.i_t2 - h2); bx[3] = min(n_t2 - 1, r.i_t2 + h2);
+    bx[4] = max(0, r.i_df - h3); bx[5] = min(n_df - 1, r.i_df + h3);
+}
+
+// MRF-ZOOM with the spatial-neighbour prior (Methods, Experiment 3), in two
+// passes over the slice: the voxels on every stride-th row and column on the
+// whole grid, then every other voxel on the box around its first-pass
+// neighbour's result (the neighbour is the first-pass voxel at (r - r mod
+// stride, c - c mod stride) instead of the preceding voxel in raster order, so
+// each pass runs all its voxels in parallel). Both passes run every step in
+// the packed kernel.
+int zoom_with_prior(mrf_ctx *ctx, const ZoomPlan &P, const SeqDev &sd, const GridDev &gdev,
+                    const mrf_grid_desc *gd, const mrf_zoom_opts *o, const void *fp, int64_t V, mrf_result *out,
+                    cudaStream_t stream)
+{
+    const int64_t W = o->prior_width, st = o->prior_stride;
+    std::vector<int> ids, nbr;
+    ids.reserve((size_t)V);
+    for (int64_t v = 0; v < V; ++v)
+        if ((v / W) % st == 0 && (v % W) % st == 0) ids.push_back((int)v);
+    const int n1 = (int)ids.size();
+    for (int64_t v = 0; v < V; ++v) {
+        const int64_t r = v / W, c = v % W;
+        if (r % st == 0 && c % st == 0) continue;
+        ids.push_back((int)v);
+        nbr.push_back((int)((r - r % st) * W + (c - c % st)));
+    }
+    const int n2 = (int)nbr.size();
+    const int h1 = (int)floor(o->prior_t1_ms / gd->t1_step + 1e-9);
+    const int h2 = (int)floor(o->prior_t2_ms / gd->t2_step + 1e-9);
+    const int h3 = (int)floor(o->prior_df_hz / gd->df_step + 1e-9);
+    // one block: counters | voxel ids (first pass, then second) | neighbours | boxes
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t o_ids = 256, o_nbr = o_ids + al(4 * (size_t)V), o_box = o_nbr + al(4 * (size_t)std::max(n2, 1));
+    const size_t total = o_box + al(24 * (size_t)std::max(n2, 1));
+    std::vector<uint8_t> host(o_box, 0);
+    memcpy(host.data() + o_ids, ids.data(), 4 * (size_t)V);
+    if (n2) memcpy(host.data() + o_nbr, nbr.data(), 4 * (size_t)n2);
+    int rc = budget_charge(ctx, total);
+    if (rc) return rc;
+    uint8_t *sb = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&sb, total, stream);
+    // pageable source: the copy is staged before the call returns
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sb, host.data(), o_box, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) {
+        if (sb) cudaFreeAsync(sb, stream);
+        budget_release(ctx, total);
+        return cuda_fail(e, "zoom prior scratch");
+    }
+    const int *d_ids = (const int *)(sb + o_ids);
+    int *box = (int *)(sb + o_box);
+    ZoomArgs A;
+    A.s = sd;
+    A.g = gdev;
+    A.dhi = A.dlo = nullptr;
+    A.dnorm = nullptr;
+    A.dscale = nullptr;
+    A.ld = 0;
+    A.plan = P;
+    A.x = (const float2 *)fp;
+    A.out = out;
+    A.err = ctx->err_flag;
+    A.max_moves = 1 << 20;
+    A.state = nullptr;
+    A.phase = kPhaseAll;
+    A.stats = ctx->dev_stats;
+    {
+        ProfScope prof(ctx, kProfZoom, stream);
+        if (n1) {
+            A.counter = (int *)sb;
+            A.vmap = d_ids;
+            A.box = nullptr;
+            A.V = n1;
+            launch_pack(A, pack_blocks(ctx, n1), stream);
+        }
+        if (n2) {
+            prior_box_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, stream>>>(
+                out, (const int *)(sb + o_nbr), n2, h1, h2, h3, gd->n_t1, gd->n_t2, gd->n_df, box);
+            A.counter = (int *)sb + 1;
+            A.vmap = d_ids + n1;
+            A.box = box;
+            A.V = n2;
+            launch_pack(A, pack_blocks(ctx, n2), stream);
+            count_launch(ctx, 2);
+        }
+    }
+    e = cudaGetLastError();
+    cudaFreeAsync(sb, stream);
+    budget_release(ctx, total);
+    if (e != cudaSuccess) return cuda_fail(e, "zoom (prior) launch");
+    return MRF_OK;
+}
+
+}  // namespace
+
 int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mrf_zoom_opts *o, const void *fp,
              int64_t V, mrf_result *out, cudaStream_t stream)
 {
@@ -1718,6 +1857,8 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     ZoomPlan P{};
     int a = (int)floor((o->t1_init_ms - gd->t1_min) / gd->t1_step + 0.5);
     int b = (int)floor((o->t2_init_ms - gd->t2_min) / gd->t2_step + 0.5);
+    P.a_raw = a;
+    P.b_raw = b;
     a = std::max(0, std::min(a, gd->n_t1 - 1));
     b = std::max(0, std::min(b, gd->n_t2 - 1));
     auto valid = [&](int aa, int bb) {
@@ -1760,6 +1901,13 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     size_t gbytes = 0;
     int rc = grid_upload_async(ctx, gd, stream, &gdev, &gblock, &gbytes);
     if (rc) return rc;
+
+    if (o->prior_width > 0) {
+        rc = zoom_with_prior(ctx, P, seq->dev(), gdev, gd, o, fp, V, out, stream);
+        cudaFreeAsync(gblock, stream);
+        budget_release(ctx, gbytes);
+        return rc;
+    }
 
     // Split search (step 3 batched by line) unless step 3 never scans. Scratch,
     // one block: counters + line counts | state | keys | line bases | per-voxel
@@ -1807,6 +1955,8 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     A.counter = counters;
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
+    A.vmap = nullptr;
+    A.box = nullptr;
     A.state = split ? (ZState *)(sb + o_state) : nullptr;
     A.phase = split ? kPhaseHead : kPhaseAll;
     A.stats = ctx->dev_stats;
@@ -1872,6 +2022,8 @@ static int plan_zoom(const mrf_seq *seq, const mrf_grid_desc *gd, const mrf_zoom
     P = ZoomPlan{};
     int a = (int)floor((o->t1_init_ms - gd->t1_min) / gd->t1_step + 0.5);
     int b = (int)floor((o->t2_init_ms - gd->t2_min) / gd->t2_step + 0.5);
+    P.a_raw = a;
+    P.b_raw = b;
     a = std::max(0, std::min(a, gd->n_t1 - 1));
     b = std::max(0, std::min(b, gd->n_t2 - 1));
     auto valid = [&](int aa, int bb) {
@@ -1908,6 +2060,8 @@ extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_z
     if (!ctx || !d) return set_error(MRF_E_INVALID, "NULL argument");
     if (d->dtype != MRF_F32 && d->dtype != MRF_BF16)
         return set_error(MRF_E_UNSUPPORTED, "zoom over a dictionary needs an MRF_F32 or MRF_BF16 dictionary");
+    if (opts && opts->prior_width != 0)
+        return set_error(MRF_E_UNSUPPORTED, "zoom over a dictionary: the spatial-neighbour prior is mrf_zoom_search's");
     if (V < 0) return set_error(MRF_E_INVALID, "V < 0");
     mrf_zoom_opts def;
     if (!opts) { mrf_zoom_opts_default(&def); opts = &def; }
@@ -1945,6 +2099,8 @@ extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_z
     A.counter = counter;
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
+    A.vmap = nullptr;
+    A.box = nullptr;
     A.state = nullptr;
     A.phase = kPhaseAll;
     A.stats = nullptr;
@@ -2016,6 +2172,8 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
         if (opts->s4_param[i] != 0 && opts->s4_param[i] != 1) return set_error(MRF_E_INVALID, "zoom: s4_param must be 0/1");
     if (!(opts->s1a_step_frac > 0) || !(opts->s1b_step_frac > 0) || opts->s1b_half_frac < 0 || opts->s3_half_frac < 0)
         return set_error(MRF_E_INVALID, "zoom: bad df search fractions");
+    if (opts->prior_width != 0)
+        return set_error(MRF_E_UNSUPPORTED, "zoom (static scratch): the spatial-neighbour prior needs mrf_zoom_search");
     // scratch layout: [counter][t1][t2][df][a_off][nb], 256-byte aligned pieces
     const size_t nt1 = gd->n_t1, nt2 = gd->n_t2, ndf = gd->n_df;
     const size_t o_t1 = 256, o_t2 = o_t1 + al256(4 * nt1), o_df = o_t2 + al256(4 * nt2);
@@ -2036,6 +2194,8 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     ZoomPlan P{};
     int a = (int)floor((opts->t1_init_ms - gd->t1_min) / gd->t1_step + 0.5);
     int b = (int)floor((opts->t2_init_ms - gd->t2_min) / gd->t2_step + 0.5);
+    P.a_raw = a;
+    P.b_raw = b;
     a = std::max(0, std::min(a, gd->n_t1 - 1));
     b = std::max(0, std::min(b, gd->n_t2 - 1));
     auto t1v = [&](int i) { return gd->t1_min + (double)i * gd->t1_step; };
@@ -2115,6 +2275,8 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     A.counter = (int *)dev;
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
+    A.vmap = nullptr;
+    A.box = nullptr;
     A.state = nullptr;
     A.phase = kPhaseAll;   // one kernel: the split search's scratch grows with V
     A.stats = ctx->dev_stats;

@@ -278,3 +278,66 @@ def test_zoom_step3_narrow_or_empty_window(M, ctx, oracle_lib, grid, s3):
     res = _gpu_zoom(M, ctx, seq, g, x, s3_half_frac=s3)
     ref = oracle_lib.zoom(seq, g, x, oracle_lib.default_zoom_opts(s3_half_frac=s3))
     _compare(oracle_lib, g, res, ref, f"s3_half_frac={s3}")
+
+
+def _piecewise_voxels(orc, seq, rows, cols, seed, snr=30.0):
+    ph = S.phantom_piecewise(seed, rows, cols)
+    clean = orc.simulate(seq, ph["t1"], ph["t2"], ph["df"])
+    g_re, g_im = S.noise_draws(seed, rows * cols, seq.n)
+    return ph, S.compose_voxels(clean, ph["m0"], ph["phase"], g_re, g_im, snr)
+
+
+@pytest.mark.parametrize("half", [(3000.0, 800.0, 150.0), (200.0, 30.0, 6.0)])
+def test_zoom_spatial_prior_against_oracle(M, ctx, oracle_lib, half):
+    """The spatial-neighbour prior (Methods, Experiment 3) on a piecewise-
+    smooth 16 x 16 slice: the paper's windows, and narrow ones that bound
+    most second-pass searches; against the oracle's two-pass search."""
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["fp32_brute"]
+    ph, x = _piecewise_voxels(oracle_lib, seq, 16, 16, 31)
+    res = _gpu_zoom(M, ctx, seq, g, x, prior=(16, 4, half))
+    ref = oracle_lib.zoom_prior(seq, g, x, 16, 4, half)
+    diff, exc = _compare(oracle_lib, g, res, ref, f"prior {half}")
+    abc = np.stack([res["i_t1"], res["i_t2"], res["i_df"]], 1)
+    box = ref["box"]
+    inside = ((abc[:, 0] >= box[:, 0]) & (abc[:, 0] <= box[:, 1]) & (abc[:, 1] >= box[:, 2]) &
+              (abc[:, 1] <= box[:, 3]) & (abc[:, 2] >= box[:, 4]) & (abc[:, 2] <= box[:, 5]))
+    assert inside.all()
+    print(f"zoom prior {half}: differ={diff} excused={exc}")
+
+
+def test_zoom_spatial_prior_covering_the_grid_is_the_plain_search(M, ctx, oracle_lib):
+    """Windows wider than every axis: both passes search the whole grid, so
+    the results are those of the plain search bit for bit (a ragged last row:
+    the slice is 13 voxels wide)."""
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["fp32_brute"]
+    ph, x = offgrid_voxels(oracle_lib, seq, 13 * 7 + 5, 20.0, 33)
+    plain = _gpu_zoom(M, ctx, seq, g, x)
+    pri = _gpu_zoom(M, ctx, seq, g, x, prior=(13, 3, (1e6, 1e6, 1e6)))
+    for f in ("index", "entries_evaluated"):
+        assert np.array_equal(plain[f], pri[f]), f
+    assert np.array_equal(plain["cc"].view(np.uint32), pri["cc"].view(np.uint32))
+
+
+def test_zoom_spatial_prior_options_checked(M, ctx):
+    import ctypes as C
+    seq = S.sequence(0, 50)
+    h = M.mrf_sequence_load(ctx, seq)
+    try:
+        g = M.grid_desc(S.GRIDS["tiny"])
+        fp = torch.zeros((4, 50), dtype=torch.complex64, device="cuda")
+        out = M.empty_results(4)
+        L = M.lib()
+        for kw in (dict(prior=(-1, 4, (3000.0, 800.0, 150.0))), dict(prior=(2, 0, (3000.0, 800.0, 150.0))),
+                   dict(prior=(2, 2, (-1.0, 800.0, 150.0)))):
+            o = M.zoom_opts(**kw)
+            rc = L.mrf_zoom_search(ctx, h, C.byref(g), C.byref(o), C.c_void_p(fp.data_ptr()), 4,
+                                   C.c_void_p(out.data_ptr()), None)
+            assert rc == M.MRF_E_INVALID
+        o = M.zoom_opts(prior=(2, 2, (3000.0, 800.0, 150.0)))
+        rc = L.mrf_zoom_search_static(ctx, h, C.byref(g), C.byref(o), C.c_void_p(fp.data_ptr()), 4,
+                                      C.c_void_p(out.data_ptr()), None)
+        assert rc == M.MRF_E_UNSUPPORTED
+    finally:
+        M.mrf_sequence_free(ctx, h)
