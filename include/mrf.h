@@ -338,8 +338,8 @@ int mrf_zoom_search(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid,
  * The dictionary must be MRF_F32 (FP32-equivalent CC) or MRF_BF16 (bf16 CC,
  * decisions may differ from the FP32 search where candidates differ by less
  * than about 1e-3). M0 and phase use the stored entry norms. Errors:
- * MRF_E_INVALID, MRF_E_UNSUPPORTED (FP8 dictionary), MRF_E_BUDGET,
- * MRF_E_CUDA. */
+ * MRF_E_INVALID, MRF_E_UNSUPPORTED (FP8 dictionary, or a spatial-neighbour
+ * prior in opts), MRF_E_BUDGET, MRF_E_CUDA. */
 int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *dict, const mrf_zoom_opts *opts, const void *fp_dev,
                          int64_t V, mrf_result *out_dev, void *stream);
 
@@ -379,7 +379,10 @@ int mrf_refine(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, cons
  * MRF_E_INVALID with the needed size. All calls share the array and it keeps
  * the last call's contents: calls that overlap on the GPU race and must be
  * serialised by the caller. The first call on a device looks up the array's
- * address; make it before any stream capture. */
+ * address; make it before any stream capture. The spatial-neighbour prior
+ * (opts->prior_width != 0) is refused with MRF_E_UNSUPPORTED: its scratch
+ * grows with V. All steps run in one kernel, with the results of
+ * mrf_zoom_search bit for bit. */
 #define MRF_ZOOM_STATIC_SCRATCH_BYTES (512 * 1024)
 int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid,
                            const mrf_zoom_opts *opts, const void *fp_dev, int64_t V, mrf_result *out_dev,
