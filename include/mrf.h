@@ -417,7 +417,9 @@ int mrf_serve_start(mrf_ctx *ctx, const mrf_serve_config *cfg);
 /* Enqueue a request; returns immediately with a ticket. The fingerprints are
  * copied, so fp_host may be reused on return. A request whose buffers could
  * never fit the budget returns MRF_E_BUDGET; otherwise it waits for memory.
- * Errors: MRF_E_INVALID, MRF_E_BUDGET. */
+ * Requests are concatenated into shared launches, so a ZOOM request with a
+ * spatial-neighbour prior is refused (MRF_E_UNSUPPORTED).
+ * Errors: MRF_E_INVALID, MRF_E_BUDGET, MRF_E_UNSUPPORTED. */
 int mrf_serve_submit(mrf_ctx *ctx, const mrf_request *req, uint64_t *ticket);
 
 /* Wait up to timeout_ms (0 = just check) for a ticket. MRF_OK: out_host (V
