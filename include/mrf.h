@@ -114,6 +114,12 @@ int mrf_profile_enable(mrf_ctx *ctx, int on);
  * zeroes all counters. */
 int mrf_profile_read(mrf_ctx *ctx, mrf_profile *out, int reset);
 
+/* The FP32 FMA rate this device sustains (the roofline of the on-the-fly
+ * Bloch and ZOOM kernels): a kernel of independent FMA chains on every SM,
+ * timed with CUDA events, best of three; *tflops = 2 x FMAs / time. Takes a
+ * few milliseconds and synchronises the device. */
+int mrf_fp32_fma_rate(mrf_ctx *ctx, double *tflops);
+
 /* ------------------------------------------------------------------------ */
 /* Sequence (Methods: IR-bSSFP train; Appendix: hard RF pulse)              */
 

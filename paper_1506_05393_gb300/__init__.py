@@ -119,7 +119,7 @@ EXPORTS = [
     "mrf_zoom_opts_default", "mrf_zoom_search", "mrf_serve_start", "mrf_serve_submit", "mrf_serve_poll",
     "mrf_serve_cancel", "mrf_serve_get_stats", "mrf_serve_stop", "mrf_profile_enable", "mrf_profile_read",
     "mrf_zoom_search_static", "mrf_zoom_search_dict", "mrf_refine", "mrf_smooth", "mrf_dict_smooth",
-    "mrf_dict_free_async", "mrf_sequence_free_async",
+    "mrf_dict_free_async", "mrf_sequence_free_async", "mrf_fp32_fma_rate",
 ]
 
 
@@ -170,6 +170,7 @@ def lib():
         L.mrf_serve_stop.argtypes = [vp]
         L.mrf_profile_enable.argtypes = [vp, C.c_int]
         L.mrf_profile_read.argtypes = [vp, C.POINTER(Profile), C.c_int]
+        L.mrf_fp32_fma_rate.argtypes = [vp, C.POINTER(C.c_double)]
         L.mrf_zoom_search_static.argtypes = [vp, vp, C.POINTER(GridDesc), C.POINTER(ZoomOpts), vp, i64, vp, vp]
         L.mrf_zoom_search_dict.argtypes = [vp, vp, C.POINTER(ZoomOpts), vp, i64, vp, vp]
         _lib = L
@@ -393,6 +394,13 @@ def mrf_serve_stop(ctx) -> None:
 
 def mrf_profile_enable(ctx, on: bool = True) -> None:
     check(lib().mrf_profile_enable(ctx, 1 if on else 0), "mrf_profile_enable")
+
+
+def mrf_fp32_fma_rate(ctx) -> float:
+    """Measured FP32 FMA rate of the device, TFLOP/s."""
+    t = C.c_double()
+    check(lib().mrf_fp32_fma_rate(ctx, C.byref(t)), "mrf_fp32_fma_rate")
+    return float(t.value)
 
 
 def mrf_profile_read(ctx, reset: bool = False) -> Profile:

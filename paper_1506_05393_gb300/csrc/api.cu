@@ -168,6 +168,63 @@ extern "C" int mrf_stream_sync(mrf_ctx *ctx, void *stream)
 }
 
 // ---------------------------------------------------------------------------
+// FP32 FMA rate: eight independent chains per thread, 64 warps per SM
+
+namespace {
+constexpr int kFmaIters = 8192;
+constexpr int kFmaChains = 8;
+
+__global__ void __launch_bounds__(256) fma_rate_kernel(float *out, float a, float b)
+{
+    float x[kFmaChains];
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) x[k] = (float)(threadIdx.x + k) * 1.0e-3f;
+    for (int i = 0; i < kFmaIters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kFmaChains; ++k) x[k] = fmaf(x[k], a, b);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) s += x[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;   // keeps the chains live
+}
+}  // namespace
+
+extern "C" int mrf_fp32_fma_rate(mrf_ctx *ctx, double *tflops)
+{
+    if (!ctx || !tflops) return set_error(MRF_E_INVALID, "NULL argument");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    const int blocks = ctx->sm_count * 8, threads = 256;
+    float *out = nullptr;
+    e = cudaMalloc(&out, sizeof(float) * blocks * threads);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(fma rate)");
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    float best = 0.f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(t0, ctx->aux);
+        fma_rate_kernel<<<blocks, threads, 0, ctx->aux>>>(out, 0.9999999f, 1.0e-7f);
+        cudaEventRecord(t1, ctx->aux);
+        e = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (e == cudaSuccess && rep > 0 && cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess && ms > 0.f &&
+            (best == 0.f || ms < best))
+            best = ms;   // the first launch only warms up
+        count_launch(ctx);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaFree(out);
+    if (e != cudaSuccess) return cuda_fail(e, "fma rate kernel");
+    const double fmas = (double)blocks * threads * kFmaIters * kFmaChains;
+    *tflops = best > 0.f ? 2.0 * fmas / (best * 1e-3) / 1e12 : 0.0;
+    return MRF_OK;
+}
+
+// ---------------------------------------------------------------------------
 // kernel accounting
 
 ProfScope::ProfScope(mrf_ctx *c, int k, cudaStream_t s) : ctx(c), kind(k), stream(s)

@@ -177,3 +177,14 @@ def test_cc_landscape_around_a_fingerprint(M, ctx):
               f"CC at df = 0 Hz on the target's T1/T2: {c[dfs == 0.0][0]:.4f}")
     finally:
         M.mrf_sequence_free(ctx, h)
+
+
+def test_fp32_fma_rate_is_plausible(M, ctx):
+    """The measured FP32 FMA rate (the roofline of the on-the-fly kernels)
+    lies between half and 1.05 x the nominal SMs x 128 FMA/clk x 2 x the
+    highest SM clock."""
+    props = torch.cuda.get_device_properties(0)
+    rate = M.mrf_fp32_fma_rate(ctx)
+    nominal = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    assert 0.5 * nominal < rate < 1.05 * nominal, (rate, nominal)
+    print(f"FP32 FMA rate {rate:.1f} TFLOP/s (nominal at 2.07 GHz {nominal:.1f})")
