@@ -10,7 +10,10 @@
 //    refinement of step 3 runs batched over the voxels that stopped at the
 //    same (T1, T2) (zoom_line_kernel, same arithmetic per candidate and
 //    voxel, so the same decisions); the packed kernel then resumes steps 4-5.
-//    mrf_zoom_search_static runs all steps in the packed kernel;
+//    mrf_zoom_search_static runs all steps in the packed kernel, and so does
+//    the spatial-neighbour prior (Methods, Experiment 3: each voxel searched
+//    on the box of grid points around a neighbour's result), in two passes
+//    of per-voxel boxes;
 //  * zoom_dict_kernel reads candidates from a resident dictionary, one warp
 //    per voxel, the warp streaming each stored row.
 // Decisions take the best candidate with ties to the earliest in the
