@@ -405,6 +405,19 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
                                         np.array_equal(res1["cc"].view(np.uint32), res["cc"].view(np.uint32)) and
                                         np.array_equal(res1["entries_evaluated"], res["entries_evaluated"]))}
 
+    # four 128x128 slices in one call: the longest voxels' chains of rounds overlap the other slices' work
+    xs4 = [x128] + [make_slice(M, ctx, seq_h, 103 + k, 128 * 128, 20.0)[1] for k in (1, 2, 3)]
+    x4d = torch.from_numpy(np.ascontiguousarray(np.concatenate(xs4, 0))).cuda()
+    out4 = M.empty_results(x4d.shape[0])
+    run4 = lambda: M.mrf_zoom_search(ctx, seq_h, gz, zf, x4d, out4)
+    run4()
+    ms4 = timed(run4, 2)
+    r4 = M.results_to_numpy(out4)[: x4d.shape[0]]
+    modes["zoom_4x128x128_fine"] = {
+        "grid": "zoom_fine", "voxels": int(x4d.shape[0]), "ms": ms4, "voxels_per_s": x4d.shape[0] / ms4 * 1e3,
+        "first_slice_identical": bool(np.array_equal(r4["index"][: x128d.shape[0]], res["index"])),
+        "note": "the slice of zoom_128x128_fine and three more (phantom seeds 104-106) searched in one call"}
+
     # the spatial-neighbour prior (Experiment 3's variant) on a piecewise-smooth 128x128 slice
     phw, xw = make_piecewise_slice(M, ctx, seq_h, 107, 128, 128, 20.0)
     xwd = torch.from_numpy(xw).cuda()
