@@ -329,7 +329,9 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
 #pragma unroll 1
             for (int gq = 0; gq < kJ / kFacG; ++gq) {
                 const int jg = j0 + gq * kFacG;
-                fac_load(nxt, fr, jg + kFacG);
+                // the row's padding slots past n need no factors (and the
+                // tables' padding covers only 2 x kFacG timepoints past n)
+                if (jg + kFacG < n) fac_load(nxt, fr, jg + kFacG);
                 float vr[kFacG], vi[kFacG];
 #pragma unroll
                 for (int q = 0; q < kFacG; ++q) {

@@ -103,6 +103,33 @@ def test_dictionary_tiny_matches_oracle(M, ctx, oracle_lib, dtype, tol):
         M.mrf_sequence_free(ctx, h)
 
 
+@pytest.mark.parametrize("n", [1, 12, 37])
+@pytest.mark.parametrize("dtype,tol", [(0, 1e-5), (1, 3e-3), (2, 7e-2)])
+def test_dictionary_short_sequences(M, ctx, oracle_lib, n, dtype, tol):
+    """Sequences far shorter than a row's padding (N = 1, 12, 37 timepoints)
+    on a grid with a df axis: rows, norms and zero padding as for N = 200."""
+    seq = S.sequence(3, n)
+    g = S.Grid(100.0, 100.0, 20, 20.0, 20.0, 10, -20.0, 5.0, 9)
+    h = M.mrf_sequence_load(ctx, seq)
+    d = M.mrf_dict_generate(ctx, h, g, dtype)
+    torch.cuda.synchronize()
+    try:
+        rows, pad, norm, info = _dict_rows(M, d, dtype)
+        a, b, c = oracle_lib.grid_params(g)
+        t1, t2, df = S.grid_values(g)
+        ref = oracle_lib.simulate(seq, t1[a], t2[b], df[c])
+        nr = np.linalg.norm(ref, axis=1)
+        live = nr > 1e-6 * nr.max()
+        refn = ref[live] / nr[live, None]
+        err = rel_l2(rows[live], refn)
+        assert err.max() < tol, f"N {n}, dtype {dtype}: max rel L2 {err.max():.3g}"
+        np.testing.assert_allclose(norm, nr, rtol=1e-5, atol=1e-7)
+        assert np.all(pad == 0)
+    finally:
+        M.mrf_dict_free(ctx, d)
+        M.mrf_sequence_free(ctx, h)
+
+
 def test_dictionary_full_size_sampled(M, ctx, oracle_lib):
     """The 614,508-entry FP32-equivalent dictionary at N = 1000: sampled rows."""
     seq = S.sequence(1, 1000)
