@@ -623,7 +623,9 @@ def run_serving_trace(M, n_requests=40, seed=104, rate_hz=50.0, budget_gb=120.0,
                "by_mode": {name: {"requests": int((modes == m).sum()),
                                   "p50_ms": float(np.percentile(lat[modes == m], 50)) if (modes == m).any() else None}
                            for m, name in enumerate(["fp32_brute", "bf16_rescore_fine", "zoom_fine"])},
-               "note": "offered load exceeds one GPU (about 6 GPU-seconds per second): latencies include queueing"}
+               "note": ("offered load exceeds one GPU (about 6 GPU-seconds per second): latencies include queueing"
+                        if rate_hz >= 20.0 else
+                        "offered load below one GPU (about 0.5 GPU-seconds per second): latency is mostly service time")}
         M.mrf_dict_free(ctx, d32)
         M.mrf_dict_free(ctx, d16)
         M.mrf_sequence_free(ctx, h)
@@ -902,6 +904,7 @@ def main():
     M.mrf_ctx_destroy(ctx)
     if not args.no_serving and not args.no_modes:
         line["serving"] = run_serving_trace(M)
+        line["serving_sustainable_rate"] = run_serving_trace(M, n_requests=24, rate_hz=4.0)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seq, x_np)
     print(json.dumps(line), flush=True)
