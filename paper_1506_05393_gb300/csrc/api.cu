@@ -735,7 +735,7 @@ extern "C" int mrf_zoom_search(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_
     if (!ctx || !seq || !grid) return set_error(MRF_E_INVALID, "NULL argument");
     int rc = grid_validate(grid);
     if (rc) return rc;
-    if (V < 0) return set_error(MRF_E_INVALID, "V < 0");
+    if (V < 0 || V > INT32_MAX) return set_error(MRF_E_INVALID, "zoom: V must be in [0, 2^31 - 1]");
     mrf_zoom_opts def;
     if (!opts) { mrf_zoom_opts_default(&def); opts = &def; }
     if (opts->n_s2 < 0 || opts->n_s2 > MRF_ZOOM_MAX_LEVELS || opts->n_s4 < 0 || opts->n_s4 > MRF_ZOOM_MAX_LEVELS)

@@ -2065,7 +2065,7 @@ extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_z
         return set_error(MRF_E_UNSUPPORTED, "zoom over a dictionary needs an MRF_F32 or MRF_BF16 dictionary");
     if (opts && opts->prior_width != 0)
         return set_error(MRF_E_UNSUPPORTED, "zoom over a dictionary: the spatial-neighbour prior is mrf_zoom_search's");
-    if (V < 0) return set_error(MRF_E_INVALID, "V < 0");
+    if (V < 0 || V > INT32_MAX) return set_error(MRF_E_INVALID, "zoom: V must be in [0, 2^31 - 1]");
     mrf_zoom_opts def;
     if (!opts) { mrf_zoom_opts_default(&def); opts = &def; }
     if (opts->n_s2 < 0 || opts->n_s2 > MRF_ZOOM_MAX_LEVELS || opts->n_s4 < 0 || opts->n_s4 > MRF_ZOOM_MAX_LEVELS)
@@ -2166,7 +2166,7 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     if (!ctx || !seq || !gd) return set_error(MRF_E_INVALID, "NULL argument");
     int rc = grid_validate(gd);
     if (rc) return rc;
-    if (V < 0) return set_error(MRF_E_INVALID, "V < 0");
+    if (V < 0 || V > INT32_MAX) return set_error(MRF_E_INVALID, "zoom: V must be in [0, 2^31 - 1]");
     mrf_zoom_opts def;
     if (!opts) { mrf_zoom_opts_default(&def); opts = &def; }
     if (opts->n_s2 < 0 || opts->n_s2 > MRF_ZOOM_MAX_LEVELS || opts->n_s4 < 0 || opts->n_s4 > MRF_ZOOM_MAX_LEVELS)
