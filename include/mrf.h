@@ -46,7 +46,7 @@ enum {
     MRF_E_TIMEOUT = -4,     /* a bounded wait ran out (host poll or device spin) */
     MRF_E_CUDA = -5,        /* CUDA runtime / driver error */
     MRF_E_NOTFOUND = -6,    /* unknown ticket or handle */
-    MRF_E_UNSUPPORTED = -7  /* valid request this build does not implement */
+    MRF_E_UNSUPPORTED = -7  /* valid request the library does not implement */
 };
 
 typedef enum {

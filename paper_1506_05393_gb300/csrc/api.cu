@@ -109,7 +109,7 @@ extern "C" int mrf_ctx_create(int device, size_t hbm_budget_bytes, mrf_ctx **out
     e = cudaGetDeviceProperties(&prop, device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
     if (!(prop.major == 10 && prop.minor == 3))
-        return set_error(MRF_E_INVALID, std::string("this build targets sm_103a only; device is sm_") +
+        return set_error(MRF_E_INVALID, std::string("the library is compiled for sm_103a only; device is sm_") +
                                             std::to_string(prop.major) + std::to_string(prop.minor));
     size_t free_b = 0, total_b = 0;
     e = cudaMemGetInfo(&free_b, &total_b);
