@@ -341,3 +341,26 @@ def test_zoom_spatial_prior_options_checked(M, ctx):
         assert rc == M.MRF_E_UNSUPPORTED
     finally:
         M.mrf_sequence_free(ctx, h)
+
+
+def test_zoom_work_counters(M, ctx, oracle_lib):
+    """The profile's ZOOM work counters after one search on a grid whose step
+    3 runs batched: step-3 positions are part of the evaluation count, the
+    line kernel simulated candidates, the packed kernel ran rounds and
+    simulated candidates, both were timed once, and a reset clears
+    everything."""
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["precision"]
+    ph, x = offgrid_voxels(oracle_lib, seq, 48, 20.0, 41)
+    M.mrf_profile_read(ctx, reset=True)
+    M.mrf_profile_enable(ctx, True)
+    res = _gpu_zoom(M, ctx, seq, g, x)
+    M.mrf_profile_enable(ctx, False)
+    p = M.mrf_profile_read(ctx, reset=True)
+    ev = int(res["entries_evaluated"].sum())
+    assert 0 < p.zoomline_pairs < ev
+    assert p.zoomline_entries > 0
+    assert p.zoom_rounds > 0 and p.zoom_candidates > 0 and p.zoom_max_voxel_rounds > 0
+    assert p.zoom_timed == 1 and p.zoomline_timed == 1 and p.zoom_ms > p.zoomline_ms > 0
+    q = M.mrf_profile_read(ctx)
+    assert q.zoomline_pairs == 0 and q.zoom_rounds == 0 and q.zoom_timed == 0
