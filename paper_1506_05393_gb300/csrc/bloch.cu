@@ -10,13 +10,20 @@
 //   re-runs the recurrence and writes the normalised (BF16, scale 1) or
 //   scaled e4m3 (FP8) row.
 // Rows are staged per warp in shared memory (32 entries x 128 bytes, XOR
-// swizzled on 16-byte chunks) and leave as fully coalesced 16-byte stores, so
-// the kernel streams HBM writes at one pass of the output.
-// Evolution factors come from tables indexed by grid axis (E1 by T1, E2 by T2,
-// e^{i theta} by df), built once per dictionary with CUDA's expf/sincospif.
+// swizzled on 16-byte chunks) and leave as full 128-byte lines of 16-byte
+// stores, so the kernel streams HBM writes at one pass of the output.
+// Symmetric x-rotation sequences (the randomised IR-bSSFP train) take the
+// df-major kernel dict_gen_xsym_kernel: a warp's lanes share the df index, so
+// e^{i theta} is a broadcast load from a [df][j] table, E1 / E2 are exp2f of
+// TE_j, and the RF of each row chunk is staged per warp. Other sequences take
+// dict_gen_kernel, whose evolution factors come from tables indexed by grid
+// axis (E1 by T1, E2 by T2, e^{i theta} by df), built once per dictionary with
+// CUDA's expf/sincospif.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "bloch.cuh"
 #include "mrf_internal.h"
@@ -418,6 +425,275 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
     }
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric x-rotation sequences (every RF phase 0 or pi, TE_j = TR_j - TE_j:
+// the randomised IR-bSSFP train of the experiments). Threads walk the grid
+// df-major: thread t takes df index c = t / P and (T1, T2) pair p = t mod P
+// (P = D / n_df valid pairs), i.e. entry p * n_df + c, so the lanes of a warp
+// share c and e^{i theta_j} is one broadcast 16-byte load per two timepoints
+// from a [c][j] table. E1 and E2 come from exp2f of TE_j, and the RF rotation
+// and TE_j of each row chunk are staged per warp in shared memory (one
+// coalesced load per chunk, fetched a chunk ahead). The arithmetic is that of
+// the on-the-fly simulator (relax_factors, bloch_start), so an entry holds the
+// same fingerprint as simulate_kernel up to the contraction of the e^{i theta}
+// argument.
+
+// e^{i theta_j} of df index c over TE_j at zt[c * ldz + j]; ldz is a multiple of
+// 8 with at least 8 slots past n (a look-ahead group reads past the end).
+__global__ void ztable_kernel(SeqDev s, GridDev g, float2 *zt, int ldz)
+{
+    const int64_t n = s.n, total = n * g.n_df;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(k / n), j = (int)(k % n);
+        const float f = g.df[c] * 1.0e-3f;
+        float ta = f * s.tau[j].x;
+        ta -= rintf(ta);
+        float sa, ca;
+        sincospif(2.0f * ta, &sa, &ca);
+        zt[(size_t)c * ldz + j] = make_float2(ca, sa);
+    }
+}
+
+struct ZGroup {
+    float2 z[kFacG];
+};
+
+__device__ __forceinline__ void zgroup_load(ZGroup &f, const float2 *zrow, int jb)
+{
+    const float4 *p = reinterpret_cast<const float4 *>(zrow + jb);
+#pragma unroll
+    for (int k = 0; k < kFacG / 2; ++k) {
+        const float4 v = __ldg(p + k);
+        f.z[2 * k] = make_float2(v.x, v.y);
+        f.z[2 * k + 1] = make_float2(v.z, v.w);
+    }
+}
+
+// One timepoint: RF (c, s, 1 - c, TE_j), then E1 / E2 e^{i theta} over TE_j,
+// the sample, and the same factors again over TR_j - TE_j = TE_j.
+__device__ __forceinline__ void step_xsym(Bloch &st, float4 rf, float k1, float k2, float2 z, float &sr, float &si)
+{
+    bloch_rf_x(st, rf);
+    const float e1 = ex2_fast(k1 * rf.w), e2 = ex2_fast(k2 * rf.w);
+    const float zr = e2 * z.x, zi = e2 * z.y;
+    bloch_evolve(st, e1, zr, zi);
+    sr = st.mx;
+    si = st.my;
+    bloch_evolve(st, e1, zr, zi);
+}
+
+// RF of timepoints j0 + lane + 32 u (zero past n), one chunk of kJ timepoints.
+template <int kJ>
+__device__ __forceinline__ void rf_fetch(float4 (&r)[kJ / 32], const SeqDev &s, int j0, int lane)
+{
+#pragma unroll
+    for (int u = 0; u < kJ / 32; ++u) {
+        const int j = j0 + lane + 32 * u;
+        r[u] = j < s.n ? __ldg(&s.rfx[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+template <int OUT>
+__global__ void __launch_bounds__(kGenThreads) dict_gen_xsym_kernel(SeqDev s, GridDev g, const float2 *zt, int ldz,
+                                                                    int64_t D, int ld, uint8_t *out_hi,
+                                                                    uint8_t *out_lo, float *norm_out, float *scale_out)
+{
+    using P = Packer<OUT>;
+    constexpr int kBpt = P::kBpt;               // bytes per timepoint per array
+    constexpr int kPerVec = 16 / kBpt;          // timepoints per 16-byte vector
+    constexpr int kJ = 128 / kBpt;              // timepoints per 128-byte row chunk
+    constexpr int kVecs = kFacG / kPerVec;      // 16-byte vectors per look-ahead group
+    constexpr bool kTwo = (OUT == MRF_F32);
+    constexpr bool kOnePass = (OUT == MRF_F32);
+    static_assert(kJ % (2 * kFacG) == 0 && 32 % (2 * kFacG) == 0 && kVecs >= 1, "chunk / group mismatch");
+
+    __shared__ uint4 stage_hi[kGenThreads / 32][32][8];
+    __shared__ uint4 stage_lo[kTwo ? kGenThreads / 32 : 1][32][8];
+    __shared__ float4 stage_rf[kGenThreads / 32][kJ];
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t tid = (int64_t)blockIdx.x * kGenThreads + threadIdx.x;
+    const bool live = tid < D;
+    const int n = s.n;
+    const int64_t pairs = D / g.n_df;
+    int64_t e = 0;
+    int a = 0, b = 0, c = 0;
+    if (live) {
+        c = (int)(tid / pairs);
+        e = (tid - (int64_t)c * pairs) * g.n_df + c;
+        unravel(g, e, a, b, c);
+    }
+    // lanes past D run the recurrence of entry 0 and write nothing
+    const Relax rx = relax_make(__ldg(&g.t1[a]), __ldg(&g.t2[b]), 0.f);
+    const float2 *zrow = zt + (size_t)c * ldz;
+    const float4 *srf = stage_rf[warp];
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    // kFacG timepoints from jg on (FULL: all below n), with the next group's
+    // e^{i theta} fetched into zn; the last look-ahead of a full chunk may
+    // read up to 7 slots past n, inside the table's padding
+    auto run_group = [&](auto full, Bloch &st, const ZGroup &zc, ZGroup &zn, int jg, int j0, float (&vr)[kFacG],
+                         float (&vi)[kFacG]) {
+        constexpr bool FULL = decltype(full)::value;
+        if (FULL || jg + kFacG < n) zgroup_load(zn, zrow, jg + kFacG);
+#pragma unroll
+        for (int q = 0; q < kFacG; ++q) {
+            vr[q] = 0.f;
+            vi[q] = 0.f;
+            if (FULL || jg + q < n) step_xsym(st, srf[jg + q - j0], rx.k1, rx.k2, zc.z[q], vr[q], vi[q]);
+        }
+    };
+
+    // pass 1 (BF16, FP8): ||d||^2 in 32-timepoint blocks (Kahan-compensated
+    // total) and, for FP8, max |component|
+    float tot = 0.f, comp = 0.f, amax = 0.f;
+    Bloch st;
+    if constexpr (!kOnePass) {
+        bloch_start(st, s, rx);
+        ZGroup za, zb;
+        zgroup_load(za, zrow, 0);
+        float4 rfn[1];
+        rf_fetch<32>(rfn, s, 0, lane);
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            stage_rf[warp][lane] = rfn[0];
+            __syncwarp();
+            rf_fetch<32>(rfn, s, j0 + 32, lane);
+            float part = 0.f;
+            auto acc = [&](const float (&vr)[kFacG], const float (&vi)[kFacG]) {
+#pragma unroll
+                for (int q = 0; q < kFacG; ++q) {
+                    part = fmaf(vr[q], vr[q], fmaf(vi[q], vi[q], part));
+                    if (OUT == MRF_FP8E4M3) amax = fmaxf(amax, fmaxf(fabsf(vr[q]), fabsf(vi[q])));
+                }
+            };
+            float vr[kFacG], vi[kFacG];
+            if (j0 + 32 <= n) {
+#pragma unroll 1
+                for (int jg = j0; jg < j0 + 32; jg += 2 * kFacG) {
+                    run_group(std::true_type{}, st, za, zb, jg, j0, vr, vi);
+                    acc(vr, vi);
+                    run_group(std::true_type{}, st, zb, za, jg + kFacG, j0, vr, vi);
+                    acc(vr, vi);
+                }
+            } else {
+#pragma unroll 1
+                for (int jg = j0; jg < j0 + 32; jg += 2 * kFacG) {
+                    run_group(std::false_type{}, st, za, zb, jg, j0, vr, vi);
+                    acc(vr, vi);
+                    run_group(std::false_type{}, st, zb, za, jg + kFacG, j0, vr, vi);
+                    acc(vr, vi);
+                }
+            }
+            const float y = part - comp;
+            const float tt = tot + y;
+            comp = (tt - tot) - y;
+            tot = tt;
+            __syncwarp();
+        }
+    }
+    float qs = 1.f;
+    if (live && !kOnePass) {
+        const float nrm = sqrtf(tot);
+        const float inv = nrm > 0.f ? 1.0f / nrm : 0.f;
+        norm_out[e] = nrm;
+        if (OUT == MRF_FP8E4M3) {
+            const float mx = amax * inv;                      // max |normalised component|
+            const float scale = mx > 0.f ? mx / 448.0f : 1.0f;
+            qs = inv / scale;                                 // raw value -> e4m3 code scale
+            scale_out[e] = scale;
+        } else {
+            qs = inv;                                         // BF16: normalised values
+            scale_out[e] = 1.0f;
+        }
+    }
+
+    // pass 2: (re-)run and write the rows through the warp stage
+    bloch_start(st, s, rx);
+    const int row_bytes = ld * (OUT == MRF_FP8E4M3 ? 1 : 2);
+    const int tp_row = row_bytes / kBpt;      // timepoint slots per row (incl. padding)
+    const int erow = live ? (int)e : -1;      // dictionaries hold fewer than 2^31 entries
+    ZGroup za, zb;
+    zgroup_load(za, zrow, 0);
+    float4 rfn[kJ / 32];
+    rf_fetch<kJ>(rfn, s, 0, lane);
+    float part1 = 0.f;                        // one-pass norm: this chunk's partial sum
+    // pack one group into the stage (vectors gq * kVecs ...)
+    auto put_group = [&](const float (&vr)[kFacG], const float (&vi)[kFacG], int gq) {
+#pragma unroll
+        for (int q = 0; q < kFacG; ++q)
+            if (kOnePass) part1 = fmaf(vr[q], vr[q], fmaf(vi[q], vi[q], part1));
+#pragma unroll
+        for (int vq = 0; vq < kVecs; ++vq) {
+            P pk;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { pk.hi[u] = 0u; pk.lo[u] = 0u; }
+#pragma unroll
+            for (int u = 0; u < kPerVec; ++u) {
+                const float xr = vr[vq * kPerVec + u], xi = vi[vq * kPerVec + u];
+                pk.put(u, xr * (OUT == MRF_FP8E4M3 ? 1.f : qs), xi * (OUT == MRF_FP8E4M3 ? 1.f : qs),
+                       OUT == MRF_FP8E4M3 ? qs : 1.f);
+            }
+            const int pq = (gq * kVecs + vq) ^ (lane & 7);
+            stage_hi[warp][lane][pq] = make_uint4(pk.hi[0], pk.hi[1], pk.hi[2], pk.hi[3]);
+            if (kTwo) stage_lo[kTwo ? warp : 0][lane][pq] = make_uint4(pk.lo[0], pk.lo[1], pk.lo[2], pk.lo[3]);
+        }
+    };
+    for (int j0 = 0; j0 < tp_row; j0 += kJ) {
+#pragma unroll
+        for (int u = 0; u < kJ / 32; ++u) stage_rf[warp][lane + 32 * u] = rfn[u];
+        __syncwarp();
+        rf_fetch<kJ>(rfn, s, j0 + kJ, lane);
+        float vr[kFacG], vi[kFacG];
+        if (j0 + kJ <= n) {
+#pragma unroll 1
+            for (int gq = 0; gq < kJ / kFacG; gq += 2) {
+                run_group(std::true_type{}, st, za, zb, j0 + gq * kFacG, j0, vr, vi);
+                put_group(vr, vi, gq);
+                run_group(std::true_type{}, st, zb, za, j0 + (gq + 1) * kFacG, j0, vr, vi);
+                put_group(vr, vi, gq + 1);
+            }
+        } else {
+#pragma unroll 1
+            for (int gq = 0; gq < kJ / kFacG; gq += 2) {
+                run_group(std::false_type{}, st, za, zb, j0 + gq * kFacG, j0, vr, vi);
+                put_group(vr, vi, gq);
+                run_group(std::false_type{}, st, zb, za, j0 + (gq + 1) * kFacG, j0, vr, vi);
+                put_group(vr, vi, gq + 1);
+            }
+        }
+        if (kOnePass) {   // 32-timepoint blocks (kJ = 32 for 4-byte timepoints)
+            const float y = part1 - comp;
+            const float tt = tot + y;
+            comp = (tt - tot) - y;
+            tot = tt;
+            part1 = 0.f;
+        }
+        __syncwarp();
+        // the warp's rows are its lanes' entries (df-major order: not consecutive)
+        const int qq = lane & 7;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = i * 4 + (lane >> 3);
+            const int row = __shfl_sync(0xffffffffu, erow, r);
+            if (row >= 0) {
+                const size_t off = (size_t)row * row_bytes + (size_t)j0 * kBpt + qq * 16;
+                const uint4 vh = stage_hi[warp][r][qq ^ (r & 7)];
+                __stcs(reinterpret_cast<uint4 *>(out_hi + off), vh);
+                if (kTwo) {
+                    const uint4 vl = stage_lo[kTwo ? warp : 0][r][qq ^ (r & 7)];
+                    __stcs(reinterpret_cast<uint4 *>(out_lo + off), vl);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (kOnePass && live) {
+        const float nrm = sqrtf(tot);
+        norm_out[e] = nrm;
+        scale_out[e] = nrm > 0.f ? 1.0f / nrm : 0.f;
+    }
+}
+
 // Arbitrary (T1, T2, df) per thread, complex64 rows of n timepoints, not normalised.
 template <bool XONLY>
 __global__ void __launch_bounds__(128) simulate_kernel(SeqDev s, int64_t count, const float *t1, const float *t2,
@@ -477,6 +753,33 @@ int launch_dict_generate(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream)
     const SeqDev s = d->seq->dev();
     const GridDev g = d->grid.dev();
     const int n = s.n;
+    uint8_t *hi = (uint8_t *)d->hi, *lo = (uint8_t *)d->lo;
+    const int64_t blocks = (d->entries + kGenThreads - 1) / kGenThreads;
+    if (s.xonly && s.symmetric) {
+        // df-major kernel: only the [c][j] e^{i theta} table
+        const int ldz = ((n + 7) & ~7) + 8;
+        const size_t zb = sizeof(float2) * (size_t)ldz * g.n_df;
+        int rc = budget_charge(ctx, zb);
+        if (rc) return rc;
+        float2 *zt = nullptr;
+        cudaError_t e = cudaMallocAsync((void **)&zt, zb, stream);
+        if (e != cudaSuccess) { budget_release(ctx, zb); return cuda_fail(e, "table scratch"); }
+        ztable_kernel<<<4 * ctx->sm_count, 256, 0, stream>>>(s, g, zt, ldz);
+        count_launch(ctx);
+        {
+            ProfScope prof(ctx, kProfDictGen, stream);
+#define MRF_XGEN(OUT) dict_gen_xsym_kernel<OUT><<<(unsigned)blocks, kGenThreads, 0, stream>>>(s, g, zt, ldz, d->entries, d->ld, hi, lo, d->norm, d->scale)
+            if (d->dtype == MRF_F32) MRF_XGEN(MRF_F32);
+            else if (d->dtype == MRF_BF16) MRF_XGEN(MRF_BF16);
+            else MRF_XGEN(MRF_FP8E4M3);
+#undef MRF_XGEN
+        }
+        e = cudaGetLastError();
+        cudaFreeAsync(zt, stream);
+        budget_release(ctx, zb);
+        if (e != cudaSuccess) return cuda_fail(e, "dictionary generation launch");
+        return MRF_OK;
+    }
     // evolution-factor tables in stream-ordered scratch
     // each table is followed by room for 2 x kFacG timepoints of padding (a
     // look-ahead group of the last entry reads past its end)
@@ -497,8 +800,6 @@ int launch_dict_generate(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream)
     tables_kernel<<<4 * ctx->sm_count, 256, 0, stream>>>(s, g, e1, e2, cis, e1i);
     count_launch(ctx);
     Tables t{e1, e2, cis, (const float *)e1, (const float *)e2, (const float2 *)cis, e1i};
-    const int64_t blocks = (d->entries + kGenThreads - 1) / kGenThreads;
-    uint8_t *hi = (uint8_t *)d->hi, *lo = (uint8_t *)d->lo;
 #define MRF_GEN(OUT, XO, SY) dict_gen_kernel<OUT, XO, SY><<<(unsigned)blocks, kGenThreads, 0, stream>>>(s, g, t, d->entries, d->ld, hi, lo, d->norm, d->scale)
 #define MRF_GEN_DT(XO, SY)                                        \
     do {                                                          \
@@ -508,8 +809,7 @@ int launch_dict_generate(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream)
     } while (0)
     {
     ProfScope prof(ctx, kProfDictGen, stream);
-    if (s.xonly && s.symmetric) MRF_GEN_DT(true, true);
-    else if (s.xonly) MRF_GEN_DT(true, false);
+    if (s.xonly) MRF_GEN_DT(true, false);
     else if (s.symmetric) MRF_GEN_DT(false, true);
     else MRF_GEN_DT(false, false);
     }

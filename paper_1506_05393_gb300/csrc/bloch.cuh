@@ -51,6 +51,14 @@ __device__ __forceinline__ void bloch_evolve(Bloch &st, float e1, float zr, floa
     st.w *= e1;
 }
 
+// 2^x on the SFU (PTX ex2.approx.ftz; relative error about 2^-22).
+__device__ __forceinline__ float ex2_fast(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Per-fingerprint constants for on-the-fly evolution factors.
 struct Relax {
     float k1;   // -log2(e) / T1

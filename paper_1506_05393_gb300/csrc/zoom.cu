@@ -101,14 +101,6 @@ struct Kahan {
     }
 };
 
-// 2^x on the SFU (PTX ex2.approx.ftz; relative error about 2^-22).
-__device__ __forceinline__ float ex2_fast(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // e^{i 2 pi f tau} on the SFU, argument first reduced to [-1/2, 1/2] cycles.
 __device__ __forceinline__ void cis_fast(float f, float tau, float &cs, float &sn)
 {

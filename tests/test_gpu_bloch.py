@@ -130,6 +130,36 @@ def test_dictionary_short_sequences(M, ctx, oracle_lib, n, dtype, tol):
         M.mrf_sequence_free(ctx, h)
 
 
+@pytest.mark.parametrize("kind", ["general_rf_asym_te", "xonly_asym_te", "general_rf_sym_te"])
+@pytest.mark.parametrize("dtype,tol", [(0, 1e-5), (1, 3e-3), (2, 7e-2)])
+def test_dictionary_other_sequence_kinds(M, ctx, oracle_lib, kind, dtype, tol):
+    """Sequences outside the symmetric x-rotation form (an RF phase off the
+    multiples of pi, TE_j != TR_j - TE_j) take the table-driven kernel: rows,
+    norms and padding against the oracle on a grid with a df axis."""
+    base = S.sequence(4, 150)
+    rng = np.random.default_rng(91)
+    phase = rng.uniform(0, 2 * math.pi, 150) if kind.startswith("general") else base.rf_phase_rad
+    te = base.tr_ms * 0.3 if kind.endswith("asym_te") else base.te_ms
+    seq = S.Sequence(base.flip_rad, phase, base.tr_ms, te, 1, 15.0)
+    g = S.Grid(100.0, 100.0, 20, 20.0, 20.0, 10, -20.0, 5.0, 9)
+    h = M.mrf_sequence_load(ctx, seq)
+    d = M.mrf_dict_generate(ctx, h, g, dtype)
+    torch.cuda.synchronize()
+    try:
+        rows, pad, norm, info = _dict_rows(M, d, dtype)
+        a, b, c = oracle_lib.grid_params(g)
+        t1, t2, df = S.grid_values(g)
+        ref = oracle_lib.simulate(seq, t1[a], t2[b], df[c])
+        nr = np.linalg.norm(ref, axis=1)
+        err = rel_l2(rows, ref / nr[:, None])
+        assert err.max() < tol, f"{kind}, dtype {dtype}: max rel L2 {err.max():.3g}"
+        np.testing.assert_allclose(norm, nr, rtol=1e-5)
+        assert np.all(pad == 0)
+    finally:
+        M.mrf_dict_free(ctx, d)
+        M.mrf_sequence_free(ctx, h)
+
+
 def test_dictionary_full_size_sampled(M, ctx, oracle_lib):
     """The 614,508-entry FP32-equivalent dictionary at N = 1000: sampled rows."""
     seq = S.sequence(1, 1000)
