@@ -433,10 +433,10 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
 // share c and e^{i theta_j} is one broadcast 16-byte load per two timepoints
 // from a [c][j] table. E1 and E2 come from exp2f of TE_j, and the RF rotation
 // and TE_j of each row chunk are staged per warp in shared memory (one
-// coalesced load per chunk, fetched a chunk ahead). The arithmetic is that of
-// the on-the-fly simulator (relax_factors, bloch_start), so an entry holds the
-// same fingerprint as simulate_kernel up to the contraction of the e^{i theta}
-// argument.
+// coalesced load per chunk, fetched a chunk ahead). The recurrence and the
+// evolution factors are those of the on-the-fly simulator (bloch_start,
+// relax_factors), with E1 and E2 taken from the SFU's ex2 as in the ZOOM
+// kernels.
 
 // e^{i theta_j} of df index c over TE_j at zt[c * ldz + j]; ldz is a multiple of
 // 8 with at least 8 slots past n (a look-ahead group reads past the end).
