@@ -289,6 +289,26 @@ typedef struct {
 int mrf_match_bruteforce(mrf_ctx *ctx, const mrf_dict *dict, const void *fp_dev, int64_t V,
                          const mrf_match_opts *opts, mrf_result *out_dev, void *stream);
 
+/* Brute-force DGS over a grid without a resident dictionary (Methods: the
+ * search over every grid entry by Eq. 1; for grids whose dictionary does not
+ * fit in HBM). The grid's valid entries, in their linear order, are cut into
+ * ranges of whole T1 rows of at most chunk_entries entries (0: 8,388,608);
+ * each range's dictionary is generated on `stream` in opts->precision,
+ * matched as by mrf_match_bruteforce, and released before the next, and the
+ * per-voxel answers merge: the higher CC wins, ties to the earlier range
+ * (smaller linear index). index and i_t1 refer to the whole grid; min_margin
+ * is the gap between the best CC and the best other CC of the ranges' re-
+ * scored candidates (-1 if there is none); entries_evaluated is the grid's
+ * entry count, saturated at 2^31 - 1. Each range's dictionary is charged to
+ * the budget while it lives; the call returns once every range has been
+ * queued (the host waits for each range's grid upload, not for the kernels).
+ * Errors: MRF_E_INVALID (NULL argument, bad options, a grid without a valid
+ * entry, chunk_entries < 0 or smaller than a T1 row's entry count),
+ * MRF_E_BUDGET, MRF_E_CUDA. */
+int mrf_match_bruteforce_grid(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid,
+                              const mrf_match_opts *opts, int64_t chunk_entries, const void *fp_dev, int64_t V,
+                              mrf_result *out_dev, void *stream);
+
 /* The tensor-core pass alone: per voxel the top_k (linear index, approximate
  * CC^2 of the normalised pair) in descending order, ties to the smaller
  * index. idx_dev: V x top_k int64, cc2_dev: V x top_k float32. */

@@ -115,7 +115,8 @@ _lib = None
 EXPORTS = [
     "mrf_last_error", "mrf_version", "mrf_ctx_create", "mrf_ctx_destroy", "mrf_ctx_memory", "mrf_stream_sync",
     "mrf_sequence_load", "mrf_sequence_free", "mrf_grid_count", "mrf_grid_unravel", "mrf_simulate",
-    "mrf_dict_generate", "mrf_dict_free", "mrf_dict_query", "mrf_match_bruteforce", "mrf_match_topk",
+    "mrf_dict_generate", "mrf_dict_free", "mrf_dict_query", "mrf_match_bruteforce", "mrf_match_bruteforce_grid",
+    "mrf_match_topk",
     "mrf_zoom_opts_default", "mrf_zoom_search", "mrf_serve_start", "mrf_serve_submit", "mrf_serve_poll",
     "mrf_serve_cancel", "mrf_serve_get_stats", "mrf_serve_stop", "mrf_profile_enable", "mrf_profile_read",
     "mrf_zoom_search_static", "mrf_zoom_search_dict", "mrf_refine", "mrf_smooth", "mrf_dict_smooth",
@@ -154,6 +155,8 @@ def lib():
         L.mrf_dict_query.argtypes = [vp, C.POINTER(DictInfo)]
         L.mrf_match_bruteforce.argtypes = [vp, vp, vp, i64, C.POINTER(MatchOpts), vp, vp]
         L.mrf_match_topk.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp]
+        L.mrf_match_bruteforce_grid.argtypes = [vp, vp, C.POINTER(GridDesc), C.POINTER(MatchOpts), i64, vp, i64, vp,
+                                                vp]
         L.mrf_zoom_opts_default.argtypes = [C.POINTER(ZoomOpts)]
         L.mrf_zoom_opts_default.restype = None
         L.mrf_zoom_search.argtypes = [vp, vp, C.POINTER(GridDesc), C.POINTER(ZoomOpts), vp, i64, vp, vp]
@@ -317,6 +320,15 @@ def mrf_match_bruteforce(ctx, d, fp, opts: MatchOpts, out, stream=None) -> None:
     V = fp.shape[0] if fp is not None else 0
     check(lib().mrf_match_bruteforce(ctx, d, _ptr(fp), V, C.byref(opts), _ptr(out), _stream_ptr(stream)),
           "mrf_match_bruteforce")
+
+
+def mrf_match_bruteforce_grid(ctx, seq, grid, fp, opts: MatchOpts, out, chunk_entries: int = 0, stream=None) -> None:
+    """Brute force over a grid without a resident dictionary (ranges of T1 rows
+    generated, matched and released in turn). fp: complex64 CUDA tensor (V, n)."""
+    g = grid_desc(grid)
+    V = fp.shape[0] if fp is not None else 0
+    check(lib().mrf_match_bruteforce_grid(ctx, seq, C.byref(g), C.byref(opts), int(chunk_entries), _ptr(fp), V,
+                                          _ptr(out), _stream_ptr(stream)), "mrf_match_bruteforce_grid")
 
 
 def mrf_match_topk(ctx, d, fp, precision: int, top_k: int, idx, cc2, stream=None) -> None:

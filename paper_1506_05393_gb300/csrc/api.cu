@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -529,6 +530,49 @@ int grid_upload(mrf_ctx *ctx, const mrf_grid_desc *g, GridBuf *out)
     return MRF_OK;
 }
 
+// The T1 rows [a0, a1) of grid g as a grid of their own: the same axis values
+// (taken from g's tables, so validity and values match the whole grid bit for
+// bit) and entry offsets counted from the range's first entry.
+static int grid_upload_rows(mrf_ctx *ctx, const mrf_grid_desc *g, const GridHost &G, int a0, int a1, GridBuf *out)
+{
+    mrf_grid_desc sub = *g;
+    sub.n_t1 = a1 - a0;
+    sub.t1_min = t1v(g, a0);
+    GridHost S;
+    grid_tables(&sub, S);   // layout for the range; the contents are replaced below
+    const float *t1 = (const float *)G.h.data();
+    const int64_t *ao = (const int64_t *)(G.h.data() + G.o_ao);
+    const int32_t *nb = (const int32_t *)(G.h.data() + G.o_nb);
+    float *st1 = (float *)S.h.data();
+    int64_t *sao = (int64_t *)(S.h.data() + S.o_ao);
+    int32_t *snb = (int32_t *)(S.h.data() + S.o_nb);
+    for (int a = a0; a < a1; ++a) {
+        st1[a - a0] = t1[a];
+        snb[a - a0] = nb[a];
+        sao[a - a0] = ao[a] - ao[a0];
+    }
+    sao[a1 - a0] = ao[a1] - ao[a0];
+    memcpy(S.h.data() + S.o_t2, G.h.data() + G.o_t2, 4 * (size_t)g->n_t2);
+    memcpy(S.h.data() + S.o_df, G.h.data() + G.o_df, 4 * (size_t)g->n_df);
+    S.count = ao[a1] - ao[a0];
+    S.a_full = std::min(std::max(G.a_full - a0, 0), a1 - a0);
+    GridBuf gb;
+    gb.desc = sub;
+    int rc = upload_block(ctx, S.h.data(), S.total, &gb.block, "grid upload");
+    if (rc) return rc;
+    uint8_t *d = (uint8_t *)gb.block;
+    gb.t1 = (float *)d;
+    gb.t2 = (float *)(d + S.o_t2);
+    gb.df = (float *)(d + S.o_df);
+    gb.a_off = (int64_t *)(d + S.o_ao);
+    gb.nb = (int32_t *)(d + S.o_nb);
+    gb.count = S.count;
+    gb.a_full = S.a_full;
+    gb.bytes = S.total;
+    *out = gb;
+    return MRF_OK;
+}
+
 int grid_upload_async(mrf_ctx *ctx, const mrf_grid_desc *g, cudaStream_t stream, GridDev *out, void **block,
                       size_t *bytes)
 {
@@ -591,6 +635,35 @@ extern "C" int mrf_dict_free(mrf_ctx *ctx, mrf_dict *d)
     return MRF_OK;
 }
 
+// Allocates d's rows (hi | lo | norm | scale in one block from the stream-
+// ordered pool, so that generating and freeing dictionaries repeatedly maps no
+// new memory) and queues their generation; d's sequence, grid, dtype, entries,
+// n and ld are set. On failure the caller frees d.
+static int dict_fill(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream)
+{
+    const size_t ebytes = d->dtype == MRF_FP8E4M3 ? 1 : 2;
+    const size_t rows = (size_t)d->entries * d->ld * ebytes;
+    auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+    const size_t b_lo = d->dtype == MRF_F32 ? al(rows) : 0, b_sc = al(4 * (size_t)d->entries);
+    const size_t total = al(rows) + b_lo + al(4 * (size_t)d->entries) + b_sc;
+    int rc = budget_charge(ctx, total);
+    if (rc) return rc;
+    cudaError_t e = cudaMallocAsync(&d->block, total, stream);
+    if (e != cudaSuccess) {
+        budget_release(ctx, total);
+        d->block = nullptr;
+        return cuda_fail(e, "dictionary");
+    }
+    d->block_bytes = total;
+    uint8_t *blk = (uint8_t *)d->block;
+    d->hi = blk;
+    d->lo = d->dtype == MRF_F32 ? blk + al(rows) : nullptr;
+    d->norm = (float *)(blk + al(rows) + b_lo);
+    d->scale = (float *)(blk + al(rows) + b_lo + al(4 * (size_t)d->entries));
+    d->bytes = total + d->grid.bytes + d->seq->bytes;
+    return launch_dict_generate(ctx, d, stream);
+}
+
 extern "C" int mrf_dict_free_async(mrf_ctx *ctx, mrf_dict *d, void *stream_v)
 {
     if (!ctx || !d) return set_error(MRF_E_INVALID, "NULL argument");
@@ -623,31 +696,7 @@ extern "C" int mrf_dict_generate(mrf_ctx *ctx, const mrf_seq *seq, const mrf_gri
     int rc = seq_clone(ctx, seq, &d->seq);
     if (rc) { delete d; return rc; }
     rc = grid_upload(ctx, grid, &d->grid);
-    const size_t ebytes = dtype == MRF_FP8E4M3 ? 1 : 2;
-    const size_t rows = (size_t)count * d->ld * ebytes;
-    // hi | lo | norm | scale in one block from the stream-ordered pool, so
-    // that generating and freeing dictionaries repeatedly maps no new memory
-    auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
-    const size_t b_lo = dtype == MRF_F32 ? al(rows) : 0, b_sc = al(4 * (size_t)count);
-    const size_t total = al(rows) + b_lo + al(4 * (size_t)count) + b_sc;
-    if (!rc) rc = budget_charge(ctx, total);
-    if (!rc) {
-        cudaError_t e = cudaMallocAsync(&d->block, total, (cudaStream_t)stream);
-        if (e != cudaSuccess) {
-            budget_release(ctx, total);
-            d->block = nullptr;
-            rc = cuda_fail(e, "dictionary");
-        }
-    }
-    if (rc) { mrf_dict_free(ctx, d); return rc; }
-    d->block_bytes = total;
-    uint8_t *blk = (uint8_t *)d->block;
-    d->hi = blk;
-    d->lo = dtype == MRF_F32 ? blk + al(rows) : nullptr;
-    d->norm = (float *)(blk + al(rows) + b_lo);
-    d->scale = (float *)(blk + al(rows) + b_lo + al(4 * (size_t)count));
-    d->bytes = total + d->grid.bytes + d->seq->bytes;
-    rc = launch_dict_generate(ctx, d, (cudaStream_t)stream);
+    if (!rc) rc = dict_fill(ctx, d, (cudaStream_t)stream);
     if (rc) { mrf_dict_free(ctx, d); return rc; }
     *out = d;
     return MRF_OK;
@@ -688,6 +737,71 @@ extern "C" int mrf_match_bruteforce(mrf_ctx *ctx, const mrf_dict *d, const void 
     cudaSetDevice(ctx->device);
     return run_match(ctx, d, fp, V, o->precision, o->top_k, o->rescore, out, nullptr, nullptr,
                      (cudaStream_t)stream);
+}
+
+extern "C" int mrf_match_bruteforce_grid(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid,
+                                         const mrf_match_opts *o, int64_t chunk_entries, const void *fp, int64_t V,
+                                         mrf_result *out, void *stream_v)
+{
+    if (!ctx || !seq || !grid || !o) return set_error(MRF_E_INVALID, "NULL argument");
+    if (V < 0) return set_error(MRF_E_INVALID, "V < 0");
+    if (o->precision != MRF_F32 && o->precision != MRF_BF16 && o->precision != MRF_FP8E4M3)
+        return set_error(MRF_E_INVALID, "unknown precision");
+    if (!valid_topk(o->top_k)) return set_error(MRF_E_INVALID, "top_k must be 1, 2, 4, 8, 16 or 32");
+    if (o->rescore != 0 && o->rescore != 1) return set_error(MRF_E_INVALID, "rescore must be 0 or 1");
+    if (chunk_entries < 0) return set_error(MRF_E_INVALID, "chunk_entries < 0");
+    int rc = grid_validate(grid);
+    if (rc) return rc;
+    GridHost G;
+    grid_tables(grid, G);
+    if (G.count == 0) return set_error(MRF_E_INVALID, "grid has no valid entry");
+    if (V == 0) return MRF_OK;
+    if (!fp || !out) return set_error(MRF_E_INVALID, "NULL device buffer");
+    const int64_t cap = std::min<int64_t>(chunk_entries > 0 ? chunk_entries : (int64_t)1 << 23, INT32_MAX);
+    const int32_t *nb = (const int32_t *)(G.h.data() + G.o_nb);
+    const int64_t *ao = (const int64_t *)(G.h.data() + G.o_ao);
+    for (int a = 0; a < grid->n_t1; ++a)
+        if ((int64_t)nb[a] * grid->n_df > cap) return set_error(MRF_E_INVALID, "chunk_entries below a T1 row's entries");
+    cudaSetDevice(ctx->device);
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    // runner-up CC per voxel and one range's results, from the pool
+    const size_t sb = (sizeof(float) * (size_t)V + 255) & ~(size_t)255;
+    const size_t scratch = sb + sizeof(mrf_result) * (size_t)V;
+    rc = budget_charge(ctx, scratch);
+    if (rc) return rc;
+    void *blk = nullptr;
+    cudaError_t e = cudaMallocAsync(&blk, scratch, stream);
+    if (e != cudaSuccess) { budget_release(ctx, scratch); return cuda_fail(e, "chunked match scratch"); }
+    float *second = (float *)blk;
+    mrf_result *part = (mrf_result *)((uint8_t *)blk + sb);
+    bool first = true;
+    for (int a0 = 0; a0 < grid->n_t1 && !rc;) {
+        int a1 = a0;
+        while (a1 < grid->n_t1 && ao[a1 + 1] - ao[a0] <= cap) ++a1;
+        const int64_t cnt = ao[a1] - ao[a0];
+        if (cnt > 0) {
+            mrf_dict *d = new mrf_dict();
+            d->seq = const_cast<mrf_seq *>(seq);   // borrowed: the range's dictionary dies in this call
+            d->dtype = o->precision;
+            d->entries = cnt;
+            d->n = seq->n;
+            d->ld = dict_ld(seq->n, o->precision);
+            rc = grid_upload_rows(ctx, grid, G, a0, a1, &d->grid);
+            if (!rc) rc = dict_fill(ctx, d, stream);
+            if (!rc)
+                rc = run_match(ctx, d, fp, V, o->precision, o->top_k, o->rescore, first ? out : part, nullptr,
+                               nullptr, stream);
+            if (!rc) rc = launch_chunk_merge(out, second, first ? nullptr : part, V, ao[a0], a0, stream);
+            first = false;
+            if (d->block) release_block(ctx, d->block, d->block_bytes, stream, false);
+            grid_release(ctx, &d->grid, stream, false);
+            delete d;
+        }
+        a0 = a1;
+    }
+    cudaFreeAsync(blk, stream);
+    budget_release(ctx, scratch);
+    return rc;
 }
 
 extern "C" int mrf_match_topk(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_t precision,

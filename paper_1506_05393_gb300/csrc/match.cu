@@ -686,6 +686,42 @@ __global__ void rescore_kernel(SeqDev s, GridDev g, const float2 *x, int64_t V, 
     }
 }
 
+// Chunked brute force (mrf_match_bruteforce_grid): per voxel, the range's
+// answer moves to whole-grid indices and replaces the running one if its CC
+// is higher (ties keep the earlier range, i.e. the smaller linear index); the
+// runner-up is the best CC among all other candidates the ranges re-scored.
+__global__ void chunk_merge_kernel(mrf_result *best, float *second, const mrf_result *part, int64_t V, int64_t base,
+                                   int a0)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    mrf_result p = part ? part[v] : best[v];
+    if (p.index >= 0) {
+        p.index += base;
+        p.i_t1 += a0;
+    }
+    const float c1 = p.index >= 0 ? p.cc : -1.f;
+    const float c2 = (p.index >= 0 && p.min_margin >= 0.f) ? p.cc - p.min_margin : -1.f;
+    mrf_result b = p;
+    float s = c2;
+    if (part) {
+        b = best[v];
+        s = second[v];
+        const float b1 = b.index >= 0 ? b.cc : -1.f;
+        const int64_t ev = (int64_t)b.entries_evaluated + p.entries_evaluated;
+        if (c1 > b1) {
+            s = fmaxf(b1, c2);
+            b = p;
+        } else {
+            s = fmaxf(s, c1);
+        }
+        b.entries_evaluated = (int32_t)min(ev, (int64_t)INT32_MAX);
+    }
+    b.min_margin = (b.index >= 0 && s > -0.5f) ? b.cc - s : -1.f;
+    second[v] = s;
+    best[v] = b;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 
@@ -762,6 +798,16 @@ int launch_match_mode(mrf_ctx *ctx, int K, const CUtensorMap &mA, const CUtensor
 }  // namespace
 
 std::mutex g_match_attr_mu;
+
+int launch_chunk_merge(mrf_result *best, float *second, const mrf_result *part, int64_t V, int64_t base, int a0,
+                       cudaStream_t stream)
+{
+    const int64_t blocks = (V + 255) / 256;
+    chunk_merge_kernel<<<(unsigned)blocks, 256, 0, stream>>>(best, second, part, V, base, a0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "chunk merge launch");
+    return MRF_OK;
+}
 
 int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_t precision, int32_t top_k,
               int rescore, mrf_result *out, int64_t *idx_out, float *cc2_out, cudaStream_t stream)

@@ -178,6 +178,11 @@ int launch_simulate(mrf_ctx *ctx, const mrf_seq *seq, int64_t count, const float
 // match.cu
 int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_t precision, int32_t top_k,
               int rescore, mrf_result *out, int64_t *idx_out, float *cc2_out, cudaStream_t stream);
+// Chunked brute force: fold one range's results (part; nullptr = the first
+// range, already in best) into best, with the range's first linear index
+// `base` and first T1 index a0; second holds each voxel's runner-up CC.
+int launch_chunk_merge(mrf_result *best, float *second, const mrf_result *part, int64_t V, int64_t base, int a0,
+                       cudaStream_t stream);
 
 // zoom.cu
 int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, const mrf_zoom_opts *opts,

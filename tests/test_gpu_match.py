@@ -248,3 +248,94 @@ def test_full_size_fp32_sampled(M, ctx, oracle_lib):
     finally:
         M.mrf_dict_free(ctx, d)
         M.mrf_sequence_free(ctx, h)
+
+
+def _run_grid(M, ctx, h, grid, x, precision, top_k, chunk):
+    fp = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+    out = M.empty_results(x.shape[0])
+    M.mrf_match_bruteforce_grid(ctx, h, grid, fp, M.match_opts(precision, top_k, 1), out, chunk)
+    M.mrf_stream_sync(ctx)
+    return M.results_to_numpy(out)[: x.shape[0]]
+
+
+def _row_entries(oracle_lib, g):
+    a, _, _ = oracle_lib.grid_params(g)
+    return int(np.bincount(a).max())
+
+
+@pytest.mark.parametrize("rows", [0, 1, 3])
+def test_chunked_grid_fp32_against_oracle(M, ctx, oracle_lib, ragged, rows):
+    """Brute force over ranges of whole T1 rows (one range; one row per range;
+    about three rows per range): whole-grid indices, parameters and counts,
+    and the oracle's answer (Theory: argmax of Eq. 1 over every entry)."""
+    g = ragged["grid"]
+    chunk = 0 if rows == 0 else rows * _row_entries(oracle_lib, g) + 5
+    res = _run_grid(M, ctx, ragged["h"], g, ragged["x"], M.MRF_F32, 4, chunk)
+    assert (res["entries_evaluated"] == ragged["D"]).all()
+    a, b, c = oracle_lib.grid_params(g)
+    t1, t2, df = S.grid_values(g)
+    i = res["index"]
+    assert ((i >= 0) & (i < ragged["D"])).all()
+    assert (a[i] == res["i_t1"]).all() and (b[i] == res["i_t2"]).all() and (c[i] == res["i_df"]).all()
+    np.testing.assert_array_equal(res["t1_ms"], t1[a[i]].astype(np.float32))
+    np.testing.assert_array_equal(res["t2_ms"], t2[b[i]].astype(np.float32))
+    diff, exc = _compare(res, ragged["ref"], f"chunked rows={rows}")
+    print(f"chunked rows={rows}: differ={diff} excused={exc}")
+    assert (res["min_margin"] >= 0).all()
+
+
+def test_chunked_grid_single_range_equals_resident(M, ctx, ragged):
+    """With one range the chunked search is the resident search, bit for bit."""
+    res = _run_grid(M, ctx, ragged["h"], ragged["grid"], ragged["x"], M.MRF_F32, 4, 0)
+    ref = _run(M, ctx, ragged["dicts"][M.MRF_F32], ragged["x"], M.MRF_F32, 4, 1)
+    for f in ("index", "i_t1", "i_t2", "i_df", "entries_evaluated"):
+        np.testing.assert_array_equal(res[f], ref[f], err_msg=f)
+    for f in ("cc", "m0", "phase"):
+        np.testing.assert_array_equal(res[f].view(np.uint32), ref[f].view(np.uint32), err_msg=f)
+    np.testing.assert_allclose(res["min_margin"], ref["min_margin"], atol=1e-7)
+
+
+@pytest.mark.parametrize("precision,top_k", [(1, 8), (2, 32)])
+def test_chunked_grid_low_precision(M, ctx, oracle_lib, ragged, precision, top_k):
+    """BF16 / FP8 ranges with the FP32 re-score: the returned entry's CC is the
+    oracle's CC of that entry, and agreement with the oracle's argmax is at
+    least the resident search's."""
+    g = ragged["grid"]
+    res = _run_grid(M, ctx, ragged["h"], g, ragged["x"], precision, top_k, 2 * _row_entries(oracle_lib, g))
+    t1, t2, df = S.grid_values(g)
+    a, b, c = oracle_lib.grid_params(g)
+    i = res["index"]
+    dd = oracle_lib.simulate(ragged["seq"], t1[a[i]], t2[b[i]], df[c[i]])
+    x = ragged["x"]
+    occ = np.abs(np.sum(dd.conj() * x, 1)) / (np.linalg.norm(dd, axis=1) * np.linalg.norm(x, axis=1))
+    assert np.abs(res["cc"] - occ).max() < CC_TOL
+    ref = ragged["ref"]
+    agree = (i == ref["idx"][:, 0]).mean()
+    resident = (_run(M, ctx, ragged["dicts"][precision], x, precision, top_k, 1)["index"] == ref["idx"][:, 0]).mean()
+    print(f"chunked precision={precision} k={top_k}: agreement {agree:.3f} (resident {resident:.3f})")
+    assert agree >= resident - 1e-9
+
+
+def test_chunked_grid_invalid_and_empty_calls(M, ctx, oracle_lib, ragged):
+    import ctypes as C
+    g = ragged["grid"]
+    x = torch.from_numpy(np.ascontiguousarray(ragged["x"][:4].astype(np.complex64))).cuda()
+    out = M.empty_results(4)
+    L = M.lib()
+    gd = M.grid_desc(g)
+    opts = M.match_opts(M.MRF_F32, 4, 1)
+    small = _row_entries(oracle_lib, g) - 1
+    for chunk in (-1, small):
+        rc = L.mrf_match_bruteforce_grid(ctx, ragged["h"], C.byref(gd), C.byref(opts), chunk,
+                                         C.c_void_p(x.data_ptr()), 4, C.c_void_p(out.data_ptr()), None)
+        assert rc == M.MRF_E_INVALID, chunk
+    bad = M.match_opts(M.MRF_F32, 3, 1)
+    rc = L.mrf_match_bruteforce_grid(ctx, ragged["h"], C.byref(gd), C.byref(bad), 0, C.c_void_p(x.data_ptr()), 4,
+                                     C.c_void_p(out.data_ptr()), None)
+    assert rc == M.MRF_E_INVALID
+    rc = L.mrf_match_bruteforce_grid(ctx, ragged["h"], C.byref(gd), C.byref(opts), 0, None, 0, None, None)
+    assert rc == M.MRF_OK
+    # a voxel of zeros matches nothing, in every range
+    z = np.zeros((2, ragged["seq"].n), np.complex64)
+    res = _run_grid(M, ctx, ragged["h"], g, z, M.MRF_F32, 4, 2 * _row_entries(oracle_lib, g))
+    assert (res["index"] == -1).all()
