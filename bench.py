@@ -440,6 +440,14 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
                                  "t2_ms": float(np.median(np.abs(rz["t2_ms"] - rb["t2_ms"]))),
                                  "df_hz": float(np.median(np.abs(rz["df_hz"] - rb["df_hz"])))},
         "bruteforce_margin_below_1e-6": int(np.sum(rb["min_margin"] < 1e-6)),
+        # searches that ended on another local maximum: where they went
+        "zoom_far_off": {"voxels": int(np.sum(rb["cc"] - rz["cc"] > 1e-2)),
+                         "zoom_df_within_2hz_of_0": int(np.sum((rb["cc"] - rz["cc"] > 1e-2) &
+                                                               (np.abs(rz["df_hz"]) < 2.0))),
+                         "median_abs_diff": {k: float(np.median(np.abs(rz[f] - rb[f])[rb["cc"] - rz["cc"] > 1e-2]))
+                                             if np.any(rb["cc"] - rz["cc"] > 1e-2) else 0.0
+                                             for k, f in (("t1_ms", "t1_ms"), ("t2_ms", "t2_ms"),
+                                                          ("df_hz", "df_hz"))}},
         "note": "mrf_match_bruteforce_grid: FP32-equivalent brute force (top-4 + FP64 re-score) over ranges of "
                 "whole T1 rows, no resident dictionary; ZOOM (and ZOOM + refinement) on the same voxels "
                 "compared with it"}
