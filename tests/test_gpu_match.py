@@ -250,6 +250,54 @@ def test_full_size_fp32_sampled(M, ctx, oracle_lib):
         M.mrf_sequence_free(ctx, h)
 
 
+def test_full_size_precision_grid_sampled(M, ctx, oracle_lib):
+    """64x64 slice, N = 1000, 12,024,855 entries (the BF16 / FP8 benchmark
+    workload): BF16 top-8 and FP8 top-32 with the re-score on all 4096 voxels,
+    against the FP32-equivalent brute force over the same grid (in ranges, no
+    resident dictionary): never above its CC, the returned entries' CCs equal
+    to the oracle's for 8 sampled voxels, and after the windowed refinement
+    its index wherever its top-two gap is at least 1e-6."""
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["precision"]
+    _, x = offgrid_voxels(oracle_lib, seq, 4096, 20.0, 101)
+    h = M.mrf_sequence_load(ctx, seq)
+    try:
+        ref = _run_grid(M, ctx, h, g, x, M.MRF_F32, 4, 0)
+        sure = ref["min_margin"] >= GAP_EXCUSE
+        t1, t2, df = S.grid_values(g)
+        a, b, c = oracle_lib.grid_params(g)
+        pick = np.random.default_rng(6).choice(4096, 8, replace=False)
+        fp = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
+        for dt, k, floor in ((M.MRF_BF16, 8, 0.98), (M.MRF_FP8E4M3, 32, 0.97)):
+            d = M.mrf_dict_generate(ctx, h, g, dt)
+            out = M.empty_results(4096)
+            try:
+                M.mrf_match_bruteforce(ctx, d, fp, M.match_opts(dt, k, 1), out)
+                M.mrf_stream_sync(ctx)
+                res = M.results_to_numpy(out)[:4096].copy()
+                M.mrf_refine(ctx, h, g, fp, out)
+                M.mrf_stream_sync(ctx)
+                ref2 = M.results_to_numpy(out)[:4096]
+            finally:
+                M.mrf_dict_free(ctx, d)
+            assert (res["entries_evaluated"] == ref["entries_evaluated"]).all()
+            # never above the FP32-equivalent brute force's CC (the maximum over every entry)
+            assert (res["cc"] <= ref["cc"] + 2e-6).all()
+            assert (ref2["cc"] <= ref["cc"] + 2e-6).all()
+            i = res["index"][pick]
+            dd = oracle_lib.simulate(seq, t1[a[i]], t2[b[i]], df[c[i]])
+            xx = x[pick]
+            occ = np.abs(np.sum(dd.conj() * xx, 1)) / (np.linalg.norm(dd, axis=1) * np.linalg.norm(xx, axis=1))
+            assert np.abs(res["cc"][pick] - occ).max() < CC_TOL
+            agree = (res["index"] == ref["index"])[sure].mean()
+            agree2 = (ref2["index"] == ref["index"])[sure].mean()
+            print(f"full-size 12M dtype={dt} top-{k}: agreement with FP32 brute force {agree:.4f}, after "
+                  f"refinement {agree2:.4f} ({int(sure.sum())} voxels with a gap >= 1e-6)")
+            assert agree2 >= floor
+    finally:
+        M.mrf_sequence_free(ctx, h)
+
+
 def _run_grid(M, ctx, h, grid, x, precision, top_k, chunk):
     fp = torch.from_numpy(np.ascontiguousarray(x.astype(np.complex64))).cuda()
     out = M.empty_results(x.shape[0])
