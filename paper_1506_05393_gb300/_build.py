@@ -2,7 +2,8 @@
 
 Each translation unit is compiled by nvcc in parallel, then linked into one
 shared library with the static CUDA runtime. Output: ``_build/`` beside this
-file (git-ignored). No CMake, no torch extension machinery.
+file (``_build_check/`` for the bounds-checked variant; both git-ignored). No
+CMake, no torch extension machinery.
 """
 from __future__ import annotations
 
@@ -14,7 +15,13 @@ import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
+# MRF_BUILD_VARIANT=check selects the bounds-checked build (-DMRF_CHECK: a
+# failed device index check sets the context's error flag, reported by
+# mrf_stream_sync, and skips the access), kept in its own folder
+VARIANT = os.environ.get("MRF_BUILD_VARIANT", "")
+if VARIANT not in ("", "check"):
+    raise ValueError(f"MRF_BUILD_VARIANT must be empty or 'check', not {VARIANT!r}")
+BUILD = os.path.join(HERE, "_build_check" if VARIANT == "check" else "_build")
 LIB = os.path.join(BUILD, "libmrf_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
@@ -52,6 +59,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         nvcc = _nvcc()
         common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo", "--expt-relaxed-constexpr",
                   "-I", os.path.join(HERE, "..", "include")] + list(extra_flags)
+        if VARIANT == "check":
+            common.append("-DMRF_CHECK")
         if verbose:
             common += ["-Xptxas", "-v"]
 

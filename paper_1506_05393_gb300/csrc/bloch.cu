@@ -222,7 +222,7 @@ struct Packer<MRF_FP8E4M3> {
 template <int OUT, bool XONLY, bool SYM>
 __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev g, Tables t, int64_t D, int ld,
                                                                uint8_t *out_hi, uint8_t *out_lo, float *norm_out,
-                                                               float *scale_out)
+                                                               float *scale_out, int *err)
 {
     using P = Packer<OUT>;
     constexpr int kBpt = P::kBpt;               // bytes per timepoint per array
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
         for (int i = 0; i < 8; ++i) {
             const int r = i * 4 + (lane >> 3);
             const int64_t row = row0 + r;
-            if (row < D) {
+            if (row < D && mrf_in_bounds((size_t)j0 * kBpt + qq * 16 + 16 <= (size_t)row_bytes, err)) {
                 const size_t off = (size_t)row * row_bytes + (size_t)j0 * kBpt + qq * 16;
                 const uint4 vh = stage_hi[warp][r][qq ^ (r & 7)];
                 __stcs(reinterpret_cast<uint4 *>(out_hi + off), vh);
@@ -496,7 +496,8 @@ __device__ __forceinline__ void rf_fetch(float4 (&r)[kJ / 32], const SeqDev &s, 
 template <int OUT>
 __global__ void __launch_bounds__(kGenThreads) dict_gen_xsym_kernel(SeqDev s, GridDev g, const float2 *zt, int ldz,
                                                                     int64_t D, int ld, uint8_t *out_hi,
-                                                                    uint8_t *out_lo, float *norm_out, float *scale_out)
+                                                                    uint8_t *out_lo, float *norm_out, float *scale_out,
+                                                                    int *err)
 {
     using P = Packer<OUT>;
     constexpr int kBpt = P::kBpt;               // bytes per timepoint per array
@@ -535,7 +536,8 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_xsym_kernel(SeqDev s, Gr
     auto run_group = [&](auto full, Bloch &st, const ZGroup &zc, ZGroup &zn, int jg, int j0, float (&vr)[kFacG],
                          float (&vi)[kFacG]) {
         constexpr bool FULL = decltype(full)::value;
-        if (FULL || jg + kFacG < n) zgroup_load(zn, zrow, jg + kFacG);
+        if ((FULL || jg + kFacG < n) && mrf_in_bounds(jg + 2 * kFacG <= ldz && c < g.n_df, err))
+            zgroup_load(zn, zrow, jg + kFacG);
 #pragma unroll
         for (int q = 0; q < kFacG; ++q) {
             vr[q] = 0.f;
@@ -675,8 +677,8 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_xsym_kernel(SeqDev s, Gr
         for (int i = 0; i < 8; ++i) {
             const int r = i * 4 + (lane >> 3);
             const int row = __shfl_sync(0xffffffffu, erow, r);
-            if (row >= 0) {
-                const size_t off = (size_t)row * row_bytes + (size_t)j0 * kBpt + qq * 16;
+            const size_t off = (size_t)row * row_bytes + (size_t)j0 * kBpt + qq * 16;
+            if (row >= 0 && mrf_in_bounds(row < D && (size_t)j0 * kBpt + qq * 16 + 16 <= (size_t)row_bytes, err)) {
                 const uint4 vh = stage_hi[warp][r][qq ^ (r & 7)];
                 __stcs(reinterpret_cast<uint4 *>(out_hi + off), vh);
                 if (kTwo) {
@@ -768,7 +770,7 @@ int launch_dict_generate(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream)
         count_launch(ctx);
         {
             ProfScope prof(ctx, kProfDictGen, stream);
-#define MRF_XGEN(OUT) dict_gen_xsym_kernel<OUT><<<(unsigned)blocks, kGenThreads, 0, stream>>>(s, g, zt, ldz, d->entries, d->ld, hi, lo, d->norm, d->scale)
+#define MRF_XGEN(OUT) dict_gen_xsym_kernel<OUT><<<(unsigned)blocks, kGenThreads, 0, stream>>>(s, g, zt, ldz, d->entries, d->ld, hi, lo, d->norm, d->scale, ctx->err_flag)
             if (d->dtype == MRF_F32) MRF_XGEN(MRF_F32);
             else if (d->dtype == MRF_BF16) MRF_XGEN(MRF_BF16);
             else MRF_XGEN(MRF_FP8E4M3);
@@ -800,7 +802,7 @@ int launch_dict_generate(mrf_ctx *ctx, mrf_dict *d, cudaStream_t stream)
     tables_kernel<<<4 * ctx->sm_count, 256, 0, stream>>>(s, g, e1, e2, cis, e1i);
     count_launch(ctx);
     Tables t{e1, e2, cis, (const float *)e1, (const float *)e2, (const float2 *)cis, e1i};
-#define MRF_GEN(OUT, XO, SY) dict_gen_kernel<OUT, XO, SY><<<(unsigned)blocks, kGenThreads, 0, stream>>>(s, g, t, d->entries, d->ld, hi, lo, d->norm, d->scale)
+#define MRF_GEN(OUT, XO, SY) dict_gen_kernel<OUT, XO, SY><<<(unsigned)blocks, kGenThreads, 0, stream>>>(s, g, t, d->entries, d->ld, hi, lo, d->norm, d->scale, ctx->err_flag)
 #define MRF_GEN_DT(XO, SY)                                        \
     do {                                                          \
         if (d->dtype == MRF_F32) MRF_GEN(MRF_F32, XO, SY);        \

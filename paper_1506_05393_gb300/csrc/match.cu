@@ -557,7 +557,8 @@ struct RescoreSmooth {
 
 template <bool XONLY>
 __global__ void rescore_kernel(SeqDev s, GridDev g, const float2 *x, int64_t V, int K, const int64_t *cand,
-                               const float *cand_cc2, int rank, int64_t D, RescoreSmooth sm, mrf_result *out)
+                               const float *cand_cc2, int rank, int64_t D, RescoreSmooth sm, mrf_result *out,
+                               int *err)
 {
     const int64_t v = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -575,7 +576,7 @@ __global__ void rescore_kernel(SeqDev s, GridDev g, const float2 *x, int64_t V, 
 
     const int ncand = rank ? K : 1;
     const int64_t e = lane < ncand ? cand[(size_t)v * K + lane] : -1;
-    const bool live = e >= 0;
+    const bool live = e >= 0 && mrf_in_bounds(e < D, err);
     int a = 0, b = 0, c = 0;
     if (live) unravel_dev(g, e, a, b, c);
     Relax r = relax_make(live ? g.t1[a] : 1.f, live ? g.t2[b] : 1.f, live ? g.df[c] : 0.f);
@@ -982,9 +983,9 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
         sm.h = d->smooth_h;
         for (int k = 0; k < 3; ++k) sm.w[k] = d->smooth_w[k];
         if (s.xonly)
-            rescore_kernel<true><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, sm, out);
+            rescore_kernel<true><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, sm, out, ctx->err_flag);
         else
-            rescore_kernel<false><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, sm, out);
+            rescore_kernel<false><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, sm, out, ctx->err_flag);
         count_launch(ctx);
         e = cudaGetLastError();
         if (e != cudaSuccess) return finish(cuda_fail(e, "re-score launch"));

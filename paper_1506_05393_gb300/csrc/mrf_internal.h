@@ -190,3 +190,21 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, const 
 
 constexpr int kDeviceErrTimeout = 1;
 constexpr int kDeviceErrBounds = 2;
+
+#ifdef __CUDACC__
+// Bounds-checked builds (compiled with -DMRF_CHECK): an index check that fails
+// records kDeviceErrBounds in the context's error flag (mrf_stream_sync reports
+// it) and the access it guards is skipped. Without MRF_CHECK every check is
+// the constant true and compiles away.
+__device__ __forceinline__ bool mrf_in_bounds(bool ok, int *err)
+{
+#ifdef MRF_CHECK
+    if (!ok && err) atomicExch(err, kDeviceErrBounds);
+    return ok;
+#else
+    (void)ok;
+    (void)err;
+    return true;
+#endif
+}
+#endif
