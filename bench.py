@@ -686,6 +686,26 @@ def C_pointer(x):
     return ctypes.pointer(x)
 
 
+def host_cpu():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip() + f" ({platform.machine()})"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip() + f" ({platform.machine()})"
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(seq, x_np):
     """The FP64 oracle on a bounded sample of the same workload: its brute
     force over the full 614,508-entry grid for 1 and for 9 voxels. The
@@ -705,7 +725,7 @@ def cpu_baseline(seq, x_np):
     t_cc = max((t9 - t1) / 8.0, 1e-9)
     t_sim = max(t1 - t_cc, 0.0)
     value = V_SLICE / (t_sim + V_SLICE * t_cc)
-    return {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    return {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "cpu": host_cpu(), "kind": "oracle",
             "sample": f"FP64 oracle brute force over the full 614,508-entry grid for 1 and 9 voxels "
                       f"({t1:.1f} s, {t9:.1f} s): t_sim {t_sim:.2f} s + 4096 x t_cc {t_cc:.3f} s/voxel "
                       f"extrapolated to the 64x64 slice",
