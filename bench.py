@@ -760,7 +760,7 @@ def run_reference(args, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "64x64 slice, N=1000, 614,508-entry grid, brute-force DGS (FP64 CPU oracle)",
                        "sample_wall_s_per_step": statistics.median(times)},
-            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": last["cores"],
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": last["cores"], "cpu": last["cpu"],
                              "sample": last["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
