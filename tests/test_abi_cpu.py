@@ -95,3 +95,24 @@ def test_result_struct_layout(M):
     assert M.RESULT_DTYPE.itemsize == 56
     assert M.RESULT_DTYPE.fields["index"][1] == 0
     assert M.RESULT_DTYPE.fields["min_margin"][1] == 48
+
+
+def test_bounds_checked_variant_compiles_and_is_kept_apart(tmp_path):
+    """The bounds-checked variant (MRF_BUILD_VARIANT=check) builds into its own
+    folder, and the translation units with device index checks compile with
+    -DMRF_CHECK for sm_103a (nvcc cross-compiles without a GPU)."""
+    code = ("import paper_1506_05393_gb300._build as b; print(b.VARIANT, b.LIB)")
+    env = dict(os.environ, MRF_BUILD_VARIANT="check")
+    out = subprocess.run(["python", "-c", code], env=env, cwd=ROOT, capture_output=True, text=True, check=True)
+    variant, lib = out.stdout.split()
+    assert variant == "check" and os.path.basename(os.path.dirname(lib)) == "_build_check"
+    bad = subprocess.run(["python", "-c", code], env=dict(os.environ, MRF_BUILD_VARIANT="fast"), cwd=ROOT,
+                         capture_output=True, text=True)
+    assert bad.returncode != 0 and "MRF_BUILD_VARIANT" in bad.stderr
+    from paper_1506_05393_gb300 import _build
+    csrc = os.path.join(ROOT, "paper_1506_05393_gb300", "csrc")
+    for name in ("bloch.cu", "match.cu"):
+        r = subprocess.run([_build._nvcc(), *_build.ARCH, "-O1", "-std=c++17", "--expt-relaxed-constexpr",
+                            "-DMRF_CHECK", "-I", os.path.join(ROOT, "include"), "-c", os.path.join(csrc, name),
+                            "-o", str(tmp_path / (name + ".o"))], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-3000:]
