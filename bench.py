@@ -708,7 +708,7 @@ def host_cpu():
 
 def cpu_baseline(seq, x_np):
     """The FP64 oracle on a bounded sample of the same workload: its brute
-    force over the full 614,508-entry grid for 1 and for 9 voxels. The
+    force over the full 614,508-entry grid for 1 and for 65 voxels. The
     difference gives the per-voxel correlation time t_cc, the rest the
     dictionary simulation time t_sim; a 4096-voxel slice is extrapolated
     as t_sim + 4096 t_cc."""
@@ -720,14 +720,14 @@ def cpu_baseline(seq, x_np):
     oracle.bruteforce(seq, g, x[:1], k=1)
     t1 = time.perf_counter() - t0
     t0 = time.perf_counter()
-    oracle.bruteforce(seq, g, x[1:10], k=1)
-    t9 = time.perf_counter() - t0
-    t_cc = max((t9 - t1) / 8.0, 1e-9)
+    oracle.bruteforce(seq, g, x[1:66], k=1)
+    t65 = time.perf_counter() - t0
+    t_cc = max((t65 - t1) / 64.0, 1e-9)
     t_sim = max(t1 - t_cc, 0.0)
     value = V_SLICE / (t_sim + V_SLICE * t_cc)
     return {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "cpu": host_cpu(), "kind": "oracle",
-            "sample": f"FP64 oracle brute force over the full 614,508-entry grid for 1 and 9 voxels "
-                      f"({t1:.1f} s, {t9:.1f} s): t_sim {t_sim:.2f} s + 4096 x t_cc {t_cc:.3f} s/voxel "
+            "sample": f"FP64 oracle brute force over the full 614,508-entry grid for 1 and 65 voxels "
+                      f"({t1:.1f} s, {t65:.1f} s): t_sim {t_sim:.2f} s + 4096 x t_cc {t_cc:.4f} s/voxel "
                       f"extrapolated to the 64x64 slice",
             "t_sim_s": t_sim, "t_cc_s_per_voxel": t_cc}
 
@@ -740,9 +740,9 @@ def run_reference(args, rank):
     seq = S.sequence(1, N_TP)
     import oracle
     oracle.build()
-    ph = S.phantom_offgrid(101, 10)
+    ph = S.phantom_offgrid(101, 66)
     clean = oracle.simulate(seq, ph["t1"], ph["t2"], ph["df"])
-    x = S.compose_voxels(clean, ph["m0"], ph["phase"], *S.noise_draws(101, 10, N_TP), 20.0)
+    x = S.compose_voxels(clean, ph["m0"], ph["phase"], *S.noise_draws(101, 66, N_TP), 20.0)
     vals = []
     times = []
     last = None
