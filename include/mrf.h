@@ -85,7 +85,11 @@ int mrf_ctx_memory(const mrf_ctx *ctx, size_t *used_bytes, size_t *budget_bytes)
 /* Synchronise `stream` and report device-side failures of the context's
  * kernels since the last check: MRF_E_TIMEOUT when a kernel's bounded wait ran
  * out (the kernel returned early, its outputs are invalid, the context stays
- * usable). Asynchronous entry points report such failures only here. */
+ * usable); MRF_E_CUDA when a device-side index check failed (the access was
+ * skipped; ZOOM and refinement check their grid points in every build, the
+ * bounds-checked build compiled with -DMRF_CHECK checks the dictionary and
+ * re-score kernels as well). The flag is cleared on report. Asynchronous entry
+ * points report such failures only here. */
 int mrf_stream_sync(mrf_ctx *ctx, void *stream);
 
 /* Kernel accounting (no counterpart in the paper; used to measure the
@@ -109,6 +113,8 @@ typedef struct {
      * and the most rounds one voxel spent in flight within a launch */
     uint64_t zoom_rounds, zoom_candidates, zoom_max_voxel_rounds;
 } mrf_profile;
+/* on != 0 starts recording the CUDA events behind the *_ms fields, 0 stops
+ * it (launch counts and work counters are kept either way). */
 int mrf_profile_enable(mrf_ctx *ctx, int on);
 /* Synchronises the device (pending profile events, work counters). reset != 0
  * zeroes all counters. */
@@ -462,6 +468,9 @@ typedef struct {
     uint64_t queued_now, running_now;
     size_t request_bytes_in_use, request_bytes_peak;
 } mrf_serve_stats;
+/* A snapshot of the serving counters (request counts by fate, shared launches,
+ * requests queued and running now, request bytes charged now and at peak).
+ * Errors: MRF_E_INVALID (NULL argument or no serving loop started). */
 int mrf_serve_get_stats(mrf_ctx *ctx, mrf_serve_stats *stats);
 
 /* Stop accepting work, finish what is admitted, join the thread. */
