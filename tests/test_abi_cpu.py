@@ -89,6 +89,8 @@ def test_null_arguments_rejected(M):
     assert L.mrf_match_bruteforce(None, None, None, 0, None, None, None) == M.MRF_E_INVALID
     assert L.mrf_zoom_search(None, None, None, None, None, 0, None, None) == M.MRF_E_INVALID
     assert "NULL" in M.last_error()
+    assert L.mrf_match_bruteforce_grid(None, None, None, None, 0, None, 0, None, None) == M.MRF_E_INVALID
+    assert "NULL" in M.last_error()
 
 
 def test_result_struct_layout(M):
