@@ -51,3 +51,24 @@ def test_single_process_needs_no_group():
     import bench
     assert bench.reduce_max(12.5, None) == 12.5
     assert bench.whole_job_rate(1, 4096, 40.0) == pytest.approx(102400.0)
+
+
+def test_bench_starts_its_own_ranks():
+    """`bench.py --gpus 2` without a launcher starts two ranks itself
+    (torch.distributed.run on 127.0.0.1); the GPU-free dry run checks that
+    both ranks join, and that rank 0 alone prints the line with n_gpus 2."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR",
+                                                             "MASTER_PORT")}
+    p = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--dry-run", "--steps", "3",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=300, env=env, cwd=root)
+    assert p.returncode == 0, p.stderr[-2000:]
+    assert "rank 0 of 2 ready" in p.stderr and "rank 1 of 2 ready" in p.stderr
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    out = json.loads(lines[-1])
+    assert out["n_gpus"] == 2 and out["steps"] == 3 and out["dry_run"] is True
+    assert out["value"] == pytest.approx(2 * 4096 / out["ms_per_step"] * 1e3)
