@@ -293,49 +293,64 @@ class _SubGrid:
         self.require_t2_lt_t1 = g.require_t2_lt_t1
 
 
-def prior_neighbours(V: int, width: int, stride: int):
-    """First-pass voxels (every stride-th row and column of a row-major slice
-    `width` voxels wide) and, for every voxel, the first-pass voxel whose
-    result bounds its search (itself for first-pass voxels)."""
-    v = np.arange(V)
-    r, c = v // width, v % width
-    first = (r % stride == 0) & (c % stride == 0)
-    nb = (r - r % stride) * width + (c - c % stride)
-    return first, nb
-
-
 def prior_box(g, abc_p, half):
     """Index box of the grid points within `half` = (T1, T2, df) half-widths of
-    the neighbour's grid point abc_p, overlapped with the grid."""
+    the preceding voxel's grid point abc_p, overlapped with the grid (Methods,
+    Experiment 3: the ranges T1p +- 3000, T2p +- 800, dfp +- 150 overlapped
+    with the original searching ranges)."""
     h = [int(math.floor(w / st + 1e-9)) for w, st in zip(half, (g.t1_step, g.t2_step, g.df_step))]
     n = (g.n_t1, g.n_t2, g.n_df)
     return [(max(0, int(abc_p[k]) - h[k]), min(n[k] - 1, int(abc_p[k]) + h[k])) for k in range(3)]
 
 
-def zoom_prior(seq, g, x, width: int, stride: int = 4, half=(3000.0, 800.0, 150.0), opts=None):
-    """MRF-ZOOM with the spatial-neighbour prior (Methods, Experiment 3): each
-    voxel's search runs on the original ranges overlapped with T1p +- 3000 ms,
-    T2p +- 800 ms, dfp +- 150 Hz around a neighbour's result (T1p, T2p, dfp).
-    The neighbour is a first-pass voxel (prior_neighbours): first-pass voxels
-    are searched on the whole grid, every other voxel on its box, as a search
-    on that sub-grid. Returns zoom()'s dict (global indices) plus `box`."""
+def zoom_prior_one(seq, g, x, abc_p, half=(3000.0, 800.0, 150.0), start_from_prior=True, opts=None):
+    """One voxel's MRF-ZOOM under the spatial-neighbour prior (Methods,
+    Experiment 3): the search runs on the grid overlapped with the ranges
+    around the preceding voxel's result abc_p, as a search on that sub-grid
+    of its own; with start_from_prior the ZOOM starts at the preceding voxel's
+    (T1, T2) (Theory, 1D ZOOM: the initial centre may be the parameter value
+    of the neighbouring voxel), else at the options' start clipped into the
+    ranges. Returns zoom()'s dict for this voxel (global indices) plus `box`."""
+    (a0, a1), (b0, b1), (c0, c1) = prior_box(g, abc_p, half)
+    sub = _SubGrid(g, a0, a1, b0, b1, c0, c1)
+    o = opts if opts is not None else default_zoom_opts()
+    if start_from_prior:
+        o2 = OrZoomOpts()
+        C.pointer(o2)[0] = o
+        o2.t1_init_ms = g.t1_min + int(abc_p[0]) * g.t1_step
+        o2.t2_init_ms = g.t2_min + int(abc_p[1]) * g.t2_step
+        o = o2
+    r = zoom(seq, sub, np.atleast_2d(x), o)
+    out = {k: r[k][0] for k in ("cc", "m0", "phase", "evaluated", "min_margin")}
+    out["abc"] = r["abc"][0] + np.array([a0, b0, c0], np.int32)
+    out["box"] = np.array([a0, a1, b0, b1, c0, c1], np.int32)
+    return out
+
+
+def zoom_prior(seq, g, x, chain=None, half=(3000.0, 800.0, 150.0), start_from_prior=True, opts=None):
+    """MRF-ZOOM with the spatial-neighbour prior (Methods, Experiment 3), in
+    the voxels' given (raster) order: each voxel's search is bounded by, and
+    (with start_from_prior) started from, the result of the voxel before it.
+    chain = None is the paper's single chain through all voxels; chain = L
+    cuts the voxels into consecutive chains of L, the first voxel of each
+    searched on the whole grid like the first voxel of the slice. A plain
+    sequential loop; returns zoom()'s dict (global indices) plus `box`."""
     x = np.atleast_2d(x)
     V = x.shape[0]
-    first, nb = prior_neighbours(V, width, stride)
+    L = V if chain is None else int(chain)
+    if L < 1:
+        raise ValueError("chain length must be >= 1")
     out = dict(abc=np.zeros((V, 3), np.int32), cc=np.zeros(V), m0=np.zeros(V), phase=np.zeros(V),
                evaluated=np.zeros(V, np.int32), min_margin=np.zeros(V), box=np.zeros((V, 6), np.int32))
-    idx1 = np.nonzero(first)[0]
-    r1 = zoom(seq, g, x[idx1], opts)
-    for k in ("abc", "cc", "m0", "phase", "evaluated", "min_margin"):
-        out[k][idx1] = r1[k]
-    out["box"][idx1] = [0, g.n_t1 - 1, 0, g.n_t2 - 1, 0, g.n_df - 1]
-    for v in np.nonzero(~first)[0]:
-        (a0, a1), (b0, b1), (c0, c1) = prior_box(g, out["abc"][nb[v]], half)
-        r = zoom(seq, _SubGrid(g, a0, a1, b0, b1, c0, c1), x[v:v + 1], opts)
-        out["abc"][v] = r["abc"][0] + np.array([a0, b0, c0], np.int32)
-        for k in ("cc", "m0", "phase", "evaluated", "min_margin"):
-            out[k][v] = r[k][0]
-        out["box"][v] = [a0, a1, b0, b1, c0, c1]
+    for v in range(V):
+        if v % L == 0:
+            r = zoom(seq, g, x[v:v + 1], opts)
+            r = {k: r[k][0] for k in r}
+            r["box"] = np.array([0, g.n_t1 - 1, 0, g.n_t2 - 1, 0, g.n_df - 1], np.int32)
+        else:
+            r = zoom_prior_one(seq, g, x[v], out["abc"][v - 1], half, start_from_prior, opts)
+        for k in out:
+            out[k][v] = r[k]
     return out
 
 

@@ -474,22 +474,97 @@ def test_smoothed_bruteforce_recovers_on_grid_voxels(oracle_lib):
 # ---------------------------------------------------------------------------
 # Spatial-neighbour prior (Methods, Experiment 3)
 
-def test_prior_neighbours_and_box_by_hand(oracle_lib):
-    """First-pass voxels of a 4 x 4 slice at stride 2 and their neighbours,
-    and the index box of T1p +- 100 ms on a 20 ms axis (5 steps each way,
-    cut by the axis ends)."""
-    first, nb = oracle_lib.prior_neighbours(16, 4, 2)
-    assert list(np.nonzero(first)[0]) == [0, 2, 8, 10]
-    assert [int(nb[v]) for v in (0, 1, 4, 5, 7, 13, 15)] == [0, 0, 0, 0, 2, 8, 10]
+def _box_by_enumeration(g, abc_p, half):
+    """The index box of the axis values within the half-widths of the
+    preceding voxel's values, found by scanning each axis (no step formula)."""
+    axes = [(g.t1_min, g.t1_step, g.n_t1), (g.t2_min, g.t2_step, g.n_t2), (g.df_min, g.df_step, g.n_df)]
+    box = []
+    for (mn, st, n), p, h in zip(axes, abc_p, half):
+        inside = [i for i in range(n) if abs((mn + i * st) - (mn + p * st)) <= h + 1e-9]
+        box.append((min(inside), max(inside)))
+    return box
+
+
+def test_prior_box_by_hand(oracle_lib):
+    """The index box of T1p +- 100 ms on a 20 ms axis is 5 steps each way,
+    cut by the axis ends; the paper's windows (3000, 800, 150) cover most of
+    this grid."""
     g = S.GRIDS["fp32_brute"]   # T1 step 20 ms (196), T2 step 5 ms (79), df step 2 Hz (41)
     assert oracle_lib.prior_box(g, (10, 40, 20), (100.0, 50.0, 6.0)) == [(5, 15), (30, 50), (17, 23)]
     assert oracle_lib.prior_box(g, (2, 77, 0), (100.0, 50.0, 6.0)) == [(0, 7), (67, 78), (0, 3)]
     assert oracle_lib.prior_box(g, (2, 77, 0), (3000.0, 800.0, 150.0)) == [(0, 152), (0, 78), (0, 40)]
+    for p in ((0, 0, 0), (195, 78, 40), (97, 12, 33)):
+        for half in ((100.0, 50.0, 6.0), (55.0, 7.5, 1.0), (3000.0, 800.0, 150.0)):
+            assert oracle_lib.prior_box(g, p, half) == _box_by_enumeration(g, p, half)
+
+
+def _uniform_slice(oracle_lib, seq, t1, t2, df, v, seed):
+    """v noise-free voxels of one (T1, T2, df), each with its own M0 and phase."""
+    rng = np.random.default_rng(seed)
+    clean = oracle_lib.simulate(seq, np.full(v, t1), np.full(v, t2), np.full(v, df))
+    return clean * (rng.uniform(0.5, 1.0, v) * np.exp(1j * rng.uniform(0, 2 * np.pi, v)))[:, None]
+
+
+def test_prior_chain_started_at_the_optimum_by_hand(oracle_lib):
+    """A 3 x 3 slice of one on-grid tissue (noise-free), on the tiny grid (T1
+    100-2000/100 ms, T2 20-200/20 ms, df 0): voxel 0 is searched plainly and
+    finds the point (a, b) = (13, 4), i.e. 1400 / 100 ms; every later voxel
+    starts at its predecessor's result, which is its own optimum (CC 1), so no
+    decision moves and its evaluation count is that of the schedule's
+    decisions around (13, 4), counted by hand: step 1 one df point; step 2 at
+    (2, 10) steps only (11, 4) and (15, 4) exist, at (1, 5) the five points
+    with b = 4 or 9; step 4 T1 at 1 step 2, T2 at 5 steps 1 (b = 9), T1 at 1
+    step 2, T2 at 3 steps 2, T2 at 1 step 2 (T1 at 20 and 10 ms snap to the
+    same 1-step level and are dropped, as is T2 at 10 ms); step 5 eight:
+    1 + 2 + 5 + 2 + 1 + 2 + 2 + 2 + 8 = 25."""
+    seq = S.sequence(0, 200)
+    g = S.GRIDS["tiny"]
+    x = _uniform_slice(oracle_lib, seq, 1400.0, 100.0, 0.0, 9, 11)
+    r = oracle_lib.zoom_prior(seq, g, x)
+    assert [tuple(v) for v in r["abc"]] == [(13, 4, 0)] * 9
+    np.testing.assert_allclose(r["cc"], 1.0, atol=1e-12)
+    assert list(r["evaluated"][1:]) == [25] * 8
+    assert r["evaluated"][0] > 25          # the first voxel walks from the default start
+    for v in range(1, 9):
+        assert tuple(r["box"][v]) == (0, 19, 0, 9, 0, 0)   # the paper's windows cover this grid
+
+
+def test_prior_chain_follows_the_preceding_voxel(oracle_lib):
+    """Voxels alternate between two tissues, (1400, 100) ms and (600, 40) ms,
+    on the tiny grid with narrow windows (T1p +- 300 ms, T2p +- 40 ms): each
+    voxel's box is the enumerated box around its predecessor's result, every
+    result lies in its box, and a (600, 40) voxel after a (1400, 100) one
+    cannot reach its own point. Cut into chains of 3, the first voxel of each
+    chain is searched on the whole grid and finds its own point, and the
+    chain's first voxels equal the single chain's."""
+    seq = S.sequence(0, 200)
+    g = S.GRIDS["tiny"]
+    xa = _uniform_slice(oracle_lib, seq, 1400.0, 100.0, 0.0, 5, 12)
+    xb = _uniform_slice(oracle_lib, seq, 600.0, 40.0, 0.0, 4, 13)
+    x = np.stack([xa[0], xb[0], xa[1], xb[1], xa[2], xb[2], xa[3], xb[3], xa[4]])
+    half = (300.0, 40.0, 0.0)
+    r = oracle_lib.zoom_prior(seq, g, x, half=half)
+    for v in range(1, 9):
+        box = _box_by_enumeration(g, r["abc"][v - 1], half)
+        assert tuple(r["box"][v]) == (box[0][0], box[0][1], box[1][0], box[1][1], box[2][0], box[2][1])
+        for k in range(3):
+            assert box[k][0] <= r["abc"][v][k] <= box[k][1]
+    assert tuple(r["abc"][0]) == (13, 4, 0)
+    assert tuple(r["abc"][1]) != (5, 1, 0)       # (600, 40) lies outside the box around (1400, 100)
+    assert abs(int(r["abc"][1][0]) - 13) <= 3
+    r3 = oracle_lib.zoom_prior(seq, g, x, chain=3, half=half)
+    for v in (0, 3, 6):
+        assert tuple(r3["box"][v]) == (0, 19, 0, 9, 0, 0)
+    assert [tuple(r3["abc"][v]) for v in (0, 3, 6)] == [(13, 4, 0), (5, 1, 0), (13, 4, 0)]
+    assert tuple(r3["abc"][4]) != (13, 4, 0) and abs(int(r3["abc"][4][0]) - 5) <= 3   # bounded by voxel 3
+    for k in ("abc", "evaluated", "cc"):
+        assert np.array_equal(r3[k][:3], r[k][:3]), k
 
 
 def test_prior_covering_the_grid_changes_nothing(oracle_lib):
-    """With windows wider than every axis the sub-grid is the grid: the prior
-    search returns exactly the plain search's results."""
+    """With windows wider than every axis and the start left at the options'
+    start, the sub-grid is the grid: the prior search returns exactly the
+    plain search's results."""
     seq = S.sequence(0, 200)
     g = S.GRIDS["fp32_brute"]
     ph = S.phantom_piecewise(5, 4, 4)
@@ -497,16 +572,17 @@ def test_prior_covering_the_grid_changes_nothing(oracle_lib):
     g_re, g_im = S.noise_draws(5, 16, seq.n)
     x = S.compose_voxels(clean, ph["m0"], ph["phase"], g_re, g_im, 30.0)
     plain = oracle_lib.zoom(seq, g, x)
-    pri = oracle_lib.zoom_prior(seq, g, x, 4, 2, (1e6, 1e6, 1e6))
+    pri = oracle_lib.zoom_prior(seq, g, x, half=(1e6, 1e6, 1e6), start_from_prior=False)
     for k in ("abc", "evaluated"):
         assert np.array_equal(plain[k], pri[k]), k
     assert np.array_equal(plain["cc"], pri["cc"])
 
 
 def test_prior_results_lie_in_their_boxes(oracle_lib):
-    """Narrow windows (T1p +- 200 ms, T2p +- 30 ms, dfp +- 6 Hz): every
-    second-pass result lies in the box of its neighbour's result, and equals
-    the plain search on that box's sub-grid."""
+    """Narrow windows (T1p +- 200 ms, T2p +- 30 ms, dfp +- 6 Hz) on a noisy
+    piecewise-smooth 4 x 4 slice: every result lies in the box around its
+    predecessor's result, and starts from it, so it equals the plain search
+    on that box's sub-grid started at the predecessor's (T1, T2)."""
     seq = S.sequence(0, 200)
     g = S.GRIDS["fp32_brute"]
     ph = S.phantom_piecewise(6, 4, 4)
@@ -514,16 +590,17 @@ def test_prior_results_lie_in_their_boxes(oracle_lib):
     g_re, g_im = S.noise_draws(6, 16, seq.n)
     x = S.compose_voxels(clean, ph["m0"], ph["phase"], g_re, g_im, 30.0)
     half = (200.0, 30.0, 6.0)
-    pri = oracle_lib.zoom_prior(seq, g, x, 4, 2, half)
-    first, nb = oracle_lib.prior_neighbours(16, 4, 2)
-    for v in np.nonzero(~first)[0]:
-        box = oracle_lib.prior_box(g, pri["abc"][nb[v]], half)
+    pri = oracle_lib.zoom_prior(seq, g, x, half=half)
+    for v in range(1, 16):
+        box = _box_by_enumeration(g, pri["abc"][v - 1], half)
         assert list(pri["box"][v]) == [box[0][0], box[0][1], box[1][0], box[1][1], box[2][0], box[2][1]]
         for k in range(3):
             assert box[k][0] <= pri["abc"][v][k] <= box[k][1]
-    v = int(np.nonzero(~first)[0][0])
-    (a0, a1), (b0, b1), (c0, c1) = oracle_lib.prior_box(g, pri["abc"][nb[v]], half)
+    v = 7
+    (a0, a1), (b0, b1), (c0, c1) = _box_by_enumeration(g, pri["abc"][v - 1], half)
     sub = S.Grid(g.t1_min + a0 * g.t1_step, g.t1_step, a1 - a0 + 1, g.t2_min + b0 * g.t2_step, g.t2_step, b1 - b0 + 1,
                  g.df_min + c0 * g.df_step, g.df_step, c1 - c0 + 1)
-    r = oracle_lib.zoom(seq, sub, x[v:v + 1])
+    p = pri["abc"][v - 1]
+    o = oracle_lib.default_zoom_opts(t1_init_ms=g.t1_min + p[0] * g.t1_step, t2_init_ms=g.t2_min + p[1] * g.t2_step)
+    r = oracle_lib.zoom(seq, sub, x[v:v + 1], o)
     assert list(r["abc"][0] + np.array([a0, b0, c0])) == list(pri["abc"][v])
