@@ -13,7 +13,10 @@ Contents
   stand-in recipe used throughout is: flip angle
   ``alpha_j = (-1)^j (10 + 50 |sin(pi j / 250)| + u_j)`` degrees with
   ``u_j ~ U(0, 5)``, ``TR_j ~ U(10.5, 14)`` ms, ``TE_j = TR_j / 2``, preceded
-  by an ideal 180 degree inversion and a 20 ms delay.
+  by an ideal 180 degree inversion and a 20 ms delay. ``sequence_paper`` is a
+  seeded stand-in shaped like the paper's recipe (gradient-noise flip angles,
+  0/90/180 degree phases, Gaussian TRs), and ``with_pulses`` gives any train
+  RF pulses of finite duration (the Appendix's off-resonant RF form).
 * ``GRIDS``: the (T1, T2, df) search grids of the workloads, as plain numbers.
 * ``phantom_*``: per-voxel true parameters, proton density, global phase and
   standard-normal noise draws.
@@ -30,7 +33,7 @@ from dataclasses import dataclass, asdict
 import numpy as np
 
 __all__ = [
-    "Sequence", "Grid", "GRIDS", "sequence", "grid_values", "grid_valid_params", "phantom_piecewise",
+    "Sequence", "Grid", "GRIDS", "sequence", "sequence_paper", "with_pulses", "grid_values", "grid_valid_params", "phantom_piecewise",
     "phantom_offgrid", "phantom_ongrid", "noise_draws", "compose_voxels",
     "write_sequence", "read_sequence",
 ]
@@ -45,10 +48,52 @@ class Sequence:
     te_ms: np.ndarray         # (n,) float64
     inversion: int = 1
     inv_delay_ms: float = 20.0
+    pulse_ms: np.ndarray | None = None   # (n,) RF pulse durations in ms; None: hard pulses
 
     @property
     def n(self) -> int:
         return int(self.flip_rad.shape[0])
+
+
+def with_pulses(seq: Sequence, tau_ms) -> Sequence:
+    """The same train with RF pulses of duration tau_ms (scalar or (n,))."""
+    from dataclasses import replace
+    return replace(seq, pulse_ms=np.broadcast_to(np.asarray(tau_ms, np.float64), (seq.n,)).copy())
+
+
+def _gradient_noise_1d(rng, n: int, cell: float) -> np.ndarray:
+    """Perlin's gradient noise in one dimension (K. Perlin, "Improving noise",
+    SIGGRAPH 2002): a random gradient in [-1, 1] at each lattice point (spacing
+    `cell` samples), the contribution g_i (x - i) of the two neighbouring
+    lattice points blended with the quintic fade 6t^5 - 15t^4 + 10t^3."""
+    x = np.arange(n) / cell
+    i0 = np.floor(x).astype(np.int64)
+    g = rng.uniform(-1.0, 1.0, int(i0.max()) + 2)
+    t = x - i0
+    fade = t * t * t * (t * (t * 6.0 - 15.0) + 10.0)
+    return (1.0 - fade) * g[i0] * t + fade * g[i0 + 1] * (t - 1.0)
+
+
+def sequence_paper(seed: int, n: int, pulse_ms=None) -> Sequence:
+    """A stand-in for the paper's own train (Methods, Experiment 1), whose
+    noise parameters and seed are unpublished: flip angles from 1D gradient
+    (Perlin) noise rescaled to 0-79 degrees, RF phases oscillating 0, 90,
+    180, 90, 0, ... degrees, TR from Gaussian noise remapped to 0-6 ms plus
+    the 14 ms minimum, TE = TR / 2, an ideal inversion and a 20 ms delay;
+    optional RF pulse durations. Draw order: gradients, then the TR noise."""
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    rng = np.random.default_rng(seed)
+    p = _gradient_noise_1d(rng, n, 40.0)
+    span = p.max() - p.min()
+    deg = 79.0 * (p - p.min()) / span if span > 0 else np.zeros(n)
+    g = rng.normal(0.0, 1.0, n)
+    gs = g.max() - g.min()
+    tr = 14.0 + (6.0 * (g - g.min()) / gs if gs > 0 else np.zeros(n))
+    phase = np.deg2rad(np.array([0.0, 90.0, 180.0, 90.0])[np.arange(n) % 4])
+    seq = Sequence(flip_rad=np.deg2rad(deg), rf_phase_rad=phase, tr_ms=tr, te_ms=tr / 2.0, inversion=1,
+                   inv_delay_ms=20.0)
+    return seq if pulse_ms is None else with_pulses(seq, pulse_ms)
 
 
 def sequence(seed: int, n: int) -> Sequence:

@@ -6,7 +6,8 @@ never imports the GPU library; the two share only ``mrf_synth`` (random draws).
 
 Every function follows the paper directly:
   * ``simulate`` / ``simulate_state``: Appendix Eq. A2 with the hard-pulse RF
-    form and the recovery term of Eq. A1.
+    form (or, for pulses of finite duration, the Appendix's off-resonant
+    effective-field form) and the recovery term of Eq. A1.
   * ``cc``: Eq. 1.
   * ``bruteforce``: argmax of Eq. 1 over every valid grid entry.
   * ``zoom`` / ``zoom_generic``: MRF-ZOOM, Theory (df search steps 1-4, Fig. 1
@@ -38,7 +39,7 @@ MAX_LEVELS = 16
 class OrSeq(C.Structure):
     _fields_ = [("n", C.c_int32), ("flip", C.POINTER(C.c_double)), ("phase", C.POINTER(C.c_double)),
                 ("tr", C.POINTER(C.c_double)), ("te", C.POINTER(C.c_double)),
-                ("inversion", C.c_int32), ("inv_delay", C.c_double)]
+                ("inversion", C.c_int32), ("inv_delay", C.c_double), ("pulse", C.POINTER(C.c_double))]
 
 
 class OrGrid(C.Structure):
@@ -125,9 +126,12 @@ class _SeqHandle:
         self.phase = np.ascontiguousarray(seq.rf_phase_rad, np.float64) if seq.rf_phase_rad is not None else None
         self.tr = np.ascontiguousarray(seq.tr_ms, np.float64)
         self.te = np.ascontiguousarray(seq.te_ms, np.float64)
+        pulse = getattr(seq, "pulse_ms", None)
+        self.pulse = np.ascontiguousarray(pulse, np.float64) if pulse is not None else None
         self.c = OrSeq(int(self.flip.shape[0]), _dp(self.flip),
                        _dp(self.phase) if self.phase is not None else C.POINTER(C.c_double)(),
-                       _dp(self.tr), _dp(self.te), int(seq.inversion), float(seq.inv_delay_ms))
+                       _dp(self.tr), _dp(self.te), int(seq.inversion), float(seq.inv_delay_ms),
+                       _dp(self.pulse) if self.pulse is not None else C.POINTER(C.c_double)())
 
 
 def _grid(g) -> OrGrid:

@@ -10,7 +10,9 @@
  * What it computes, and where the paper defines it:
  *   - Bloch propagation, Appendix Eq. A2 (M <- R_off R_relax R_RF M) with the
  *     hard-pulse RF form R_RF = R_z(phi) R_x(-alpha) R_z(-phi) stated at the
- *     end of the Appendix, and the longitudinal recovery term of Eq. A1.
+ *     end of the Appendix, and the longitudinal recovery term of Eq. A1; for
+ *     pulses of finite duration tau the Appendix's off-resonant form
+ *     R_RF = R_z(phi) R_y(beta) R_x(alpha') R_y(-beta) R_z(-phi).
  *   - Complex correlation coefficient, Eq. 1 (Theory).
  *   - Brute-force DGS: argmax of Eq. 1 over every grid entry (Theory, "the
  *     original DGS"; Experiment 2).
@@ -57,6 +59,7 @@ typedef struct {
     const double *te;      /* TE_j in ms, 0 <= TE_j <= TR_j */
     int32_t inversion;     /* 1: ideal 180 degree pulse, then inv_delay */
     double inv_delay;      /* ms */
+    const double *pulse;   /* RF pulse duration tau_j in ms, NULL means all hard (0) */
 } or_seq;
 
 typedef struct {
@@ -102,11 +105,40 @@ static void rot_z(double th, double M[3])
     M[1] = s * x + c * y;
 }
 
+static void rot_y(double th, double M[3])
+{
+    double c = cos(th), s = sin(th);
+    double x = M[0], z = M[2];
+    M[0] = c * x + s * z;
+    M[2] = -s * x + c * z;
+}
+
 /* Hard pulse: R_RF = R_z(phi) R_x(-alpha) R_z(-phi), applied right to left. */
 static void rf_pulse(double alpha, double phi, double M[3])
 {
     rot_z(-phi, M);
     rot_x(-alpha, M);
+    rot_z(phi, M);
+}
+
+/* Pulse of duration tau ms off resonance by df Hz (Appendix): R_RF =
+ * R_z(phi) R_y(beta) R_x(alpha') R_y(-beta) R_z(-phi) with beta the angle
+ * between the x axis and the effective field, tan(beta) = tau dw / alpha,
+ * and alpha' = -tau sqrt(dw^2 + (alpha / tau)^2) the rotation about it over
+ * the pulse, dw = 2 pi df / 1000 rad/ms. beta is taken as atan2(tau dw,
+ * alpha), which is the printed arctangent for alpha > 0 and keeps the signed
+ * (alternating) flip angles and alpha = 0 on the same effective field; tau = 0
+ * is the hard pulse. No relaxation acts during the pulse (R_RF has none). */
+static void rf_pulse_finite(double alpha, double phi, double tau, double df, double M[3])
+{
+    if (!(tau > 0.0)) { rf_pulse(alpha, phi, M); return; }
+    double tdw = tau * 2.0 * M_PI * df / 1000.0;
+    double beta = atan2(tdw, alpha);
+    double ap = -sqrt(alpha * alpha + tdw * tdw);
+    rot_z(-phi, M);
+    rot_y(-beta, M);
+    rot_x(ap, M);
+    rot_y(beta, M);
     rot_z(phi, M);
 }
 
@@ -123,7 +155,8 @@ static void free_evolve(double tau, double T1, double T2, double df, double M[3]
 }
 
 /* One fingerprint. Start state (0,0,1) unless m_init is given. For each j:
- * RF pulse, evolve TE_j, sample s_j = Mx + i My, evolve TR_j - TE_j.
+ * RF pulse (hard, or of duration tau_j), evolve TE_j, sample s_j = Mx + i My,
+ * evolve TR_j - TE_j. The inversion is an ideal hard pulse.
  * sig: n interleaved (re, im). state (optional): n x 3 state at each sample. */
 static void simulate_one(const or_seq *s, double T1, double T2, double df,
                          const double *m_init, double *sig, double *state)
@@ -135,7 +168,7 @@ static void simulate_one(const or_seq *s, double T1, double T2, double df,
         free_evolve(s->inv_delay, T1, T2, df, M);
     }
     for (int32_t j = 0; j < s->n; ++j) {
-        rf_pulse(s->flip[j], s->phase ? s->phase[j] : 0.0, M);
+        rf_pulse_finite(s->flip[j], s->phase ? s->phase[j] : 0.0, s->pulse ? s->pulse[j] : 0.0, df, M);
         free_evolve(s->te[j], T1, T2, df, M);
         if (sig) { sig[2 * j] = M[0]; sig[2 * j + 1] = M[1]; }
         if (state) { state[3 * j] = M[0]; state[3 * j + 1] = M[1]; state[3 * j + 2] = M[2]; }

@@ -31,6 +31,81 @@ def _seq(n, flip, tr, te, inversion=0, delay=0.0, phase=None):
     return S.Sequence(flip, ph, tr, te, inversion, delay)
 
 
+# ------------------------------------------------ finite RF pulses (Appendix)
+
+def _bloch_pulse_rk4(m, alpha, phi, tau, df, steps=4000):
+    """Integrate the rotating-frame Bloch equation (Eq. A1 without relaxation)
+    over one RF pulse of duration tau ms: dM/dt = W x M with the RF field of
+    phase phi turning M about (cos phi, sin phi, 0) by -alpha over tau (the
+    hard-pulse sense), and off-resonance turning it counterclockwise about z
+    at 2 pi df / 1000 rad/ms (the sense of R_off), both at once (RK4)."""
+    w = np.array([-alpha / tau * math.cos(phi), -alpha / tau * math.sin(phi), 2.0 * math.pi * df / 1000.0])
+    f = lambda v: np.cross(w, v)
+    h = tau / steps
+    v = np.array(m, float)
+    for _ in range(steps):
+        k1 = f(v)
+        k2 = f(v + 0.5 * h * k1)
+        k3 = f(v + 0.5 * h * k2)
+        k4 = f(v + h * k3)
+        v = v + h / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return v
+
+
+def _one_pulse(oracle_lib, m, alpha, phi, tau, df):
+    """The oracle's state right after one pulse: n = 1, TE = 0 (the free
+    evolution before the sample is the identity), no inversion."""
+    seq = S.with_pulses(_seq(1, alpha, 10.0, 0.0, phase=phi), tau)
+    _, st = oracle_lib.simulate_state(seq, 1e9, 1e9, df, m_init=m)
+    return st[0]
+
+
+@pytest.mark.parametrize("alpha,phi,tau,df", [(0.7, 0.0, 1.0, 40.0), (-0.7, 0.0, 1.0, 40.0), (0.3, 1.2, 2.0, -25.0),
+                                              (1.4, math.pi / 2, 0.5, 300.0), (0.0, 0.0, 1.5, 30.0),
+                                              (-0.2, math.pi, 3.0, -400.0)])
+def test_finite_pulse_against_the_bloch_equation(oracle_lib, alpha, phi, tau, df):
+    """The Appendix's off-resonant RF rotation R_z(phi) R_y(beta) R_x(alpha')
+    R_y(-beta) R_z(-phi) equals the Bloch equation integrated through the
+    pulse with the RF and off-resonance fields together (signed flip angles,
+    alpha = 0, far off resonance), and keeps |M|."""
+    rng = np.random.default_rng(int(1000 * abs(alpha) + abs(df)))
+    m = rng.normal(size=3)
+    m /= np.linalg.norm(m)
+    got = _one_pulse(oracle_lib, m, alpha, phi, tau, df)
+    want = _bloch_pulse_rk4(m, alpha, phi, tau, df)
+    np.testing.assert_allclose(got, want, atol=1e-10)
+    assert abs(np.linalg.norm(got) - 1.0) < 1e-13
+
+
+def test_finite_pulse_without_rf_is_free_precession(oracle_lib):
+    """alpha = 0: the pulse interval is precession alone, a counterclockwise
+    z rotation by 2 pi df tau / 1000."""
+    m = np.array([0.6, -0.3, 0.74])
+    got = _one_pulse(oracle_lib, m, 0.0, 0.4, 2.5, 37.0)
+    th = 2 * math.pi * 37.0 * 2.5 / 1000.0
+    want = np.array([math.cos(th) * m[0] - math.sin(th) * m[1], math.sin(th) * m[0] + math.cos(th) * m[1], m[2]])
+    np.testing.assert_allclose(got, want, atol=1e-15)
+
+
+def test_finite_pulse_limits_are_the_hard_pulse(oracle_lib):
+    """tau = 0 is the hard pulse exactly; tau -> 0 converges to it; on
+    resonance (df = 0) the effective field lies along the RF axis, so any tau
+    gives the hard pulse (alternating signs, 0/90/180 degree phases)."""
+    base = S.sequence_paper(4, 120)
+    alt = S.sequence(5, 120)
+    for seq in (base, alt):
+        hard = oracle_lib.simulate(seq, [900.0, 1500.0], [80.0, 40.0], [12.0, -30.0])
+        zero = oracle_lib.simulate(S.with_pulses(seq, 0.0), [900.0, 1500.0], [80.0, 40.0], [12.0, -30.0])
+        assert np.array_equal(hard, zero)
+        tiny = oracle_lib.simulate(S.with_pulses(seq, 1e-9), [900.0, 1500.0], [80.0, 40.0], [12.0, -30.0])
+        np.testing.assert_allclose(tiny, hard, atol=1e-9)
+        on = oracle_lib.simulate(S.with_pulses(seq, 2.0), [900.0, 1500.0], [80.0, 40.0], [0.0, 0.0])
+        np.testing.assert_allclose(on, oracle_lib.simulate(seq, [900.0, 1500.0], [80.0, 40.0], [0.0, 0.0]),
+                                   atol=1e-13)
+        off = oracle_lib.simulate(S.with_pulses(seq, 2.0), [900.0], [80.0], [30.0])
+        assert np.abs(off - hard[:1]).max() > 1e-3          # a 2 ms pulse 30 Hz off resonance matters
+
+
 # ----------------------------------------------------------------- simulator
 
 def test_pure_t1_recovery_after_inversion(oracle_lib):
