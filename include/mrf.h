@@ -339,16 +339,19 @@ typedef struct {
     int32_t s4_param[MRF_ZOOM_MAX_LEVELS];   /* 0: T1, 1: T2 */
     double s4_ms[MRF_ZOOM_MAX_LEVELS];
     /* Spatial-neighbour prior (Methods, Experiment 3), mrf_zoom_search only:
-     * prior_width > 0 treats the V voxels as a row-major slice prior_width
-     * voxels wide. Voxels on every prior_stride-th row and column are searched
-     * first on the whole grid; every other voxel is then searched on the grid
-     * overlapped with T1p +- prior_t1_ms, T2p +- prior_t2_ms, dfp +-
-     * prior_df_hz around the result of the first-pass voxel at (r - r mod
-     * stride, c - c mod stride): the index box |i - i_p| <= floor(half /
-     * step), searched as a grid of its own. Defaults 0 (off), 4, 3000, 800,
-     * 150. */
-    int32_t prior_width;
-    int32_t prior_stride;
+     * prior_chain > 0 searches the V voxels in their given (raster) order as
+     * chains of prior_chain consecutive voxels (prior_chain >= V: the paper's
+     * single chain through the slice). A chain's first voxel is searched on
+     * the whole grid; every later voxel on the grid overlapped with T1p +-
+     * prior_t1_ms, T2p +- prior_t2_ms, dfp +- prior_df_hz around the result
+     * (T1p, T2p, dfp) of the voxel before it -- the index box |i - i_p| <=
+     * floor(half / step), searched as a grid of its own -- starting at (T1p,
+     * T2p) when prior_start is 1 (the initial ZOOM centre taken from the
+     * neighbouring voxel, Theory) or at t1_init/t2_init clipped into the box
+     * when it is 0. Voxels of one chain run one after another; chains run in
+     * parallel. Defaults: 0 (off), 1, 3000, 800, 150. */
+    int32_t prior_chain;
+    int32_t prior_start;
     double prior_t1_ms, prior_t2_ms, prior_df_hz;
 } mrf_zoom_opts;
 
@@ -412,8 +415,7 @@ int mrf_refine(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid, cons
  * the last call's contents: calls that overlap on the GPU race and must be
  * serialised by the caller. The first call on a device looks up the array's
  * address; make it before any stream capture. The spatial-neighbour prior
- * (opts->prior_width != 0) is refused with MRF_E_UNSUPPORTED: its scratch
- * grows with V. All steps run in one kernel, with the results of
+ * (opts->prior_chain != 0) is refused with MRF_E_UNSUPPORTED. All steps run in one kernel, with the results of
  * mrf_zoom_search bit for bit. */
 #define MRF_ZOOM_STATIC_SCRATCH_BYTES (512 * 1024)
 int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid,

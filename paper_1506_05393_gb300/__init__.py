@@ -73,7 +73,7 @@ class ZoomOpts(C.Structure):
                 ("s3_half_frac", C.c_double), ("n_s2", C.c_int32),
                 ("s2_t1_ms", C.c_double * ZOOM_MAX_LEVELS), ("s2_t2_ms", C.c_double * ZOOM_MAX_LEVELS),
                 ("n_s4", C.c_int32), ("s4_param", C.c_int32 * ZOOM_MAX_LEVELS),
-                ("s4_ms", C.c_double * ZOOM_MAX_LEVELS), ("prior_width", C.c_int32), ("prior_stride", C.c_int32),
+                ("s4_ms", C.c_double * ZOOM_MAX_LEVELS), ("prior_chain", C.c_int32), ("prior_start", C.c_int32),
                 ("prior_t1_ms", C.c_double), ("prior_t2_ms", C.c_double), ("prior_df_hz", C.c_double)]
 
 
@@ -453,8 +453,9 @@ def zoom_opts(**kw) -> ZoomOpts:
         o.n_s4 = len(kw["s4"])
         for i, (p, h) in enumerate(kw["s4"]):
             o.s4_param[i], o.s4_ms[i] = p, h
-    if "prior" in kw:   # (width, stride, (T1, T2, df) half-widths)
-        width, stride, half = kw["prior"]
-        o.prior_width, o.prior_stride = int(width), int(stride)
+    if "prior" in kw:   # (chain length, (T1, T2, df) half-widths[, start from the prior 1/0])
+        chain, half = kw["prior"][:2]
+        o.prior_chain = int(chain)
+        o.prior_start = int(kw["prior"][2]) if len(kw["prior"]) > 2 else 1
         o.prior_t1_ms, o.prior_t2_ms, o.prior_df_hz = (float(v) for v in half)
     return o

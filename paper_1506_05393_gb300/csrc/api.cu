@@ -835,8 +835,8 @@ extern "C" void mrf_zoom_opts_default(mrf_zoom_opts *o)
     const double h[8] = {100.0, 100.0, 50.0, 20.0, 10.0, 50.0, 20.0, 10.0};
     o->n_s4 = 8;
     for (int i = 0; i < 8; ++i) { o->s4_param[i] = p[i]; o->s4_ms[i] = h[i]; }
-    o->prior_width = 0;
-    o->prior_stride = 4;
+    o->prior_chain = 0;
+    o->prior_start = 1;
     o->prior_t1_ms = 3000.0;
     o->prior_t2_ms = 800.0;
     o->prior_df_hz = 150.0;
@@ -858,11 +858,11 @@ extern "C" int mrf_zoom_search(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_
         if (opts->s4_param[i] != 0 && opts->s4_param[i] != 1) return set_error(MRF_E_INVALID, "zoom: s4_param must be 0/1");
     if (!(opts->s1a_step_frac > 0) || !(opts->s1b_step_frac > 0) || opts->s1b_half_frac < 0 || opts->s3_half_frac < 0)
         return set_error(MRF_E_INVALID, "zoom: bad df search fractions");
-    if (opts->prior_width < 0 || (opts->prior_width > 0 && opts->prior_stride < 1) ||
-        (opts->prior_width > 0 && !(opts->prior_t1_ms >= 0 && opts->prior_t2_ms >= 0 && opts->prior_df_hz >= 0 &&
+    if (opts->prior_chain < 0 || (opts->prior_chain > 0 && opts->prior_start != 0 && opts->prior_start != 1) ||
+        (opts->prior_chain > 0 && !(opts->prior_t1_ms >= 0 && opts->prior_t2_ms >= 0 && opts->prior_df_hz >= 0 &&
                                     std::isfinite(opts->prior_t1_ms) && std::isfinite(opts->prior_t2_ms) &&
                                     std::isfinite(opts->prior_df_hz))))
-        return set_error(MRF_E_INVALID, "zoom: prior_width >= 0; with a prior, prior_stride >= 1 and finite "
+        return set_error(MRF_E_INVALID, "zoom: prior_chain >= 0; with a prior, prior_start 0 or 1 and finite "
                                         "non-negative half-widths");
     if (V == 0) return MRF_OK;
     if (!fp || !out) return set_error(MRF_E_INVALID, "NULL device buffer");

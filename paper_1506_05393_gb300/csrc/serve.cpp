@@ -315,7 +315,7 @@ extern "C" int mrf_serve_submit(mrf_ctx *ctx, const mrf_request *rq, uint64_t *t
         if (rq->zoom) r->zoom = *rq->zoom;
         else mrf_zoom_opts_default(&r->zoom);
         // requests are concatenated into shared launches: no slice geometry
-        if (r->zoom.prior_width != 0)
+        if (r->zoom.prior_chain != 0)
             return set_error(MRF_E_UNSUPPORTED, "serve: the spatial-neighbour prior needs mrf_zoom_search");
         r->n = rq->seq->n;
     } else {

@@ -84,8 +84,12 @@ struct ZoomArgs {
     int max_moves;
     ZState *state;           // split search only
     int phase;               // ZPhase
-    const int *vmap;         // voxel of each work item (nullptr: item = voxel)
-    const int *box;          // per work item: a_lo, a_hi, b_lo, b_hi, c_lo, c_hi of its search (nullptr: the grid)
+    // spatial-neighbour prior: chains of chain_len consecutive voxels (0: off),
+    // each voxel after a chain's first searched on the box of +-prior_h steps
+    // around its predecessor's result, from that result when prior_start
+    int chain_len;
+    int prior_h1, prior_h2, prior_h3;
+    int prior_start;
     unsigned long long *stats;   // work counters: [2] warp rounds, [3] candidates simulated, [4] most rounds of a voxel
 };
 
@@ -718,6 +722,8 @@ struct Slot {
     int moves, la, lb, h1, h2, line, param, ia, ib, da, db;
     int run;               // consecutive moves in the direction (da, db)
     int alo, ahi, blo, bhi, clo, chi;   // the voxel's search box (the whole grid unless a prior bounds it)
+    int chain_next, chain_end;          // prior chains: the chain's voxels still to search
+    int pa, pb, pc;                     // prior chains: the result of the voxel searched last
     // listed points: ra/rb/rw[0..nreq) missing, then nspec speculative (rw: window index)
     int nreq, nspec;
     int ra[kReqMax], rb[kReqMax], rw[kReqMax];
@@ -1151,6 +1157,7 @@ __device__ void ingest(PackShared &W, int lane, const GridDev &g, mrf_result *ou
             out[S.v] = r;
             if (state) state[S.v].flags = kZDone;
             if (stats) atomicMax(&stats[4], (unsigned long long)S.rounds);
+            S.pa = S.a; S.pb = S.b; S.pc = S.c;   // the next voxel of a prior chain is bounded by this result
             S.v = -1;
         }
     }
@@ -1213,7 +1220,7 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
     const int lane = threadIdx.x & 31;
     PackShared &W = sW[threadIdx.x >> 5];
     if (threadIdx.x == 0) sP = A.plan;
-    if (lane < kSlots) { W.s[lane].v = -1; W.s[lane].scan_n = 0; }
+    if (lane < kSlots) { W.s[lane].v = -1; W.s[lane].scan_n = 0; W.s[lane].chain_next = W.s[lane].chain_end = 0; }
     if (lane == 0) { W.drained = 0; W.rot = 0; W.norm_mask = 0; W.used = 0; }
     __syncthreads();
     const ZoomPlan &P = sP;
@@ -1230,11 +1237,43 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
             ingest_scan(W, s);
             Slot &S = W.s[s];
             // a slot parked at step 3 is free at once: refill it until it has
-            // work or the voxels run out, so no warp leaves with voxels left
+            // work or the voxels run out, so no warp leaves with voxels left; a
+            // slot in a prior chain goes on with the chain's next voxel
             for (;;) {
-                while (S.v < 0 && !W.drained) {
+                while (S.v < 0 && (S.chain_next < S.chain_end || !W.drained)) {
+                    if (A.chain_len > 0 && S.chain_next < S.chain_end) {
+                        // the next voxel of the chain: the box of the prior's
+                        // half-widths around the preceding voxel's result, cut
+                        // by the grid, and (prior_start) that result as start
+                        S.v = S.chain_next++;
+                        S.alo = max(0, S.pa - A.prior_h1); S.ahi = min(A.g.n_t1 - 1, S.pa + A.prior_h1);
+                        S.blo = max(0, S.pb - A.prior_h2); S.bhi = min(A.g.n_t2 - 1, S.pb + A.prior_h2);
+                        S.clo = max(0, S.pc - A.prior_h3); S.chi = min(A.g.n_df - 1, S.pc + A.prior_h3);
+                        int a = S.pa, b = S.pb;
+                        if (!A.prior_start) {
+                            // the options' start clipped into the box, then moved
+                            // to a valid point inside it
+                            a = min(max(P.a_raw, S.alo), S.ahi);
+                            b = min(max(P.b_raw, S.blo), S.bhi);
+                            while (b > S.blo && !point_valid(A.g, a, b, S.clo)) --b;
+                            while (a < S.ahi && !point_valid(A.g, a, b, S.clo)) ++a;
+                        }
+                        if (!point_valid(A.g, a, b, S.clo)) atomicExch(A.err, kDeviceErrBounds);
+                        S.a = a; S.b = b;
+                        S.c = S.clo;
+                        S.centre = -INFINITY;
+                        S.evaluated = 0;
+                        S.mm = INFINITY;
+                        S.ok = 1;
+                        S.rounds = 0;
+                        S.level = 0;
+                        atomicOr(&W.norm_mask, 1 << s);
+                        enter(W, s, kS1a, P, A.g.n_df, false);
+                        break;
+                    }
                     const int nv = atomicAdd(A.counter, 1);
-                    if (nv >= A.V) { W.drained = 1; break; }
+                    const int64_t first = A.chain_len > 0 ? (int64_t)nv * A.chain_len : (int64_t)nv;
+                    if (first >= A.V) { W.drained = 1; break; }
                     if (A.phase == kPhaseTail) {
                         // resume after step 3 (voxels finished earlier are skipped)
                         const ZState z = A.state[nv];
@@ -1252,23 +1291,15 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
                         S.level = 0;
                         enter(W, s, kS4, P, A.g.n_df, false);
                     } else {
-                        S.v = A.vmap ? __ldg(&A.vmap[nv]) : nv;
-                        if (A.box) {
-                            // a search bounded by a prior: the start clipped into
-                            // the box, then moved to a valid point inside it
-                            const int *bx = A.box + 6 * (size_t)nv;
-                            S.alo = __ldg(&bx[0]); S.ahi = __ldg(&bx[1]); S.blo = __ldg(&bx[2]);
-                            S.bhi = __ldg(&bx[3]); S.clo = __ldg(&bx[4]); S.chi = __ldg(&bx[5]);
-                            int a = min(max(P.a_raw, S.alo), S.ahi), b = min(max(P.b_raw, S.blo), S.bhi);
-                            while (b > S.blo && !point_valid(A.g, a, b, S.clo)) --b;
-                            while (a < S.ahi && !point_valid(A.g, a, b, S.clo)) ++a;
-                            if (!point_valid(A.g, a, b, S.clo)) atomicExch(A.err, kDeviceErrBounds);
-                            S.a = a; S.b = b;
-                        } else {
-                            S.alo = 0; S.ahi = A.g.n_t1 - 1; S.blo = 0; S.bhi = A.g.n_t2 - 1;
-                            S.clo = 0; S.chi = A.g.n_df - 1;
-                            S.a = P.a0; S.b = P.b0;
+                        // a voxel (or a prior chain's first voxel) on the whole grid
+                        S.v = (int)first;
+                        if (A.chain_len > 0) {
+                            S.chain_next = (int)first + 1;
+                            S.chain_end = (int)(first + A.chain_len < A.V ? first + A.chain_len : A.V);
                         }
+                        S.alo = 0; S.ahi = A.g.n_t1 - 1; S.blo = 0; S.bhi = A.g.n_t2 - 1;
+                        S.clo = 0; S.chi = A.g.n_df - 1;
+                        S.a = P.a0; S.b = P.b0;
                         S.c = S.clo;
                         S.centre = -INFINITY;
                         S.evaluated = 0;
@@ -1281,7 +1312,7 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
                     }
                 }
                 advance(W, s, P, A.g, A.max_moves, head);
-                if (S.v >= 0 || W.drained) break;
+                if (S.v >= 0 || (W.drained && S.chain_next >= S.chain_end)) break;
             }
             if (S.v >= 0) S.rounds += 1;
         }
@@ -1738,68 +1769,31 @@ void launch_line(const mrf_ctx *ctx, const LineArgs &L, int64_t max_items, cudaS
 
 namespace {
 
-// Boxes of the second pass of the spatial-neighbour prior: the grid points
-// within h1, h2, h3 steps of the first-pass neighbour's result, cut by the
-// grid.
-__global__ void prior_box_kernel(const mrf_result *out, const int *nbr, int n2, int h1, int h2, int h3, int n_t1,
-                                 int n_t2, int n_df, int *box)
+// MRF-ZOOM with the spatial-neighbour prior (Methods, Experiment 3): the
+// voxels, in their given (raster) order, form chains of opts->prior_chain
+// consecutive voxels (the whole slice when it is V or more: the paper's
+// single chain); a chain's first voxel is searched on the whole grid, every
+// later one on the grid overlapped with the prior's ranges around the result
+// of the voxel before it, started there (prior_start) or at the options'
+// start clipped into those ranges. Each chain runs in one slot of the packed
+// kernel, every step in that kernel; chains run in parallel.
+int zoom_with_chains(mrf_ctx *ctx, const ZoomPlan &P, const SeqDev &sd, const GridDev &gdev,
+                     const mrf_grid_desc *gd, const mrf_zoom_opts *o, const void *fp, int64_t V, mrf_result *out,
+                     cudaStream_t stream)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n2) return;
-    const mrf_result r = out[nbr[i]];
-    int *bx = box + 6 * (size_t)i;
-    bx[0] = max(0, r.i_t1 - h1); bx[1] = min(n_t1 - 1, r.i_t1 + h1);
-    bx[2] = max(0, r.i_t2 - h2); bx[3] = min(n_t2 - 1, r.i_t2 + h2);
-    bx[4] = max(0, r.i_df - h3); bx[5] = min(n_df - 1, r.i_df + h3);
-}
-
-// MRF-ZOOM with the spatial-neighbour prior (Methods, Experiment 3), in two
-// passes over the slice: the voxels on every stride-th row and column on the
-// whole grid, then every other voxel on the box around its first-pass
-// neighbour's result (the neighbour is the first-pass voxel at (r - r mod
-// stride, c - c mod stride) instead of the preceding voxel in raster order, so
-// each pass runs all its voxels in parallel). Both passes run every step in
-// the packed kernel.
-int zoom_with_prior(mrf_ctx *ctx, const ZoomPlan &P, const SeqDev &sd, const GridDev &gdev,
-                    const mrf_grid_desc *gd, const mrf_zoom_opts *o, const void *fp, int64_t V, mrf_result *out,
-                    cudaStream_t stream)
-{
-    const int64_t W = o->prior_width, st = o->prior_stride;
-    std::vector<int> ids, nbr;
-    ids.reserve((size_t)V);
-    for (int64_t v = 0; v < V; ++v)
-        if ((v / W) % st == 0 && (v % W) % st == 0) ids.push_back((int)v);
-    const int n1 = (int)ids.size();
-    for (int64_t v = 0; v < V; ++v) {
-        const int64_t r = v / W, c = v % W;
-        if (r % st == 0 && c % st == 0) continue;
-        ids.push_back((int)v);
-        nbr.push_back((int)((r - r % st) * W + (c - c % st)));
-    }
-    const int n2 = (int)nbr.size();
-    const int h1 = (int)floor(o->prior_t1_ms / gd->t1_step + 1e-9);
-    const int h2 = (int)floor(o->prior_t2_ms / gd->t2_step + 1e-9);
-    const int h3 = (int)floor(o->prior_df_hz / gd->df_step + 1e-9);
-    // one block: counters | voxel ids (first pass, then second) | neighbours | boxes
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t o_ids = 256, o_nbr = o_ids + al(4 * (size_t)V), o_box = o_nbr + al(4 * (size_t)std::max(n2, 1));
-    const size_t total = o_box + al(24 * (size_t)std::max(n2, 1));
-    std::vector<uint8_t> host(o_box, 0);
-    memcpy(host.data() + o_ids, ids.data(), 4 * (size_t)V);
-    if (n2) memcpy(host.data() + o_nbr, nbr.data(), 4 * (size_t)n2);
+    const int64_t L = std::min<int64_t>(o->prior_chain, std::max<int64_t>(V, 1));
+    const int64_t chains = (V + L - 1) / L;
+    const size_t total = 256;
     int rc = budget_charge(ctx, total);
     if (rc) return rc;
-    uint8_t *sb = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&sb, total, stream);
-    // pageable source: the copy is staged before the call returns
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sb, host.data(), o_box, cudaMemcpyHostToDevice, stream);
+    int *counter = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&counter, total, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, total, stream);
     if (e != cudaSuccess) {
-        if (sb) cudaFreeAsync(sb, stream);
+        if (counter) cudaFreeAsync(counter, stream);
         budget_release(ctx, total);
         return cuda_fail(e, "zoom prior scratch");
     }
-    const int *d_ids = (const int *)(sb + o_ids);
-    int *box = (int *)(sb + o_box);
     ZoomArgs A;
     A.s = sd;
     A.g = gdev;
@@ -1809,34 +1803,27 @@ int zoom_with_prior(mrf_ctx *ctx, const ZoomPlan &P, const SeqDev &sd, const Gri
     A.ld = 0;
     A.plan = P;
     A.x = (const float2 *)fp;
+    A.V = V;
     A.out = out;
+    A.counter = counter;
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
     A.state = nullptr;
     A.phase = kPhaseAll;
+    A.chain_len = (int)L;
+    // half-widths in whole grid steps (an axis's length at most: wider windows change nothing)
+    auto steps = [](double half, double step, int n) { return (int)std::min<double>(floor(half / step + 1e-9), n); };
+    A.prior_h1 = steps(o->prior_t1_ms, gd->t1_step, gd->n_t1);
+    A.prior_h2 = steps(o->prior_t2_ms, gd->t2_step, gd->n_t2);
+    A.prior_h3 = steps(o->prior_df_hz, gd->df_step, gd->n_df);
+    A.prior_start = o->prior_start;
     A.stats = ctx->dev_stats;
     {
         ProfScope prof(ctx, kProfZoom, stream);
-        if (n1) {
-            A.counter = (int *)sb;
-            A.vmap = d_ids;
-            A.box = nullptr;
-            A.V = n1;
-            launch_pack(A, pack_blocks(ctx, n1), stream);
-        }
-        if (n2) {
-            prior_box_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, stream>>>(
-                out, (const int *)(sb + o_nbr), n2, h1, h2, h3, gd->n_t1, gd->n_t2, gd->n_df, box);
-            A.counter = (int *)sb + 1;
-            A.vmap = d_ids + n1;
-            A.box = box;
-            A.V = n2;
-            launch_pack(A, pack_blocks(ctx, n2), stream);
-            count_launch(ctx, 2);
-        }
+        launch_pack(A, pack_blocks(ctx, chains), stream);
     }
     e = cudaGetLastError();
-    cudaFreeAsync(sb, stream);
+    cudaFreeAsync(counter, stream);
     budget_release(ctx, total);
     if (e != cudaSuccess) return cuda_fail(e, "zoom (prior) launch");
     return MRF_OK;
@@ -1897,8 +1884,8 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     int rc = grid_upload_async(ctx, gd, stream, &gdev, &gblock, &gbytes);
     if (rc) return rc;
 
-    if (o->prior_width > 0) {
-        rc = zoom_with_prior(ctx, P, seq->dev(), gdev, gd, o, fp, V, out, stream);
+    if (o->prior_chain > 0) {
+        rc = zoom_with_chains(ctx, P, seq->dev(), gdev, gd, o, fp, V, out, stream);
         cudaFreeAsync(gblock, stream);
         budget_release(ctx, gbytes);
         return rc;
@@ -1950,8 +1937,9 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     A.counter = counters;
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
-    A.vmap = nullptr;
-    A.box = nullptr;
+    A.chain_len = 0;
+    A.prior_h1 = A.prior_h2 = A.prior_h3 = 0;
+    A.prior_start = 0;
     A.state = split ? (ZState *)(sb + o_state) : nullptr;
     A.phase = split ? kPhaseHead : kPhaseAll;
     A.stats = ctx->dev_stats;
@@ -2055,7 +2043,7 @@ extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_z
     if (!ctx || !d) return set_error(MRF_E_INVALID, "NULL argument");
     if (d->dtype != MRF_F32 && d->dtype != MRF_BF16)
         return set_error(MRF_E_UNSUPPORTED, "zoom over a dictionary needs an MRF_F32 or MRF_BF16 dictionary");
-    if (opts && opts->prior_width != 0)
+    if (opts && opts->prior_chain != 0)
         return set_error(MRF_E_UNSUPPORTED, "zoom over a dictionary: the spatial-neighbour prior is mrf_zoom_search's");
     if (V < 0 || V > INT32_MAX) return set_error(MRF_E_INVALID, "zoom: V must be in [0, 2^31 - 1]");
     mrf_zoom_opts def;
@@ -2094,8 +2082,9 @@ extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_z
     A.counter = counter;
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
-    A.vmap = nullptr;
-    A.box = nullptr;
+    A.chain_len = 0;
+    A.prior_h1 = A.prior_h2 = A.prior_h3 = 0;
+    A.prior_start = 0;
     A.state = nullptr;
     A.phase = kPhaseAll;
     A.stats = nullptr;
@@ -2167,7 +2156,7 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
         if (opts->s4_param[i] != 0 && opts->s4_param[i] != 1) return set_error(MRF_E_INVALID, "zoom: s4_param must be 0/1");
     if (!(opts->s1a_step_frac > 0) || !(opts->s1b_step_frac > 0) || opts->s1b_half_frac < 0 || opts->s3_half_frac < 0)
         return set_error(MRF_E_INVALID, "zoom: bad df search fractions");
-    if (opts->prior_width != 0)
+    if (opts->prior_chain != 0)
         return set_error(MRF_E_UNSUPPORTED, "zoom (static scratch): the spatial-neighbour prior needs mrf_zoom_search");
     // scratch layout: [counter][t1][t2][df][a_off][nb], 256-byte aligned pieces
     const size_t nt1 = gd->n_t1, nt2 = gd->n_t2, ndf = gd->n_df;
@@ -2270,8 +2259,9 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     A.counter = (int *)dev;
     A.err = ctx->err_flag;
     A.max_moves = 1 << 20;
-    A.vmap = nullptr;
-    A.box = nullptr;
+    A.chain_len = 0;
+    A.prior_h1 = A.prior_h2 = A.prior_h3 = 0;
+    A.prior_start = 0;
     A.state = nullptr;
     A.phase = kPhaseAll;   // one kernel: the split search's scratch grows with V
     A.stats = ctx->dev_stats;

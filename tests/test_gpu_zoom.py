@@ -313,40 +313,100 @@ def _piecewise_voxels(orc, seq, rows, cols, seed, snr=30.0):
     return ph, S.compose_voxels(clean, ph["m0"], ph["phase"], g_re, g_im, snr)
 
 
-@pytest.mark.parametrize("half", [(3000.0, 800.0, 150.0), (200.0, 30.0, 6.0)])
-def test_zoom_spatial_prior_against_oracle(M, ctx, oracle_lib, half):
-    """The spatial-neighbour prior (Methods, Experiment 3) on a piecewise-
-    smooth 16 x 16 slice: the paper's windows, and narrow ones that bound
-    most second-pass searches; against the oracle's two-pass search."""
+def _compare_chains(orc, g, res, ref, L, half, label):
+    """GPU prior chains against the oracle's: within each chain of L voxels,
+    voxel by voxel, the final point must match (CC within 1e-5, same index,
+    same evaluation count where margins exceed 1e-5) until the first voxel
+    the oracle's margin excuses (< 1e-6) and the GPU answers differently;
+    the rest of that chain starts from another result and is not compared.
+    Every GPU result lies in the box around its own predecessor's result."""
+    V = res.shape[0]
+    abc = np.stack([res["i_t1"], res["i_t2"], res["i_df"]], 1)
+    h = [int(np.floor(w / s + 1e-9)) for w, s in zip(half, (g.t1_step, g.t2_step, g.df_step))]
+    compared, cut = 0, 0
+    for c0 in range(0, V, L):
+        for v in range(c0, min(c0 + L, V)):
+            if v > c0:
+                assert (np.abs(abc[v] - abc[v - 1]) <= h).all(), f"{label}: voxel {v} outside its prior box"
+            if not (abc[v] == ref["abc"][v]).all():
+                assert ref["min_margin"][v] < MARGIN_EXCUSE, (
+                    f"{label}: voxel {v} differs with margin {ref['min_margin'][v]}: "
+                    f"gpu {abc[v].tolist()} oracle {ref['abc'][v].tolist()}")
+                cut += min(c0 + L, V) - v
+                break
+            compared += 1
+            assert abs(res["cc"][v] - ref["cc"][v]) < 1e-5
+            assert res["index"][v] == orc.grid_index(g, *ref["abc"][v])
+            if ref["min_margin"][v] >= 1e-5:
+                assert res["entries_evaluated"][v] == ref["evaluated"][v], f"{label}: voxel {v} evaluations"
+    return compared, cut
+
+
+def test_zoom_prior_single_chain_against_oracle(M, ctx, oracle_lib):
+    """The paper's spatial-neighbour prior (Methods, Experiment 3) as its
+    single chain through an 8 x 8 piecewise-smooth slice in raster order,
+    with the paper's windows (T1p +- 3000 ms, T2p +- 800 ms, dfp +- 150 Hz)
+    and each search started at the preceding voxel's result: against the
+    oracle's chain."""
     seq = S.sequence(1, 1000)
     g = S.GRIDS["fp32_brute"]
-    ph, x = _piecewise_voxels(oracle_lib, seq, 16, 16, 31)
-    res = _gpu_zoom(M, ctx, seq, g, x, prior=(16, 4, half))
-    ref = oracle_lib.zoom_prior(seq, g, x, 16, 4, half)
-    diff, exc = _compare(oracle_lib, g, res, ref, f"prior {half}")
-    abc = np.stack([res["i_t1"], res["i_t2"], res["i_df"]], 1)
-    box = ref["box"]
-    inside = ((abc[:, 0] >= box[:, 0]) & (abc[:, 0] <= box[:, 1]) & (abc[:, 1] >= box[:, 2]) &
-              (abc[:, 1] <= box[:, 3]) & (abc[:, 2] >= box[:, 4]) & (abc[:, 2] <= box[:, 5]))
-    assert inside.all()
-    print(f"zoom prior {half}: differ={diff} excused={exc}")
+    ph, x = _piecewise_voxels(oracle_lib, seq, 8, 8, 31)
+    half = (3000.0, 800.0, 150.0)
+    res = _gpu_zoom(M, ctx, seq, g, x, prior=(64, half))
+    ref = oracle_lib.zoom_prior(seq, g, x, half=half)
+    compared, cut = _compare_chains(oracle_lib, g, res, ref, 64, half, "single chain")
+    print(f"zoom prior, one chain of 64: compared={compared} after an excused divergence={cut}")
+    assert compared >= 16
 
 
-def test_zoom_spatial_prior_covering_the_grid_is_the_plain_search(M, ctx, oracle_lib):
-    """Windows wider than every axis: both passes search the whole grid, so
-    the results are those of the plain search bit for bit (a ragged last row:
-    the slice is 13 voxels wide)."""
+@pytest.mark.parametrize("half,start", [((3000.0, 800.0, 150.0), 1), ((200.0, 30.0, 6.0), 1),
+                                        ((200.0, 30.0, 6.0), 0)])
+def test_zoom_prior_chains_against_oracle(M, ctx, oracle_lib, half, start):
+    """Chains of one row (16 voxels) through a 16 x 16 piecewise-smooth slice:
+    the paper's windows and narrow ones that bound most searches, started at
+    the preceding voxel's result or at the options' start clipped into the
+    box; against the oracle's chains."""
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["fp32_brute"]
+    ph, x = _piecewise_voxels(oracle_lib, seq, 16, 16, 32)
+    res = _gpu_zoom(M, ctx, seq, g, x, prior=(16, half, start))
+    ref = oracle_lib.zoom_prior(seq, g, x, chain=16, half=half, start_from_prior=bool(start))
+    compared, cut = _compare_chains(oracle_lib, g, res, ref, 16, half, f"chains {half} start={start}")
+    print(f"zoom prior chains {half} start={start}: compared={compared} cut={cut}")
+    assert compared >= 128
+
+
+def test_zoom_prior_covering_the_grid_is_the_plain_search(M, ctx, oracle_lib):
+    """Windows wider than every axis and the start left at the options'
+    start: every search runs on the whole grid from the same point, so the
+    results are those of the plain search bit for bit (chains of 13 voxels,
+    a ragged last chain)."""
     seq = S.sequence(1, 1000)
     g = S.GRIDS["fp32_brute"]
     ph, x = offgrid_voxels(oracle_lib, seq, 13 * 7 + 5, 20.0, 33)
     plain = _gpu_zoom(M, ctx, seq, g, x)
-    pri = _gpu_zoom(M, ctx, seq, g, x, prior=(13, 3, (1e6, 1e6, 1e6)))
+    pri = _gpu_zoom(M, ctx, seq, g, x, prior=(13, (1e6, 1e6, 1e6), 0))
     for f in ("index", "entries_evaluated"):
         assert np.array_equal(plain[f], pri[f]), f
     assert np.array_equal(plain["cc"].view(np.uint32), pri["cc"].view(np.uint32))
 
 
-def test_zoom_spatial_prior_options_checked(M, ctx):
+def test_zoom_prior_started_at_the_optimum(M, ctx, oracle_lib):
+    """Noise-free voxels of one on-grid tissue in a chain: every voxel after
+    the first starts at its own optimum, so no decision moves and each needs
+    the 25 evaluations the oracle pin counts by hand on the tiny grid."""
+    seq = S.sequence(0, 200)
+    g = S.GRIDS["tiny"]
+    rng = np.random.default_rng(11)
+    clean = oracle_lib.simulate(seq, np.full(9, 1400.0), np.full(9, 100.0), np.zeros(9))
+    x = clean * (rng.uniform(0.5, 1.0, 9) * np.exp(1j * rng.uniform(0, 2 * np.pi, 9)))[:, None]
+    res = _gpu_zoom(M, ctx, seq, g, x, prior=(9, (3000.0, 800.0, 150.0)))
+    assert list(res["i_t1"]) == [13] * 9 and list(res["i_t2"]) == [4] * 9
+    assert list(res["entries_evaluated"][1:]) == [25] * 8
+    np.testing.assert_allclose(res["cc"], 1.0, atol=1e-5)
+
+
+def test_zoom_prior_options_checked(M, ctx):
     import ctypes as C
     seq = S.sequence(0, 50)
     h = M.mrf_sequence_load(ctx, seq)
@@ -355,13 +415,13 @@ def test_zoom_spatial_prior_options_checked(M, ctx):
         fp = torch.zeros((4, 50), dtype=torch.complex64, device="cuda")
         out = M.empty_results(4)
         L = M.lib()
-        for kw in (dict(prior=(-1, 4, (3000.0, 800.0, 150.0))), dict(prior=(2, 0, (3000.0, 800.0, 150.0))),
-                   dict(prior=(2, 2, (-1.0, 800.0, 150.0)))):
+        for kw in (dict(prior=(-1, (3000.0, 800.0, 150.0))), dict(prior=(2, (3000.0, 800.0, 150.0), 2)),
+                   dict(prior=(2, (-1.0, 800.0, 150.0))), dict(prior=(2, (3000.0, float("inf"), 150.0)))):
             o = M.zoom_opts(**kw)
             rc = L.mrf_zoom_search(ctx, h, C.byref(g), C.byref(o), C.c_void_p(fp.data_ptr()), 4,
                                    C.c_void_p(out.data_ptr()), None)
             assert rc == M.MRF_E_INVALID
-        o = M.zoom_opts(prior=(2, 2, (3000.0, 800.0, 150.0)))
+        o = M.zoom_opts(prior=(2, (3000.0, 800.0, 150.0)))
         rc = L.mrf_zoom_search_static(ctx, h, C.byref(g), C.byref(o), C.c_void_p(fp.data_ptr()), 4,
                                       C.c_void_p(out.data_ptr()), None)
         assert rc == M.MRF_E_UNSUPPORTED
