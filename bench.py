@@ -43,6 +43,9 @@ FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1
 # FP32 flops per timepoint of one candidate in the on-the-fly recurrence with an
 # x-axis RF (RF 6, two free evolutions 2 x 7, correlation and norm 12)
 FLOPS_PER_TP = 32.0
+# bound on |approximate - exact| CC of unit vectors stored in bf16 / e4m3 (relative
+# rounding u per operand, both operands rounded: sqrt(2) (2u + u^2)), plus FP32 slack
+CERT_EPS = {1: math.sqrt(2) * (2 * 2 ** -9 + 2 ** -18) + 1e-5, 2: math.sqrt(2) * (2 * 2 ** -4 + 2 ** -8) + 1e-5}
 
 
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "match_kernel_f32_traffic_147k_4096.txt")
@@ -240,6 +243,11 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
     V = x_dev.shape[0]
     g = S.GRIDS[GRID]
     D = M.mrf_grid_count(g)
+    # the matcher MMA shape's own dense rate (mrf_mma_rate): the FP8 roofline, and a check of the
+    # measured bf16 peak
+    mma_rates = {M.MRF_BF16: M.mrf_mma_rate(ctx, M.MRF_BF16), M.MRF_FP8E4M3: M.mrf_mma_rate(ctx, M.MRF_FP8E4M3)}
+    modes["mma_rate_tflops"] = {"bf16": mma_rates[M.MRF_BF16], "fp8e4m3": mma_rates[M.MRF_FP8E4M3],
+                                "note": "tcgen05.mma M=128 N=256 from shared memory, one CTA per SM, CUDA events"}
 
     def match_mode(name, grid_name, dtype, k, ref_index=None, refine=False):
         gg = S.GRIDS[grid_name]
@@ -264,13 +272,30 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
         mm = prof.matcher_ms / max(prof.matcher_timed, 1)
         flops = 8.0 * N_TP * Dg * V
         peak = pk["bf16_tflops"] * (2.0 if dtype == M.MRF_FP8E4M3 else 1.0)
+        own = mma_rates.get(dtype)
         entry = {"grid": grid_name, "entries": Dg, "dtype": ["f32 (bf16x3)", "bf16", "fp8e4m3"][dtype], "top_k": k,
                  "voxels_per_s": V / ms * 1e3, "ms": ms, "matcher_ms": mm, "dict_generate_s": gen_s,
                  "matcher_tflops_algorithmic": flops / mm / 1e9,
                  "matcher_frac_of_peak": flops / mm / 1e9 / peak,
                  "peak_tflops": peak, "peak_note": "bf16 measured" + (" x 2 (fp8 nominal ratio)" if dtype == 2 else "")}
+        if own:
+            entry["matcher_frac_of_measured_mma_rate"] = flops / mm / 1e9 / own
+            entry["measured_mma_rate_tflops"] = own
         if refine:
             entry["refined"] = "windowed refinement (26-point hill climb, FP64 CC) after the re-score, timed"
+        if dtype != M.MRF_F32 and not refine:
+            # rigorous certificate of the candidate list: a_1 - a_k > 2 eps (eps bounds the
+            # low-precision CC error) means no entry outside the list can beat its best
+            idx = torch.empty((V, k), dtype=torch.int64, device="cuda")
+            cc2 = torch.empty((V, k), dtype=torch.float32, device="cuda")
+            M.mrf_match_topk(ctx, d, x_dev, dtype, k, idx, cc2)
+            torch.cuda.synchronize()
+            c2 = cc2.cpu().numpy()
+            eps = CERT_EPS[dtype]
+            a1, ak = np.sqrt(np.maximum(c2[:, 0], 0)), np.sqrt(np.maximum(c2[:, -1], 0))
+            entry["certified_voxels"] = int(np.sum(a1 - ak > 2 * eps))
+            entry["uncertified_voxels"] = int(V - entry["certified_voxels"])
+            entry["certificate"] = f"a_1 - a_{k} > 2 eps, eps = {eps:.3g} (rigorous bound of the stored precision)"
         if ref_index is not None:
             entry["index_agreement_vs_fp32"] = float(np.mean(res["index"] == ref_index))
         if ph is not None:
@@ -506,11 +531,17 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
         "ms": ms_prior, "voxels_per_s": xwd.shape[0] / ms_prior * 1e3,
         "plain_ms": ms_plain, "plain_voxels_per_s": xwd.shape[0] / ms_plain * 1e3,
         "index_agreement_with_plain": float(np.mean(rp["index"] == rw["index"])),
+        "within_one_step_of_plain": float(np.mean((np.abs(rp["i_t1"] - rw["i_t1"]) <= 1) &
+                                                  (np.abs(rp["i_t2"] - rw["i_t2"]) <= 1) &
+                                                  (np.abs(rp["i_df"] - rw["i_df"]) <= 1))),
+        "cc_minus_plain_median": float(np.median(rp["cc"] - rw["cc"])),
+        "cc_at_least_plain_fraction": float(np.mean(rp["cc"] >= rw["cc"])),
         "mean_entries_evaluated": float(rp["entries_evaluated"].mean()),
         "plain_mean_entries_evaluated": float(rw["entries_evaluated"].mean()),
         "single_chain_32x32": {
             "voxels": int(x32d.shape[0]), "ms": ms_chain, "voxels_per_s": x32d.shape[0] / ms_chain * 1e3,
             "index_agreement_with_plain": float(np.mean(r32p["index"] == r32["index"])),
+            "cc_minus_plain_median": float(np.median(r32p["cc"] - r32["cc"])),
             "mean_entries_evaluated": float(r32p["entries_evaluated"].mean()),
             "plain_mean_entries_evaluated": float(r32["entries_evaluated"].mean()),
             "note": "the paper's single raster chain (phantom seed 108): one voxel after another"}}

@@ -126,14 +126,33 @@ int mrf_profile_read(mrf_ctx *ctx, mrf_profile *out, int reset);
  * few milliseconds and synchronises the device. */
 int mrf_fp32_fma_rate(mrf_ctx *ctx, double *tflops);
 
+/* The dense tensor-core rate of the matcher's MMA shape (the roofline of the
+ * BF16 and FP8 brute-force forms): tcgen05.mma kind::f16 (bf16) or
+ * kind::f8f6f4 (e4m3), M = 128, N = 256, FP32 accumulation in TMEM, operands
+ * resident in 128-byte-swizzled shared memory, one CTA per SM issuing
+ * back-to-back MMAs; timed with CUDA events, best of three after a warm-up;
+ * *tflops = 2 M N K x MMAs / time. precision: MRF_BF16 or MRF_FP8E4M3. Takes
+ * some tens of milliseconds and synchronises the library's stream. Errors:
+ * MRF_E_INVALID, MRF_E_CUDA (a wait that timed out is reported by
+ * mrf_stream_sync). */
+int mrf_mma_rate(mrf_ctx *ctx, int32_t precision, double *tflops);
+
 /* ------------------------------------------------------------------------ */
 /* Sequence (Methods: IR-bSSFP train; Appendix: hard RF pulse)              */
 
 /* Acquisition train of n timepoints. For timepoint j the simulator applies
- * the hard RF pulse R_z(phi_j) R_x(-alpha_j) R_z(-phi_j) (Appendix, small-beta
- * form), evolves TE_j, samples s_j = Mx + i My, then evolves TR_j - TE_j.
- * With inversion != 0 an ideal 180 degree pulse about x and inv_delay_ms of
- * free evolution come first. Equilibrium magnetisation M0 = 1. */
+ * the RF pulse, evolves TE_j, samples s_j = Mx + i My, then evolves TR_j -
+ * TE_j. A hard pulse (tau_j = 0) is R_z(phi_j) R_x(-alpha_j) R_z(-phi_j)
+ * (Appendix, small-beta form). A pulse of duration tau_j > 0 is the
+ * Appendix's off-resonant form R_z(phi) R_y(beta) R_x(alpha') R_y(-beta)
+ * R_z(-phi) for each candidate's df: beta = atan2(tau dw, alpha) is the angle
+ * of the effective field from the x axis and alpha' = -sqrt(alpha^2 + (tau
+ * dw)^2) the rotation about it over the pulse, dw = 2 pi df / 1000 rad/ms
+ * (the printed arctangent for alpha > 0; the Appendix's Delta-t in alpha' is
+ * the pulse duration). No relaxation acts during a pulse; TE_j and TR_j are
+ * counted from the pulse. With inversion != 0 an ideal 180 degree pulse about
+ * x and inv_delay_ms of free evolution come first. Equilibrium magnetisation
+ * M0 = 1. */
 typedef struct {
     int32_t n;                   /* timepoints, >= 1 */
     const double *flip_rad;      /* n signed flip angles alpha_j */
@@ -142,14 +161,15 @@ typedef struct {
     const double *te_ms;         /* n echo times, 0 <= TE_j <= TR_j */
     int32_t inversion;           /* 0 or 1 */
     double inv_delay_ms;         /* >= 0 */
+    const double *pulse_ms;      /* n RF pulse durations tau_j >= 0, or NULL for hard pulses */
 } mrf_sequence_desc;
 
 /* Copy a host sequence to the device (FP64 host values; per-timepoint RF
  * rotation coefficients are formed in FP64 on the host and stored as FP32).
  * Synchronous for the upload only: it runs on the library's own stream and
  * does not wait for work queued on the caller's streams. Errors:
- * MRF_E_INVALID (n < 1, non-finite values, TE outside [0, TR], TR <= 0),
- * MRF_E_BUDGET, MRF_E_CUDA.
+ * MRF_E_INVALID (n < 1, non-finite values, TE outside [0, TR], TR <= 0, a
+ * negative pulse duration), MRF_E_BUDGET, MRF_E_CUDA.
  * mrf_sequence_free waits for all work on the device, then releases the
  * sequence. mrf_sequence_free_async releases it in the order of `stream`
  * without waiting: every use of the sequence must already be enqueued on

@@ -46,7 +46,7 @@ class MrfError(RuntimeError):
 class SequenceDesc(C.Structure):
     _fields_ = [("n", C.c_int32), ("flip_rad", C.POINTER(C.c_double)), ("rf_phase_rad", C.POINTER(C.c_double)),
                 ("tr_ms", C.POINTER(C.c_double)), ("te_ms", C.POINTER(C.c_double)),
-                ("inversion", C.c_int32), ("inv_delay_ms", C.c_double)]
+                ("inversion", C.c_int32), ("inv_delay_ms", C.c_double), ("pulse_ms", C.POINTER(C.c_double))]
 
 
 class GridDesc(C.Structure):
@@ -120,7 +120,7 @@ EXPORTS = [
     "mrf_zoom_opts_default", "mrf_zoom_search", "mrf_serve_start", "mrf_serve_submit", "mrf_serve_poll",
     "mrf_serve_cancel", "mrf_serve_get_stats", "mrf_serve_stop", "mrf_profile_enable", "mrf_profile_read",
     "mrf_zoom_search_static", "mrf_zoom_search_dict", "mrf_refine", "mrf_smooth", "mrf_dict_smooth",
-    "mrf_dict_free_async", "mrf_sequence_free_async", "mrf_fp32_fma_rate",
+    "mrf_dict_free_async", "mrf_sequence_free_async", "mrf_fp32_fma_rate", "mrf_mma_rate",
 ]
 
 
@@ -174,6 +174,7 @@ def lib():
         L.mrf_profile_enable.argtypes = [vp, C.c_int]
         L.mrf_profile_read.argtypes = [vp, C.POINTER(Profile), C.c_int]
         L.mrf_fp32_fma_rate.argtypes = [vp, C.POINTER(C.c_double)]
+        L.mrf_mma_rate.argtypes = [vp, C.c_int32, C.POINTER(C.c_double)]
         L.mrf_zoom_search_static.argtypes = [vp, vp, C.POINTER(GridDesc), C.POINTER(ZoomOpts), vp, i64, vp, vp]
         L.mrf_zoom_search_dict.argtypes = [vp, vp, C.POINTER(ZoomOpts), vp, i64, vp, vp]
         _lib = L
@@ -242,13 +243,16 @@ class _SeqArrays:
         self.phase = None if ph is None else np.ascontiguousarray(ph, np.float64)
         self.tr = np.ascontiguousarray(seq.tr_ms, np.float64)
         self.te = np.ascontiguousarray(seq.te_ms, np.float64)
+        pu = getattr(seq, "pulse_ms", None)
+        self.pulse = None if pu is None else np.ascontiguousarray(pu, np.float64)
         dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else C.POINTER(C.c_double)()
         self.desc = SequenceDesc(int(self.flip.shape[0]), dp(self.flip), dp(self.phase), dp(self.tr), dp(self.te),
-                                 int(seq.inversion), float(seq.inv_delay_ms))
+                                 int(seq.inversion), float(seq.inv_delay_ms), dp(self.pulse))
 
 
 def mrf_sequence_load(ctx, seq):
-    """seq: object with flip_rad, rf_phase_rad (or None), tr_ms, te_ms, inversion, inv_delay_ms."""
+    """seq: object with flip_rad, rf_phase_rad (or None), tr_ms, te_ms, inversion, inv_delay_ms
+    and optionally pulse_ms (RF pulse durations, None for hard pulses)."""
     arr = _SeqArrays(seq)
     h = C.c_void_p()
     check(lib().mrf_sequence_load(ctx, C.byref(arr.desc), C.byref(h)), "mrf_sequence_load")
@@ -412,6 +416,13 @@ def mrf_fp32_fma_rate(ctx) -> float:
     """Measured FP32 FMA rate of the device, TFLOP/s."""
     t = C.c_double()
     check(lib().mrf_fp32_fma_rate(ctx, C.byref(t)), "mrf_fp32_fma_rate")
+    return float(t.value)
+
+
+def mrf_mma_rate(ctx, precision) -> float:
+    """Measured dense tensor-core rate of the matcher's MMA shape (MRF_BF16 or MRF_FP8E4M3), TFLOP/s."""
+    t = C.c_double()
+    check(lib().mrf_mma_rate(ctx, int(precision), C.byref(t)), "mrf_mma_rate")
     return float(t.value)
 
 

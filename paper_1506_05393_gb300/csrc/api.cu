@@ -318,24 +318,32 @@ extern "C" int mrf_sequence_load(mrf_ctx *ctx, const mrf_sequence_desc *d, mrf_s
     if (n < 1 || !d->flip_rad || !d->tr_ms || !d->te_ms) return set_error(MRF_E_INVALID, "sequence: n < 1 or NULL array");
     if (d->inversion != 0 && d->inversion != 1) return set_error(MRF_E_INVALID, "sequence: inversion must be 0 or 1");
     if (!is_fin(d->inv_delay_ms) || d->inv_delay_ms < 0) return set_error(MRF_E_INVALID, "sequence: bad inversion delay");
-    bool xonly = true, symmetric = true;
+    bool xonly = true, symmetric = true, finite = false;
     double min_tr = INFINITY;
     for (int j = 0; j < n; ++j) {
         double a = d->flip_rad[j], tr = d->tr_ms[j], te = d->te_ms[j];
         double ph = d->rf_phase_rad ? d->rf_phase_rad[j] : 0.0;
-        if (!is_fin(a) || !is_fin(tr) || !is_fin(te) || !is_fin(ph))
+        double tp = d->pulse_ms ? d->pulse_ms[j] : 0.0;
+        if (!is_fin(a) || !is_fin(tr) || !is_fin(te) || !is_fin(ph) || !is_fin(tp))
             return set_error(MRF_E_INVALID, "sequence: non-finite value at j=" + std::to_string(j));
+        if (tp < 0) return set_error(MRF_E_INVALID, "sequence: negative pulse duration at j=" + std::to_string(j));
+        if (tp > 0) finite = true;
         if (!(tr > 0) || te < 0 || te > tr)
             return set_error(MRF_E_INVALID, "sequence: need TR > 0 and 0 <= TE <= TR at j=" + std::to_string(j));
         if (fabs(sin(ph)) > 1e-12) xonly = false;
         if (fabs(te - (tr - te)) > 1e-12 * tr) symmetric = false;
         if (tr < min_tr) min_tr = tr;
     }
+    if (finite) xonly = false;   // the effective field of a finite pulse is tilted out of the x-y plane
     std::vector<float4> rfx(n);
     std::vector<float> rfg(12 * (size_t)n, 0.f);
     std::vector<float2> tau(n);
+    std::vector<float4> rff(n);
     for (int j = 0; j < n; ++j) {
         double a = d->flip_rad[j], ph = d->rf_phase_rad ? d->rf_phase_rad[j] : 0.0;
+        // finite pulse (Appendix): rotation about (-alpha cos phi, -alpha sin phi, tau dw) by its length
+        const double tp = d->pulse_ms ? d->pulse_ms[j] : 0.0;
+        rff[j] = make_float4((float)(-a * cos(ph)), (float)(-a * sin(ph)), (float)(a * a), (float)(2.0 * M_PI * tp));
         // Hard pulse R_z(phi) R_x(-alpha) R_z(-phi) (Appendix). For phi = k pi it is
         // a rotation about x by beta = -alpha (k even) or +alpha (k odd).
         double beta = cos(ph) > 0 ? -a : a;
@@ -355,21 +363,24 @@ extern "C" int mrf_sequence_load(mrf_ctx *ctx, const mrf_sequence_desc *d, mrf_s
     cudaSetDevice(ctx->device);
     mrf_seq *s = new mrf_seq();
     s->n = n; s->xonly = xonly; s->symmetric = symmetric; s->inversion = d->inversion;
-    s->inv_delay = d->inv_delay_ms; s->min_tr = min_tr;
-    // rfx | rfg | tau in one block, 256-byte aligned pieces
+    s->inv_delay = d->inv_delay_ms; s->min_tr = min_tr; s->finite = finite;
+    // rfx | rfg | tau | rff in one block, 256-byte aligned pieces
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t b1 = sizeof(float4) * n, b2 = sizeof(float) * 12 * (size_t)n, b3 = sizeof(float2) * n;
-    const size_t o2 = al(b1), o3 = o2 + al(b2), total = o3 + al(b3);
+    const size_t b4 = sizeof(float4) * n;
+    const size_t o2 = al(b1), o3 = o2 + al(b2), o4 = o3 + al(b3), total = o4 + al(b4);
     std::vector<uint8_t> h(total, 0);
     memcpy(h.data(), rfx.data(), b1);
     memcpy(h.data() + o2, rfg.data(), b2);
     memcpy(h.data() + o3, tau.data(), b3);
+    memcpy(h.data() + o4, rff.data(), b4);
     int rc = upload_block(ctx, h.data(), total, &s->block, "sequence upload");
     if (rc) { delete s; return rc; }
     s->bytes = total;
     s->rfx = (float4 *)s->block;
     s->rfg = (float *)((uint8_t *)s->block + o2);
     s->tau = (float2 *)((uint8_t *)s->block + o3);
+    s->rff = (float4 *)((uint8_t *)s->block + o4);
     *out = s;
     return MRF_OK;
 }
@@ -394,6 +405,7 @@ int seq_clone(mrf_ctx *ctx, const mrf_seq *src, mrf_seq **out)
     s->rfx = (float4 *)((uint8_t *)src->rfx + d);
     s->rfg = (float *)((uint8_t *)src->rfg + d);
     s->tau = (float2 *)((uint8_t *)src->tau + d);
+    s->rff = (float4 *)((uint8_t *)src->rff + d);
     *out = s;
     return MRF_OK;
 }

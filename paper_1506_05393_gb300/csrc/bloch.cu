@@ -109,9 +109,9 @@ __device__ __forceinline__ void unravel(const GridDev &g, int64_t e, int &a, int
 // intervals of the step).
 template <bool XONLY, bool SYM>
 __device__ __forceinline__ void step_tab(Bloch &st, const SeqDev &s, const Tables &t, int n, int n_df, int a, int b,
-                                         int c, int j, float &sr, float &si)
+                                         int c, int j, float fdf, float &sr, float &si)
 {
-    bloch_rf<XONLY>(st, s, j);
+    bloch_rf<XONLY>(st, s, j, fdf);
     if (SYM) {
         const float e1 = __ldg(&t.e1s[(int64_t)a * n + j]);
         const float e2 = __ldg(&t.e2s[(int64_t)b * n + j]);
@@ -164,10 +164,10 @@ __device__ __forceinline__ void fac_load(FacGroup &f, const FacRows &r, int jb)
 
 // One timepoint from preloaded symmetric factors (the same arithmetic as step_tab).
 template <bool XONLY>
-__device__ __forceinline__ void step_fac(Bloch &st, const SeqDev &s, const FacGroup &f, int g, int j, float &sr,
-                                         float &si)
+__device__ __forceinline__ void step_fac(Bloch &st, const SeqDev &s, const FacGroup &f, int g, int j, float fdf,
+                                         float &sr, float &si)
 {
-    bloch_rf<XONLY>(st, s, j);
+    bloch_rf<XONLY>(st, s, j, fdf);
     const float zr = f.e2[g] * f.z[g].x, zi = f.e2[g] * f.z[g].y;
     bloch_evolve(st, f.e1[g], zr, zi);
     sr = st.mx;
@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
     const int n = s.n;
     int a = 0, b = 0, c = 0;
     if (live) unravel(g, e, a, b, c);
+    const float fdf = live && s.finite ? __ldg(&g.df[c]) * 1.0e-3f : 0.f;   // finite pulses: RF depends on df
     const float e1inv = live && s.inversion ? __ldg(&t.e1_inv[a]) : 1.f;
     FacRows fr;
     if (SYM) {
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
                     const int j = j0 + q;
                     if (j < n) {
                         float sr, si;
-                        step_fac<XONLY>(st, s, cur, q, j, sr, si);
+                        step_fac<XONLY>(st, s, cur, q, j, fdf, sr, si);
                         part = fmaf(sr, sr, fmaf(si, si, part));
                         if (OUT == MRF_FP8E4M3) amax = fmaxf(amax, fmaxf(fabsf(sr), fabsf(si)));
                     }
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
 #pragma unroll 8
                 for (int j = j0; j < j1; ++j) {
                     float sr, si;
-                    step_tab<XONLY, SYM>(st, s, t, n, g.n_df, a, b, c, j, sr, si);
+                    step_tab<XONLY, SYM>(st, s, t, n, g.n_df, a, b, c, j, fdf, sr, si);
                     part = fmaf(sr, sr, fmaf(si, si, part));
                     if (OUT == MRF_FP8E4M3) amax = fmaxf(amax, fmaxf(fabsf(sr), fabsf(si)));
                 }
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
                     vr[q] = 0.f;
                     vi[q] = 0.f;
                     if (live && j < n) {
-                        step_fac<XONLY>(st, s, cur, q, j, vr[q], vi[q]);
+                        step_fac<XONLY>(st, s, cur, q, j, fdf, vr[q], vi[q]);
                         if (kOnePass) part1 = fmaf(vr[q], vr[q], fmaf(vi[q], vi[q], part1));
                     }
                 }
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
                     float vr = 0.f, vi = 0.f;
                     if (live && j < n) {
                         float sr, si;
-                        step_tab<XONLY, SYM>(st, s, t, n, g.n_df, a, b, c, j, sr, si);
+                        step_tab<XONLY, SYM>(st, s, t, n, g.n_df, a, b, c, j, fdf, sr, si);
                         vr = sr;
                         vi = si;
                         if (kOnePass) part1 = fmaf(sr, sr, fmaf(si, si, part1));

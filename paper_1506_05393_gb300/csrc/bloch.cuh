@@ -1,8 +1,10 @@
-// Bloch propagation on the GPU (Appendix, Eq. A2 with the hard-pulse RF form
-// and the recovery term of Eq. A1), FP32, one fingerprint per thread.
+// Bloch propagation on the GPU (Appendix, Eq. A2 with the hard-pulse RF form,
+// or the off-resonant form for pulses of finite duration, and the recovery
+// term of Eq. A1), FP32, one fingerprint per thread.
 //
 // State (mx, my, w) with w = 1 - Mz. Per timepoint j:
-//   RF:  M <- R_z(phi_j) R_x(-alpha_j) R_z(-phi_j) M     (coefficients from SeqDev)
+//   RF:  M <- R_z(phi_j) R_x(-alpha_j) R_z(-phi_j) M     (coefficients from SeqDev;
+//        finite pulses: the effective-field rotation, per candidate df)
 //   evolve TE_j:         (mx + i my) <- E2 e^{i theta} (mx + i my),  w <- E1 w
 //   sample s_j = mx + i my
 //   evolve TR_j - TE_j
@@ -39,6 +41,39 @@ __device__ __forceinline__ void bloch_rf_general(Bloch &st, const float *q)
     st.mx = fmaf(q[0], mx, fmaf(q[1], my, fmaf(-q[2], w, q[2])));
     st.my = fmaf(q[3], mx, fmaf(q[4], my, fmaf(-q[5], w, q[5])));
     st.w = fmaf(q[8], w, fmaf(-q[6], mx, fmaf(-q[7], my, q[9])));
+}
+
+// RF pulse of finite duration tau off resonance by df (Appendix): R_RF =
+// R_z(phi) R_y(beta) R_x(alpha') R_y(-beta) R_z(-phi) is the counterclockwise
+// rotation by theta = |a| about a = (-alpha cos phi, -alpha sin phi, tau dw),
+// dw = 2 pi df / 1000 rad/ms (the RF and off-resonance fields acting
+// together), written in Rodrigues' form with half-angle factors,
+//   R = cos(theta) I + k1 [a]x + k2 a a^T,  h = theta / 2,
+//   k1 = sin(theta) / theta = sinc(h) cos(h),  k2 = (1 - cos theta) / theta^2 = sinc(h)^2 / 2,
+// and 1 - R22 = k2 alpha^2 in deficit form. p = (-alpha cos phi, -alpha sin
+// phi, alpha^2, 2 pi tau), f = df / 1000 (cycles per ms). Accurate sqrtf and
+// sincosf.
+__device__ __forceinline__ void bloch_rf_finite(Bloch &st, float4 p, float f)
+{
+    const float ax = p.x, ay = p.y, az = p.w * f;
+    const float h = 0.5f * sqrtf(fmaf(az, az, p.z));
+    float sh, ch;
+    sincosf(h, &sh, &ch);
+    const float sc = h > 0.f ? sh / h : 1.f;
+    const float k1 = sc * ch, k2 = 0.5f * sc * sc;
+    const float cth = fmaf(-2.f * sh, sh, 1.f);
+    float q[10];
+    q[0] = fmaf(k2 * ax, ax, cth);
+    q[1] = fmaf(k2 * ax, ay, -k1 * az);
+    q[2] = fmaf(k2 * ax, az, k1 * ay);
+    q[3] = fmaf(k2 * ay, ax, k1 * az);
+    q[4] = fmaf(k2 * ay, ay, cth);
+    q[5] = fmaf(k2 * ay, az, -k1 * ax);
+    q[6] = fmaf(k2 * az, ax, -k1 * ay);
+    q[7] = fmaf(k2 * az, ay, k1 * ax);
+    q[8] = fmaf(k2 * az, az, cth);
+    q[9] = k2 * p.z;
+    bloch_rf_general(st, q);
 }
 
 // Free evolution with precomputed z = E2 e^{i theta} and E1.
@@ -89,12 +124,16 @@ __device__ __forceinline__ void relax_factors(const Relax &r, float tau, float &
     zi = e2 * sn;
 }
 
-// RF pulse of timepoint j (dispatch on the sequence kind; `xonly` is uniform).
+// RF pulse of timepoint j for a candidate off resonance by f = df / 1000
+// cycles per ms (dispatch on the sequence kind; `xonly` and `finite` are
+// uniform).
 template <bool XONLY>
-__device__ __forceinline__ void bloch_rf(Bloch &st, const SeqDev &s, int j)
+__device__ __forceinline__ void bloch_rf(Bloch &st, const SeqDev &s, int j, float f)
 {
     if (XONLY) {
         bloch_rf_x(st, __ldg(&s.rfx[j]));
+    } else if (s.finite) {
+        bloch_rf_finite(st, __ldg(&s.rff[j]), f);
     } else {
         float q[10];
         const float4 *p = reinterpret_cast<const float4 *>(s.rfg + 12 * j);
@@ -123,7 +162,7 @@ template <bool XONLY>
 __device__ __forceinline__ void bloch_step_otf(Bloch &st, const SeqDev &s, const Relax &r, int j, float &sr,
                                                float &si)
 {
-    bloch_rf<XONLY>(st, s, j);
+    bloch_rf<XONLY>(st, s, j, r.f);
     const float2 tau = __ldg(&s.tau[j]);
     float e1, zr, zi;
     relax_factors(r, tau.x, e1, zr, zi);

@@ -28,6 +28,8 @@ struct SeqDev {
     const float4 *rfx;  // xonly: (c, s, 1 - c, TE_j) of the x-rotation by beta_j
     const float *rfg;   // general: 12 floats per j: R00..R22 row-major, 1 - R22, 0, 0
     const float2 *tau;  // (TE_j, TR_j - TE_j) in ms
+    int finite;         // some RF pulse has a finite duration: R_RF depends on df (xonly is 0 then)
+    const float4 *rff;  // finite: (-alpha cos phi, -alpha sin phi, alpha^2, 2 pi tau) per j
 };
 
 struct GridDev {
@@ -49,15 +51,18 @@ struct mrf_seq {
     int xonly = 0, symmetric = 0, inversion = 0;
     double inv_delay = 0.0;
     double min_tr = 0.0;
-    float4 *rfx = nullptr;      // rfx, rfg and tau live in one block from the stream-ordered pool
+    int finite = 0;
+    float4 *rfx = nullptr;      // rfx, rfg, tau and rff live in one block from the stream-ordered pool
     float *rfg = nullptr;
     float2 *tau = nullptr;
+    float4 *rff = nullptr;
     void *block = nullptr;
     size_t bytes = 0;
     SeqDev dev() const {
         SeqDev s;
         s.n = n; s.xonly = xonly; s.symmetric = symmetric; s.inversion = inversion;
         s.inv_delay = (float)inv_delay; s.rfx = rfx; s.rfg = rfg; s.tau = tau;
+        s.finite = finite; s.rff = rff;
         return s;
     }
 };

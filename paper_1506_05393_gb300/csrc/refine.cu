@@ -43,7 +43,7 @@ __device__ __forceinline__ void refine_point(const SeqDev &s, const float2 *__re
         float pr = 0.f, pi = 0.f, pd = 0.f;
         const int j1 = min(n, j0 + 8);
         for (int j = j0; j < j1; ++j) {
-            bloch_rf<XONLY>(st, s, j);
+            bloch_rf<XONLY>(st, s, j, r.f);
             const float2 tau = __ldg(&s.tau[j]);
             float e1, zr, zi;
             relax_factors(r, tau.x, e1, zr, zi);

@@ -90,6 +90,7 @@ struct ZoomArgs {
     int chain_len;
     int prior_h1, prior_h2, prior_h3;
     int prior_start;
+    int max_slots;           // slots per warp that take new work (1..kSlots): few chains spread over warps
     unsigned long long *stats;   // work counters: [2] warp rounds, [3] candidates simulated, [4] most rounds of a voxel
 };
 
@@ -154,9 +155,13 @@ __device__ __forceinline__ void step_multi(const SeqDev &s, int j, const float (
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
     float q[10];
     float ta, tb = 0.f;
+    const bool fin = !XONLY && s.finite;   // finite pulses: each candidate's rotation depends on its df
     if (XONLY) {
         r = __ldg(&s.rfx[j]);
         ta = r.w;
+    } else if (fin) {
+        r = __ldg(&s.rff[j]);
+        ta = __ldg(&s.tau[j]).x;
     } else {
         const float4 *p = reinterpret_cast<const float4 *>(s.rfg + 12 * j);
         const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
@@ -169,6 +174,7 @@ __device__ __forceinline__ void step_multi(const SeqDev &s, int j, const float (
 #pragma unroll
     for (int u = 0; u < C; ++u) {
         if (XONLY) bloch_rf_x(st[u], r);
+        else if (fin) bloch_rf_finite(st[u], r, f[u]);
         else bloch_rf_general(st[u], q);
         float cs, sn;
         const float e1 = ex2_fast(k1[u] * ta), e2 = ex2_fast(k2[u] * ta);
@@ -1240,7 +1246,8 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
             // work or the voxels run out, so no warp leaves with voxels left; a
             // slot in a prior chain goes on with the chain's next voxel
             for (;;) {
-                while (S.v < 0 && (S.chain_next < S.chain_end || !W.drained)) {
+                const bool takes = s < A.max_slots;
+                while (S.v < 0 && (S.chain_next < S.chain_end || (takes && !W.drained))) {
                     if (A.chain_len > 0 && S.chain_next < S.chain_end) {
                         // the next voxel of the chain: the box of the prior's
                         // half-widths around the preceding voxel's result, cut
@@ -1312,7 +1319,7 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
                     }
                 }
                 advance(W, s, P, A.g, A.max_moves, head);
-                if (S.v >= 0 || (W.drained && S.chain_next >= S.chain_end)) break;
+                if (S.v >= 0 || ((W.drained || !takes) && S.chain_next >= S.chain_end)) break;
             }
             if (S.v >= 0) S.rounds += 1;
         }
@@ -1583,9 +1590,13 @@ __global__ void __launch_bounds__(kLineThreads, 3) zoom_line_kernel(LineArgs L)
             float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
             float q[10];
             float ta, tb = 0.f;
+            const bool fin = !XONLY && L.s.finite;
             if (XONLY) {
                 r = s_rf[jj];
                 ta = r.w;
+            } else if (fin) {
+                r = s_rf[3 * jj];
+                ta = s_tau[jj].x;
             } else {
                 const float4 a4 = s_rf[3 * jj], b4 = s_rf[3 * jj + 1], c4 = s_rf[3 * jj + 2];
                 q[0] = a4.x; q[1] = a4.y; q[2] = a4.z; q[3] = a4.w;
@@ -1595,6 +1606,7 @@ __global__ void __launch_bounds__(kLineThreads, 3) zoom_line_kernel(LineArgs L)
             }
             if (!SYM) tb = s_tau[jj].y;
             if (XONLY) bloch_rf_x(st, r);
+            else if (fin) bloch_rf_finite(st, r, f);
             else bloch_rf_general(st, q);
             float cs, sn;
             const float e1 = ex2_fast(k1 * ta), e2 = ex2_fast(k2 * ta);
@@ -1631,6 +1643,8 @@ __global__ void __launch_bounds__(kLineThreads, 3) zoom_line_kernel(LineArgs L)
             if (tid < len) {
                 if (XONLY) {
                     s_rf[tid] = __ldg(&L.s.rfx[j0 + tid]);
+                } else if (L.s.finite) {
+                    s_rf[3 * tid] = __ldg(&L.s.rff[j0 + tid]);
                 } else {
                     const float4 *p = reinterpret_cast<const float4 *>(L.s.rfg + 12 * (j0 + tid));
                     s_rf[3 * tid] = __ldg(p);
@@ -1818,9 +1832,18 @@ int zoom_with_chains(mrf_ctx *ctx, const ZoomPlan &P, const SeqDev &sd, const Gr
     A.prior_h3 = steps(o->prior_df_hz, gd->df_step, gd->n_df);
     A.prior_start = o->prior_start;
     A.stats = ctx->dev_stats;
+    // chains run one voxel after another: spread them over the resident warps,
+    // as few per warp as fill the device (a warp's candidate table then serves
+    // fewer chains, which advance in fewer rounds)
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, zoom_pack_kernel<true, true>, kPackThreads, 0);
+    const int64_t warps = (int64_t)std::max(1, per_sm) * ctx->sm_count * kPackWarps;
+    A.max_slots = (int)std::min<int64_t>(kSlots, std::max<int64_t>(1, (chains + warps - 1) / warps));
+    const int64_t per_cta = (int64_t)A.max_slots * kPackWarps;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(warps / kPackWarps, (chains + per_cta - 1) / per_cta));
     {
         ProfScope prof(ctx, kProfZoom, stream);
-        launch_pack(A, pack_blocks(ctx, chains), stream);
+        launch_pack(A, blocks, stream);
     }
     e = cudaGetLastError();
     cudaFreeAsync(counter, stream);
@@ -1831,12 +1854,12 @@ int zoom_with_chains(mrf_ctx *ctx, const ZoomPlan &P, const SeqDev &sd, const Gr
 
 }  // namespace
 
-int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mrf_zoom_opts *o, const void *fp,
-             int64_t V, mrf_result *out, cudaStream_t stream)
+// The search plan on the host, in FP64, with the stage machine's snapping
+// rules (every on-the-fly and dictionary-backed search uses this one).
+static int plan_zoom(const mrf_seq *seq, const mrf_grid_desc *gd, const mrf_zoom_opts *o, ZoomPlan &P)
 {
-    // plan on the host, in FP64, with the stage machine's snapping rules
     const double omega = o->omega_hz > 0 ? o->omega_hz : 1000.0 / seq->min_tr;
-    ZoomPlan P{};
+    P = ZoomPlan{};
     int a = (int)floor((o->t1_init_ms - gd->t1_min) / gd->t1_step + 0.5);
     int b = (int)floor((o->t2_init_ms - gd->t2_min) / gd->t2_step + 0.5);
     P.a_raw = a;
@@ -1844,8 +1867,7 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     a = std::max(0, std::min(a, gd->n_t1 - 1));
     b = std::max(0, std::min(b, gd->n_t2 - 1));
     auto valid = [&](int aa, int bb) {
-        if (!gd->require_t2_lt_t1) return true;
-        return gd->t2_min + (double)bb * gd->t2_step < gd->t1_min + (double)aa * gd->t1_step;
+        return !gd->require_t2_lt_t1 || gd->t2_min + (double)bb * gd->t2_step < gd->t1_min + (double)aa * gd->t1_step;
     };
     while (b > 0 && !valid(a, b)) --b;
     while (a < gd->n_t1 - 1 && !valid(a, b)) ++a;
@@ -1853,35 +1875,36 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     P.a0 = a;
     P.b0 = b;
     P.hA = snap(o->s1a_step_frac * omega, gd->df_step);
-    const int W1 = (int)floor(o->s1b_half_frac * omega / gd->df_step + 0.5);
     P.hB = snap(o->s1b_step_frac * omega, gd->df_step);
-    P.K1b = W1 / P.hB;
+    P.K1b = (int)floor(o->s1b_half_frac * omega / gd->df_step + 0.5) / P.hB;
     P.hC = snap(omega, gd->df_step);
     P.W3 = (int)floor(o->s3_half_frac * omega / gd->df_step + 0.5);
-    int ph1 = -1, ph2 = -1;
-    for (int l = 0; l < o->n_s2; ++l) {
+    for (int l = 0, p1 = -1, p2 = -1; l < o->n_s2; ++l) {
         const int h1 = snap(o->s2_t1_ms[l], gd->t1_step), h2 = snap(o->s2_t2_ms[l], gd->t2_step);
-        if (h1 == ph1 && h2 == ph2) continue;
-        ph1 = h1; ph2 = h2;
-        P.s2_h1[P.n_s2] = h1;
-        P.s2_h2[P.n_s2] = h2;
-        P.n_s2++;
+        if (h1 == p1 && h2 == p2) continue;
+        p1 = h1; p2 = h2;
+        P.s2_h1[P.n_s2] = h1; P.s2_h2[P.n_s2] = h2; P.n_s2++;
     }
-    int pp = -1, phh = -1;
-    for (int l = 0; l < o->n_s4; ++l) {
-        const int p = o->s4_param[l];
-        const int h = snap(o->s4_ms[l], p == 0 ? gd->t1_step : gd->t2_step);
-        if (p == pp && h == phh) continue;
-        pp = p; phh = h;
-        P.s4_p[P.n_s4] = p;
-        P.s4_h[P.n_s4] = h;
-        P.n_s4++;
+    for (int l = 0, pp = -1, ph = -1; l < o->n_s4; ++l) {
+        const int p = o->s4_param[l], h = snap(o->s4_ms[l], p == 0 ? gd->t1_step : gd->t2_step);
+        if (p == pp && h == ph) continue;
+        pp = p; ph = h;
+        P.s4_p[P.n_s4] = p; P.s4_h[P.n_s4] = h; P.n_s4++;
     }
+    return MRF_OK;
+}
+
+int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mrf_zoom_opts *o, const void *fp,
+             int64_t V, mrf_result *out, cudaStream_t stream)
+{
+    ZoomPlan P;
+    int rc = plan_zoom(seq, gd, o, P);
+    if (rc) return rc;
 
     GridDev gdev;
     void *gblock = nullptr;
     size_t gbytes = 0;
-    int rc = grid_upload_async(ctx, gd, stream, &gdev, &gblock, &gbytes);
+    rc = grid_upload_async(ctx, gd, stream, &gdev, &gblock, &gbytes);
     if (rc) return rc;
 
     if (o->prior_chain > 0) {
@@ -1940,6 +1963,7 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     A.chain_len = 0;
     A.prior_h1 = A.prior_h2 = A.prior_h3 = 0;
     A.prior_start = 0;
+    A.max_slots = kSlots;
     A.state = split ? (ZState *)(sb + o_state) : nullptr;
     A.phase = split ? kPhaseHead : kPhaseAll;
     A.stats = ctx->dev_stats;
@@ -1999,44 +2023,6 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
 // dictionary" variant): the same search on the dictionary's grid, every
 // candidate's CC read from the stored normalised entry.
 
-static int plan_zoom(const mrf_seq *seq, const mrf_grid_desc *gd, const mrf_zoom_opts *o, ZoomPlan &P)
-{
-    const double omega = o->omega_hz > 0 ? o->omega_hz : 1000.0 / seq->min_tr;
-    P = ZoomPlan{};
-    int a = (int)floor((o->t1_init_ms - gd->t1_min) / gd->t1_step + 0.5);
-    int b = (int)floor((o->t2_init_ms - gd->t2_min) / gd->t2_step + 0.5);
-    P.a_raw = a;
-    P.b_raw = b;
-    a = std::max(0, std::min(a, gd->n_t1 - 1));
-    b = std::max(0, std::min(b, gd->n_t2 - 1));
-    auto valid = [&](int aa, int bb) {
-        return !gd->require_t2_lt_t1 || gd->t2_min + (double)bb * gd->t2_step < gd->t1_min + (double)aa * gd->t1_step;
-    };
-    while (b > 0 && !valid(a, b)) --b;
-    while (a < gd->n_t1 - 1 && !valid(a, b)) ++a;
-    if (!valid(a, b)) return set_error(MRF_E_INVALID, "zoom: the grid has no valid starting point");
-    P.a0 = a;
-    P.b0 = b;
-    P.hA = snap(o->s1a_step_frac * omega, gd->df_step);
-    P.hB = snap(o->s1b_step_frac * omega, gd->df_step);
-    P.K1b = (int)floor(o->s1b_half_frac * omega / gd->df_step + 0.5) / P.hB;
-    P.hC = snap(omega, gd->df_step);
-    P.W3 = (int)floor(o->s3_half_frac * omega / gd->df_step + 0.5);
-    for (int l = 0, p1 = -1, p2 = -1; l < o->n_s2; ++l) {
-        const int h1 = snap(o->s2_t1_ms[l], gd->t1_step), h2 = snap(o->s2_t2_ms[l], gd->t2_step);
-        if (h1 == p1 && h2 == p2) continue;
-        p1 = h1; p2 = h2;
-        P.s2_h1[P.n_s2] = h1; P.s2_h2[P.n_s2] = h2; P.n_s2++;
-    }
-    for (int l = 0, pp = -1, ph = -1; l < o->n_s4; ++l) {
-        const int p = o->s4_param[l], h = snap(o->s4_ms[l], p == 0 ? gd->t1_step : gd->t2_step);
-        if (p == pp && h == ph) continue;
-        pp = p; ph = h;
-        P.s4_p[P.n_s4] = p; P.s4_h[P.n_s4] = h; P.n_s4++;
-    }
-    return MRF_OK;
-}
-
 extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_zoom_opts *opts, const void *fp,
                                     int64_t V, mrf_result *out, void *stream_v)
 {
@@ -2085,6 +2071,7 @@ extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_z
     A.chain_len = 0;
     A.prior_h1 = A.prior_h2 = A.prior_h3 = 0;
     A.prior_start = 0;
+    A.max_slots = kSlots;
     A.state = nullptr;
     A.phase = kPhaseAll;
     A.stats = nullptr;
@@ -2173,40 +2160,13 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     cudaStream_t stream = (cudaStream_t)stream_v;
 
-    // the same plan as mrf_zoom_search (FP64 snapping on the host)
-    const double omega = opts->omega_hz > 0 ? opts->omega_hz : 1000.0 / seq->min_tr;
-    ZoomPlan P{};
-    int a = (int)floor((opts->t1_init_ms - gd->t1_min) / gd->t1_step + 0.5);
-    int b = (int)floor((opts->t2_init_ms - gd->t2_min) / gd->t2_step + 0.5);
-    P.a_raw = a;
-    P.b_raw = b;
-    a = std::max(0, std::min(a, gd->n_t1 - 1));
-    b = std::max(0, std::min(b, gd->n_t2 - 1));
+    // the plan of mrf_zoom_search
+    ZoomPlan P;
+    rc = plan_zoom(seq, gd, opts, P);
+    if (rc) return rc;
     auto t1v = [&](int i) { return gd->t1_min + (double)i * gd->t1_step; };
     auto t2v = [&](int i) { return gd->t2_min + (double)i * gd->t2_step; };
     auto valid = [&](int aa, int bb) { return !gd->require_t2_lt_t1 || t2v(bb) < t1v(aa); };
-    while (b > 0 && !valid(a, b)) --b;
-    while (a < gd->n_t1 - 1 && !valid(a, b)) ++a;
-    if (!valid(a, b)) return set_error(MRF_E_INVALID, "zoom: the grid has no valid starting point");
-    P.a0 = a;
-    P.b0 = b;
-    P.hA = snap(opts->s1a_step_frac * omega, gd->df_step);
-    P.hB = snap(opts->s1b_step_frac * omega, gd->df_step);
-    P.K1b = (int)floor(opts->s1b_half_frac * omega / gd->df_step + 0.5) / P.hB;
-    P.hC = snap(omega, gd->df_step);
-    P.W3 = (int)floor(opts->s3_half_frac * omega / gd->df_step + 0.5);
-    for (int l = 0, p1 = -1, p2 = -1; l < opts->n_s2; ++l) {
-        const int h1 = snap(opts->s2_t1_ms[l], gd->t1_step), h2 = snap(opts->s2_t2_ms[l], gd->t2_step);
-        if (h1 == p1 && h2 == p2) continue;
-        p1 = h1; p2 = h2;
-        P.s2_h1[P.n_s2] = h1; P.s2_h2[P.n_s2] = h2; P.n_s2++;
-    }
-    for (int l = 0, pp = -1, ph = -1; l < opts->n_s4; ++l) {
-        const int p = opts->s4_param[l], h = snap(opts->s4_ms[l], p == 0 ? gd->t1_step : gd->t2_step);
-        if (p == pp && h == ph) continue;
-        pp = p; ph = h;
-        P.s4_p[P.n_s4] = p; P.s4_h[P.n_s4] = h; P.n_s4++;
-    }
 
     std::lock_guard<std::mutex> lk(g_static_mu);
     if (!g_static_addr[ctx->device]) {
@@ -2262,12 +2222,13 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     A.chain_len = 0;
     A.prior_h1 = A.prior_h2 = A.prior_h3 = 0;
     A.prior_start = 0;
+    A.max_slots = kSlots;
     A.state = nullptr;
     A.phase = kPhaseAll;   // one kernel: the split search's scratch grows with V
     A.stats = ctx->dev_stats;
     const unsigned blocks = pack_blocks(ctx, V);
     launch_pack(A, blocks, stream);
-    count_launch(ctx);
+    count_launch(ctx);   // no profile events here: creating them is not allocation-free
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "zoom launch (static scratch)");
     return MRF_OK;

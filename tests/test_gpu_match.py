@@ -264,6 +264,12 @@ def test_full_size_precision_grid_sampled(M, ctx, oracle_lib):
     try:
         ref = _run_grid(M, ctx, h, g, x, M.MRF_F32, 4, 0)
         sure = ref["min_margin"] >= GAP_EXCUSE
+        # the FP32-equivalent brute force over the whole grid pinned to the oracle's exhaustive search
+        # on 4 voxels (12,024,855 FP64 fingerprints simulated once, every entry correlated)
+        pick4 = np.random.default_rng(7).choice(4096, 4, replace=False)
+        orc = oracle_lib.bruteforce(seq, g, x[pick4], k=2)
+        diff, exc = _compare(ref[pick4], orc, "12M-entry grid, FP32-equivalent brute force in ranges")
+        print(f"12M-entry grid vs the oracle's exhaustive search: differ={diff} excused={exc} of 4")
         t1, t2, df = S.grid_values(g)
         a, b, c = oracle_lib.grid_params(g)
         pick = np.random.default_rng(6).choice(4096, 8, replace=False)
@@ -291,6 +297,8 @@ def test_full_size_precision_grid_sampled(M, ctx, oracle_lib):
             assert np.abs(res["cc"][pick] - occ).max() < CC_TOL
             agree = (res["index"] == ref["index"])[sure].mean()
             agree2 = (ref2["index"] == ref["index"])[sure].mean()
+            print(f"  oracle exhaustive on 4 voxels: re-scored index equal {int((res['index'][pick4] == orc['idx'][:, 0]).sum())}"
+                  f"/4, after refinement {int((ref2['index'][pick4] == orc['idx'][:, 0]).sum())}/4")
             print(f"full-size 12M dtype={dt} top-{k}: agreement with FP32 brute force {agree:.4f}, after "
                   f"refinement {agree2:.4f} ({int(sure.sum())} voxels with a gap >= 1e-6)")
             assert agree2 >= floor
