@@ -335,6 +335,25 @@ int mrf_match_bruteforce_grid(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_d
                               const mrf_match_opts *opts, int64_t chunk_entries, const void *fp_dev, int64_t V,
                               mrf_result *out_dev, void *stream);
 
+/* Brute force over a grid with no dictionary stored anywhere (the brute-force
+ * counterpart of ZOOM's on-the-fly candidates; Theory, brute-force DGS):
+ * inside the tensor-core matcher, simulation warps run the Bloch recurrence
+ * (FP32, factors on the fly) for each tile of 256 entries and write the raw
+ * entries as bf16 (hi + lo for MRF_F32, hi for MRF_BF16) straight into the
+ * shared-memory stages the MMAs read, with 1 / ||d|| as each entry's column
+ * scale; the top_k lists, their merge and the re-score are those of
+ * mrf_match_bruteforce, and so are the results' meaning and layout (index
+ * over the grid's valid entries, entries_evaluated = the entry count). Every
+ * entry is simulated once per voxel unit (64 voxels for MRF_F32, 128 for
+ * MRF_BF16), so it pays for small voxel counts: it needs neither the
+ * dictionary's HBM nor its write and read. fp_dev: V x n complex64; out_dev:
+ * V results. Errors: MRF_E_INVALID (NULL argument, precision other than
+ * MRF_F32 / MRF_BF16, bad top_k or rescore, a grid without a valid entry or
+ * with more than 2^31 - 1), MRF_E_BUDGET, MRF_E_CUDA. */
+int mrf_match_bruteforce_fused(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid,
+                               const mrf_match_opts *opts, const void *fp_dev, int64_t V, mrf_result *out_dev,
+                               void *stream);
+
 /* The tensor-core pass alone: per voxel the top_k (linear index, approximate
  * CC^2 of the normalised pair) in descending order, ties to the smaller
  * index. idx_dev: V x top_k int64, cc2_dev: V x top_k float32. */

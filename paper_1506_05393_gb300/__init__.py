@@ -120,7 +120,7 @@ EXPORTS = [
     "mrf_zoom_opts_default", "mrf_zoom_search", "mrf_serve_start", "mrf_serve_submit", "mrf_serve_poll",
     "mrf_serve_cancel", "mrf_serve_get_stats", "mrf_serve_stop", "mrf_profile_enable", "mrf_profile_read",
     "mrf_zoom_search_static", "mrf_zoom_search_dict", "mrf_refine", "mrf_smooth", "mrf_dict_smooth",
-    "mrf_dict_free_async", "mrf_sequence_free_async", "mrf_fp32_fma_rate", "mrf_mma_rate",
+    "mrf_dict_free_async", "mrf_sequence_free_async", "mrf_fp32_fma_rate", "mrf_mma_rate", "mrf_match_bruteforce_fused",
 ]
 
 
@@ -157,6 +157,7 @@ def lib():
         L.mrf_match_topk.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp]
         L.mrf_match_bruteforce_grid.argtypes = [vp, vp, C.POINTER(GridDesc), C.POINTER(MatchOpts), i64, vp, i64, vp,
                                                 vp]
+        L.mrf_match_bruteforce_fused.argtypes = [vp, vp, C.POINTER(GridDesc), C.POINTER(MatchOpts), vp, i64, vp, vp]
         L.mrf_zoom_opts_default.argtypes = [C.POINTER(ZoomOpts)]
         L.mrf_zoom_opts_default.restype = None
         L.mrf_zoom_search.argtypes = [vp, vp, C.POINTER(GridDesc), C.POINTER(ZoomOpts), vp, i64, vp, vp]
@@ -333,6 +334,15 @@ def mrf_match_bruteforce_grid(ctx, seq, grid, fp, opts: MatchOpts, out, chunk_en
     V = fp.shape[0] if fp is not None else 0
     check(lib().mrf_match_bruteforce_grid(ctx, seq, C.byref(g), C.byref(opts), int(chunk_entries), _ptr(fp), V,
                                           _ptr(out), _stream_ptr(stream)), "mrf_match_bruteforce_grid")
+
+
+def mrf_match_bruteforce_fused(ctx, seq, grid, fp, opts: MatchOpts, out, stream=None) -> None:
+    """Brute force with every dictionary tile generated inside the matcher (no
+    dictionary stored). fp: complex64 CUDA tensor (V, n)."""
+    g = grid_desc(grid)
+    V = fp.shape[0] if fp is not None else 0
+    check(lib().mrf_match_bruteforce_fused(ctx, seq, C.byref(g), C.byref(opts), _ptr(fp), V, _ptr(out),
+                                           _stream_ptr(stream)), "mrf_match_bruteforce_fused")
 
 
 def mrf_match_topk(ctx, d, fp, precision: int, top_k: int, idx, cc2, stream=None) -> None:

@@ -816,6 +816,39 @@ extern "C" int mrf_match_bruteforce_grid(mrf_ctx *ctx, const mrf_seq *seq, const
     return rc;
 }
 
+extern "C" int mrf_match_bruteforce_fused(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid,
+                                          const mrf_match_opts *o, const void *fp, int64_t V, mrf_result *out,
+                                          void *stream_v)
+{
+    if (!ctx || !seq || !grid || !o) return set_error(MRF_E_INVALID, "NULL argument");
+    if (V < 0) return set_error(MRF_E_INVALID, "V < 0");
+    if (o->precision != MRF_F32 && o->precision != MRF_BF16)
+        return set_error(MRF_E_INVALID, "fused brute force: precision must be MRF_F32 or MRF_BF16");
+    if (!valid_topk(o->top_k)) return set_error(MRF_E_INVALID, "top_k must be 1, 2, 4, 8, 16 or 32");
+    if (o->rescore != 0 && o->rescore != 1) return set_error(MRF_E_INVALID, "rescore must be 0 or 1");
+    int rc = grid_validate(grid);
+    if (rc) return rc;
+    const int64_t D = mrf_grid_count(grid);
+    if (D == 0) return set_error(MRF_E_INVALID, "grid has no valid entry");
+    if (D > INT32_MAX) return set_error(MRF_E_INVALID, "fused brute force: more than 2^31 - 1 entries");
+    if (V == 0) return MRF_OK;
+    if (!fp || !out) return set_error(MRF_E_INVALID, "NULL device buffer");
+    cudaSetDevice(ctx->device);
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    // a dictionary with nothing stored: its entries are generated inside the matcher
+    mrf_dict d;
+    d.seq = const_cast<mrf_seq *>(seq);   // borrowed for the call
+    d.dtype = o->precision;
+    d.entries = D;
+    d.n = seq->n;
+    d.ld = dict_ld(seq->n, o->precision);
+    rc = grid_upload(ctx, grid, &d.grid);
+    if (rc) return rc;
+    rc = run_match(ctx, &d, fp, V, o->precision, o->top_k, o->rescore, out, nullptr, nullptr, stream, true);
+    grid_release(ctx, &d.grid, stream, false);
+    return rc;
+}
+
 extern "C" int mrf_match_topk(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_t precision,
                               int32_t top_k, int64_t *idx, float *cc2, void *stream)
 {

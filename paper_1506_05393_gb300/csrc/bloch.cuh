@@ -124,6 +124,14 @@ __device__ __forceinline__ void relax_factors(const Relax &r, float tau, float &
     zi = e2 * sn;
 }
 
+// e^{i 2 pi f tau} on the SFU, the argument first reduced to [-1/2, 1/2] cycles.
+__device__ __forceinline__ void cis_sfu(float f, float tau, float &cs, float &sn)
+{
+    float t = f * tau;
+    t -= rintf(t);
+    __sincosf(6.283185307179586f * t, &sn, &cs);
+}
+
 // RF pulse of timepoint j for a candidate off resonance by f = df / 1000
 // cycles per ms (dispatch on the sequence kind; `xonly` and `finite` are
 // uniform).

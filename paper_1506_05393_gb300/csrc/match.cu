@@ -72,8 +72,11 @@ template <int MODE>
 constexpr int stage_bytes() { return Cfg<MODE>::kOps * (Cfg<MODE>::kNB * kTileA + kTileB); }
 template <int MODE>
 constexpr int smem_bytes() { return Cfg<MODE>::kStages * stage_bytes<MODE>() + 1024; }
-template <int MODE>
-constexpr int threads_of() { return 64 + 128 * Cfg<MODE>::kNB; }
+// Generated dictionary tiles (mrf_match_bruteforce_fused): kSimWarps warps
+// simulate each tile's entries into the B stages, two entries per thread.
+constexpr int kSimWarps = 4;
+template <int MODE, bool GEN = false>
+constexpr int threads_of() { return 64 + 128 * Cfg<MODE>::kNB + (GEN ? 32 * kSimWarps : 0); }
 
 struct MatchParams {
     int64_t D;           // dictionary entries
@@ -92,6 +95,10 @@ struct MatchParams {
     float *thr_live;     // per-voxel bound shared by the CTAs of one pass (atomic max of their K-th bests), or nullptr
     float2 *part;        // [V][n_chunks][K]: (cc2, idx bits)
     int *err;
+    // generated tiles (GEN): the entries' sequence and grid, timepoints
+    SeqDev s;
+    GridDev g;
+    int n;
 };
 
 // order: higher cc2 first, then smaller index
@@ -148,8 +155,28 @@ __device__ __forceinline__ float sel16(const float (&a)[16], int q)
     return r;
 }
 
-template <int MODE, int K>
-__global__ void __launch_bounds__(threads_of<MODE>(), 1)
+// Linear entry index -> grid indices (a, b, c): binary search over the T1 offsets.
+__device__ __forceinline__ void unravel_dev(const GridDev &g, int64_t e, int &a, int &b, int &c)
+{
+    int lo = 0, hi = g.n_t1 - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&g.a_off[mid]) <= e) lo = mid; else hi = mid - 1;
+    }
+    a = lo;
+    const int64_t rem = e - __ldg(&g.a_off[a]);
+    b = (int)(rem / g.n_df);
+    c = (int)(rem % g.n_df);
+}
+
+// GEN: the dictionary is not read but generated. kSimWarps simulation warps
+// run each tile's entries through the Bloch recurrence (FP32, factors on the
+// fly) and write the raw entries, 32 timepoints per K block, as bf16 (hi, and
+// lo for MRF_F32) straight into the B stages in the 128-byte-swizzled K-major
+// layout TMA would produce; each entry's 1 / ||d|| becomes its column scale.
+// The voxel operands still arrive by TMA. No dictionary reaches HBM.
+template <int MODE, int K, bool GEN>
+__global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
     match_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
                  const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapB2,
                  MatchParams p)
@@ -160,15 +187,26 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
     constexpr int NBUF = NB == 1 ? 2 : 1;       // accumulator buffers (TMEM holds 512 columns)
     constexpr int NEPI = 4 * NB;                // epilogue warps
     constexpr uint32_t kStageBytes = stage_bytes<MODE>();
+    // bytes TMA brings into a stage (GEN: the voxel operands only)
+    constexpr uint32_t kTmaBytes = GEN ? (uint32_t)(C::kOps * NB * kTileA) : kStageBytes;
     constexpr uint32_t kIdesc = MODE == MRF_FP8E4M3 ? make_idesc(0, 0, BM, BN) : make_idesc(1, 1, BM, BN);
+    constexpr bool kScaled = MODE != MRF_BF16 || GEN;   // columns carry a scale (stored x scale = unit norm)
+    static_assert(!GEN || MODE != MRF_FP8E4M3, "generated tiles are bf16 (hi, lo)");
 
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S], tfull_bar[NBUF], tempty_bar[NBUF], drain_bar;
+    __shared__ __align__(8) uint64_t scale_bar[GEN ? NBUF : 1];   // GEN: a tile's column scales are written
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     // per epilogue warp: the column scales of its current tile, fetched while
-    // the tile's MMAs run
-    __shared__ __align__(16) float sc_tile[NEPI][MODE == MRF_BF16 ? 1 : BN];
+    // the tile's MMAs run (GEN: written by the simulation warps, per accumulator buffer)
+    __shared__ __align__(16) float sc_tile[GEN ? 1 : NEPI][kScaled && !GEN ? BN : 1];
+    __shared__ __align__(16) float sc_gen[GEN ? NBUF : 1][GEN ? BN : 1];
+    // GEN: per simulation warp, the sequence coefficients of the current K block's 32
+    // timepoints (RF rotation: rfx, or the general matrix in 3 float4, or the finite-
+    // pulse parameters; TE_j and TR_j - TE_j), staged once per K block
+    __shared__ __align__(16) float4 sim_rf[GEN ? kSimWarps : 1][GEN ? 3 * 32 : 1];
+    __shared__ __align__(16) float2 sim_tau[GEN ? kSimWarps : 1][GEN ? 32 : 1];
 
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     // stage s: [A(block 0..NB-1, hi) | A lo? | B hi | B lo?]
@@ -177,16 +215,22 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int q = 0; q < S; ++q) { mbar_init(&full_bar[q], 1); mbar_init(&empty_bar[q], 1); }
+        // GEN: a stage is full once TMA's bytes and every simulation warp have arrived
+        for (int q = 0; q < S; ++q) { mbar_init(&full_bar[q], GEN ? 1 + kSimWarps : 1); mbar_init(&empty_bar[q], 1); }
         for (int a = 0; a < NBUF; ++a) { mbar_init(&tfull_bar[a], 1); mbar_init(&tempty_bar[a], NEPI); }
+        if (GEN)
+            for (int a = 0; a < NBUF; ++a) mbar_init(&scale_bar[a], kSimWarps);
         mbar_init(&drain_bar, 1);
         abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&mapA);
-        tma_prefetch_desc(&mapB);
-        if (C::kOps == 2) { tma_prefetch_desc(&mapA2); tma_prefetch_desc(&mapB2); }
+        if (!GEN) tma_prefetch_desc(&mapB);
+        if (C::kOps == 2) {
+            tma_prefetch_desc(&mapA2);
+            if (!GEN) tma_prefetch_desc(&mapB2);
+        }
     }
     if (warp == 1) {
         tmem_alloc(&tmem_slot, 2 * BN);
@@ -217,7 +261,7 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                 for (int t = t0; t < t1; ++t) {
                     for (int kb = 0; kb < p.k_blocks; ++kb) {
                         if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kWaitLimitNs)) goto producer_done;
-                        mbar_arrive_expect_tx(&full_bar[s], kStageBytes);
+                        mbar_arrive_expect_tx(&full_bar[s], kTmaBytes);
                         const int kx = kb * C::kBK;
 #pragma unroll
                         for (int i = 0; i < NB; ++i) {
@@ -225,8 +269,10 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                             tma_load_2d_hint(tileA(s, 0, i), &mapA, &full_bar[s], kx, row, keep);
                             if (C::kOps == 2) tma_load_2d_hint(tileA(s, 1, i), &mapA2, &full_bar[s], kx, row, keep);
                         }
-                        tma_load_2d(tileB(s, 0), &mapB, &full_bar[s], kx, t * BN);
-                        if (C::kOps == 2) tma_load_2d(tileB(s, 1), &mapB2, &full_bar[s], kx, t * BN);
+                        if (!GEN) {
+                            tma_load_2d(tileB(s, 0), &mapB, &full_bar[s], kx, t * BN);
+                            if (C::kOps == 2) tma_load_2d(tileB(s, 1), &mapB2, &full_bar[s], kx, t * BN);
+                        }
                         issued[s] = true;
                         issued_ph[s] = ph;
                         if (++s == S) { s = 0; ph ^= 1; }
@@ -302,6 +348,145 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                 }
             }
         }
+    } else if (GEN && warp >= 2 + NEPI) {
+        // ---------------- simulation: generated B tiles ----------------
+        // thread r simulates rows r and r + 128 of each tile (entries t * BN + row)
+        const int r0 = threadIdx.x - 32 * (2 + NEPI);
+        const int wsim = warp - (2 + NEPI);
+        const int n = p.n;
+        // one timepoint jj of the staged K block; evolution factors from the SFU
+        // (the candidates are ranked here and re-scored exactly afterwards)
+        auto sim_step = [&](Bloch &bs, const Relax &rr, int jj, float &sr, float &si) {
+            if (p.s.xonly) {
+                bloch_rf_x(bs, sim_rf[wsim][jj]);
+            } else if (p.s.finite) {
+                bloch_rf_finite(bs, sim_rf[wsim][jj], rr.f);
+            } else {
+                const float4 a4 = sim_rf[wsim][3 * jj], b4 = sim_rf[wsim][3 * jj + 1], c4 = sim_rf[wsim][3 * jj + 2];
+                const float qm[10] = {a4.x, a4.y, a4.z, a4.w, b4.x, b4.y, b4.z, b4.w, c4.x, c4.y};
+                bloch_rf_general(bs, qm);
+            }
+            const float2 tau = sim_tau[wsim][jj];
+            float cs, sn;
+            cis_sfu(rr.f, tau.x, cs, sn);
+            float e1 = ex2_fast(rr.k1 * tau.x), e2 = ex2_fast(rr.k2 * tau.x);
+            bloch_evolve(bs, e1, e2 * cs, e2 * sn);
+            sr = bs.mx;
+            si = bs.my;
+            if (!p.s.symmetric) {
+                cis_sfu(rr.f, tau.y, cs, sn);
+                e1 = ex2_fast(rr.k1 * tau.y);
+                e2 = ex2_fast(rr.k2 * tau.y);
+            }
+            bloch_evolve(bs, e1, e2 * cs, e2 * sn);
+        };
+        int s = 0, buf = 0;
+        uint32_t ph = 0, buf_ph = 0;
+        for (int u = blockIdx.x; u < n_units && !abort_flag; u += gridDim.x) {
+            int chunk, vu;
+            decode_unit(p, u, chunk, vu);
+            (void)vu;
+            const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
+            const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
+            for (int t = t0; t < t1; ++t) {
+                Bloch st[2];
+                Relax rx[2];
+                bool live[2];
+                float tot[2], comp[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t e = (int64_t)t * BN + r0 + 128 * h;
+                    live[h] = e < p.D;
+                    int a = 0, b = 0, c = 0;
+                    if (live[h]) unravel_dev(p.g, e, a, b, c);
+                    rx[h] = relax_make(live[h] ? __ldg(&p.g.t1[a]) : 1000.f, live[h] ? __ldg(&p.g.t2[b]) : 100.f,
+                                       live[h] ? __ldg(&p.g.df[c]) : 0.f);
+                    bloch_start(st[h], p.s, rx[h]);
+                    tot[h] = 0.f;
+                    comp[h] = 0.f;
+                }
+                for (int kb = 0; kb < p.k_blocks; ++kb) {
+                    // this K block's sequence coefficients, fetched before waiting for the stage
+                    __syncwarp();
+                    {
+                        const int jl = kb * 32 + lane;
+                        if (jl < n) {
+                            if (p.s.xonly) {
+                                sim_rf[wsim][lane] = __ldg(&p.s.rfx[jl]);
+                            } else if (p.s.finite) {
+                                sim_rf[wsim][lane] = __ldg(&p.s.rff[jl]);
+                            } else {
+                                const float4 *gq = reinterpret_cast<const float4 *>(p.s.rfg + 12 * (size_t)jl);
+                                sim_rf[wsim][3 * lane] = __ldg(gq);
+                                sim_rf[wsim][3 * lane + 1] = __ldg(gq + 1);
+                                sim_rf[wsim][3 * lane + 2] = __ldg(gq + 2);
+                            }
+                            sim_tau[wsim][lane] = __ldg(&p.s.tau[jl]);
+                        }
+                    }
+                    __syncwarp();   // the staged coefficients are visible to every lane of the warp
+                    const bool ok = mbar_wait_bounded(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kWaitLimitNs);
+                    if (!__all_sync(0xffffffffu, ok)) goto sim_done;   // leave as a whole warp
+                    // the two entries interleaved (independent recurrences)
+                    float part[2] = {0.f, 0.f};
+#pragma unroll 1
+                    for (int q = 0; q < 8; ++q) {
+                        uint32_t hi4[2][4], lo4[2][4];
+#pragma unroll
+                        for (int u4 = 0; u4 < 4; ++u4) {
+                            const int j = kb * 32 + q * 4 + u4;
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                float sr = 0.f, si = 0.f;
+                                if (live[h] && j < n) {
+                                    sim_step(st[h], rx[h], q * 4 + u4, sr, si);
+                                    part[h] = fmaf(sr, sr, fmaf(si, si, part[h]));
+                                }
+                                const __nv_bfloat162 hv = __floats2bfloat162_rn(sr, si);
+                                const float2 hf = __bfloat1622float2(hv);
+                                const __nv_bfloat162 lv = __floats2bfloat162_rn(sr - hf.x, si - hf.y);
+                                hi4[h][u4] = *reinterpret_cast<const uint32_t *>(&hv);
+                                lo4[h][u4] = *reinterpret_cast<const uint32_t *>(&lv);
+                            }
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            // 16-byte chunk q of the row, 128-byte swizzle (chunk index ^ row % 8)
+                            const int row = r0 + 128 * h;
+                            const int pq = q ^ (row & 7);
+                            *reinterpret_cast<uint4 *>(tileB(s, 0) + row * 128 + pq * 16) =
+                                make_uint4(hi4[h][0], hi4[h][1], hi4[h][2], hi4[h][3]);
+                            if (C::kOps == 2)
+                                *reinterpret_cast<uint4 *>(tileB(s, C::kOps - 1) + row * 128 + pq * 16) =
+                                    make_uint4(lo4[h][0], lo4[h][1], lo4[h][2], lo4[h][3]);
+                        }
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        // the norm: 32-timepoint FP32 blocks, compensated total
+                        const float y = part[h] - comp[h];
+                        const float tt = tot[h] + y;
+                        comp[h] = (tt - tot[h]) - y;
+                        tot[h] = tt;
+                    }
+                    // the generic-proxy stores must be visible to the tensor core's reads
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&full_bar[s]);
+                    if (++s == S) { s = 0; ph ^= 1; }
+                }
+                // the tile's column scales, once the epilogue is done with this buffer's previous ones
+                const bool ok = mbar_wait_bounded(&tempty_bar[buf], buf_ph ^ 1, &abort_flag, p.err, kWaitLimitNs);
+                if (!__all_sync(0xffffffffu, ok)) goto sim_done;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    sc_gen[GEN ? buf : 0][GEN ? r0 + 128 * h : 0] = (live[h] && tot[h] > 0.f) ? rsqrtf(tot[h]) : 0.f;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&scale_bar[GEN ? buf : 0]);
+                if (++buf == NBUF) { buf = 0; buf_ph ^= 1; }
+            }
+        }
+    sim_done:;
     } else {
         // ---------------- epilogue: TMEM -> CC^2 -> running top-k ----------------
         const int blk = (warp - 2) / 4;            // which voxel block of the unit
@@ -332,15 +517,16 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
             const int64_t vrow = (int64_t)(vu * NB + blk) * (BM / 2) + (row >> 1);
             const bool vlive = vrow < p.V;
             for (int t = t0; t < t1; ++t) {
-                if (MODE != MRF_BF16) {
-                    float *sct = sc_tile[warp - 2];
+                if (kScaled && !GEN) {
+                    float *sct = sc_tile[GEN ? 0 : warp - 2];
                     for (int q = lane; q < BN; q += 32) {
                         const int col = t * BN + q;
                         sct[q] = col < p.D ? __ldg(&p.colscale[(int64_t)col * p.col_stride]) : 0.f;
                     }
                     __syncwarp();
                 }
-                const bool ok = mbar_wait_bounded(&tfull_bar[buf], buf_ph, &abort_flag, p.err, kWaitLimitNs);
+                bool ok = mbar_wait_bounded(&tfull_bar[buf], buf_ph, &abort_flag, p.err, kWaitLimitNs);
+                if (GEN && ok) ok = mbar_wait_bounded(&scale_bar[GEN ? buf : 0], buf_ph, &abort_flag, p.err, kWaitLimitNs);
                 if (!__all_sync(0xffffffffu, ok)) goto epi_done;   // leave as a whole warp
                 tc_fence_after();
                 const uint32_t tbase =
@@ -353,8 +539,10 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                     const int col0 = t * BN + ch * 32 + (par ? 16 : 0);
                     float c2v[16];
                     float sc16[16];
-                    if (MODE != MRF_BF16) {
-                        const float4 *s4 = reinterpret_cast<const float4 *>(&sc_tile[warp - 2][ch * 32 + (par ? 16 : 0)]);
+                    if (kScaled) {
+                        const float *scs = GEN ? &sc_gen[GEN ? buf : 0][GEN ? ch * 32 + (par ? 16 : 0) : 0]
+                                               : &sc_tile[GEN ? 0 : warp - 2][GEN ? 0 : ch * 32 + (par ? 16 : 0)];
+                        const float4 *s4 = reinterpret_cast<const float4 *>(scs);
 #pragma unroll
                         for (int q4 = 0; q4 < 4; ++q4) {
                             const float4 f = s4[q4];
@@ -372,7 +560,7 @@ __global__ void __launch_bounds__(threads_of<MODE>(), 1)
                         const float im = par ? mine_hi : recv;
                         float c2 = fmaf(re, re, im * im);
                         const int col = col0 + q;
-                        if (MODE != MRF_BF16) c2 *= sc16[q] * sc16[q];
+                        if (kScaled) c2 *= sc16[q] * sc16[q];
                         c2v[q] = c2;
                         mask |= (col < p.D && c2 > thr) ? (1u << q) : 0u;
                     }
@@ -535,18 +723,6 @@ __global__ void merge_kernel(const float2 *part, int64_t V, int n_chunks, const 
 // re-score: FP32 re-simulation of each candidate, FP64 accumulation of the
 // inner product and norms, best by FP64 CC (ties to the smaller index)
 
-__device__ __forceinline__ void unravel_dev(const GridDev &g, int64_t e, int &a, int &b, int &c)
-{
-    int lo = 0, hi = g.n_t1 - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&g.a_off[mid]) <= e) lo = mid; else hi = mid - 1;
-    }
-    a = lo;
-    const int64_t rem = e - __ldg(&g.a_off[a]);
-    b = (int)(rem / g.n_df);
-    c = (int)(rem % g.n_df);
-}
 
 // Temporal smoothing of the re-simulated candidates (the dictionary's own,
 // see mrf_dict_smooth): half-width h and weights w[k], k = 0..h.
@@ -762,7 +938,7 @@ int make_map(CUtensorMap *m, const void *base, int64_t rows, int ld, int elem_by
 
 int gcd_i(int a, int b) { while (b) { int t = a % b; a = b; b = t; } return a; }
 
-template <int MODE, int K>
+template <int MODE, int K, bool GEN>
 int launch_match_k(mrf_ctx *ctx, const CUtensorMap &mA, const CUtensorMap &mA2, const CUtensorMap &mB,
                    const CUtensorMap &mB2, const MatchParams &p, cudaStream_t stream)
 {
@@ -773,30 +949,30 @@ int launch_match_k(mrf_ctx *ctx, const CUtensorMap &mA, const CUtensorMap &mA2, 
     static bool attr_set[kDevs] = {};
     const int dev = ctx->device;
     if (dev < 0 || dev >= kDevs || !attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(match_kernel<MODE, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(match_kernel<MODE, K, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              smem_bytes<MODE>());
         if (e != cudaSuccess) return cuda_fail(e, "matcher shared-memory attribute");
         if (dev >= 0 && dev < kDevs) attr_set[dev] = true;
     }
     const int units = p.n_vu * p.n_chunks;
     const int grid = std::min(units, ctx->sm_count);
-    match_kernel<MODE, K><<<grid, threads_of<MODE>(), smem_bytes<MODE>(), stream>>>(mA, mA2, mB, mB2, p);
+    match_kernel<MODE, K, GEN><<<grid, threads_of<MODE, GEN>(), smem_bytes<MODE>(), stream>>>(mA, mA2, mB, mB2, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "matcher launch");
     return MRF_OK;
 }
 
-template <int MODE>
+template <int MODE, bool GEN = false>
 int launch_match_mode(mrf_ctx *ctx, int K, const CUtensorMap &mA, const CUtensorMap &mA2, const CUtensorMap &mB,
                       const CUtensorMap &mB2, const MatchParams &p, cudaStream_t stream)
 {
     switch (K) {
-    case 1: return launch_match_k<MODE, 1>(ctx, mA, mA2, mB, mB2, p, stream);
-    case 2: return launch_match_k<MODE, 2>(ctx, mA, mA2, mB, mB2, p, stream);
-    case 4: return launch_match_k<MODE, 4>(ctx, mA, mA2, mB, mB2, p, stream);
-    case 8: return launch_match_k<MODE, 8>(ctx, mA, mA2, mB, mB2, p, stream);
-    case 16: return launch_match_k<MODE, 16>(ctx, mA, mA2, mB, mB2, p, stream);
-    case 32: return launch_match_k<MODE, 32>(ctx, mA, mA2, mB, mB2, p, stream);
+    case 1: return launch_match_k<MODE, 1, GEN>(ctx, mA, mA2, mB, mB2, p, stream);
+    case 2: return launch_match_k<MODE, 2, GEN>(ctx, mA, mA2, mB, mB2, p, stream);
+    case 4: return launch_match_k<MODE, 4, GEN>(ctx, mA, mA2, mB, mB2, p, stream);
+    case 8: return launch_match_k<MODE, 8, GEN>(ctx, mA, mA2, mB, mB2, p, stream);
+    case 16: return launch_match_k<MODE, 16, GEN>(ctx, mA, mA2, mB, mB2, p, stream);
+    case 32: return launch_match_k<MODE, 32, GEN>(ctx, mA, mA2, mB, mB2, p, stream);
     }
     return set_error(MRF_E_INVALID, "top_k");
 }
@@ -816,7 +992,7 @@ int launch_chunk_merge(mrf_result *best, float *second, const mrf_result *part, 
 }
 
 int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_t precision, int32_t top_k,
-              int rescore, mrf_result *out, int64_t *idx_out, float *cc2_out, cudaStream_t stream)
+              int rescore, mrf_result *out, int64_t *idx_out, float *cc2_out, cudaStream_t stream, bool fused)
 {
     const int mode = precision;
     const int K = top_k;
@@ -848,7 +1024,7 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     constexpr int kSample = 64;
     const int64_t D_s = (d->entries + kSample - 1) / kSample;
     const int n_tiles_s = (int)((D_s + BN - 1) / BN);
-    const bool seeded = K >= 8 && n_tiles_s >= 4;
+    const bool seeded = !fused && K >= 8 && n_tiles_s >= 4;   // generated tiles have no stored sample
     const int n_chunks_s = seeded ? std::max(1, std::min(n_tiles_s, ctx->sm_count / std::max(1, n_vu))) : 0;
 
     // scratch: A operands, row scales, partial lists, candidates, pre-pass lists and bounds
@@ -901,11 +1077,13 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     // 2. tensor-core pass
     CUtensorMap mA, mA2, mB, mB2;
     rc = make_map(&mA, pA, 2 * V_pad, d->ld, ebytes, BM);
-    if (!rc) rc = make_map(&mB, d->hi, d->entries, d->ld, ebytes, BN);
+    if (!rc && !fused) rc = make_map(&mB, d->hi, d->entries, d->ld, ebytes, BN);
     if (!rc && mode == MRF_F32) rc = make_map(&mA2, pA2, 2 * V_pad, d->ld, ebytes, BM);
-    if (!rc && mode == MRF_F32) rc = make_map(&mB2, d->lo, d->entries, d->ld, ebytes, BN);
+    if (!rc && mode == MRF_F32 && !fused) rc = make_map(&mB2, d->lo, d->entries, d->ld, ebytes, BN);
     if (rc) return finish(rc);
-    if (mode != MRF_F32) { mA2 = mA; mB2 = mB; }
+    if (mode != MRF_F32) mA2 = mA;
+    if (fused) { mB = mA; mB2 = mA2; }   // unused: the kernel generates its B tiles
+    else if (mode != MRF_F32) mB2 = mB;
     MatchParams p;
     p.D = d->entries;
     p.V = V;
@@ -922,6 +1100,10 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     p.thr_live = nullptr;
     p.part = pP;
     p.err = ctx->err_flag;
+    p.s = d->seq->dev();
+    p.g = d->grid.dev();
+    p.n = d->n;
+    if (fused) p.colscale = nullptr;
 
     const unsigned mblocks = (unsigned)((V + 3) / 4);
     auto merge = [&](const float2 *part, int chunks, const float *row_scale, int64_t *io, float *co) {
@@ -938,6 +1120,8 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     };
     auto launch_all = [&](const CUtensorMap &b, const CUtensorMap &b2, const MatchParams &pp) {
         std::lock_guard<std::mutex> lk(g_match_attr_mu);
+        if (fused && mode == MRF_F32) return launch_match_mode<MRF_F32, true>(ctx, K, mA, mA2, b, b2, pp, stream);
+        if (fused) return launch_match_mode<MRF_BF16, true>(ctx, K, mA, mA2, b, b2, pp, stream);
         if (mode == MRF_F32) return launch_match_mode<MRF_F32>(ctx, K, mA, mA2, b, b2, pp, stream);
         if (mode == MRF_BF16) return launch_match_mode<MRF_BF16>(ctx, K, mA, mA2, b, b2, pp, stream);
         return launch_match_mode<MRF_FP8E4M3>(ctx, K, mA, mA2, b, b2, pp, stream);

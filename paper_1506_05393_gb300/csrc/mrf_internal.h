@@ -182,7 +182,8 @@ int launch_simulate(mrf_ctx *ctx, const mrf_seq *seq, int64_t count, const float
 
 // match.cu
 int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_t precision, int32_t top_k,
-              int rescore, mrf_result *out, int64_t *idx_out, float *cc2_out, cudaStream_t stream);
+              int rescore, mrf_result *out, int64_t *idx_out, float *cc2_out, cudaStream_t stream,
+              bool fused = false);
 // Chunked brute force: fold one range's results (part; nullptr = the first
 // range, already in best) into best, with the range's first linear index
 // `base` and first T1 index a0; second holds each voxel's runner-up CC.

@@ -107,12 +107,7 @@ struct Kahan {
 };
 
 // e^{i 2 pi f tau} on the SFU, argument first reduced to [-1/2, 1/2] cycles.
-__device__ __forceinline__ void cis_fast(float f, float tau, float &cs, float &sn)
-{
-    float t = f * tau;
-    t -= rintf(t);
-    __sincosf(6.283185307179586f * t, &sn, &cs);
-}
+__device__ __forceinline__ void cis_fast(float f, float tau, float &cs, float &sn) { cis_sfu(f, tau, cs, sn); }
 
 // Start state of a candidate: equilibrium, or inverted and relaxed over the
 // inversion delay (transverse magnetisation is zero after an ideal inversion).
