@@ -348,6 +348,32 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
         modes["zoom_over_dictionary_same_grid"]["median_abs_error_vs_truth"] = param_errors(res, ph)
     M.mrf_dict_free(ctx, d)
 
+    # brute force without a stored dictionary, for small voxel counts: the fused form (tiles simulated
+    # inside the matcher) against the resident dictionary (generation not timed) and the chunked form
+    # (each range generated, matched, released), at V = 64, 256, 1024
+    fused = {}
+    for gname, dt, k in ((GRID, M.MRF_F32, 4), ("precision", M.MRF_BF16, 8)):
+        gg = S.GRIDS[gname]
+        dres = M.mrf_dict_generate(ctx, seq_h, gg, dt)
+        rows = []
+        for Vs in (64, 256, 1024):
+            xs = x_dev[:Vs].contiguous()
+            o1, o2, o3 = M.empty_results(Vs), M.empty_results(Vs), M.empty_results(Vs)
+            mo = M.match_opts(dt, k, 1)
+            f = lambda: M.mrf_match_bruteforce_fused(ctx, seq_h, gg, xs, mo, o1)
+            r = lambda: M.mrf_match_bruteforce(ctx, dres, xs, mo, o2)
+            c = lambda: M.mrf_match_bruteforce_grid(ctx, seq_h, gg, xs, mo, o3)
+            f(), r(), c()
+            tf, tr, tc = timed(f, 2), timed(r, 2), timed(c, 2)
+            a, b = M.results_to_numpy(o1)[:Vs], M.results_to_numpy(o2)[:Vs]
+            rows.append({"voxels": Vs, "fused_ms": tf, "resident_ms": tr, "chunked_ms": tc,
+                         "fused_index_equal_to_resident": float(np.mean(a["index"] == b["index"]))})
+        M.mrf_dict_free(ctx, dres)
+        fused[f"{gname}_{['f32', 'bf16', 'fp8'][dt]}"] = rows
+    modes["bruteforce_without_stored_dictionary"] = {
+        "rows": fused, "note": "fused: mrf_match_bruteforce_fused; resident: mrf_match_bruteforce over a dictionary "
+                               "generated beforehand (not timed); chunked: mrf_match_bruteforce_grid"}
+
     # finer grids: BF16 / FP8 + re-score on the 12,024,855-entry grid, FP32 there for agreement
     ref = match_mode("fp32_fine_grid", "precision", M.MRF_F32, 4)
     match_mode("bf16_rescore_k8_fine_grid", "precision", M.MRF_BF16, 8, ref["index"])
