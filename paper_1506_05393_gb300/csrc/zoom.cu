@@ -845,163 +845,226 @@ __device__ __forceinline__ Lattice lattice_of(const Slot &S)
     return L;
 }
 
-// List lattice point (i, k) for simulation unless it is off the grid, known,
-// or already listed (bit of its window slot in `listed`); `cnt` counts the
-// slot's listed points (S.ra/rb/rw[0..cnt)).
-__device__ __forceinline__ bool list_point(PackShared &W, int s, const GridDev &g, const Lattice &L, int &cnt, int i,
-                                           int k, unsigned long long &listed, bool &known, float &v)
-{
-    const int a = L.la + i * L.h1, b = L.lb + k * L.h2;
-    known = false;
-    if (a < L.alo || a > L.ahi || b < L.blo || b > L.bhi || !point_valid(g, a, b, L.c)) {
-        known = true;
-        v = -INFINITY;
-        return false;
-    }
-    const int idx = L.line ? ((L.param == 0 ? i : k) & (kWin - 1)) : (((i & 7) << 3) | (k & 7));
-    if (win_get(W, s, idx, a, b, v)) { known = true; return false; }
-    if ((listed >> idx) & 1ull) return false;
-    if (cnt >= kReqMax) return false;
-    listed |= 1ull << idx;
-    Slot &S = W.s[s];
-    S.ra[cnt] = a;
-    S.rb[cnt] = b;
-    S.rw[cnt] = idx;
-    ++cnt;
-    return true;
-}
-
 // Points that later decisions of a blocked move level will want if the walk
-// goes on: the 3 x 3 neighbourhoods of the next kSpecCentres centres along the
-// last move, nearest first (before the first move, the 16 points at distance
-// 2), or the next eight points of a 1D line in the direction of travel (both
-// sides before the first move). The long walks of the final 2D ZOOM run
-// straight for tens of moves, so a round can settle up to kSpecCentres + 1
-// moves. With the current 3 x 3 block these points span at most 8 lattice
-// steps along each axis (9 on a line), which the window holds without
-// collisions, so every decision a round's results allow finds its values.
-// Speculative points fill only lanes that required points leave idle.
-__device__ void speculate(PackShared &W, int s, const GridDev &g, const Lattice &L, int ia, int ib, int da, int db,
-                          int &cnt, unsigned long long listed)
+// goes on, listed by the whole warp, one candidate point per lane, nearest
+// first: the points the 3 x 3 neighbourhoods of the next kSpecCentres centres
+// along the last move add to the current one (3 per step on a straight walk,
+// 5 per diagonal step; before the first move the 16 points at distance 2), or
+// the next eight points of a 1D line in the direction of travel (both sides
+// before the first move). The long walks of the final 2D ZOOM run straight
+// for tens of moves, so a round can settle up to kSpecCentres + 1 moves. These
+// points span at most 8 lattice steps along each axis (9 on a line), which the
+// window holds without collisions, so every decision a round's results allow
+// finds its values. Speculative points fill only lanes that required points
+// leave idle (assign). Returns the points listed after the first `nreq`.
+__device__ int speculate_warp(PackShared &W, int s, int lane, const GridDev &g, const Lattice &L, int ia, int ib,
+                              int da, int db, int nreq, unsigned long long listed)
 {
-    bool known;
-    float v;
-    auto add = [&](int i, int k) { list_point(W, s, g, L, cnt, i, k, listed, known, v); };
+    const unsigned FULL = 0xffffffffu;
+    int i = 0, k = 0;
+    bool have = false;
     if (L.line) {
         const int d = L.param == 0 ? da : db;
-        for (int t = 2; t < 10; ++t) {
+        if (lane < 8) {
+            const int t = lane + 2;
             const int m = d != 0 ? d * t : ((t & 1) ? -(t / 2 + 1) : (t / 2 + 1));
-            add(ia + (L.param == 0 ? m : 0), ib + (L.param == 1 ? m : 0));
+            i = ia + (L.param == 0 ? m : 0);
+            k = ib + (L.param == 1 ? m : 0);
+            have = true;
         }
-        return;
+    } else if (da == 0 && db == 0) {
+        if (lane < 16) {   // the ring at distance 2, T1 offset outer, -2 before +2
+            int r = lane, ii = 0, kk = 0;
+            if (r < 5) { ii = -2; kk = r - 2; }
+            else if (r < 11) { r -= 5; ii = -1 + r / 2; kk = (r & 1) ? 2 : -2; }
+            else { ii = 2; kk = r - 13; }
+            i = ia + ii;
+            k = ib + kk;
+            have = true;
+        }
+    } else if (da == 0 || db == 0) {
+        if (lane < 3 * kSpecCentres) {   // straight: the three points ahead of centre t
+            const int t = 2 + lane / 3, u = lane % 3 - 1;
+            i = ia + (da != 0 ? t * da : u);
+            k = ib + (db != 0 ? t * db : u);
+            have = true;
+        }
+    } else {
+        if (lane < 5 * kSpecCentres) {   // diagonal: the far row and column around centre t
+            const int t = 1 + lane / 5, q = lane % 5;
+            int u, w;
+            if (q < 3) { u = da; w = q - 1; }
+            else { u = q == 3 ? -da : 0; w = db; }
+            i = ia + t * da + u;
+            k = ib + t * db + w;
+            have = true;
+        }
     }
-    if (da == 0 && db == 0) {
-        for (int i = -2; i <= 2; ++i)
-            for (int k = -2; k <= 2; ++k)
-                if (i == -2 || i == 2 || k == -2 || k == 2) add(ia + i, ib + k);
-        return;
+    int a = 0, b = 0, idx = 0;
+    bool want = false;
+    if (have) {
+        a = L.la + i * L.h1;
+        b = L.lb + k * L.h2;
+        if (a >= L.alo && a <= L.ahi && b >= L.blo && b <= L.bhi && point_valid(g, a, b, L.c)) {
+            idx = L.line ? ((L.param == 0 ? i : k) & (kWin - 1)) : (((i & 7) << 3) | (k & 7));
+            float v;
+            want = !win_get(W, s, idx, a, b, v) && !((listed >> idx) & 1ull);
+        }
     }
-    for (int t = 1; t <= kSpecCentres; ++t)
-        for (int i = -1; i <= 1; ++i)
-            for (int k = -1; k <= 1; ++k) add(ia + t * da + i, ib + t * db + k);
+    const unsigned m = __ballot_sync(FULL, want);
+    const int pos = nreq + __popc(m & ((1u << lane) - 1u));
+    if (want && pos < kReqMax) {
+        Slot &S = W.s[s];
+        S.ra[pos] = a;
+        S.rb[pos] = b;
+        S.rw[pos] = idx;
+    }
+    return min(__popc(m), kReqMax - nreq);
 }
 
-// Run slot s's decisions as far as the known values allow. On return the slot
-// is scanning (positions are handed out elastically), waits for its S.nreq
-// listed points, or is idle.
-__device__ void advance(PackShared &W, int s, const ZoomPlan &P, const GridDev &g, int max_moves, ZState *state)
+// Run slot s's decisions as far as the known values allow, by the whole warp:
+// the stage machine runs uniformly on every lane (the slot's state in shared
+// memory, written by lane 0), each decision's points are looked up one per
+// lane, and the missing and speculative points are listed in parallel. On
+// return the slot is scanning (positions are handed out elastically), waits
+// for its S.nreq listed points, or is idle. Decisions, margins and evaluation
+// counts are those of the canonical search: every comparison keeps its order.
+__device__ void advance_warp(PackShared &W, int s, int lane, const ZoomPlan &P, const GridDev &g, int max_moves,
+                             ZState *state)
 {
+    const unsigned FULL = 0xffffffffu;
     Slot &S = W.s[s];
-    S.nreq = 0;
-    S.nspec = 0;
+    if (lane == 0) { S.nreq = 0; S.nspec = 0; }
+    __syncwarp();
     const bool stop3 = state != nullptr;
     for (;;) {
         const int st = S.stage;
         if (S.v < 0) return;
         if (st == kStop) {
             // the stages before step 3 are done: save the search and free the slot
-            ZState z;
-            z.a = S.a; z.b = S.b; z.c = S.c; z.evaluated = S.evaluated;
-            z.centre = S.centre; z.mm = S.mm; z.inv_xn = S.inv_xn;
-            z.flags = (S.ok ? kZOk : 0) | (S.rounds << 8);
-            state[S.v] = z;
-            S.v = -1;
+            if (lane == 0) {
+                ZState z;
+                z.a = S.a; z.b = S.b; z.c = S.c; z.evaluated = S.evaluated;
+                z.centre = S.centre; z.mm = S.mm; z.inv_xn = S.inv_xn;
+                z.flags = (S.ok ? kZOk : 0) | (S.rounds << 8);
+                state[S.v] = z;
+                S.v = -1;
+            }
+            __syncwarp();
             return;
         }
         if (is_scan(st)) {
             if (S.p <= S.p_end) return;
-            if (isfinite(S.g2)) S.mm = fminf(S.mm, S.g1 - S.g2);
-            S.level = 0;
-            enter(W, s, st == kS1a ? kS1b : st == kS1b ? kS1c : st == kS1c ? kS2 : kS4, P, g.n_df, stop3);
+            if (lane == 0) {
+                if (isfinite(S.g2)) S.mm = fminf(S.mm, S.g1 - S.g2);
+                S.level = 0;
+                enter(W, s, st == kS1a ? kS1b : st == kS1b ? kS1c : st == kS1c ? kS2 : kS4, P, g.n_df, stop3);
+            }
+            __syncwarp();
             continue;
         }
         if (st == kFinal) {
-            S.ra[0] = S.a;
-            S.rb[0] = S.b;
-            S.rw[0] = 0;
-            S.nreq = 1;
+            if (lane == 0) {
+                S.ra[0] = S.a;
+                S.rb[0] = S.b;
+                S.rw[0] = 0;
+                S.nreq = 1;
+            }
+            __syncwarp();
             return;
         }
-        // the points of the next decision, in the canonical order: a 1D line
-        // compares left then right, a 2D move the 8 neighbours with the T1
-        // offset outer and -1 before +1
+        // the points of the next decision, in the canonical order (lane q: point q): a
+        // 1D line compares left then right, a 2D move the 8 neighbours with the T1 offset
+        // outer and -1 before +1
         const Lattice L = lattice_of(S);
         const int ia = S.ia, ib = S.ib;
         const int npts = L.line ? 2 : 8;
-        float vals[8];
-        int di[8], dk[8];
-        unsigned long long listed = 0;
-        bool missing = false;
-        int cnt = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            vals[q] = -INFINITY;
-            di[q] = dk[q] = 0;
-            if (q >= npts) continue;
-            if (L.line) {
-                const int m = q == 0 ? -1 : 1;
-                di[q] = L.param == 0 ? m : 0;
-                dk[q] = L.param == 1 ? m : 0;
-            } else {
-                const int k = q < 4 ? q : q + 1;
-                di[q] = k / 3 - 1;
-                dk[q] = k % 3 - 1;
-            }
-            bool known;
-            list_point(W, s, g, L, cnt, ia + di[q], ib + dk[q], listed, known, vals[q]);
-            if (!known) missing = true;
+        int di = 0, dk = 0;
+        if (L.line) {
+            const int m = lane == 0 ? -1 : 1;
+            di = L.param == 0 ? m : 0;
+            dk = L.param == 1 ? m : 0;
+        } else {
+            const int k = lane < 4 ? lane : lane + 1;
+            di = k / 3 - 1;
+            dk = k % 3 - 1;
         }
-        if (missing) {
-            const int nreq = cnt;
-            speculate(W, s, g, L, ia, ib, S.da, S.db, cnt, listed);
-            S.nreq = nreq;
-            S.nspec = cnt - nreq;
+        float v = -INFINITY;
+        bool known = true;
+        int a = 0, b = 0, idx = 0;
+        if (lane < npts) {
+            a = L.la + (ia + di) * L.h1;
+            b = L.lb + (ib + dk) * L.h2;
+            if (a >= L.alo && a <= L.ahi && b >= L.blo && b <= L.bhi && point_valid(g, a, b, L.c)) {
+                idx = L.line ? ((L.param == 0 ? ia + di : ib + dk) & (kWin - 1))
+                             : ((((ia + di) & 7) << 3) | ((ib + dk) & 7));
+                known = win_get(W, s, idx, a, b, v);
+            }
+        }
+        const unsigned miss = __ballot_sync(FULL, lane < npts && !known);
+        if (miss) {
+            // list the missing points in the decision's order, then the speculative ones
+            const int pos = __popc(miss & ((1u << lane) - 1u));
+            if (lane < npts && !known) {
+                S.ra[pos] = a;
+                S.rb[pos] = b;
+                S.rw[pos] = idx;
+            }
+            const int nreq = __popc(miss);
+            const unsigned lo = (lane < npts && !known && idx < 32) ? 1u << idx : 0u;
+            const unsigned hi = (lane < npts && !known && idx >= 32) ? 1u << (idx - 32) : 0u;
+            const unsigned long long listed =
+                ((unsigned long long)__reduce_or_sync(FULL, hi) << 32) | __reduce_or_sync(FULL, lo);
+            __syncwarp();
+            const int nspec = speculate_warp(W, s, lane, g, L, ia, ib, S.da, S.db, nreq, listed);
+            __syncwarp();
+            if (lane == 0) { S.nreq = nreq; S.nspec = nspec; }
+            __syncwarp();
             return;
         }
-        if (++S.moves > max_moves) { S.ok = 0; S.stage = kFinal; continue; }
+        // every value known: the decision, on every lane alike
+        float vals[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) vals[q] = __shfl_sync(FULL, v, q);
+        const bool over = S.moves + 1 > max_moves;
         float t1 = S.centre, t2 = -INFINITY, best = -INFINITY;
-        int bdi = 0, bdk = 0;
+        int bq = 0, cnt = 0;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const float v = vals[q];
-            if (isfinite(v)) { S.evaluated += 1; top2_add(v, t1, t2); }
-            if (v > best) { best = v; bdi = di[q]; bdk = dk[q]; }
+            if (q >= npts) continue;
+            const float vq = vals[q];
+            if (isfinite(vq)) { cnt += 1; top2_add(vq, t1, t2); }
+            if (vq > best) { best = vq; bq = q; }
         }
-        if (isfinite(t2)) S.mm = fminf(S.mm, t1 - t2);
-        if (best > S.centre) {
-            S.run = (bdi == S.da && bdk == S.db) ? S.run + 1 : 1;
-            S.ia = ia + bdi;
-            S.ib = ib + bdk;
-            S.da = bdi;
-            S.db = bdk;
-            S.a = L.la + (ia + bdi) * L.h1;
-            S.b = L.lb + (ib + bdk) * L.h2;
-            S.centre = best;
-            continue;
+        const int bdi = __shfl_sync(FULL, di, bq), bdk = __shfl_sync(FULL, dk, bq);
+        const bool moved = best > S.centre;
+        __syncwarp();
+        if (lane == 0) {
+            S.moves += 1;
+            if (over) {
+                S.ok = 0;
+                S.stage = kFinal;
+            } else {
+                S.evaluated += cnt;
+                if (isfinite(t2)) S.mm = fminf(S.mm, t1 - t2);
+                if (moved) {
+                    S.run = (bdi == S.da && bdk == S.db) ? S.run + 1 : 1;
+                    S.ia = ia + bdi;
+                    S.ib = ib + bdk;
+                    S.da = bdi;
+                    S.db = bdk;
+                    S.a = L.la + (ia + bdi) * L.h1;
+                    S.b = L.lb + (ib + bdk) * L.h2;
+                    S.centre = best;
+                } else if (st == kS5) {
+                    S.stage = kFinal;
+                } else {
+                    S.level += 1;
+                    enter(W, s, st, P, g.n_df, stop3);
+                }
+            }
         }
-        if (st == kS5) { S.stage = kFinal; continue; }
-        S.level += 1;
-        enter(W, s, st, P, g.n_df, stop3);
+        __syncwarp();
     }
 }
 
@@ -1212,6 +1275,86 @@ __device__ __forceinline__ void eval_entries(PackShared &W, const ZoomArgs &A, i
     }
 }
 
+// Lane 0: slot s takes work if it is idle -- the next voxel of its prior
+// chain, a resumed search (steps 4-5), or a new voxel -- until it has work or
+// the voxels run out.
+__device__ void refill_slot(PackShared &W, int s, const ZoomArgs &A, const ZoomPlan &P, ZState *head)
+{
+    Slot &S = W.s[s];
+    const bool takes = s < A.max_slots;
+    while (S.v < 0 && (S.chain_next < S.chain_end || (takes && !W.drained))) {
+        if (A.chain_len > 0 && S.chain_next < S.chain_end) {
+            // the next voxel of the chain: the box of the prior's
+            // half-widths around the preceding voxel's result, cut
+            // by the grid, and (prior_start) that result as start
+            S.v = S.chain_next++;
+            S.alo = max(0, S.pa - A.prior_h1); S.ahi = min(A.g.n_t1 - 1, S.pa + A.prior_h1);
+            S.blo = max(0, S.pb - A.prior_h2); S.bhi = min(A.g.n_t2 - 1, S.pb + A.prior_h2);
+            S.clo = max(0, S.pc - A.prior_h3); S.chi = min(A.g.n_df - 1, S.pc + A.prior_h3);
+            int a = S.pa, b = S.pb;
+            if (!A.prior_start) {
+                // the options' start clipped into the box, then moved
+                // to a valid point inside it
+                a = min(max(P.a_raw, S.alo), S.ahi);
+                b = min(max(P.b_raw, S.blo), S.bhi);
+                while (b > S.blo && !point_valid(A.g, a, b, S.clo)) --b;
+                while (a < S.ahi && !point_valid(A.g, a, b, S.clo)) ++a;
+            }
+            if (!point_valid(A.g, a, b, S.clo)) atomicExch(A.err, kDeviceErrBounds);
+            S.a = a; S.b = b;
+            S.c = S.clo;
+            S.centre = -INFINITY;
+            S.evaluated = 0;
+            S.mm = INFINITY;
+            S.ok = 1;
+            S.rounds = 0;
+            S.level = 0;
+            atomicOr(&W.norm_mask, 1 << s);
+            enter(W, s, kS1a, P, A.g.n_df, false);
+            break;
+        }
+        const int nv = atomicAdd(A.counter, 1);
+        const int64_t first = A.chain_len > 0 ? (int64_t)nv * A.chain_len : (int64_t)nv;
+        if (first >= A.V) { W.drained = 1; break; }
+        if (A.phase == kPhaseTail) {
+            // resume after step 3 (voxels finished earlier are skipped)
+            const ZState z = A.state[nv];
+            S.alo = 0; S.ahi = A.g.n_t1 - 1; S.blo = 0; S.bhi = A.g.n_t2 - 1;
+            S.clo = 0; S.chi = A.g.n_df - 1;
+            if (z.flags & kZDone) continue;
+            S.v = nv;
+            S.a = z.a; S.b = z.b; S.c = z.c;
+            S.centre = z.centre;
+            S.evaluated = z.evaluated;
+            S.mm = z.mm;
+            S.ok = z.flags & kZOk;
+            S.rounds = z.flags >> 8;
+            S.inv_xn = z.inv_xn;
+            S.level = 0;
+            enter(W, s, kS4, P, A.g.n_df, false);
+        } else {
+            // a voxel (or a prior chain's first voxel) on the whole grid
+            S.v = (int)first;
+            if (A.chain_len > 0) {
+                S.chain_next = (int)first + 1;
+                S.chain_end = (int)(first + A.chain_len < A.V ? first + A.chain_len : A.V);
+            }
+            S.alo = 0; S.ahi = A.g.n_t1 - 1; S.blo = 0; S.bhi = A.g.n_t2 - 1;
+            S.clo = 0; S.chi = A.g.n_df - 1;
+            S.a = P.a0; S.b = P.b0;
+            S.c = S.clo;
+            S.centre = -INFINITY;
+            S.evaluated = 0;
+            S.mm = INFINITY;
+            S.ok = 1;
+            S.rounds = 0;
+            S.level = 0;
+            atomicOr(&W.norm_mask, 1 << s);
+            enter(W, s, kS1a, P, A.g.n_df, head != nullptr);
+        }
+    }
+}
+
 template <bool XONLY, bool SYM>
 __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
 {
@@ -1233,91 +1376,23 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
         // decisions (one lane per slot)
         ingest(W, lane, A.g, A.out, A.err, head, A.stats);
         __syncwarp();
-        if (lane < kSlots) {
-            const int s = lane;
-            ingest_scan(W, s);
-            Slot &S = W.s[s];
-            // a slot parked at step 3 is free at once: refill it until it has
-            // work or the voxels run out, so no warp leaves with voxels left; a
-            // slot in a prior chain goes on with the chain's next voxel
+        if (lane < kSlots) ingest_scan(W, lane);
+        __syncwarp();
+        // every slot in turn: it takes a voxel if idle (lane 0), then the whole warp runs
+        // its decisions. A slot parked at step 3 is free at once and takes the next voxel,
+        // so no warp leaves with voxels left; a slot in a prior chain goes on with the
+        // chain's next voxel.
+        for (int s = 0; s < kSlots; ++s) {
             for (;;) {
-                const bool takes = s < A.max_slots;
-                while (S.v < 0 && (S.chain_next < S.chain_end || (takes && !W.drained))) {
-                    if (A.chain_len > 0 && S.chain_next < S.chain_end) {
-                        // the next voxel of the chain: the box of the prior's
-                        // half-widths around the preceding voxel's result, cut
-                        // by the grid, and (prior_start) that result as start
-                        S.v = S.chain_next++;
-                        S.alo = max(0, S.pa - A.prior_h1); S.ahi = min(A.g.n_t1 - 1, S.pa + A.prior_h1);
-                        S.blo = max(0, S.pb - A.prior_h2); S.bhi = min(A.g.n_t2 - 1, S.pb + A.prior_h2);
-                        S.clo = max(0, S.pc - A.prior_h3); S.chi = min(A.g.n_df - 1, S.pc + A.prior_h3);
-                        int a = S.pa, b = S.pb;
-                        if (!A.prior_start) {
-                            // the options' start clipped into the box, then moved
-                            // to a valid point inside it
-                            a = min(max(P.a_raw, S.alo), S.ahi);
-                            b = min(max(P.b_raw, S.blo), S.bhi);
-                            while (b > S.blo && !point_valid(A.g, a, b, S.clo)) --b;
-                            while (a < S.ahi && !point_valid(A.g, a, b, S.clo)) ++a;
-                        }
-                        if (!point_valid(A.g, a, b, S.clo)) atomicExch(A.err, kDeviceErrBounds);
-                        S.a = a; S.b = b;
-                        S.c = S.clo;
-                        S.centre = -INFINITY;
-                        S.evaluated = 0;
-                        S.mm = INFINITY;
-                        S.ok = 1;
-                        S.rounds = 0;
-                        S.level = 0;
-                        atomicOr(&W.norm_mask, 1 << s);
-                        enter(W, s, kS1a, P, A.g.n_df, false);
-                        break;
-                    }
-                    const int nv = atomicAdd(A.counter, 1);
-                    const int64_t first = A.chain_len > 0 ? (int64_t)nv * A.chain_len : (int64_t)nv;
-                    if (first >= A.V) { W.drained = 1; break; }
-                    if (A.phase == kPhaseTail) {
-                        // resume after step 3 (voxels finished earlier are skipped)
-                        const ZState z = A.state[nv];
-                        S.alo = 0; S.ahi = A.g.n_t1 - 1; S.blo = 0; S.bhi = A.g.n_t2 - 1;
-                        S.clo = 0; S.chi = A.g.n_df - 1;
-                        if (z.flags & kZDone) continue;
-                        S.v = nv;
-                        S.a = z.a; S.b = z.b; S.c = z.c;
-                        S.centre = z.centre;
-                        S.evaluated = z.evaluated;
-                        S.mm = z.mm;
-                        S.ok = z.flags & kZOk;
-                        S.rounds = z.flags >> 8;
-                        S.inv_xn = z.inv_xn;
-                        S.level = 0;
-                        enter(W, s, kS4, P, A.g.n_df, false);
-                    } else {
-                        // a voxel (or a prior chain's first voxel) on the whole grid
-                        S.v = (int)first;
-                        if (A.chain_len > 0) {
-                            S.chain_next = (int)first + 1;
-                            S.chain_end = (int)(first + A.chain_len < A.V ? first + A.chain_len : A.V);
-                        }
-                        S.alo = 0; S.ahi = A.g.n_t1 - 1; S.blo = 0; S.bhi = A.g.n_t2 - 1;
-                        S.clo = 0; S.chi = A.g.n_df - 1;
-                        S.a = P.a0; S.b = P.b0;
-                        S.c = S.clo;
-                        S.centre = -INFINITY;
-                        S.evaluated = 0;
-                        S.mm = INFINITY;
-                        S.ok = 1;
-                        S.rounds = 0;
-                        S.level = 0;
-                        atomicOr(&W.norm_mask, 1 << s);
-                        enter(W, s, kS1a, P, A.g.n_df, head != nullptr);
-                    }
-                }
-                advance(W, s, P, A.g, A.max_moves, head);
-                if (S.v >= 0 || ((W.drained || !takes) && S.chain_next >= S.chain_end)) break;
+                if (lane == 0) refill_slot(W, s, A, P, head);
+                __syncwarp();
+                if (W.s[s].v < 0) break;
+                advance_warp(W, s, lane, P, A.g, A.max_moves, head);
+                const Slot &S = W.s[s];
+                if (S.v >= 0 || ((W.drained || s >= A.max_slots) && S.chain_next >= S.chain_end)) break;
             }
-            if (S.v >= 0) S.rounds += 1;
         }
+        if (lane < kSlots && W.s[lane].v >= 0) W.s[lane].rounds += 1;
         __syncwarp();
         const bool busy = lane < kSlots && W.s[lane].v >= 0;
         if (!__any_sync(FULL, busy)) break;
