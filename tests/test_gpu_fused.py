@@ -140,3 +140,16 @@ def test_fused_options_checked(M, ctx):
             assert rc == M.MRF_E_INVALID
     finally:
         M.mrf_sequence_free(ctx, h)
+
+
+@pytest.mark.parametrize("V", [1, 65])
+def test_fused_ragged_voxel_counts(M, ctx, oracle_lib, V):
+    """One voxel, and one voxel past a 64-voxel unit: the padding rows of the
+    voxel operand take no part."""
+    seq = S.sequence(2, 200)
+    g = S.Grid(150.0, 45.0, 37, 12.0, 9.0, 33, -12.0, 3.0, 9)
+    ph, x = offgrid_voxels(oracle_lib, seq, V, 25.0, 10, t1_range=(200.0, 1700.0), t2_range=(15.0, 300.0),
+                           df_range=(-11.0, 11.0))
+    ref = oracle_lib.bruteforce(seq, g, x, k=2)
+    res = _fused(M, ctx, seq, g, x, M.MRF_F32, 4)
+    _compare(res, ref, f"fused V={V}")

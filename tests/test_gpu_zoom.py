@@ -450,3 +450,23 @@ def test_zoom_work_counters(M, ctx, oracle_lib):
     assert p.zoom_timed == 1 and p.zoomline_timed == 1 and p.zoom_ms > p.zoomline_ms > 0
     q = M.mrf_profile_read(ctx)
     assert q.zoomline_pairs == 0 and q.zoom_rounds == 0 and q.zoom_timed == 0
+
+
+def test_zoom_prior_edge_chains(M, ctx, oracle_lib):
+    """Chains of one voxel are the plain search bit for bit (every voxel is a
+    chain's first); a single voxel, and a chain longer than the slice, are
+    the oracle's chain."""
+    seq = S.sequence(1, 1000)
+    g = S.GRIDS["fp32_brute"]
+    ph, x = offgrid_voxels(oracle_lib, seq, 21, 20.0, 34)
+    plain = _gpu_zoom(M, ctx, seq, g, x)
+    one = _gpu_zoom(M, ctx, seq, g, x, prior=(1, (200.0, 30.0, 6.0)))
+    for f in ("index", "entries_evaluated"):
+        assert np.array_equal(plain[f], one[f]), f
+    assert np.array_equal(plain["cc"].view(np.uint32), one["cc"].view(np.uint32))
+    half = (200.0, 30.0, 6.0)
+    for V, L in ((1, 1), (21, 1000)):
+        res = _gpu_zoom(M, ctx, seq, g, x[:V], prior=(L, half))
+        ref = oracle_lib.zoom_prior(seq, g, x[:V], chain=min(L, V), half=half)
+        compared, cut = _compare_chains(oracle_lib, g, res, ref, min(L, V), half, f"V={V} chain={L}")
+        assert compared >= 1
