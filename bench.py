@@ -54,7 +54,7 @@ TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "match_kernel_f32_traffic_147k_
 def matcher_sources_sha256():
     import hashlib
     csrc = os.path.join(ROOT, "paper_1506_05393_gb300", "csrc")
-    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("match.cu", "tc.cuh"))
+    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("match.cu", "tc.cuh", "split.cuh"))
     return hashlib.sha256(src).hexdigest()
 
 
@@ -273,7 +273,7 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
         flops = 8.0 * N_TP * Dg * V
         peak = pk["bf16_tflops"] * (2.0 if dtype == M.MRF_FP8E4M3 else 1.0)
         own = mma_rates.get(dtype)
-        entry = {"grid": grid_name, "entries": Dg, "dtype": ["f32 (bf16x3)", "bf16", "fp8e4m3"][dtype], "top_k": k,
+        entry = {"grid": grid_name, "entries": Dg, "dtype": ["f32 (fp16 + 2 e4m3 residual products)", "bf16", "fp8e4m3"][dtype], "top_k": k,
                  "voxels_per_s": V / ms * 1e3, "ms": ms, "matcher_ms": mm, "dict_generate_s": gen_s,
                  "matcher_tflops_algorithmic": flops / mm / 1e9,
                  "matcher_frac_of_peak": flops / mm / 1e9 / peak,
@@ -334,7 +334,7 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
                                       "mean_entries_evaluated": float(res["entries_evaluated"].mean()),
                                       "index_agreement_vs_fp32": float(np.mean(res["index"] == fp32_index))}
 
-    # ZOOM over the resident FP32-equivalent dictionary (Experiment 2's full-dictionary variant)
+    # ZOOM over the resident MRF_F32 dictionary (Experiment 2's full-dictionary variant)
     d = M.mrf_dict_generate(ctx, seq_h, g, M.MRF_F32)
     run = lambda: M.mrf_zoom_search_dict(ctx, d, zo, x_dev, out)
     run()
@@ -508,7 +508,7 @@ def run_modes(M, ctx, seq, seq_h, x_dev, fp32_index, pk, clock_mhz, ph=None):
                                              if np.any(rb["cc"] - rz["cc"] > 1e-2) else 0.0
                                              for k, f in (("t1_ms", "t1_ms"), ("t2_ms", "t2_ms"),
                                                           ("df_hz", "df_hz"))}},
-        "note": "mrf_match_bruteforce_grid: FP32-equivalent brute force (top-4 + FP64 re-score) over ranges of "
+        "note": "mrf_match_bruteforce_grid: FP32-class brute force (top-4 + FP64 re-score) over ranges of "
                 "whole T1 rows, no resident dictionary; ZOOM (and ZOOM + refinement) on the same voxels "
                 "compared with it"}
 
@@ -873,7 +873,7 @@ def run_reference(args, rank):
 
 # ---------------------------------------------------------------------------- ncu cases
 
-# A 147,476-entry grid (1.2 GB FP32-equivalent dictionary: larger than L2, a
+# A 147,476-entry grid (1.2 GB MRF_F32 dictionary: larger than L2, a
 # few GB on the device) used for profiling captures of the matcher.
 NCU_GRID = S.Grid(100.0, 20.0, 60, 10.0, 5.0, 79, -40.0, 2.0, 41)
 
@@ -1076,15 +1076,16 @@ def main():
             "traffic": matcher_traffic(D), "traffic_unit": "bytes per launch (ncu dram read + write of a 147,476-entry "
                                                           "launch, scaled by the entry count)",
             "algorithmic_bytes": 8192 * 2 * 2 * 2112 + D * 2 * 2 * 2112, "kernel": "match_kernel<MRF_F32, 4>",
-            "issued_frac": 3.0 * achieved / peak,
+            "issued_frac": 2.0 * achieved / peak,
             "note": f"achieved = 8*N*D*V algorithmic flops / CUDA-event matcher time ({matcher_ms:.3f} ms); "
-                    f"the bf16x3 split issues 3x these flops; peak = bf16 dense sustained "
-                    f"({pk['_source']})"}
+                    f"the split form (one fp16 product, K = 16 per MMA, and two e4m3 residual products, "
+                    f"K = 32 per MMA of the same duration) issues 2x these flops in bf16-rate time; peak = bf16 "
+                    f"dense sustained ({pk['_source']})"}
 
     if rank != 0:
         return
     dg_ms = prof.dictgen_ms / max(prof.dictgen_timed, 1)
-    # stored bytes: bf16 hi + lo rows of the library's row stride (ld elements) per entry
+    # stored bytes: fp16 row + two e4m3 planes (4 bytes per element) of the library's row stride (ld elements)
     d1 = M.mrf_dict_generate(ctx, seq_h, S.GRIDS["tiny"], M.MRF_F32)
     ld = M.mrf_dict_query(d1).ld
     M.mrf_dict_free(ctx, d1)
@@ -1097,7 +1098,7 @@ def main():
             "fingerprints_per_s": D / dg_ms * 1e3, "ms": dg_ms, "entries": D,
             "roofline": {"bound": "hbm", "achieved": dg_bytes / dg_ms / 1e6, "peak": pk.get("hbm_gbs", 6690.8),
                          "unit": "GB/s", "frac": dg_bytes / dg_ms / 1e6 / pk.get("hbm_gbs", 6690.8),
-                         "note": "bytes of the stored FP32-equivalent dictionary (bf16 hi + lo rows) per "
+                         "note": "bytes of the stored MRF_F32 dictionary (fp16 row and two e4m3 planes) per "
                                  "CUDA-event launch time; peak = measured HBM copy bandwidth"}},
         "paper_context": {
             "hardware": "C++ on a 2.0 GHz dual-core laptop CPU (the paper's only platform)",
@@ -1138,8 +1139,9 @@ def main():
 
 
 WORKLOAD = ("64x64 slice, N=1000, T1 100-4000/20 ms x T2 10-400/5 ms x df -40..40/2 Hz (614,508 entries): "
-            "FP32-equivalent brute-force DGS per step = sequence upload + dictionary generation + voxel prep + "
-            "tensor-core match (bf16x3, fp32 accumulate, top-4) + FP32 re-simulation / FP64 re-score + M0/phase")
+            "FP32-class brute-force DGS per step = sequence upload + dictionary generation + voxel prep + "
+            "tensor-core match (fp16 product + two e4m3 residual products, fp32 accumulate, top-4) + FP32 "
+            "re-simulation / FP64 re-score + M0/phase")
 
 
 def emit(line, details, details_out):

@@ -50,9 +50,14 @@ enum {
 };
 
 typedef enum {
-    MRF_F32 = 0,      /* FP32-equivalent: the raw FP32 entries split into bf16 hi + lo
-                         with a per-entry scale 1 / ||d||, three tensor-core products
-                         (hi.hi + hi.lo + lo.hi) */
+    MRF_F32 = 0,      /* FP32-class: the raw FP32 entries (per-entry scale 1 / ||d||)
+                         stored as fp16 (x 2^15) plus e4m3 planes of the values (x 2^8)
+                         and of the fp16 residuals (x 2^19); the voxels alike (fp16
+                         x 2^12). Each product is the fp16 product plus the two e4m3
+                         products of each residual with the other operand (at most
+                         about 2^-13 |x_j d_j| per term, rms about 2^-16), the e4m3
+                         ones accumulated first. Generated tiles (mrf_match_bruteforce_fused)
+                         use bf16 hi + lo with three products (hi.hi + hi.lo + lo.hi). */
     MRF_BF16 = 1,     /* normalised entries rounded to bf16 (nearest even), scale 1 */
     MRF_FP8E4M3 = 2   /* normalised entries scaled to max |value| = 448 per entry,
                          stored as fp8 e4m3 with an fp32 per-entry scale */
@@ -236,8 +241,9 @@ typedef struct {
     int32_t ld;            /* row stride in elements: 2n rounded up to 128, plus 128 bytes of
                               padding (rows off a power-of-two stride); entries past 2n are 0 */
     int32_t dtype;         /* mrf_dtype */
-    const void *hi_dev;    /* D x ld: bf16 (F32 hi, BF16) or e4m3 bytes (FP8) */
-    const void *lo_dev;    /* D x ld bf16 residual (F32 only), else NULL */
+    const void *hi_dev;    /* D x ld: fp16 x 2^15 (F32), bf16 (BF16) or e4m3 bytes (FP8) */
+    const void *lo_dev;    /* F32 only, else NULL: two D x ld e4m3 planes, the values x 2^8,
+                              then the fp16 residuals x 2^19 (value = hi 2^-15 + residual 2^-19) */
     const float *norm_dev; /* D: L2 norm of the un-normalised FP32 signal */
     const float *scale_dev;/* D: per-entry scale, stored value x scale = unit-norm entry
                               (F32: 1 / norm; BF16: 1; FP8: the dequantisation scale) */
@@ -409,7 +415,7 @@ int mrf_zoom_search(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *grid,
  * full pre-defined dictionary"): the search of mrf_zoom_search on the
  * dictionary's own grid and sequence, each candidate's CC read from the
  * stored normalised entry (one warp streams the row) instead of simulated.
- * The dictionary must be MRF_F32 (FP32-equivalent CC) or MRF_BF16 (bf16 CC,
+ * The dictionary must be MRF_F32 (FP32-class CC of the stored values) or MRF_BF16 (bf16 CC,
  * decisions may differ from the FP32 search where candidates differ by less
  * than about 1e-3). M0 and phase use the stored entry norms. Errors:
  * MRF_E_INVALID, MRF_E_UNSUPPORTED (FP8 dictionary, or a spatial-neighbour

@@ -300,7 +300,7 @@ def mrf_smooth(ctx, fp_in, fp_out, width: int, sigma: float = 1.0, stream=None) 
 
 
 def mrf_dict_smooth(ctx, d, width: int, sigma: float = 1.0, stream=None) -> None:
-    """Smooth a generated FP32-equivalent or BF16 dictionary in place."""
+    """Smooth a generated MRF_F32 or BF16 dictionary in place."""
     check(lib().mrf_dict_smooth(ctx, d, int(width), float(sigma), _stream_ptr(stream)), "mrf_dict_smooth")
 
 

@@ -4,8 +4,9 @@
 // Dictionary generation (Theory: brute-force DGS simulates every grid entry;
 // entries normalised to unit norm so CC is |inner product|):
 //   one thread per entry, FP32 recurrence in registers (bloch.cuh);
-//   FP32-equivalent (bf16 hi + lo): one pass writes the raw signal and
-//   accumulates ||d||^2; the entry's scale 1 / ||d|| makes it unit norm;
+//   MRF_F32 (fp16 row plus e4m3 planes of the values and of the fp16
+//   residuals, split.cuh): one pass writes the raw signal and accumulates
+//   ||d||^2; the entry's scale 1 / ||d|| makes it unit norm;
 //   BF16 / FP8: pass 1 accumulates ||d||^2 (and max |d| for FP8), pass 2
 //   re-runs the recurrence and writes the normalised (BF16, scale 1) or
 //   scaled e4m3 (FP8) row.
@@ -27,6 +28,7 @@
 
 #include "bloch.cuh"
 #include "mrf_internal.h"
+#include "split.cuh"
 
 namespace {
 
@@ -179,20 +181,23 @@ __device__ __forceinline__ void step_fac(Bloch &st, const SeqDev &s, const FacGr
 template <int OUT>
 struct Packer;
 
-// F32 (hi + lo bf16) and BF16: 4 bytes per timepoint per array.
+// F32: the fp16 pair (4 bytes per timepoint) in `hi`; in `lo`, words 0-1 the
+// e4m3 value pairs and words 2-3 the e4m3 residual pairs of the four slots.
 template <>
 struct Packer<MRF_F32> {
     static constexpr int kBpt = 4;
     uint32_t hi[4], lo[4];
     __device__ __forceinline__ void put(int slot, float vr, float vi, float)
     {
-        __nv_bfloat162 h = __floats2bfloat162_rn(vr, vi);
-        float2 hf = __bfloat1622float2(h);
-        __nv_bfloat162 l = __floats2bfloat162_rn(vr - hf.x, vi - hf.y);
-        hi[slot] = *reinterpret_cast<uint32_t *>(&h);
-        lo[slot] = *reinterpret_cast<uint32_t *>(&l);
+        const SplitPair p = split_pair(vr, vi, kSplitHiD);
+        hi[slot] = p.hi;
+        const int w = slot >> 1, sh = 16 * (slot & 1);
+        lo[w] |= (uint32_t)p.h8 << sh;
+        lo[2 + w] |= (uint32_t)p.l8 << sh;
     }
 };
+
+// BF16: 4 bytes per timepoint.
 
 template <>
 struct Packer<MRF_BF16> {
@@ -218,6 +223,20 @@ struct Packer<MRF_FP8E4M3> {
         else hi[word] |= ((uint32_t)q) << 16;
     }
 };
+
+// The F32 form's two e4m3 planes (the values, then the residuals; D x ld
+// bytes each) for one 32-timepoint row chunk: lane piece qq < 4 writes 16
+// bytes (8 timepoints) of the value plane, qq >= 4 of the residual plane,
+// gathered from the two staged vectors that hold those timepoints (stage
+// slots swizzled by r7, the row's index mod 8).
+__device__ __forceinline__ void store_split_lo(uint8_t *out_lo, int64_t D, int ld, int64_t row, int j0, int qq,
+                                               const uint4 *srow, int r7)
+{
+    const int sel = qq >> 2, p = qq & 3;
+    const uint4 v0 = srow[(2 * p) ^ r7], v1 = srow[(2 * p + 1) ^ r7];
+    const uint4 o = sel ? make_uint4(v0.z, v0.w, v1.z, v1.w) : make_uint4(v0.x, v0.y, v1.x, v1.y);
+    __stcs(reinterpret_cast<uint4 *>(out_lo + (size_t)sel * D * ld + (size_t)row * ld + (size_t)j0 * 2 + p * 16), o);
+}
 
 template <int OUT, bool XONLY, bool SYM>
 __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev g, Tables t, int64_t D, int ld,
@@ -411,10 +430,7 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_kernel(SeqDev s, GridDev
                 const size_t off = (size_t)row * row_bytes + (size_t)j0 * kBpt + qq * 16;
                 const uint4 vh = stage_hi[warp][r][qq ^ (r & 7)];
                 __stcs(reinterpret_cast<uint4 *>(out_hi + off), vh);
-                if (kTwo) {
-                    const uint4 vl = stage_lo[kTwo ? warp : 0][r][qq ^ (r & 7)];
-                    __stcs(reinterpret_cast<uint4 *>(out_lo + off), vl);
-                }
+                if (kTwo) store_split_lo(out_lo, D, ld, row, j0, qq, stage_lo[kTwo ? warp : 0][r], r & 7);
             }
         }
         __syncwarp();
@@ -682,10 +698,7 @@ __global__ void __launch_bounds__(kGenThreads) dict_gen_xsym_kernel(SeqDev s, Gr
             if (row >= 0 && mrf_in_bounds(row < D && (size_t)j0 * kBpt + qq * 16 + 16 <= (size_t)row_bytes, err)) {
                 const uint4 vh = stage_hi[warp][r][qq ^ (r & 7)];
                 __stcs(reinterpret_cast<uint4 *>(out_hi + off), vh);
-                if (kTwo) {
-                    const uint4 vl = stage_lo[kTwo ? warp : 0][r][qq ^ (r & 7)];
-                    __stcs(reinterpret_cast<uint4 *>(out_lo + off), vl);
-                }
+                if (kTwo) store_split_lo(out_lo, D, ld, row, j0, qq, stage_lo[kTwo ? warp : 0][r], r & 7);
             }
         }
         __syncwarp();

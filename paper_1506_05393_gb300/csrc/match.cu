@@ -19,11 +19,13 @@
 // leaves the SM; each (voxel block, dictionary chunk) work unit writes only
 // its top-k, merged across chunks afterwards.
 //
-// Precisions: MRF_F32 = bf16 hi/lo split of the raw entries with three
-// products (hi.hi + hi.lo + lo.hi, ~2^-16 relative per term), the entry's
-// scale 1 / ||d|| applied to CC^2; MRF_BF16 = one bf16 product of unit-norm
-// entries; MRF_FP8E4M3 = one e4m3 product (kind::f8f6f4) with per-entry and
-// per-voxel scales applied to CC^2.
+// Precisions: MRF_F32 = the split form of split.cuh over raw entries: an
+// fp16 product and two e4m3 products of the fp16 residuals (per term at most
+// about 2^-13, rms about 2^-16 relative), the e4m3 ones accumulated first,
+// the entry's scale 1 / ||d|| applied to CC^2 (generated tiles: the bf16
+// hi/lo split, hi.hi + hi.lo + lo.hi); MRF_BF16 = one bf16 product of
+// unit-norm entries; MRF_FP8E4M3 = one e4m3 product (kind::f8f6f4) with
+// per-entry and per-voxel scales applied to CC^2.
 //
 // Re-score (Discussion: normalised-CC errors fixed by a non-normalised final
 // comparison): each voxel's candidates are re-simulated in FP32 and their CC
@@ -39,6 +41,7 @@
 
 #include "bloch.cuh"
 #include "mrf_internal.h"
+#include "split.cuh"
 #include "tc.cuh"
 
 namespace {
@@ -49,7 +52,9 @@ constexpr uint64_t kWaitLimitNs = 4000000000ull;   // 4 s per barrier wait
 
 template <int MODE>
 struct Cfg;
-// FP32-equivalent: hi and lo of both operands, one voxel block per CTA
+// MRF_F32: two operand tiles per side (split form: the e4m3 residual and value
+// planes, or two fp16 K blocks; generated tiles: bf16 hi and lo), one voxel
+// block per CTA
 template <>
 struct Cfg<MRF_F32> {
     static constexpr int kBK = 64, kStages = 2, kOps = 2, kNB = 1;
@@ -88,6 +93,7 @@ struct MatchParams {
                          // while the dictionary streams past them once
     int k_blocks;        // K blocks of 128 bytes
     int last_ksteps;     // MMA k-steps in the last K block (rest is zero padding)
+    int last_ks16;       // MRF_F32 split form: fp16 k-steps in the last 128-element chunk
     const float *colscale;   // per-entry scale (stored value x scale = unit-norm entry), nullptr when 1
     int col_stride;      // dictionary entry of tile column c is c * col_stride (sampled pre-pass)
     const float *thr0;   // per-voxel lower bound on the K-th best CC^2 (thr0[v * thr0_stride]), or nullptr
@@ -178,10 +184,19 @@ __device__ __forceinline__ void unravel_dev(const GridDev &g, int64_t e, int &a,
 template <int MODE, int K, bool GEN>
 __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
     match_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
-                 const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapB2,
-                 MatchParams p)
+                 const __grid_constant__ CUtensorMap mapA3, const __grid_constant__ CUtensorMap mapB,
+                 const __grid_constant__ CUtensorMap mapB2, const __grid_constant__ CUtensorMap mapB3, MatchParams p)
 {
     using C = Cfg<MODE>;
+    // MRF_F32 over a stored dictionary: the split form (fp16 product and two
+    // e4m3 residual products). Per tile, p.k_blocks e4m3 stages of 128
+    // elements (A: x residuals, x values; B: d values, d residuals) come
+    // first, then p.k_blocks fp16 stages of two 64-element K blocks.
+    // Generated tiles (GEN) use the bf16 hi/lo split.
+    constexpr bool kSplit = MODE == MRF_F32 && !GEN;
+    constexpr uint32_t kIdescF16 = make_idesc(0, 0, BM, BN);   // kind::f16 with fp16 operands
+    constexpr uint32_t kIdescE4 = make_idesc(0, 0, BM, BN);    // kind::f8f6f4 with e4m3 operands
+    constexpr float kColMul = kSplit ? kSplitUnscale : 1.0f;   // removes the split form's 2^27 per operand side
     constexpr int S = C::kStages;
     constexpr int NB = C::kNB;                  // voxel blocks per CTA
     constexpr int NBUF = NB == 1 ? 2 : 1;       // accumulator buffers (TMEM holds 512 columns)
@@ -231,6 +246,10 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
             tma_prefetch_desc(&mapA2);
             if (!GEN) tma_prefetch_desc(&mapB2);
         }
+        if (kSplit) {
+            tma_prefetch_desc(&mapA3);
+            tma_prefetch_desc(&mapB3);
+        }
     }
     if (warp == 1) {
         tmem_alloc(&tmem_slot, 2 * BN);
@@ -259,9 +278,32 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
                 const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
                 const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
                 for (int t = t0; t < t1; ++t) {
-                    for (int kb = 0; kb < p.k_blocks; ++kb) {
+                    const int n_st = kSplit ? 2 * p.k_blocks : p.k_blocks;
+                    for (int kb = 0; kb < n_st; ++kb) {
                         if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kWaitLimitNs)) goto producer_done;
                         mbar_arrive_expect_tx(&full_bar[s], kTmaBytes);
+                        if (kSplit) {
+                            const int row = vu * BM;
+                            if (kb < p.k_blocks) {
+                                // e4m3 stage: 128 elements of the residual and value planes
+                                const int kx = kb * 128;
+                                tma_load_2d_hint(tileA(s, 0, 0), &mapA2, &full_bar[s], kx, row, keep);
+                                tma_load_2d_hint(tileA(s, 1, 0), &mapA3, &full_bar[s], kx, row, keep);
+                                tma_load_2d(tileB(s, 0), &mapB2, &full_bar[s], kx, t * BN);
+                                tma_load_2d(tileB(s, 1), &mapB3, &full_bar[s], kx, t * BN);
+                            } else {
+                                // fp16 stage: two K blocks of 64 elements
+                                const int kx = (kb - p.k_blocks) * 128;
+                                tma_load_2d_hint(tileA(s, 0, 0), &mapA, &full_bar[s], kx, row, keep);
+                                tma_load_2d_hint(tileA(s, 1, 0), &mapA, &full_bar[s], kx + 64, row, keep);
+                                tma_load_2d(tileB(s, 0), &mapB, &full_bar[s], kx, t * BN);
+                                tma_load_2d(tileB(s, 1), &mapB, &full_bar[s], kx + 64, t * BN);
+                            }
+                            issued[s] = true;
+                            issued_ph[s] = ph;
+                            if (++s == S) { s = 0; ph ^= 1; }
+                            continue;
+                        }
                         const int kx = kb * C::kBK;
 #pragma unroll
                         for (int i = 0; i < NB; ++i) {
@@ -304,9 +346,36 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
                 for (int t = t0; t < t1; ++t) {
                     if (!mbar_wait_bounded(&tempty_bar[buf], buf_ph ^ 1, &abort_flag, p.err, kWaitLimitNs)) goto mma_done;
                     tc_fence_after();
-                    for (int kb = 0; kb < p.k_blocks; ++kb) {
+                    const int n_st = kSplit ? 2 * p.k_blocks : p.k_blocks;
+                    for (int kb = 0; kb < n_st; ++kb) {
                         if (!mbar_wait_bounded(&full_bar[s], ph, &abort_flag, p.err, kWaitLimitNs)) goto mma_done;
                         tc_fence_after();
+                        if (kSplit) {
+                            const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+                            const uint64_t a0 = smem_desc_sw128(tileA(s, 0, 0)), a1 = smem_desc_sw128(tileA(s, 1, 0));
+                            const uint64_t b0 = smem_desc_sw128(tileB(s, 0)), b1 = smem_desc_sw128(tileB(s, 1));
+                            if (kb < p.k_blocks) {
+                                // the e4m3 products first: x residual . d value, x value . d residual
+                                const int nk = (kb == p.k_blocks - 1) ? p.last_ksteps : 4;
+                                for (int kk = 0; kk < nk; ++kk) {
+                                    const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+                                    mma_f8(d_tmem, a0 + adv, b0 + adv, kIdescE4, (kb | kk) != 0);
+                                    mma_f8(d_tmem, a1 + adv, b1 + adv, kIdescE4, 1u);
+                                }
+                            } else {
+                                // then the fp16 product over the stage's two K blocks
+                                const int nk = (kb == n_st - 1) ? p.last_ks16 : 8;
+                                for (int kk = 0; kk < nk; ++kk) {
+                                    const uint64_t adv = (uint64_t)((kk & 3) * 32) >> 4;
+                                    if (kk < 4) mma_f16(d_tmem, a0 + adv, b0 + adv, kIdescF16, 1u);
+                                    else mma_f16(d_tmem, a1 + adv, b1 + adv, kIdescF16, 1u);
+                                }
+                            }
+                            mma_commit(&empty_bar[s]);
+                            any = true;
+                            if (++s == S) { s = 0; ph ^= 1; }
+                            continue;
+                        }
                         const uint64_t b0 = smem_desc_sw128(tileB(s, 0));
                         const int nk = (kb == p.k_blocks - 1) ? p.last_ksteps : 4;
                         for (int kk = 0; kk < nk; ++kk) {
@@ -546,7 +615,8 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
 #pragma unroll
                         for (int q4 = 0; q4 < 4; ++q4) {
                             const float4 f = s4[q4];
-                            sc16[4 * q4] = f.x; sc16[4 * q4 + 1] = f.y; sc16[4 * q4 + 2] = f.z; sc16[4 * q4 + 3] = f.w;
+                            sc16[4 * q4] = f.x * kColMul; sc16[4 * q4 + 1] = f.y * kColMul;
+                            sc16[4 * q4 + 2] = f.z * kColMul; sc16[4 * q4 + 3] = f.w * kColMul;
                         }
                     }
                     uint32_t mask = 0;
@@ -615,11 +685,13 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
 }
 
 // ---------------------------------------------------------------------------
-// voxel prep: normalise and lay out the two real rows per voxel
+// voxel prep: normalise and lay out the two real rows per voxel. SPLIT
+// (MRF_F32 over a stored dictionary): fp16 rows in a_hi, and in a_lo the e4m3
+// residual plane followed, plane8 bytes on, by the e4m3 value plane.
 
-template <int MODE>
+template <int MODE, bool SPLIT = false>
 __global__ void __launch_bounds__(256) voxel_prep_kernel(const float2 *x, int64_t V, int n, int ld, uint8_t *a_hi,
-                                                         uint8_t *a_lo, float *row_scale)
+                                                         uint8_t *a_lo, float *row_scale, size_t plane8)
 {
     const int64_t v = blockIdx.x;
     __shared__ float red[2][8];
@@ -658,7 +730,15 @@ __global__ void __launch_bounds__(256) voxel_prep_kernel(const float2 *x, int64_
             xi = z.y * qs;
         }
         const size_t r0 = (size_t)(2 * v) * ld, r1 = (size_t)(2 * v + 1) * ld;
-        if (MODE == MRF_FP8E4M3) {
+        if (SPLIT) {
+            const SplitPair p0 = split_pair(xr, xi, kSplitHiX), p1 = split_pair(xi, -xr, kSplitHiX);
+            reinterpret_cast<uint32_t *>(a_hi + 2 * r0)[j] = p0.hi;
+            reinterpret_cast<uint32_t *>(a_hi + 2 * r1)[j] = p1.hi;
+            reinterpret_cast<uint16_t *>(a_lo + r0)[j] = p0.l8;
+            reinterpret_cast<uint16_t *>(a_lo + r1)[j] = p1.l8;
+            reinterpret_cast<uint16_t *>(a_lo + plane8 + r0)[j] = p0.h8;
+            reinterpret_cast<uint16_t *>(a_lo + plane8 + r1)[j] = p1.h8;
+        } else if (MODE == MRF_FP8E4M3) {
             __nv_fp8x2_storage_t q0 = __nv_cvt_float2_to_fp8x2(make_float2(xr, xi), __NV_SATFINITE, __NV_E4M3);
             __nv_fp8x2_storage_t q1 = __nv_cvt_float2_to_fp8x2(make_float2(xi, -xr), __NV_SATFINITE, __NV_E4M3);
             reinterpret_cast<__nv_fp8x2_storage_t *>(a_hi + r0)[j] = q0;
@@ -938,9 +1018,13 @@ int make_map(CUtensorMap *m, const void *base, int64_t rows, int ld, int elem_by
 
 int gcd_i(int a, int b) { while (b) { int t = a % b; a = b; b = t; } return a; }
 
+// Operand maps of one launch: A (voxels) and B (dictionary), each up to three planes.
+struct MatchMaps {
+    CUtensorMap a, a2, a3, b, b2, b3;
+};
+
 template <int MODE, int K, bool GEN>
-int launch_match_k(mrf_ctx *ctx, const CUtensorMap &mA, const CUtensorMap &mA2, const CUtensorMap &mB,
-                   const CUtensorMap &mB2, const MatchParams &p, cudaStream_t stream)
+int launch_match_k(mrf_ctx *ctx, const MatchMaps &m, const MatchParams &p, cudaStream_t stream)
 {
     // the opt-in for large dynamic shared memory is a property of the kernel on
     // one device: set once per instantiation and device, under the matcher mutex
@@ -956,23 +1040,23 @@ int launch_match_k(mrf_ctx *ctx, const CUtensorMap &mA, const CUtensorMap &mA2, 
     }
     const int units = p.n_vu * p.n_chunks;
     const int grid = std::min(units, ctx->sm_count);
-    match_kernel<MODE, K, GEN><<<grid, threads_of<MODE, GEN>(), smem_bytes<MODE>(), stream>>>(mA, mA2, mB, mB2, p);
+    match_kernel<MODE, K, GEN><<<grid, threads_of<MODE, GEN>(), smem_bytes<MODE>(), stream>>>(m.a, m.a2, m.a3, m.b, m.b2,
+                                                                                           m.b3, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "matcher launch");
     return MRF_OK;
 }
 
 template <int MODE, bool GEN = false>
-int launch_match_mode(mrf_ctx *ctx, int K, const CUtensorMap &mA, const CUtensorMap &mA2, const CUtensorMap &mB,
-                      const CUtensorMap &mB2, const MatchParams &p, cudaStream_t stream)
+int launch_match_mode(mrf_ctx *ctx, int K, const MatchMaps &m, const MatchParams &p, cudaStream_t stream)
 {
     switch (K) {
-    case 1: return launch_match_k<MODE, 1, GEN>(ctx, mA, mA2, mB, mB2, p, stream);
-    case 2: return launch_match_k<MODE, 2, GEN>(ctx, mA, mA2, mB, mB2, p, stream);
-    case 4: return launch_match_k<MODE, 4, GEN>(ctx, mA, mA2, mB, mB2, p, stream);
-    case 8: return launch_match_k<MODE, 8, GEN>(ctx, mA, mA2, mB, mB2, p, stream);
-    case 16: return launch_match_k<MODE, 16, GEN>(ctx, mA, mA2, mB, mB2, p, stream);
-    case 32: return launch_match_k<MODE, 32, GEN>(ctx, mA, mA2, mB, mB2, p, stream);
+    case 1: return launch_match_k<MODE, 1, GEN>(ctx, m, p, stream);
+    case 2: return launch_match_k<MODE, 2, GEN>(ctx, m, p, stream);
+    case 4: return launch_match_k<MODE, 4, GEN>(ctx, m, p, stream);
+    case 8: return launch_match_k<MODE, 8, GEN>(ctx, m, p, stream);
+    case 16: return launch_match_k<MODE, 16, GEN>(ctx, m, p, stream);
+    case 32: return launch_match_k<MODE, 32, GEN>(ctx, m, p, stream);
     }
     return set_error(MRF_E_INVALID, "top_k");
 }
@@ -1010,11 +1094,15 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     // chunks: make each group's units a multiple of the SM count where possible
     int n_chunks = ctx->sm_count / gcd_i(group_vu, ctx->sm_count);
     n_chunks = std::max(1, std::min(n_chunks, n_tiles));
-    const int kbe = mode == MRF_FP8E4M3 ? 128 : 64;    // elements per K block
+    // MRF_F32 over a stored dictionary takes the split form (fp16 and e4m3
+    // planes, 128-element chunks); generated tiles the bf16 hi/lo split
+    const bool split = mode == MRF_F32 && !fused;
+    const int kbe = (mode == MRF_FP8E4M3 || split) ? 128 : 64;   // elements per K block
     const int k_blocks = (2 * d->n + kbe - 1) / kbe;   // K blocks holding at least one real element
     const int k_valid = 2 * d->n - (k_blocks - 1) * kbe;  // real elements in the last one (1..kbe)
-    const int kstep = mode == MRF_FP8E4M3 ? 32 : 16;
+    const int kstep = (mode == MRF_FP8E4M3 || split) ? 32 : 16;
     const int last_ksteps = (k_valid + kstep - 1) / kstep;
+    const int last_ks16 = (k_valid + 15) / 16;
 
     // Threshold pre-pass (K >= 8 on large dictionaries): the same matcher
     // over every kSample-th entry gives each voxel the K-th best CC^2 of that
@@ -1063,27 +1151,44 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
         return code;
     };
 
-    // 1. voxel prep
-    if (mode == MRF_F32)
-        voxel_prep_kernel<MRF_F32><<<(unsigned)V_pad, 256, 0, stream>>>((const float2 *)fp, V, d->n, d->ld, pA, pA2, pRS);
+    // 1. voxel prep (split: the e4m3 value plane follows the residual plane in pA2)
+    const size_t plane8 = (size_t)(2 * V_pad) * d->ld;
+    if (split)
+        voxel_prep_kernel<MRF_F32, true><<<(unsigned)V_pad, 256, 0, stream>>>((const float2 *)fp, V, d->n, d->ld, pA, pA2, pRS, plane8);
+    else if (mode == MRF_F32)
+        voxel_prep_kernel<MRF_F32><<<(unsigned)V_pad, 256, 0, stream>>>((const float2 *)fp, V, d->n, d->ld, pA, pA2, pRS, 0);
     else if (mode == MRF_BF16)
-        voxel_prep_kernel<MRF_BF16><<<(unsigned)V_pad, 256, 0, stream>>>((const float2 *)fp, V, d->n, d->ld, pA, pA2, pRS);
+        voxel_prep_kernel<MRF_BF16><<<(unsigned)V_pad, 256, 0, stream>>>((const float2 *)fp, V, d->n, d->ld, pA, pA2, pRS, 0);
     else
-        voxel_prep_kernel<MRF_FP8E4M3><<<(unsigned)V_pad, 256, 0, stream>>>((const float2 *)fp, V, d->n, d->ld, pA, pA2, pRS);
+        voxel_prep_kernel<MRF_FP8E4M3><<<(unsigned)V_pad, 256, 0, stream>>>((const float2 *)fp, V, d->n, d->ld, pA, pA2, pRS, 0);
     count_launch(ctx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return finish(cuda_fail(e, "voxel prep launch"));
 
-    // 2. tensor-core pass
-    CUtensorMap mA, mA2, mB, mB2;
-    rc = make_map(&mA, pA, 2 * V_pad, d->ld, ebytes, BM);
-    if (!rc && !fused) rc = make_map(&mB, d->hi, d->entries, d->ld, ebytes, BN);
-    if (!rc && mode == MRF_F32) rc = make_map(&mA2, pA2, 2 * V_pad, d->ld, ebytes, BM);
-    if (!rc && mode == MRF_F32 && !fused) rc = make_map(&mB2, d->lo, d->entries, d->ld, ebytes, BN);
-    if (rc) return finish(rc);
-    if (mode != MRF_F32) mA2 = mA;
-    if (fused) { mB = mA; mB2 = mA2; }   // unused: the kernel generates its B tiles
-    else if (mode != MRF_F32) mB2 = mB;
+    // 2. tensor-core pass. Split maps: a = fp16 rows, a2 / a3 = e4m3 residual /
+    // value planes of the voxels; b = fp16 rows, b2 / b3 = e4m3 value /
+    // residual planes of the dictionary (each plane D x ld bytes).
+    MatchMaps mm;
+    const size_t dplane8 = (size_t)d->entries * d->ld;
+    if (split) {
+        rc = make_map(&mm.a, pA, 2 * V_pad, d->ld, 2, BM);
+        if (!rc) rc = make_map(&mm.a2, pA2, 2 * V_pad, d->ld, 1, BM);
+        if (!rc) rc = make_map(&mm.a3, pA2 + plane8, 2 * V_pad, d->ld, 1, BM);
+        if (!rc) rc = make_map(&mm.b, d->hi, d->entries, d->ld, 2, BN);
+        if (!rc) rc = make_map(&mm.b2, d->lo, d->entries, d->ld, 1, BN);
+        if (!rc) rc = make_map(&mm.b3, (const uint8_t *)d->lo + dplane8, d->entries, d->ld, 1, BN);
+        if (rc) return finish(rc);
+    } else {
+        rc = make_map(&mm.a, pA, 2 * V_pad, d->ld, ebytes, BM);
+        if (!rc && !fused) rc = make_map(&mm.b, d->hi, d->entries, d->ld, ebytes, BN);
+        if (!rc && mode == MRF_F32) rc = make_map(&mm.a2, pA2, 2 * V_pad, d->ld, ebytes, BM);
+        if (rc) return finish(rc);
+        if (mode != MRF_F32) mm.a2 = mm.a;
+        if (fused) mm.b = mm.a;   // unused: the kernel generates its B tiles
+        mm.b2 = mm.b;
+        mm.a3 = mm.a;
+        mm.b3 = mm.b;
+    }
     MatchParams p;
     p.D = d->entries;
     p.V = V;
@@ -1093,6 +1198,7 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     p.group_vu = group_vu;
     p.k_blocks = k_blocks;
     p.last_ksteps = last_ksteps;
+    p.last_ks16 = last_ks16;
     p.colscale = mode == MRF_BF16 ? nullptr : d->scale;
     p.col_stride = 1;
     p.thr0 = nullptr;
@@ -1118,23 +1224,25 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
         count_launch(ctx);
         return cudaGetLastError();
     };
-    auto launch_all = [&](const CUtensorMap &b, const CUtensorMap &b2, const MatchParams &pp) {
+    auto launch_all = [&](const MatchMaps &m, const MatchParams &pp) {
         std::lock_guard<std::mutex> lk(g_match_attr_mu);
-        if (fused && mode == MRF_F32) return launch_match_mode<MRF_F32, true>(ctx, K, mA, mA2, b, b2, pp, stream);
-        if (fused) return launch_match_mode<MRF_BF16, true>(ctx, K, mA, mA2, b, b2, pp, stream);
-        if (mode == MRF_F32) return launch_match_mode<MRF_F32>(ctx, K, mA, mA2, b, b2, pp, stream);
-        if (mode == MRF_BF16) return launch_match_mode<MRF_BF16>(ctx, K, mA, mA2, b, b2, pp, stream);
-        return launch_match_mode<MRF_FP8E4M3>(ctx, K, mA, mA2, b, b2, pp, stream);
+        if (fused && mode == MRF_F32) return launch_match_mode<MRF_F32, true>(ctx, K, m, pp, stream);
+        if (fused) return launch_match_mode<MRF_BF16, true>(ctx, K, m, pp, stream);
+        if (mode == MRF_F32) return launch_match_mode<MRF_F32>(ctx, K, m, pp, stream);
+        if (mode == MRF_BF16) return launch_match_mode<MRF_BF16>(ctx, K, m, pp, stream);
+        return launch_match_mode<MRF_FP8E4M3>(ctx, K, m, pp, stream);
     };
     {
         // one timed region: pre-pass, its merge and the full pass
         ProfScope prof(ctx, kProfMatcher, stream);
         if (seeded) {
-            CUtensorMap mBs, mB2s;
-            rc = make_map(&mBs, d->hi, D_s, d->ld, ebytes, BN, kSample);
-            if (!rc && mode == MRF_F32) rc = make_map(&mB2s, d->lo, D_s, d->ld, ebytes, BN, kSample);
+            // every kSample-th stored row of each plane
+            MatchMaps ms = mm;
+            rc = make_map(&ms.b, d->hi, D_s, d->ld, split ? 2 : ebytes, BN, kSample);
+            if (!rc && split) rc = make_map(&ms.b2, d->lo, D_s, d->ld, 1, BN, kSample);
+            if (!rc && split) rc = make_map(&ms.b3, (const uint8_t *)d->lo + dplane8, D_s, d->ld, 1, BN, kSample);
             if (rc) return finish(rc);
-            if (mode != MRF_F32) mB2s = mBs;
+            if (!split) ms.b2 = ms.b3 = ms.b;
             MatchParams ps = p;
             ps.D = D_s;
             ps.n_tiles = n_tiles_s;
@@ -1142,7 +1250,7 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
             ps.group_vu = n_vu;
             ps.col_stride = kSample;
             ps.part = pPs;
-            rc = launch_all(mBs, mB2s, ps);
+            rc = launch_all(ms, ps);
             if (rc) return finish(rc);
             count_launch(ctx);
             // bounds in the kernel's units (no FP8 row scale)
@@ -1156,7 +1264,7 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
             if (e != cudaSuccess) return finish(cuda_fail(e, "bound scratch"));
             p.thr_live = pL;
         }
-        rc = launch_all(mB, mB2, p);
+        rc = launch_all(mm, p);
     }
     if (rc) return finish(rc);
 

@@ -5,7 +5,7 @@
 // ends of the timecourse; Re and Im alike.
 //
 // mrf_smooth: fingerprints, one thread per output sample.
-// mrf_dict_smooth: a generated FP32-equivalent or BF16 dictionary in place,
+// mrf_dict_smooth: a generated MRF_F32 or BF16 dictionary in place,
 // one thread per entry re-simulating it from the dictionary's own sequence
 // and grid (FP32 recurrence, accurate factors) twice: the norm of the
 // smoothed entry, then the write in the dictionary's convention, rounded to
@@ -18,6 +18,7 @@
 
 #include "bloch.cuh"
 #include "mrf_internal.h"
+#include "split.cuh"
 
 namespace {
 
@@ -107,8 +108,8 @@ struct RawStream {
 // Re-simulates each entry (the generator's FP32 recurrence with accurate
 // factors), smooths it, and writes the normalised result with one rounding.
 template <bool XONLY>
-__global__ void dict_smooth_kernel(SeqDev s, GridDev g, __nv_bfloat16 *hi, __nv_bfloat16 *lo, float *norm,
-                                   float *scale, int64_t D, int ld, SmoothW sw)
+__global__ void dict_smooth_kernel(SeqDev s, GridDev g, uint8_t *hi, uint8_t *lo, float *norm, float *scale,
+                                   int64_t D, int ld, SmoothW sw)
 {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= D) return;
@@ -136,20 +137,24 @@ __global__ void dict_smooth_kernel(SeqDev s, GridDev g, __nv_bfloat16 *hi, __nv_
     ss += part;
     const float inv = ss > 0.0 ? (float)(1.0 / sqrt(ss)) : 0.f;
     // pass 2: the smoothed entry, stored as the dictionary stores entries: the
-    // raw signal with scale 1 / ||d|| (FP32-equivalent, lo present), or the
-    // unit-norm signal with scale 1 (BF16)
+    // raw signal with scale 1 / ||d|| (MRF_F32: fp16 row and the two e4m3
+    // planes of the values and the residuals, lo present), or the unit-norm
+    // signal with scale 1 (BF16)
     const float wmul = lo ? 1.f : inv;
-    __nv_bfloat16 *h = hi + (size_t)e * ld;
-    __nv_bfloat16 *l = lo ? lo + (size_t)e * ld : nullptr;
+    uint8_t *h = hi + (size_t)e * ld * 2;
+    uint8_t *l8h = lo ? lo + (size_t)e * ld : nullptr;
+    uint8_t *l8l = lo ? lo + (size_t)D * ld + (size_t)e * ld : nullptr;
     rs.start(s, rr);
     for (int t = 0; t < n; ++t) {
         const float2 z = smoothed(rs.win, t, n, sw);
         const float zr = z.x * wmul, zi = z.y * wmul;
-        const __nv_bfloat162 hv = __floats2bfloat162_rn(zr, zi);
-        *reinterpret_cast<__nv_bfloat162 *>(h + 2 * t) = hv;
-        if (l) {
-            const float2 hf = __bfloat1622float2(hv);
-            *reinterpret_cast<__nv_bfloat162 *>(l + 2 * t) = __floats2bfloat162_rn(zr - hf.x, zi - hf.y);
+        if (lo) {
+            const SplitPair sp = split_pair(zr, zi, kSplitHiD);
+            *reinterpret_cast<uint32_t *>(h + 4 * t) = sp.hi;
+            *reinterpret_cast<uint16_t *>(l8h + 2 * t) = sp.h8;
+            *reinterpret_cast<uint16_t *>(l8l + 2 * t) = sp.l8;
+        } else {
+            *reinterpret_cast<__nv_bfloat162 *>(h + 4 * t) = __floats2bfloat162_rn(zr, zi);
         }
         rs.advance(s);
     }
@@ -198,10 +203,10 @@ extern "C" int mrf_dict_smooth(mrf_ctx *ctx, mrf_dict *d, int32_t width, double 
     count_launch(ctx);
     if (s.xonly)
         dict_smooth_kernel<true><<<blocks, 128, 0, (cudaStream_t)stream>>>(
-            s, g, (__nv_bfloat16 *)d->hi, (__nv_bfloat16 *)d->lo, d->norm, d->scale, d->entries, d->ld, sw);
+            s, g, (uint8_t *)d->hi, (uint8_t *)d->lo, d->norm, d->scale, d->entries, d->ld, sw);
     else
         dict_smooth_kernel<false><<<blocks, 128, 0, (cudaStream_t)stream>>>(
-            s, g, (__nv_bfloat16 *)d->hi, (__nv_bfloat16 *)d->lo, d->norm, d->scale, d->entries, d->ld, sw);
+            s, g, (uint8_t *)d->hi, (uint8_t *)d->lo, d->norm, d->scale, d->entries, d->ld, sw);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "dictionary smoothing launch");
     d->smooth_h = sw.h;

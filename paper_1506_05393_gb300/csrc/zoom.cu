@@ -32,6 +32,7 @@
 
 #include "bloch.cuh"
 #include "mrf_internal.h"
+#include "split.cuh"
 
 namespace {
 
@@ -70,8 +71,9 @@ enum ZPhase : int { kPhaseAll = 0, kPhaseHead = 1, kPhaseTail = 2 };
 struct ZoomArgs {
     SeqDev s;
     GridDev g;
-    // factor mode 3 (resident dictionary): normalised rows, bf16 hi (+ lo)
-    const __nv_bfloat16 *dhi, *dlo;
+    // factor mode 3 (resident dictionary): the stored rows, bf16 (MRF_BF16)
+    // or fp16 with the e4m3 residual plane (MRF_F32: dlo8 non-null)
+    const uint8_t *dhi, *dlo8;
     const float *dnorm;      // L2 norm of each un-normalised entry
     const float *dscale;     // per-entry scale: stored row x scale = unit-norm entry
     int ld;                  // row stride in elements
@@ -273,28 +275,32 @@ __device__ __forceinline__ Eval eval_dict(const ZoomArgs &A, const float2 *x, fl
         const int q = __ffs(todo) - 1;
         todo &= todo - 1;
         const long long eq = __shfl_sync(0xffffffffu, e, q);
-        const __nv_bfloat16 *hi = A.dhi + (size_t)eq * A.ld;
-        const __nv_bfloat16 *lo = A.dlo ? A.dlo + (size_t)eq * A.ld : nullptr;
+        const uint8_t *hi = A.dhi + (size_t)eq * A.ld * 2;
+        const uint8_t *lo = A.dlo8 ? A.dlo8 + (size_t)eq * A.ld : nullptr;
         float re = 0.f, im = 0.f;
 #pragma unroll 4
         for (int base = lane * 8; base < n2; base += 256) {
             float d[8];
-            const uint4 h = __ldg(reinterpret_cast<const uint4 *>(hi + base));
-            const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&h);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float2 f = __bfloat1622float2(h2[k]);
-                d[2 * k] = f.x;
-                d[2 * k + 1] = f.y;
-            }
+            const uint4 h = __ldg(reinterpret_cast<const uint4 *>(hi + 2 * (size_t)base));
             if (lo) {
-                const uint4 l = __ldg(reinterpret_cast<const uint4 *>(lo + base));
-                const __nv_bfloat162 *l2 = reinterpret_cast<const __nv_bfloat162 *>(&l);
+                // value = fp16 part 2^-15 + e4m3 residual 2^-19
+                const __half2 *h2 = reinterpret_cast<const __half2 *>(&h);
+                const uint2 l = __ldg(reinterpret_cast<const uint2 *>(lo + base));
+                const uint16_t *l2 = reinterpret_cast<const uint16_t *>(&l);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const float2 f = __bfloat1622float2(l2[k]);
-                    d[2 * k] += f.x;
-                    d[2 * k + 1] += f.y;
+                    const float2 f = __half22float2(h2[k]);
+                    const float2 r = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(l2[k], __NV_E4M3)));
+                    d[2 * k] = fmaf(r.x, kSplitDecLo, f.x * kSplitDecHi);
+                    d[2 * k + 1] = fmaf(r.y, kSplitDecLo, f.y * kSplitDecHi);
+                }
+            } else {
+                const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&h);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 f = __bfloat1622float2(h2[k]);
+                    d[2 * k] = f.x;
+                    d[2 * k + 1] = f.y;
                 }
             }
             if (base + 8 <= n2) {
@@ -1881,7 +1887,7 @@ int zoom_with_chains(mrf_ctx *ctx, const ZoomPlan &P, const SeqDev &sd, const Gr
     ZoomArgs A;
     A.s = sd;
     A.g = gdev;
-    A.dhi = A.dlo = nullptr;
+    A.dhi = A.dlo8 = nullptr;
     A.dnorm = nullptr;
     A.dscale = nullptr;
     A.ld = 0;
@@ -2019,7 +2025,7 @@ int run_zoom(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_desc *gd, const mr
     ZoomArgs A;
     A.s = seq->dev();
     A.g = gdev;
-    A.dhi = A.dlo = nullptr;
+    A.dhi = A.dlo8 = nullptr;
     A.dnorm = nullptr;
     A.dscale = nullptr;
     A.ld = 0;
@@ -2126,8 +2132,8 @@ extern "C" int mrf_zoom_search_dict(mrf_ctx *ctx, const mrf_dict *d, const mrf_z
     ZoomArgs A;
     A.s = d->seq->dev();
     A.g = d->grid.dev();
-    A.dhi = (const __nv_bfloat16 *)d->hi;
-    A.dlo = (const __nv_bfloat16 *)d->lo;
+    A.dhi = (const uint8_t *)d->hi;
+    A.dlo8 = d->lo ? (const uint8_t *)d->lo + (size_t)d->entries * d->ld : nullptr;   // the residual plane
     A.dnorm = d->norm;
     A.dscale = d->scale;
     A.ld = d->ld;
@@ -2278,7 +2284,7 @@ extern "C" int mrf_zoom_search_static(mrf_ctx *ctx, const mrf_seq *seq, const mr
     A.g.count = ao[gd->n_t1];
     A.g.a_full = gd->n_t1;
     while (A.g.a_full > 0 && nb[A.g.a_full - 1] == gd->n_t2) --A.g.a_full;
-    A.dhi = A.dlo = nullptr;
+    A.dhi = A.dlo8 = nullptr;
     A.dnorm = nullptr;
     A.dscale = nullptr;
     A.ld = 0;

@@ -24,3 +24,10 @@ def rel_l2(a, b, axis=-1):
     a = np.asarray(a)
     b = np.asarray(b)
     return np.linalg.norm(a - b, axis=axis) / np.linalg.norm(b, axis=axis)
+
+
+# Relative L2 bound on a stored MRF_F32 dictionary row against the FP64
+# oracle: each value is held as fp16 plus an e4m3 copy of the fp16 residual
+# (residual <= 2^-11 of the value, e4m3 unit roundoff 2^-4), i.e. to at most
+# 2^-15 relative, on top of the FP32 simulation's 1e-5.
+F32_STORE_TOL = 2.0 ** -15 + 1e-5

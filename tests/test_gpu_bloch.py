@@ -8,7 +8,7 @@ import torch
 
 import mrf_synth as S
 from conftest import device_bytes
-from helpers import rel_l2
+from helpers import F32_STORE_TOL, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +59,11 @@ def test_simulate_without_inversion(M, ctx, oracle_lib):
     assert err.max() < 1e-5
 
 
+def _f32_values(hi16, lo8):
+    """Stored MRF_F32 values: fp16 part 2^-15 plus e4m3 residual 2^-19."""
+    return hi16.double() * 2.0 ** -15 + lo8.float().double() * 2.0 ** -19
+
+
 def _dict_rows(M, d, dtype):
     info = M.mrf_dict_query(d)
     D, ld = info.entries, info.ld
@@ -70,17 +75,19 @@ def _dict_rows(M, d, dtype):
     if dtype == M.MRF_FP8E4M3:
         q = torch.from_numpy(hi).view(torch.float8_e4m3fn).float().numpy().reshape(D, ld)
         vals = q * sc[:, None]
+    elif dtype == M.MRF_F32:
+        # fp16 part x 2^-15 + e4m3 residual x 2^-19 (the second of the two e4m3 planes)
+        lo = device_bytes(info.lo_dev, D * ld * 2).cpu()
+        vals = _f32_values(torch.from_numpy(hi).view(torch.float16), lo[D * ld:].view(torch.float8_e4m3fn))
+        vals = vals.numpy().reshape(D, ld) * sc[:, None]
     else:
         vals = torch.from_numpy(hi).view(torch.bfloat16).float().numpy().reshape(D, ld).astype(np.float64)
-        if dtype == M.MRF_F32:
-            lo = device_bytes(info.lo_dev, D * ld * 2).cpu()
-            vals = vals + lo.view(torch.bfloat16).float().numpy().reshape(D, ld)
         vals = vals * sc[:, None]
     n = info.n
     return vals[:, 0:2 * n:2] + 1j * vals[:, 1:2 * n:2], vals[:, 2 * n:], norm, info
 
 
-@pytest.mark.parametrize("dtype,tol", [(0, 1e-5), (1, 3e-3), (2, 7e-2)])
+@pytest.mark.parametrize("dtype,tol", [(0, F32_STORE_TOL), (1, 3e-3), (2, 7e-2)])
 def test_dictionary_tiny_matches_oracle(M, ctx, oracle_lib, dtype, tol):
     seq = S.sequence(0, 200)
     g = S.GRIDS["tiny"]
@@ -104,7 +111,7 @@ def test_dictionary_tiny_matches_oracle(M, ctx, oracle_lib, dtype, tol):
 
 
 @pytest.mark.parametrize("n", [1, 12, 37])
-@pytest.mark.parametrize("dtype,tol", [(0, 1e-5), (1, 3e-3), (2, 7e-2)])
+@pytest.mark.parametrize("dtype,tol", [(0, F32_STORE_TOL), (1, 3e-3), (2, 7e-2)])
 def test_dictionary_short_sequences(M, ctx, oracle_lib, n, dtype, tol):
     """Sequences far shorter than a row's padding (N = 1, 12, 37 timepoints)
     on a grid with a df axis: rows, norms and zero padding as for N = 200."""
@@ -131,7 +138,7 @@ def test_dictionary_short_sequences(M, ctx, oracle_lib, n, dtype, tol):
 
 
 @pytest.mark.parametrize("kind", ["general_rf_asym_te", "xonly_asym_te", "general_rf_sym_te"])
-@pytest.mark.parametrize("dtype,tol", [(0, 1e-5), (1, 3e-3), (2, 7e-2)])
+@pytest.mark.parametrize("dtype,tol", [(0, F32_STORE_TOL), (1, 3e-3), (2, 7e-2)])
 def test_dictionary_other_sequence_kinds(M, ctx, oracle_lib, kind, dtype, tol):
     """Sequences outside the symmetric x-rotation form (an RF phase off the
     multiples of pi, TE_j != TR_j - TE_j) take the table-driven kernel: rows,
@@ -173,19 +180,21 @@ def test_dictionary_full_size_sampled(M, ctx, oracle_lib):
         assert D == 614508 and ld >= 2000 and (ld * 2) % 128 == 0
         rng = np.random.default_rng(3)
         idx = np.unique(np.concatenate([rng.integers(0, D, 250), [0, D - 1]]))
-        hi = device_bytes(info.hi_dev, D * ld * 2).view(torch.bfloat16).view(D, ld)
-        lo = device_bytes(info.lo_dev, D * ld * 2).view(torch.bfloat16).view(D, ld)
+        hi = device_bytes(info.hi_dev, D * ld * 2).view(torch.float16).view(D, ld)
+        lo = device_bytes(info.lo_dev, D * ld * 2)[D * ld:].view(torch.float8_e4m3fn).view(D, ld)
         sc = device_bytes(info.scale_dev, 4 * D).view(torch.float32)
         it = torch.from_numpy(idx).cuda()
         # stored value x per-entry scale = unit-norm entry
-        vals = ((hi[it].double() + lo[it].double()) * sc[it].double()[:, None]).cpu().numpy()
+        vals = (_f32_values(hi[it], lo[it]) * sc[it].double()[:, None]).cpu().numpy()
         rows = vals[:, 0:2000:2] + 1j * vals[:, 1:2000:2]
         params = [M.mrf_grid_unravel(g, int(i)) for i in idx]
         t1, t2, df = S.grid_values(g)
         ref = oracle_lib.simulate(seq, t1[[p[0] for p in params]], t2[[p[1] for p in params]], df[[p[2] for p in params]])
         refn = ref / np.linalg.norm(ref, axis=1, keepdims=True)
         err = rel_l2(rows, refn)
-        assert err.max() < 1e-5, f"max rel L2 {err.max():.3g}"
+        # the storage bound, and the rms of 2000 rounded values well inside it
+        assert err.max() < F32_STORE_TOL, f"max rel L2 {err.max():.3g}"
+        assert np.median(err) < 1e-5, f"median rel L2 {np.median(err):.3g}"
         assert torch.count_nonzero(hi[it][:, 2000:]).item() == 0
     finally:
         M.mrf_dict_free(ctx, d)

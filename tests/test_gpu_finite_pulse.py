@@ -13,7 +13,7 @@ import pytest
 import torch
 
 import mrf_synth as S
-from helpers import offgrid_voxels, rel_l2
+from helpers import F32_STORE_TOL, offgrid_voxels, rel_l2
 from test_gpu_bloch import _dict_rows, _gpu_simulate
 from test_gpu_match import _compare as _compare_brute
 from test_gpu_match import _run as _run_brute
@@ -67,7 +67,7 @@ def test_zero_pulse_durations_are_the_hard_pulse_bit_for_bit(M, ctx, oracle_lib)
     assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
 
 
-@pytest.mark.parametrize("dtype,tol", [(0, 1e-5), (1, 3e-3), (2, 7e-2)])
+@pytest.mark.parametrize("dtype,tol", [(0, F32_STORE_TOL), (1, 3e-3), (2, 7e-2)])
 def test_finite_pulse_dictionary(M, ctx, oracle_lib, dtype, tol):
     """Rows, norms and padding of a dictionary on a grid with a df axis
     (each entry's RF rotation from its own df)."""

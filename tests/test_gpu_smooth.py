@@ -1,6 +1,6 @@
 """GPU temporal smoothing (Methods, Experiment 4) against the FP64 oracle:
 mrf_smooth on fingerprints, mrf_dict_smooth on a generated dictionary (entries
-within 1e-5 relative L2 for FP32-equivalent storage), and brute force with
+within the MRF_F32 storage bound, 2^-15 + 1e-5 relative L2), and brute force with
 both sides smoothed (indices identical except where the oracle's top-two gap
 is below 1e-6; CC within 1e-5)."""
 import ctypes as C
@@ -10,7 +10,7 @@ import pytest
 import torch
 
 import mrf_synth as S
-from helpers import offgrid_voxels, rel_l2
+from helpers import F32_STORE_TOL, offgrid_voxels, rel_l2
 from test_gpu_bloch import _dict_rows
 
 pytestmark = pytest.mark.gpu
@@ -28,7 +28,7 @@ def test_smooth_fingerprints(M, ctx, oracle_lib, width, sigma):
     assert np.abs(xout.cpu().numpy() - ref).max() < 2e-6
 
 
-@pytest.mark.parametrize("dtype,width,tol", [(0, 3, 1e-5), (0, 5, 1e-5), (1, 3, 4e-3)])
+@pytest.mark.parametrize("dtype,width,tol", [(0, 3, F32_STORE_TOL), (0, 5, F32_STORE_TOL), (1, 3, 4e-3)])
 def test_dictionary_smoothing_matches_oracle(M, ctx, oracle_lib, dtype, width, tol):
     seq = S.sequence(0, 200)
     g = S.GRIDS["tiny"]
