@@ -238,8 +238,9 @@ int mrf_dict_free_async(mrf_ctx *ctx, mrf_dict *dict, void *stream);
 typedef struct {
     int64_t entries;       /* D, valid grid entries */
     int32_t n;             /* timepoints */
-    int32_t ld;            /* row stride in elements: 2n rounded up to 128, plus 128 bytes of
-                              padding (rows off a power-of-two stride); entries past 2n are 0 */
+    int32_t ld;            /* row stride in elements of every plane: 2n rounded up to 128, plus
+                              64 (BF16) or 128 elements of padding (rows off a power-of-two
+                              stride, 1-byte rows on 128-byte lines); entries past 2n are 0 */
     int32_t dtype;         /* mrf_dtype */
     const void *hi_dev;    /* D x ld: fp16 x 2^15 (F32), bf16 (BF16) or e4m3 bytes (FP8) */
     const void *lo_dev;    /* F32 only, else NULL: two D x ld e4m3 planes, the values x 2^8,

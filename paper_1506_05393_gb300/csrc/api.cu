@@ -632,7 +632,10 @@ extern "C" int mrf_simulate(mrf_ctx *ctx, const mrf_seq *seq, int64_t count, con
 
 // Row length in elements: 2n rounded up to 128, plus 128 bytes so that rows do
 // not sit on a power-of-two stride (which crowds them into few L2 sets).
-static int dict_ld(int n, int dtype) { return ((2 * n + 127) / 128) * 128 + (dtype == MRF_FP8E4M3 ? 128 : 64); }
+// Row stride in elements: 2n rounded up to 128, plus padding that keeps rows
+// off a power-of-two stride and every 1-byte plane's rows on 128-byte lines
+// (FP8 rows; the e4m3 planes of MRF_F32): 128 elements, 64 for BF16.
+static int dict_ld(int n, int dtype) { return ((2 * n + 127) / 128) * 128 + (dtype == MRF_BF16 ? 64 : 128); }
 
 extern "C" int mrf_dict_free(mrf_ctx *ctx, mrf_dict *d)
 {

@@ -50,14 +50,23 @@ constexpr int BM = 128;          // voxel rows per tile (64 voxels)
 constexpr int BN = 256;          // dictionary entries per tile
 constexpr uint64_t kWaitLimitNs = 4000000000ull;   // 4 s per barrier wait
 
+// Kernel form of MRF_F32 over a stored dictionary (the split form of
+// split.cuh); MRF_F32 itself is the form of generated tiles (bf16 hi / lo).
+constexpr int kModeSplit = 3;
+
 template <int MODE>
 struct Cfg;
-// MRF_F32: two operand tiles per side (split form: the e4m3 residual and value
-// planes, or two fp16 K blocks; generated tiles: bf16 hi and lo), one voxel
-// block per CTA
+// MRF_F32, generated tiles: hi and lo of both operands, one voxel block per CTA
 template <>
 struct Cfg<MRF_F32> {
     static constexpr int kBK = 64, kStages = 2, kOps = 2, kNB = 1;
+};
+// split form: two voxel blocks per CTA share each dictionary tile, as BF16;
+// a stage holds one operand plane of 128 bytes per row (e4m3 residual or
+// value plane, or one fp16 K block)
+template <>
+struct Cfg<kModeSplit> {
+    static constexpr int kBK = 64, kStages = 3, kOps = 1, kNB = 2;
 };
 // BF16 / FP8: two voxel blocks per CTA share each dictionary tile (two
 // accumulators), which halves the dictionary bytes per flop through L2
@@ -93,7 +102,8 @@ struct MatchParams {
                          // while the dictionary streams past them once
     int k_blocks;        // K blocks of 128 bytes
     int last_ksteps;     // MMA k-steps in the last K block (rest is zero padding)
-    int last_ks16;       // MRF_F32 split form: fp16 k-steps in the last 128-element chunk
+    int k_blocks16;      // split form: fp16 K blocks of 64 elements (k_blocks: e4m3 blocks of 128)
+    int last_ks16;       // split form: k-steps in the last fp16 K block
     const float *colscale;   // per-entry scale (stored value x scale = unit-norm entry), nullptr when 1
     int col_stride;      // dictionary entry of tile column c is c * col_stride (sampled pre-pass)
     const float *thr0;   // per-voxel lower bound on the K-th best CC^2 (thr0[v * thr0_stride]), or nullptr
@@ -188,12 +198,13 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
                  const __grid_constant__ CUtensorMap mapB2, const __grid_constant__ CUtensorMap mapB3, MatchParams p)
 {
     using C = Cfg<MODE>;
-    // MRF_F32 over a stored dictionary: the split form (fp16 product and two
-    // e4m3 residual products). Per tile, p.k_blocks e4m3 stages of 128
-    // elements (A: x residuals, x values; B: d values, d residuals) come
-    // first, then p.k_blocks fp16 stages of two 64-element K blocks.
-    // Generated tiles (GEN) use the bf16 hi/lo split.
-    constexpr bool kSplit = MODE == MRF_F32 && !GEN;
+    // Split form (MRF_F32 over a stored dictionary): per tile, first 2
+    // p.k_blocks e4m3 stages, for each 128-element K block the pair (x
+    // residuals with d values, x values with d residuals), then p.k_blocks16
+    // fp16 stages of 64 elements; every stage holds both voxel blocks' A
+    // tiles and one B tile.
+    constexpr bool kSplit = MODE == kModeSplit;
+    static_assert(!kSplit || !GEN, "generated tiles use the bf16 hi / lo split");
     constexpr uint32_t kIdescF16 = make_idesc(0, 0, BM, BN);   // kind::f16 with fp16 operands
     constexpr uint32_t kIdescE4 = make_idesc(0, 0, BM, BN);    // kind::f8f6f4 with e4m3 operands
     constexpr float kColMul = kSplit ? kSplitUnscale : 1.0f;   // removes the split form's 2^27 per operand side
@@ -247,7 +258,9 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
             if (!GEN) tma_prefetch_desc(&mapB2);
         }
         if (kSplit) {
+            tma_prefetch_desc(&mapA2);
             tma_prefetch_desc(&mapA3);
+            tma_prefetch_desc(&mapB2);
             tma_prefetch_desc(&mapB3);
         }
     }
@@ -278,27 +291,21 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
                 const int t0 = (int)((int64_t)chunk * p.n_tiles / p.n_chunks);
                 const int t1 = (int)((int64_t)(chunk + 1) * p.n_tiles / p.n_chunks);
                 for (int t = t0; t < t1; ++t) {
-                    const int n_st = kSplit ? 2 * p.k_blocks : p.k_blocks;
+                    const int n_st = kSplit ? 2 * p.k_blocks + p.k_blocks16 : p.k_blocks;
                     for (int kb = 0; kb < n_st; ++kb) {
                         if (!mbar_wait_bounded(&empty_bar[s], ph ^ 1, &abort_flag, p.err, kWaitLimitNs)) goto producer_done;
                         mbar_arrive_expect_tx(&full_bar[s], kTmaBytes);
                         if (kSplit) {
-                            const int row = vu * BM;
-                            if (kb < p.k_blocks) {
-                                // e4m3 stage: 128 elements of the residual and value planes
-                                const int kx = kb * 128;
-                                tma_load_2d_hint(tileA(s, 0, 0), &mapA2, &full_bar[s], kx, row, keep);
-                                tma_load_2d_hint(tileA(s, 1, 0), &mapA3, &full_bar[s], kx, row, keep);
-                                tma_load_2d(tileB(s, 0), &mapB2, &full_bar[s], kx, t * BN);
-                                tma_load_2d(tileB(s, 1), &mapB3, &full_bar[s], kx, t * BN);
-                            } else {
-                                // fp16 stage: two K blocks of 64 elements
-                                const int kx = (kb - p.k_blocks) * 128;
-                                tma_load_2d_hint(tileA(s, 0, 0), &mapA, &full_bar[s], kx, row, keep);
-                                tma_load_2d_hint(tileA(s, 1, 0), &mapA, &full_bar[s], kx + 64, row, keep);
-                                tma_load_2d(tileB(s, 0), &mapB, &full_bar[s], kx, t * BN);
-                                tma_load_2d(tileB(s, 1), &mapB, &full_bar[s], kx + 64, t * BN);
-                            }
+                            // e4m3 stages: x residuals with d values (even), x values with
+                            // d residuals (odd), 128 elements; then fp16 blocks of 64
+                            const bool e4 = kb < 2 * p.k_blocks;
+                            const int kx = e4 ? (kb >> 1) * 128 : (kb - 2 * p.k_blocks) * 64;
+                            const CUtensorMap *ma = e4 ? ((kb & 1) ? &mapA3 : &mapA2) : &mapA;
+                            const CUtensorMap *mb = e4 ? ((kb & 1) ? &mapB3 : &mapB2) : &mapB;
+#pragma unroll
+                            for (int i = 0; i < NB; ++i)
+                                tma_load_2d_hint(tileA(s, 0, i), ma, &full_bar[s], kx, (vu * NB + i) * BM, keep);
+                            tma_load_2d(tileB(s, 0), mb, &full_bar[s], kx, t * BN);
                             issued[s] = true;
                             issued_ph[s] = ph;
                             if (++s == S) { s = 0; ph ^= 1; }
@@ -346,29 +353,33 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
                 for (int t = t0; t < t1; ++t) {
                     if (!mbar_wait_bounded(&tempty_bar[buf], buf_ph ^ 1, &abort_flag, p.err, kWaitLimitNs)) goto mma_done;
                     tc_fence_after();
-                    const int n_st = kSplit ? 2 * p.k_blocks : p.k_blocks;
+                    const int n_st = kSplit ? 2 * p.k_blocks + p.k_blocks16 : p.k_blocks;
                     for (int kb = 0; kb < n_st; ++kb) {
                         if (!mbar_wait_bounded(&full_bar[s], ph, &abort_flag, p.err, kWaitLimitNs)) goto mma_done;
                         tc_fence_after();
                         if (kSplit) {
-                            const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
-                            const uint64_t a0 = smem_desc_sw128(tileA(s, 0, 0)), a1 = smem_desc_sw128(tileA(s, 1, 0));
-                            const uint64_t b0 = smem_desc_sw128(tileB(s, 0)), b1 = smem_desc_sw128(tileB(s, 1));
-                            if (kb < p.k_blocks) {
-                                // the e4m3 products first: x residual . d value, x value . d residual
-                                const int nk = (kb == p.k_blocks - 1) ? p.last_ksteps : 4;
+                            // the e4m3 products of the whole K range first, then the fp16 product
+                            const bool e4 = kb < 2 * p.k_blocks;
+                            const int nk = e4 ? ((kb >> 1) == p.k_blocks - 1 ? p.last_ksteps : 4)
+                                              : (kb == n_st - 1 ? p.last_ks16 : 4);
+                            const uint64_t b0 = smem_desc_sw128(tileB(s, 0));
+                            // one loop per instruction kind (32 bytes of K per MMA in both)
+                            if (e4) {
                                 for (int kk = 0; kk < nk; ++kk) {
                                     const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-                                    mma_f8(d_tmem, a0 + adv, b0 + adv, kIdescE4, (kb | kk) != 0);
-                                    mma_f8(d_tmem, a1 + adv, b1 + adv, kIdescE4, 1u);
+                                    const uint32_t accum = (kb | kk) != 0;
+#pragma unroll
+                                    for (int i = 0; i < NB; ++i)
+                                        mma_f8(tmem_base + (uint32_t)((buf * NB + i) * BN),
+                                               smem_desc_sw128(tileA(s, 0, i)) + adv, b0 + adv, kIdescE4, accum);
                                 }
                             } else {
-                                // then the fp16 product over the stage's two K blocks
-                                const int nk = (kb == n_st - 1) ? p.last_ks16 : 8;
                                 for (int kk = 0; kk < nk; ++kk) {
-                                    const uint64_t adv = (uint64_t)((kk & 3) * 32) >> 4;
-                                    if (kk < 4) mma_f16(d_tmem, a0 + adv, b0 + adv, kIdescF16, 1u);
-                                    else mma_f16(d_tmem, a1 + adv, b1 + adv, kIdescF16, 1u);
+                                    const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+#pragma unroll
+                                    for (int i = 0; i < NB; ++i)
+                                        mma_f16(tmem_base + (uint32_t)((buf * NB + i) * BN),
+                                                smem_desc_sw128(tileA(s, 0, i)) + adv, b0 + adv, kIdescF16, 1u);
                                 }
                             }
                             mma_commit(&empty_bar[s]);
@@ -1080,7 +1091,10 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
 {
     const int mode = precision;
     const int K = top_k;
-    const int nb = mode == MRF_F32 ? Cfg<MRF_F32>::kNB : Cfg<MRF_BF16>::kNB;   // voxel blocks per CTA
+    // MRF_F32 over a stored dictionary takes the split form (fp16 and e4m3
+    // planes); generated tiles the bf16 hi/lo split
+    const bool split = mode == MRF_F32 && !fused;
+    const int nb = split ? Cfg<kModeSplit>::kNB : mode == MRF_F32 ? Cfg<MRF_F32>::kNB : Cfg<MRF_BF16>::kNB;   // voxel blocks per CTA
     const int n_vu = (int)((V + 64 * nb - 1) / (64 * nb));
     const int64_t V_pad = (int64_t)n_vu * nb * 64;
     const int ebytes = mode == MRF_FP8E4M3 ? 1 : 2;
@@ -1094,15 +1108,14 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     // chunks: make each group's units a multiple of the SM count where possible
     int n_chunks = ctx->sm_count / gcd_i(group_vu, ctx->sm_count);
     n_chunks = std::max(1, std::min(n_chunks, n_tiles));
-    // MRF_F32 over a stored dictionary takes the split form (fp16 and e4m3
-    // planes, 128-element chunks); generated tiles the bf16 hi/lo split
-    const bool split = mode == MRF_F32 && !fused;
-    const int kbe = (mode == MRF_FP8E4M3 || split) ? 128 : 64;   // elements per K block
+    const int kbe = (mode == MRF_FP8E4M3 || split) ? 128 : 64;   // elements per K block (split: e4m3 blocks)
     const int k_blocks = (2 * d->n + kbe - 1) / kbe;   // K blocks holding at least one real element
     const int k_valid = 2 * d->n - (k_blocks - 1) * kbe;  // real elements in the last one (1..kbe)
     const int kstep = (mode == MRF_FP8E4M3 || split) ? 32 : 16;
     const int last_ksteps = (k_valid + kstep - 1) / kstep;
-    const int last_ks16 = (k_valid + 15) / 16;
+    // split form: fp16 K blocks of 64 elements and the k-steps of the last
+    const int k_blocks16 = (2 * d->n + 63) / 64;
+    const int last_ks16 = (2 * d->n - (k_blocks16 - 1) * 64 + 15) / 16;
 
     // Threshold pre-pass (K >= 8 on large dictionaries): the same matcher
     // over every kSample-th entry gives each voxel the K-th best CC^2 of that
@@ -1198,6 +1211,7 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
     p.group_vu = group_vu;
     p.k_blocks = k_blocks;
     p.last_ksteps = last_ksteps;
+    p.k_blocks16 = k_blocks16;
     p.last_ks16 = last_ks16;
     p.colscale = mode == MRF_BF16 ? nullptr : d->scale;
     p.col_stride = 1;
@@ -1228,7 +1242,7 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
         std::lock_guard<std::mutex> lk(g_match_attr_mu);
         if (fused && mode == MRF_F32) return launch_match_mode<MRF_F32, true>(ctx, K, m, pp, stream);
         if (fused) return launch_match_mode<MRF_BF16, true>(ctx, K, m, pp, stream);
-        if (mode == MRF_F32) return launch_match_mode<MRF_F32>(ctx, K, m, pp, stream);
+        if (mode == MRF_F32) return launch_match_mode<kModeSplit>(ctx, K, m, pp, stream);
         if (mode == MRF_BF16) return launch_match_mode<MRF_BF16>(ctx, K, m, pp, stream);
         return launch_match_mode<MRF_FP8E4M3>(ctx, K, m, pp, stream);
     };
