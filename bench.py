@@ -1128,7 +1128,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "voxels_per_gpu": V_SLICE, "entries": D, "n": N_TP,
-                   "l2": "inputs larger than L2 (4.9 GB dictionary regenerated and streamed every step)"},
+                   "l2": "inputs larger than L2 (5.35 GB dictionary regenerated and streamed every step)"},
         "clocks": {k: clk.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
         "e2e": {"value": whole_job_rate(world, V_SLICE, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": int(x_pin.numel() * 8), "d2h_bytes_per_step": int(out_pin.numel())},
