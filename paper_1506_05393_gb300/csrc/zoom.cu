@@ -697,14 +697,24 @@ __global__ void __launch_bounds__(kZoomThreads) zoom_dict_kernel(ZoomArgs A)
 // still counts every visit of the canonical search. The final centre is
 // simulated once more for its <x, d> and ||d||^2 (M0, phase).
 
-constexpr int kSlots = 8;
+constexpr int kSlots = 4;
 constexpr int kPackWarps = 4;
 constexpr int kPackThreads = 32 * kPackWarps;
-constexpr int kPerLane = 2;                  // table entries a lane can simulate in one round
+constexpr int kPerLane = 1;                  // table entries a lane can simulate in one round
 constexpr int kTable = 32 * kPerLane;
+// every slot's missing decision points (at most 8: a 2D neighbourhood) fit in one round's table
+static_assert(kSlots * 8 <= kTable, "round table smaller than the slots' missing points");
 constexpr int kWin = 64;
 constexpr int kReqMax = 24;                  // listed points per slot and round (8 missing + speculative)
 constexpr int kSpecCentres = 5;              // 2D walks: future centres whose neighbourhoods are speculated
+// A slot's window holds 8 x 8 lattice points, indexed by (i mod 8, k mod 8): collision free within
+// any 8-step span per axis. The current neighbourhood and those of the speculated centres span
+// kSpecCentres + 3 steps along a walk; past 8, a speculated point would evict a point the next
+// decision needs, which would then be listed again every round.
+static_assert(kSpecCentres + 3 <= 8, "speculated neighbourhoods must fit one window span");
+// No search comes near this many rounds per voxel (the longest take a few hundred); a slot past it
+// is not making progress, and the warp ends with an error instead of looping.
+constexpr int kMaxSlotRounds = 1 << 16;
 constexpr int kRunPrio = 3;                  // straight 2D run length whose speculation goes first
 
 enum Stage : int { kS1a = 0, kS1b, kS1c, kS2, kS3, kS4, kS5, kFinal, kStop };
@@ -1402,6 +1412,10 @@ __global__ void __launch_bounds__(kPackThreads) zoom_pack_kernel(ZoomArgs A)
         __syncwarp();
         const bool busy = lane < kSlots && W.s[lane].v >= 0;
         if (!__any_sync(FULL, busy)) break;
+        if (__any_sync(FULL, busy && W.s[lane].rounds > kMaxSlotRounds)) {
+            if (lane == 0) atomicExch(A.err, kDeviceErrBounds);
+            break;
+        }
         // ||x|| of the voxels that arrived this round (whole warp)
         int mask = W.norm_mask;
         while (mask) {
