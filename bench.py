@@ -44,8 +44,11 @@ FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1
 # x-axis RF (RF 6, two free evolutions 2 x 7, correlation and norm 12)
 FLOPS_PER_TP = 32.0
 # bound on |approximate - exact| CC of unit vectors stored in bf16 / e4m3 (relative
-# rounding u per operand, both operands rounded: sqrt(2) (2u + u^2)), plus FP32 slack
-CERT_EPS = {1: math.sqrt(2) * (2 * 2 ** -9 + 2 ** -18) + 1e-5, 2: math.sqrt(2) * (2 * 2 ** -4 + 2 ** -8) + 1e-5}
+# rounding u per operand, both operands rounded: sqrt(2) (2u + u^2)), plus the FP32
+# accumulation: at most one unit in the last place of the running sum (magnitude
+# below 1) per MMA, sqrt(2) * steps * 2^-23 with 2N/16 bf16 or 2N/32 e4m3 MMAs
+CERT_EPS = {1: math.sqrt(2) * (2 * 2 ** -9 + 2 ** -18) + math.sqrt(2) * (2 * N_TP // 16) * 2.0 ** -23,
+            2: math.sqrt(2) * (2 * 2 ** -4 + 2 ** -8) + math.sqrt(2) * (2 * N_TP // 32) * 2.0 ** -23}
 
 
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "match_kernel_f32_traffic_147k_4096.txt")

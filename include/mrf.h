@@ -363,7 +363,13 @@ int mrf_match_bruteforce_fused(mrf_ctx *ctx, const mrf_seq *seq, const mrf_grid_
 
 /* The tensor-core pass alone: per voxel the top_k (linear index, approximate
  * CC^2 of the normalised pair) in descending order, ties to the smaller
- * index. idx_dev: V x top_k int64, cc2_dev: V x top_k float32. */
+ * index. idx_dev: V x top_k int64, cc2_dev: V x top_k float32. Besides the
+ * stored precision, the values carry the FP32 accumulation of the MMAs: at
+ * most one unit in the last place of the running sum per MMA, i.e. a CC off by
+ * at most sqrt(2) * steps * 2^-23 (steps = 2n/16 bf16 or fp16 MMAs, 2n/32 e4m3
+ * ones; MRF_F32 takes both kinds). Measured at n = 1000 (MRF_F32) the values
+ * run low by about 1e-5 on average and 2.3e-5 at most. mrf_result CCs never
+ * carry this: they come from the FP64-accumulated re-simulation. */
 int mrf_match_topk(mrf_ctx *ctx, const mrf_dict *dict, const void *fp_dev, int64_t V, int32_t precision,
                    int32_t top_k, int64_t *idx_dev, float *cc2_dev, void *stream);
 

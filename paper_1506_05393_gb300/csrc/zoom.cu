@@ -1607,7 +1607,7 @@ __global__ void line_scatter_kernel(int64_t V, const int *vslot, const int *vran
 // Work items are (tile, chunk) pairs taken from a counter; the chunks of one
 // tile are consecutive items, so its voxels' samples are read from L2.
 template <bool XONLY, bool SYM>
-__global__ void __launch_bounds__(kLineThreads, 3) zoom_line_kernel(LineArgs L)
+__global__ void __launch_bounds__(kLineThreads, 4) zoom_line_kernel(LineArgs L)
 {
     __shared__ __align__(16) float2 xs[kLineTJ][kLineVox];
     __shared__ float4 s_rf[3 * kLineTJ];   // x rotation (c, s, 1 - c, TE), or 12 floats of a general rotation
