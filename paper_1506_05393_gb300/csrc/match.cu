@@ -640,11 +640,13 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
                         const float re = par ? recv : mine_lo;
                         const float im = par ? mine_hi : recv;
                         float c2 = fmaf(re, re, im * im);
-                        const int col = col0 + q;
                         if (kScaled) c2 *= sc16[q] * sc16[q];
                         c2v[q] = c2;
-                        mask |= (col < p.D && c2 > thr) ? (1u << q) : 0u;
+                        mask |= c2 > thr ? (1u << q) : 0u;
                     }
+                    // columns past the dictionary (the last tile) take no part
+                    const int64_t lim = p.D - col0;
+                    if (lim < 16) mask &= lim <= 0 ? 0u : ((1u << lim) - 1u);
                     // columns arrive in increasing index order: strictly better enters
                     while (mask) {
                         const int q = __ffs(mask) - 1;
