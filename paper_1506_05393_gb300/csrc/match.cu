@@ -207,7 +207,8 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
     static_assert(!kSplit || !GEN, "generated tiles use the bf16 hi / lo split");
     constexpr uint32_t kIdescF16 = make_idesc(0, 0, BM, BN);   // kind::f16 with fp16 operands
     constexpr uint32_t kIdescE4 = make_idesc(0, 0, BM, BN);    // kind::f8f6f4 with e4m3 operands
-    constexpr float kColMul = kSplit ? kSplitUnscale : 1.0f;   // removes the split form's 2^27 per operand side
+    // squared column scales carry the split form's 2^-54 (2^-27 per operand side; exact)
+    constexpr float kColMul2 = kSplit ? kSplitUnscale * kSplitUnscale : 1.0f;
     constexpr int S = C::kStages;
     constexpr int NB = C::kNB;                  // voxel blocks per CTA
     constexpr int NBUF = NB == 1 ? 2 : 1;       // accumulator buffers (TMEM holds 512 columns)
@@ -559,8 +560,11 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
                 const bool ok = mbar_wait_bounded(&tempty_bar[buf], buf_ph ^ 1, &abort_flag, p.err, kWaitLimitNs);
                 if (!__all_sync(0xffffffffu, ok)) goto sim_done;
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    sc_gen[GEN ? buf : 0][GEN ? r0 + 128 * h : 0] = (live[h] && tot[h] > 0.f) ? rsqrtf(tot[h]) : 0.f;
+                for (int h = 0; h < 2; ++h) {
+                    // the squared column scale (1 / ||d||)^2, as the epilogue applies it
+                    const float sc = (live[h] && tot[h] > 0.f) ? rsqrtf(tot[h]) : 0.f;
+                    sc_gen[GEN ? buf : 0][GEN ? r0 + 128 * h : 0] = sc * sc;
+                }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&scale_bar[GEN ? buf : 0]);
                 if (++buf == NBUF) { buf = 0; buf_ph ^= 1; }
@@ -601,7 +605,8 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
                     float *sct = sc_tile[GEN ? 0 : warp - 2];
                     for (int q = lane; q < BN; q += 32) {
                         const int col = t * BN + q;
-                        sct[q] = col < p.D ? __ldg(&p.colscale[(int64_t)col * p.col_stride]) : 0.f;
+                        const float sc = col < p.D ? __ldg(&p.colscale[(int64_t)col * p.col_stride]) : 0.f;
+                        sct[q] = sc * sc * kColMul2;   // squared, as the epilogue applies it
                     }
                     __syncwarp();
                 }
@@ -626,8 +631,7 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
 #pragma unroll
                         for (int q4 = 0; q4 < 4; ++q4) {
                             const float4 f = s4[q4];
-                            sc16[4 * q4] = f.x * kColMul; sc16[4 * q4 + 1] = f.y * kColMul;
-                            sc16[4 * q4 + 2] = f.z * kColMul; sc16[4 * q4 + 3] = f.w * kColMul;
+                            sc16[4 * q4] = f.x; sc16[4 * q4 + 1] = f.y; sc16[4 * q4 + 2] = f.z; sc16[4 * q4 + 3] = f.w;
                         }
                     }
                     uint32_t mask = 0;
@@ -640,7 +644,7 @@ __global__ void __launch_bounds__(threads_of<MODE, GEN>(), 1)
                         const float re = par ? recv : mine_lo;
                         const float im = par ? mine_hi : recv;
                         float c2 = fmaf(re, re, im * im);
-                        if (kScaled) c2 *= sc16[q] * sc16[q];
+                        if (kScaled) c2 *= sc16[q];   // squared column scale
                         c2v[q] = c2;
                         mask |= c2 > thr ? (1u << q) : 0u;
                     }
