@@ -829,26 +829,39 @@ struct RescoreSmooth {
 };
 
 template <bool XONLY>
+// A warp re-scores 32 / W voxels, W = the candidates per voxel (a power of
+// two): lane l takes candidate l mod W of voxel l / W, so every lane
+// simulates (W = 1 for the rank-1 form: 32 voxels per warp).
 __global__ void rescore_kernel(SeqDev s, GridDev g, const float2 *x, int64_t V, int K, const int64_t *cand,
                                const float *cand_cc2, int rank, int64_t D, RescoreSmooth sm, mrf_result *out,
                                int *err)
 {
-    const int64_t v = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (v >= V) return;
+    const int ncand = rank ? K : 1;   // 1, 2, 4, ..., 32
+    const int W = ncand, per_warp = 32 / W;
+    const int64_t v0 = ((int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * per_warp;
+    if (v0 >= V) return;   // whole warps only
+    const int grp = lane / W, sub = lane % W;
+    const int64_t v = v0 + grp;
+    const bool vlive = v < V;
     const int n = s.n;
-    const float2 *xv = x + (size_t)v * n;
-    // ||x||^2 in FP64
+    const float2 *xv = x + (size_t)(vlive ? v : v0) * n;
+    // ||x||^2 in FP64, each voxel's sum taken by the whole warp in the same
+    // order whatever W is
     double xx = 0.0;
-    for (int j = lane; j < n; j += 32) {
-        const float2 z = xv[j];
-        xx += (double)z.x * z.x + (double)z.y * z.y;
-    }
+    for (int p = 0; p < per_warp && v0 + p < V; ++p) {
+        const float2 *xp = x + (size_t)(v0 + p) * n;
+        double t = 0.0;
+        for (int j = lane; j < n; j += 32) {
+            const float2 z = xp[j];
+            t += (double)z.x * z.x + (double)z.y * z.y;
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) xx += __shfl_xor_sync(0xffffffffu, xx, o);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (p == grp) xx = t;
+    }
 
-    const int ncand = rank ? K : 1;
-    const int64_t e = lane < ncand ? cand[(size_t)v * K + lane] : -1;
+    const int64_t e = vlive ? cand[(size_t)v * K + sub] : -1;
     const bool live = e >= 0 && mrf_in_bounds(e < D, err);
     int a = 0, b = 0, c = 0;
     if (live) unravel_dev(g, e, a, b, c);
@@ -919,12 +932,12 @@ __global__ void rescore_kernel(SeqDev s, GridDev g, const float2 *x, int64_t V, 
     }
     const double mag = sqrt(ipr * ipr + ipi * ipi);
     double cc = (live && dd > 0.0 && xx > 0.0) ? mag / sqrt(xx * dd) : -1.0;
-    // best by FP64 CC, ties to the smaller index; also the runner-up CC
+    // best by FP64 CC within the voxel's W lanes, ties to the smaller index;
+    // also the runner-up CC
     double bc = cc, sc = -2.0;
     int64_t bi = live ? e : INT64_MAX;
     int bl = lane;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = W / 2; o > 0; o >>= 1) {
         const double oc = __shfl_xor_sync(0xffffffffu, bc, o);
         const double os = __shfl_xor_sync(0xffffffffu, sc, o);
         const long long oi = __shfl_xor_sync(0xffffffffu, (long long)bi, o);
@@ -939,7 +952,7 @@ __global__ void rescore_kernel(SeqDev s, GridDev g, const float2 *x, int64_t V, 
     const double wd = __shfl_sync(0xffffffffu, dd, bl);
     const int wa = __shfl_sync(0xffffffffu, a, bl), wb = __shfl_sync(0xffffffffu, b, bl),
               wc = __shfl_sync(0xffffffffu, c, bl);
-    if (lane == 0) {
+    if (sub == 0 && vlive) {
         mrf_result res;
         if (bi == INT64_MAX || bc < 0.0) {
             res.index = -1; res.i_t1 = res.i_t2 = res.i_df = -1;
@@ -1299,10 +1312,12 @@ int run_match(mrf_ctx *ctx, const mrf_dict *d, const void *fp, int64_t V, int32_
         RescoreSmooth sm;
         sm.h = d->smooth_h;
         for (int k = 0; k < 3; ++k) sm.w[k] = d->smooth_w[k];
+        const int64_t per_block = 4 * (32 / (rescore ? K : 1));   // 4 warps of 32 / W voxels
+        const unsigned rblocks = (unsigned)((V + per_block - 1) / per_block);
         if (s.xonly)
-            rescore_kernel<true><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, sm, out, ctx->err_flag);
+            rescore_kernel<true><<<rblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, sm, out, ctx->err_flag);
         else
-            rescore_kernel<false><<<mblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, sm, out, ctx->err_flag);
+            rescore_kernel<false><<<rblocks, 128, 0, stream>>>(s, g, (const float2 *)fp, V, K, pI, pC, rescore, d->entries, sm, out, ctx->err_flag);
         count_launch(ctx);
         e = cudaGetLastError();
         if (e != cudaSuccess) return finish(cuda_fail(e, "re-score launch"));
