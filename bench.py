@@ -4,8 +4,9 @@
 Workload (one step): a 64x64 slice of N = 1000 fingerprints matched by brute
 force on the T1 100-4000/20 ms x T2 10-400/5 ms x df -40..40/2 Hz grid
 (614,508 valid entries): sequence upload, dictionary generation (FP32 Bloch
-recurrence, normalise, bf16 hi/lo split), voxel prep, tensor-core matcher
-with fused per-voxel top-4, FP32 re-simulation / FP64 re-score, M0 and phase.
+recurrence, per-entry scale, fp16 rows with e4m3 value and residual planes),
+voxel prep, tensor-core matcher with fused per-voxel top-4, FP32
+re-simulation / FP64 re-score, M0 and phase.
 Metric: voxels matched per second. Inputs are synthetic phantoms (seeded),
 simulated by this library's own kernel. Extra modes (ZOOM, BF16/FP8 +
 re-score, finer grids) are timed once each and reported with their index
